@@ -1,0 +1,214 @@
+/*
+ * iedd.h -- C ABI of the GB300 (sm_103a) library for preconditioned conjugate gradient on the
+ * dense SPD collocation system of the first-kind Laplace volume integral equation, with the
+ * additive overlapping domain-decomposition preconditioner of Chen & Biros, "Overlapping
+ * Domain Decomposition Preconditioner for Integral Equations" (arXiv 2108.12574).
+ *
+ * The problem (Sec. 2.1, Eqs. e:ie, e:k):   int_Omega K(x - y) u(y) dy = f(x),  Omega = [0,1]^d,
+ *   K(r) = -(1/2pi) log|r| (d = 2),  K(r) = 1/(4 pi |r|) (d = 3),
+ * discretized by piecewise-constant collocation on an n^d grid into A u = f (Eq. e:dis) with
+ *   A_ij = h^d K(x_i - x_j) for i != j and A_ii = the integral of K over the h^d self cell
+ *   (Eqs. e:a_2d, e:a_3d), h = 1/n,  plus an optional second-kind shift a on the diagonal
+ *   (the a u term of Eq. e:int).
+ * The preconditioner (Sec. 3, Eqs. e:ai, e:ad):  T^{-1} = sum_i R_i^T A_i^{-1} R_i,
+ *   A_i = R_i A R_i^T, over the subdomains of Table t:dd (block Jacobi, Schwarz, CBD).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Grid index: row-major, last coordinate fastest (2D: i = i1 * n + i2).
+ *  - Vectors are FP64.  A batch of nrhs vectors is column-major: entry (i, k) at x[k * ld + i],
+ *    ld >= N.  A vector pointer may be device memory or host memory (pageable or pinned); the
+ *    library detects which with cudaPointerGetAttributes and, for host memory, stages through
+ *    device memory itself (the copies are enqueued on the caller's stream and the call
+ *    synchronizes that stream before returning).
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.  All
+ *    device work is enqueued on it.  Calls that return data to the host (dd_factor's info,
+ *    pcg_solve's report, any call given host vectors) synchronize the stream.
+ *  - Handles are opaque, owned by the library, created by the call that returns them and freed
+ *    by the matching *_destroy (which accepts NULL).  A handle may be used from one host thread
+ *    at a time.
+ *  - No call aborts or exits.  Every call returns an ie_status; on failure ie_last_error()
+ *    returns a message for the calling thread.  A CUDA error inside a call is reported as
+ *    IE_ERR_CUDA and leaves output buffers unspecified.
+ */
+#ifndef IEDD_H
+#define IEDD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define IEDD_API __attribute__((visibility("default")))
+#else
+#define IEDD_API
+#endif
+
+typedef enum {
+    IE_OK = 0,
+    IE_ERR_ARG = -1,         /* invalid argument (sizes, pointers, modes)                      */
+    IE_ERR_CUDA = -2,        /* a CUDA runtime call failed                                     */
+    IE_ERR_OOM = -3,         /* device allocation failed                                       */
+    IE_ERR_NOT_SPD = -4,     /* a subdomain block had a non-positive Cholesky pivot            */
+    IE_ERR_BREAKDOWN = -5,   /* PCG met p^T A p <= 0, r^T z <= 0 or a NaN                      */
+    IE_ERR_MAXIT = -6,       /* PCG reached max_it before the tolerance                        */
+    IE_ERR_STAGNATION = -7,  /* the true residual stopped decreasing                            */
+    IE_ERR_TIMEOUT = -8      /* the wall-clock budget of pcg_opts.timeout_s ran out            */
+} ie_status;
+
+typedef enum {
+    IE_FP64 = 0,   /* every step in FP64: entries regenerated in FP64, FP64 factors            */
+    IE_MIXED = 1   /* FP32 matvec and FP32 factors; FP64 CG scalars, FP64 residual replacement */
+} ie_precision;
+
+typedef enum { DD_JACOBI = 0, DD_SCHWARZ = 1, DD_CBD = 2 } dd_kind;
+
+typedef enum {
+    IE_GRID_TEXT = 0,  /* x_j = h (j - 1/2), j = 1..n: the cell-centred grid of Sec. 2.1          */
+    IE_GRID_TABLE = 1  /* x_j = (j - 1)/(n - 1) with weight (1/n)^d: the spacing under which the
+                          paper's 2D eigenvalue tables (Sec. 3-4) are reproduced; for checks only */
+} ie_grid;
+
+typedef struct ie_problem ie_problem;
+typedef struct dd_partition_t dd_partition_t;
+typedef struct dd_factor_t dd_factor_t;
+
+/* Thread-local message describing the last failure of a call on this thread ("" if none). */
+IEDD_API const char *ie_last_error(void);
+
+/* Library version string. */
+IEDD_API const char *ie_version(void);
+
+/*
+ * ie_discretize -- the collocation discretization of Sec. 2.1 (Eqs. e:a_2d, e:a_3d).
+ *   dim      2 or 3
+ *   n        grid points per dimension, 2 <= n; N = n^dim <= 2^26
+ *   a_shift  second-kind term a added to the diagonal (0 for the first-kind equation); A stays
+ *            SPD for a >= 0, a negative a can make it (and its blocks) indefinite
+ *   grid     ie_grid convention
+ *   device   CUDA device ordinal used by everything created from this problem
+ *   out      receives the new handle
+ * Builds the point coordinates and the per-offset entry table (used by the accurate residual)
+ * on the device; synchronous.  The diagonal is the closed-form self-cell integral
+ *   2D: -(h^2/(4 pi)) (2 ln(h/2) + ln 2 - 3 + pi/2);   3D: (h^2/(2 pi)) (3 ln(1+sqrt 3) - 1.5 ln 2 - pi/4).
+ * Errors: IE_ERR_ARG for bad sizes, IE_ERR_OOM, IE_ERR_CUDA.
+ */
+IEDD_API int ie_discretize(int dim, int n, double a_shift, int grid, int device, ie_problem **out);
+
+/* Sizes and constants of a problem: any output pointer may be NULL.  diag is A_ii. */
+IEDD_API int ie_problem_info(const ie_problem *p, int *dim, int *n, long long *N, double *h, double *diag);
+
+IEDD_API void ie_destroy(ie_problem *p);
+
+/*
+ * ie_matvec -- y = A x (Eq. e:dis), matrix-free: every entry is regenerated from the point
+ * coordinates and the quadrature weight; nothing of A is stored.
+ *   x, y       N x nrhs, column-major with leading dimension ld (host or device, FP64);
+ *              x and y must not overlap
+ *   precision  IE_FP64: entries and sums in FP64.
+ *              IE_MIXED: entries h^d K in FP32 through the SFU (log2 / rsqrt), FP32 sums per
+ *              tile, combined with the FP64 diagonal term in FP64.  Relative error of order
+ *              1e-6 of ||A|| ||x||.
+ *              IE_MIXED + 2 (= 3, "accurate"): double-float sums of a per-offset FP64 entry
+ *              table; FP64-class result (relative error ~1e-13 of sum |A_ij x_j|).
+ * Errors: IE_ERR_ARG (nrhs < 1, ld < N, NULL pointers), IE_ERR_CUDA.
+ */
+IEDD_API int ie_matvec(const ie_problem *p, const double *x, double *y, int nrhs, long long ld,
+              int precision, void *stream);
+#define IE_ACCURATE 3
+
+/*
+ * dd_partition -- index sets of the subdomains (Sec. 2.2-2.3, Eqs. e:dd, e:first, e:cbd).
+ *   m      partitions per dimension (M = m^dim boxes of w = n/m cells; n % m == 0 required)
+ *   delta  overlap: each box is extended by delta grid layers in every direction, clipped to
+ *          the grid (ignored for DD_JACOBI)
+ *   kind   DD_JACOBI (the boxes), DD_SCHWARZ (the extended boxes, D = M) or DD_CBD (extended
+ *          boxes unioned by the parity colour (k_1 mod 2, ..., k_d mod 2), D = 2^dim)
+ * Index sets are in ascending global order.  Host-side; the sets are also copied to the device.
+ * Errors: IE_ERR_ARG (n % m != 0, delta < 0, a subdomain larger than 16384 points), IE_ERR_OOM.
+ */
+IEDD_API int dd_partition(const ie_problem *p, int m, int delta, int kind, dd_partition_t **out);
+
+/* Number of subdomains D, total index count sum_i n_i and the largest n_i. */
+IEDD_API int dd_partition_info(const dd_partition_t *s, int *nblocks, long long *total, int *max_block);
+
+/* Copies the CSR form to host arrays: offsets[nblocks + 1] (int64) and index[total] (int32). */
+IEDD_API int dd_partition_export(const dd_partition_t *s, long long *offsets, int *index);
+
+IEDD_API void dd_partition_destroy(dd_partition_t *s);
+
+/*
+ * dd_factor -- regenerate every A_i = R_i A R_i^T (Eq. e:ai) and factor it, A_i = L_i L_i^T,
+ * by dense Cholesky (the exact subdomain solver of Sec. 4.3), all blocks in one launch.
+ *   precision  IE_FP64: FP64 entries and factors.  IE_MIXED: FP32 entries and factors.
+ *   info       (host, may be NULL) receives -1 if every block is SPD, else the first failing
+ *              block index; the call then returns IE_ERR_NOT_SPD and *out is still created
+ *              (its failing blocks are unusable).
+ * The factor keeps references to p's device data: destroy it before the problem.
+ * Synchronizes the stream (to read the per-block status).
+ */
+IEDD_API int dd_factor(const ie_problem *p, const dd_partition_t *s, int precision, dd_factor_t **out,
+              int *info, void *stream);
+
+IEDD_API void dd_factor_destroy(dd_factor_t *f);
+
+/*
+ * dd_apply -- z = T^{-1} r = sum_i R_i^T L_i^{-T} L_i^{-1} R_i r (Eq. e:ad): gather, forward and
+ * backward triangular solves per subdomain, then a plain (unweighted) sum over the overlaps,
+ * taken in a fixed order so the result is bitwise reproducible.
+ *   r, z  N x nrhs column-major, leading dimension ld (host or device, FP64); must not overlap.
+ * Arithmetic is in the factor's precision; z is FP64.
+ */
+IEDD_API int dd_apply(const dd_factor_t *f, const double *r, double *z, int nrhs, long long ld,
+             void *stream);
+
+typedef struct {
+    double tol;          /* stop when ||f - A u||_2 <= tol ||f||_2 (true residual, see below)     */
+    int max_it;          /* iteration cap per right-hand side (products q = A p)                  */
+    int precision;       /* IE_FP64 or IE_MIXED (the factor may have either precision)            */
+    int replace_every;   /* IE_MIXED: replace r by the accurate f - A u every k iterations (0: off) */
+    int use_x0;          /* 1: u holds the initial iterate on entry; 0: start from u = 0           */
+    double timeout_s;    /* wall-clock budget (0: none); exceeded -> IE_ERR_TIMEOUT                */
+    int check_every;     /* IE_FP64: iterations per CUDA-graph launch between host checks (>= 1)  */
+    int verify;          /* IE_FP64: 1 = compute the true residual at the end (one more matvec)    */
+} pcg_opts;
+
+typedef struct {
+    int iterations;          /* products q = A p for this right-hand side                       */
+    int replacements;        /* accurate residual recomputations (IE_MIXED)                       */
+    int status;              /* ie_status of this right-hand side                                 */
+    int pad_;
+    double recursive_relres; /* ||r_k||_2 / ||f||_2 of the recurrence                             */
+    double true_relres;      /* ||f - A u||_2 / ||f||_2 with the accurate matvec (-1 if not run)  */
+} pcg_report;
+
+/* Fills *o with the defaults: tol 1e-8, max_it 1000, IE_MIXED, replace_every 50, use_x0 0,
+ * timeout_s 0, check_every 8, verify 1. */
+IEDD_API void pcg_default_opts(pcg_opts *o);
+
+/*
+ * pcg_solve -- preconditioned conjugate gradient (Hestenes-Stiefel, as used in Sec. 6) on
+ * A u = f with T^{-1} from dd_factor, nrhs independent recurrences (per-column scalars; a
+ * converged column is frozen).
+ *   f      N x nrhs right-hand sides (host or device), column-major, leading dimension ld
+ *   u      N x nrhs output (host or device); the initial iterate on entry if opts->use_x0
+ *   opts   NULL for the defaults
+ *   rep    (host, may be NULL) nrhs reports
+ * Iteration: r = f - A u0; z = T^{-1} r; p = z; then q = A p, alpha = r^T z / p^T q,
+ * u += alpha p, r -= alpha q, z = T^{-1} r, beta = r_new^T z_new / r^T z, p = z + beta p.
+ * IE_MIXED: q = A p in FP32 (ie_matvec IE_MIXED), T^{-1} in the factor's precision, vectors and
+ * scalars in FP64.  When the recursive residual reaches tol (and every replace_every
+ * iterations) r is replaced by the accurate f - A u (ie_matvec IE_ACCURATE); a column is done
+ * only when that true residual is <= tol.  IE_FP64: stops on the recursive residual; with
+ * verify = 1 the true residual is reported.
+ * Returns IE_OK if every column converged, else the first failing column's status.
+ * Synchronizes the stream.
+ */
+IEDD_API int pcg_solve(const ie_problem *p, const dd_factor_t *f, const double *rhs, double *u, int nrhs,
+              long long ld, const pcg_opts *opts, pcg_report *rep, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IEDD_H */

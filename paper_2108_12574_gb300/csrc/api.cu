@@ -1,0 +1,400 @@
+// C-ABI entry points of libiedd: handles, argument checks, host/device staging, and the
+// host-side domain decomposition (Sec. 2.2-2.3).  The compute steps live in matvec.cu,
+// factor.cu, apply.cu and pcg.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "iedd_internal.cuh"
+
+static thread_local std::string g_last_error;
+
+void ie_set_error(const std::string &msg) { g_last_error = msg; }
+
+extern "C" const char *ie_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char *ie_version(void) { return "iedd-gb300 0.1 (sm_103a)"; }
+
+bool ie_is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // clear: an unknown pointer is host memory
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int DevBuf::alloc(size_t b, cudaStream_t st) {
+    s = st;
+    bytes = b;
+    if (b == 0) return IE_OK;
+    IE_TRY_CUDA(cudaMallocAsync(&ptr, b, st));
+    return IE_OK;
+}
+
+DevBuf::~DevBuf() {
+    if (ptr) cudaFreeAsync(ptr, s);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Problem (Sec. 2.1)
+// ---------------------------------------------------------------------------------------------
+static double self_cell_integral(int dim, double h) {
+    const double pi = 3.14159265358979323846;
+    if (dim == 2) {
+        // -(h^2/(4 pi)) (2 ln(h/2) + int_{[0,1]^2} ln(s^2+t^2)),  the integral = ln 2 - 3 + pi/2
+        return -(h * h / (4.0 * pi)) * (2.0 * std::log(h / 2.0) + std::log(2.0) - 3.0 + pi / 2.0);
+    }
+    // (h^2/(2 pi)) int_{[0,1]^3} 1/|x|,  the integral = 3 ln(1+sqrt 3) - 1.5 ln 2 - pi/4
+    return (h * h / (2.0 * pi)) *
+           (3.0 * std::log(1.0 + std::sqrt(3.0)) - 1.5 * std::log(2.0) - pi / 4.0);
+}
+
+extern "C" int ie_discretize(int dim, int n, double a_shift, int grid, int device, ie_problem **out) {
+    if (!out) { ie_set_error("ie_discretize: out is NULL"); return IE_ERR_ARG; }
+    *out = nullptr;
+    if (dim != 2 && dim != 3) { ie_set_error("ie_discretize: dim must be 2 or 3"); return IE_ERR_ARG; }
+    if (n < 2) { ie_set_error("ie_discretize: n must be >= 2"); return IE_ERR_ARG; }
+    long long N = 1;
+    for (int d = 0; d < dim; ++d) N *= n;
+    if (N > (1LL << 26)) { ie_set_error("ie_discretize: N = n^dim exceeds 2^26"); return IE_ERR_ARG; }
+    if (!std::isfinite(a_shift)) {
+        ie_set_error("ie_discretize: a_shift must be finite"); return IE_ERR_ARG;
+    }
+    if (grid != IE_GRID_TEXT && grid != IE_GRID_TABLE) {
+        ie_set_error("ie_discretize: unknown grid convention"); return IE_ERR_ARG;
+    }
+    int ndev = 0;
+    IE_TRY_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) { ie_set_error("ie_discretize: bad device ordinal"); return IE_ERR_ARG; }
+    DeviceGuard g(device);
+
+    ie_problem *p = new (std::nothrow) ie_problem();
+    if (!p) { ie_set_error("ie_discretize: out of host memory"); return IE_ERR_OOM; }
+    const double pi = 3.14159265358979323846;
+    p->dim = dim; p->n = n; p->N = N; p->grid = grid; p->device = device; p->a_shift = a_shift;
+    p->h = 1.0 / n;
+    p->spacing = grid == IE_GRID_TEXT ? p->h : 1.0 / (n - 1);
+    p->weight = dim == 2 ? p->h * p->h : p->h * p->h * p->h;
+    p->diag = self_cell_integral(dim, p->h) + a_shift;
+    // A_ij = w K(s D): 2D  -w/(2 pi) (ln s + ln(r2)/2);  3D  w / (4 pi s sqrt(r2))
+    p->c_const = -p->weight * std::log(p->spacing) / (2.0 * pi);
+    p->c_ln = -p->weight / (4.0 * pi);
+    p->c_log2 = p->c_ln * std::log(2.0);
+    p->c_r = p->weight / (4.0 * pi * p->spacing);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete p; ie_set_error("cudaGetDeviceProperties failed"); return IE_ERR_CUDA; }
+    p->sm_count = prop.multiProcessorCount;
+    int st = build_problem_tables(p);
+    if (st != IE_OK) { ie_destroy(p); return st; }
+    *out = p;
+    return IE_OK;
+}
+
+extern "C" int ie_problem_info(const ie_problem *p, int *dim, int *n, long long *N, double *h, double *diag) {
+    if (!p) { ie_set_error("ie_problem_info: NULL problem"); return IE_ERR_ARG; }
+    if (dim) *dim = p->dim;
+    if (n) *n = p->n;
+    if (N) *N = p->N;
+    if (h) *h = p->h;
+    if (diag) *diag = p->diag;
+    return IE_OK;
+}
+
+extern "C" void ie_destroy(ie_problem *p) {
+    if (!p) return;
+    DeviceGuard g(p->device);
+    cudaFree(p->d_coord);
+    cudaFree(p->d_table);
+    cudaFree(p->d_table64);
+    delete p;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Staging of host vectors
+// ---------------------------------------------------------------------------------------------
+namespace {
+struct Staged {
+    const double *dev = nullptr;   // device view of the vector
+    long long ld = 0;
+    DevBuf buf;
+};
+
+int stage_in(const double *x, long long N, int nrhs, long long ld, bool copy, cudaStream_t s,
+             Staged &st) {
+    if (ie_is_device_ptr(x)) { st.dev = x; st.ld = ld; return IE_OK; }
+    IE_TRY(st.buf.alloc(sizeof(double) * N * nrhs, s));
+    if (copy)
+        IE_TRY_CUDA(cudaMemcpy2DAsync(st.buf.ptr, sizeof(double) * N, x, sizeof(double) * ld,
+                                      sizeof(double) * N, nrhs, cudaMemcpyHostToDevice, s));
+    st.dev = st.buf.as<double>();
+    st.ld = N;
+    return IE_OK;
+}
+
+int stage_out(double *y, const Staged &st, long long N, int nrhs, long long ld, cudaStream_t s) {
+    if (st.buf.ptr == nullptr) return IE_OK;
+    IE_TRY_CUDA(cudaMemcpy2DAsync(y, sizeof(double) * ld, st.buf.ptr, sizeof(double) * N,
+                                  sizeof(double) * N, nrhs, cudaMemcpyDeviceToHost, s));
+    return IE_OK;
+}
+
+int check_vec_args(const char *who, const ie_problem *p, const void *a, const void *b, int nrhs,
+                   long long ld) {
+    if (!p) { ie_set_error(std::string(who) + ": NULL problem"); return IE_ERR_ARG; }
+    if (!a || !b) { ie_set_error(std::string(who) + ": NULL vector"); return IE_ERR_ARG; }
+    if (nrhs < 1) { ie_set_error(std::string(who) + ": nrhs must be >= 1"); return IE_ERR_ARG; }
+    if (ld < p->N) { ie_set_error(std::string(who) + ": ld must be >= N"); return IE_ERR_ARG; }
+    const char *pa = static_cast<const char *>(a), *pb = static_cast<const char *>(b);
+    size_t span = sizeof(double) * (size_t)(ld * (nrhs - 1) + p->N);
+    if (pa < pb + span && pb < pa + span) {
+        ie_set_error(std::string(who) + ": input and output overlap"); return IE_ERR_ARG;
+    }
+    return IE_OK;
+}
+}  // namespace
+
+extern "C" int ie_matvec(const ie_problem *p, const double *x, double *y, int nrhs, long long ld,
+                         int precision, void *stream) {
+    IE_TRY(check_vec_args("ie_matvec", p, x, y, nrhs, ld));
+    if (precision != IE_FP64 && precision != IE_MIXED && precision != IE_ACCURATE) {
+        ie_set_error("ie_matvec: unknown precision"); return IE_ERR_ARG;
+    }
+    DeviceGuard g(p->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Staged sx, sy;
+    IE_TRY(stage_in(x, p->N, nrhs, ld, true, s, sx));
+    IE_TRY(stage_in(y, p->N, nrhs, ld, false, s, sy));
+    IE_TRY(launch_matvec(p, sx.dev, sx.ld, const_cast<double *>(sy.dev), sy.ld, nrhs, precision, s));
+    IE_TRY(stage_out(y, sy, p->N, nrhs, ld, s));
+    if (sx.buf.ptr || sy.buf.ptr) IE_TRY_CUDA(cudaStreamSynchronize(s));
+    return IE_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Domain decomposition (Sec. 2.2-2.3; Eqs. e:dd, e:first, e:cbd; Table t:dd)
+// ---------------------------------------------------------------------------------------------
+static const int kMaxBlock = 16384;
+
+extern "C" int dd_partition(const ie_problem *p, int m, int delta, int kind, dd_partition_t **out) {
+    if (!out) { ie_set_error("dd_partition: out is NULL"); return IE_ERR_ARG; }
+    *out = nullptr;
+    if (!p) { ie_set_error("dd_partition: NULL problem"); return IE_ERR_ARG; }
+    if (m < 1 || p->n % m != 0) { ie_set_error("dd_partition: n must be a positive multiple of m"); return IE_ERR_ARG; }
+    if (delta < 0) { ie_set_error("dd_partition: delta must be >= 0"); return IE_ERR_ARG; }
+    if (kind != DD_JACOBI && kind != DD_SCHWARZ && kind != DD_CBD) {
+        ie_set_error("dd_partition: unknown kind"); return IE_ERR_ARG;
+    }
+    const int dim = p->dim, n = p->n, w = n / m;
+    const int ext = kind == DD_JACOBI ? 0 : std::min(delta, n);
+    long long M = 1;
+    for (int d = 0; d < dim; ++d) M *= m;
+
+    // every extended box, enumerated row-major so its indices come out ascending
+    std::vector<std::vector<int>> boxes((size_t)M);
+    std::vector<int> colour((size_t)M);
+    for (long long b = 0; b < M; ++b) {
+        int k[3] = {0, 0, 0};
+        long long t = b;
+        for (int d = dim - 1; d >= 0; --d) { k[d] = (int)(t % m); t /= m; }
+        int lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+        int c = 0;
+        for (int d = 0; d < dim; ++d) {
+            lo[d] = std::max(k[d] * w - ext, 0);
+            hi[d] = std::min((k[d] + 1) * w + ext, n);
+            c = c * 2 + (k[d] & 1);
+        }
+        colour[(size_t)b] = c;
+        auto &v = boxes[(size_t)b];
+        if (dim == 2) {
+            for (int i = lo[0]; i < hi[0]; ++i)
+                for (int j = lo[1]; j < hi[1]; ++j) v.push_back(i * n + j);
+        } else {
+            for (int i = lo[0]; i < hi[0]; ++i)
+                for (int j = lo[1]; j < hi[1]; ++j)
+                    for (int l = lo[2]; l < hi[2]; ++l) v.push_back((i * n + j) * n + l);
+        }
+    }
+    std::vector<std::vector<int>> blocks;
+    if (kind == DD_CBD) {
+        int ncol = 1 << dim;
+        for (int c = 0; c < ncol; ++c) {
+            std::vector<int> u;
+            for (long long b = 0; b < M; ++b)
+                if (colour[(size_t)b] == c) u.insert(u.end(), boxes[(size_t)b].begin(), boxes[(size_t)b].end());
+            if (u.empty()) continue;
+            std::sort(u.begin(), u.end());
+            u.erase(std::unique(u.begin(), u.end()), u.end());
+            blocks.push_back(std::move(u));
+        }
+    } else {
+        blocks = std::move(boxes);
+    }
+
+    dd_partition_t *s = new (std::nothrow) dd_partition_t();
+    if (!s) { ie_set_error("dd_partition: out of host memory"); return IE_ERR_OOM; }
+    s->prob = p; s->device = p->device; s->kind = kind; s->m = m; s->delta = ext;
+    s->nblocks = (int)blocks.size();
+    s->offs.assign(blocks.size() + 1, 0);
+    for (size_t i = 0; i < blocks.size(); ++i) {
+        s->offs[i + 1] = s->offs[i] + (long long)blocks[i].size();
+        s->max_block = std::max(s->max_block, (int)blocks[i].size());
+    }
+    s->total = s->offs.back();
+    if (s->max_block > kMaxBlock) {
+        delete s;
+        ie_set_error("dd_partition: a subdomain has more than 16384 points");
+        return IE_ERR_ARG;
+    }
+    s->idx.reserve((size_t)s->total);
+    for (auto &b : blocks) s->idx.insert(s->idx.end(), b.begin(), b.end());
+
+    // inverse map (point -> positions of its occurrences, in increasing block order)
+    std::vector<long long> inv_ptr((size_t)p->N + 1, 0), inv_pos((size_t)s->total);
+    for (long long q = 0; q < s->total; ++q) inv_ptr[(size_t)s->idx[(size_t)q] + 1]++;
+    for (long long i = 0; i < p->N; ++i) inv_ptr[(size_t)i + 1] += inv_ptr[(size_t)i];
+    {
+        std::vector<long long> fill(inv_ptr.begin(), inv_ptr.end() - 1);
+        for (long long q = 0; q < s->total; ++q) inv_pos[(size_t)fill[(size_t)s->idx[(size_t)q]]++] = q;
+    }
+
+    DeviceGuard g(p->device);
+    auto fail = [&](cudaError_t e) {
+        ie_set_error(std::string("dd_partition: ") + cudaGetErrorString(e));
+        dd_partition_destroy(s);
+        return e == cudaErrorMemoryAllocation ? IE_ERR_OOM : IE_ERR_CUDA;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&s->d_offs, sizeof(long long) * s->offs.size())) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&s->d_idx, sizeof(int) * std::max<long long>(s->total, 1))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&s->d_inv_ptr, sizeof(long long) * inv_ptr.size())) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&s->d_inv_pos, sizeof(long long) * std::max<long long>(s->total, 1))) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(s->d_offs, s->offs.data(), sizeof(long long) * s->offs.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(s->d_idx, s->idx.data(), sizeof(int) * s->total, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(s->d_inv_ptr, inv_ptr.data(), sizeof(long long) * inv_ptr.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(s->d_inv_pos, inv_pos.data(), sizeof(long long) * s->total, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    *out = s;
+    return IE_OK;
+}
+
+extern "C" int dd_partition_info(const dd_partition_t *s, int *nblocks, long long *total, int *max_block) {
+    if (!s) { ie_set_error("dd_partition_info: NULL partition"); return IE_ERR_ARG; }
+    if (nblocks) *nblocks = s->nblocks;
+    if (total) *total = s->total;
+    if (max_block) *max_block = s->max_block;
+    return IE_OK;
+}
+
+extern "C" int dd_partition_export(const dd_partition_t *s, long long *offsets, int *index) {
+    if (!s) { ie_set_error("dd_partition_export: NULL partition"); return IE_ERR_ARG; }
+    if (offsets) std::memcpy(offsets, s->offs.data(), sizeof(long long) * s->offs.size());
+    if (index) std::memcpy(index, s->idx.data(), sizeof(int) * s->idx.size());
+    return IE_OK;
+}
+
+extern "C" void dd_partition_destroy(dd_partition_t *s) {
+    if (!s) return;
+    DeviceGuard g(s->device);
+    cudaFree(s->d_offs);
+    cudaFree(s->d_idx);
+    cudaFree(s->d_inv_ptr);
+    cudaFree(s->d_inv_pos);
+    delete s;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Factor and apply (Sec. 3, Eqs. e:ai, e:ad; exact Cholesky subdomain solver of Sec. 4.3)
+// ---------------------------------------------------------------------------------------------
+extern "C" int dd_factor(const ie_problem *p, const dd_partition_t *s, int precision, dd_factor_t **out,
+                         int *info, void *stream) {
+    if (!out) { ie_set_error("dd_factor: out is NULL"); return IE_ERR_ARG; }
+    *out = nullptr;
+    if (info) *info = -1;
+    if (!p || !s) { ie_set_error("dd_factor: NULL problem or partition"); return IE_ERR_ARG; }
+    if (s->prob != p) { ie_set_error("dd_factor: partition belongs to another problem"); return IE_ERR_ARG; }
+    if (precision != IE_FP64 && precision != IE_MIXED) { ie_set_error("dd_factor: unknown precision"); return IE_ERR_ARG; }
+    DeviceGuard g(p->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    dd_factor_t *f = new (std::nothrow) dd_factor_t();
+    if (!f) { ie_set_error("dd_factor: out of host memory"); return IE_ERR_OOM; }
+    f->prob = p; f->device = p->device; f->part = s; f->precision = precision; f->nblocks = s->nblocks;
+
+    std::vector<long long> loff((size_t)s->nblocks + 1, 0);
+    std::vector<int> npad((size_t)s->nblocks), nb((size_t)s->nblocks), order((size_t)s->nblocks);
+    for (int i = 0; i < s->nblocks; ++i) {
+        nb[(size_t)i] = (int)(s->offs[(size_t)i + 1] - s->offs[(size_t)i]);
+        npad[(size_t)i] = (nb[(size_t)i] + 31) / 32 * 32;
+        if (npad[(size_t)i] == 0) npad[(size_t)i] = 32;
+        f->max_pad = std::max(f->max_pad, npad[(size_t)i]);
+        loff[(size_t)i + 1] = loff[(size_t)i] + (long long)npad[(size_t)i] * npad[(size_t)i];
+        order[(size_t)i] = i;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nb[(size_t)a] > nb[(size_t)b]; });
+    f->pool_elems = loff.back();
+    size_t esz = precision == IE_FP64 ? sizeof(double) : sizeof(float);
+    auto fail = [&](cudaError_t e) {
+        ie_set_error(std::string("dd_factor: ") + cudaGetErrorString(e));
+        dd_factor_destroy(f);
+        return e == cudaErrorMemoryAllocation ? IE_ERR_OOM : IE_ERR_CUDA;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&f->d_loff, sizeof(long long) * loff.size())) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&f->d_npad, sizeof(int) * npad.size())) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&f->d_n, sizeof(int) * nb.size())) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&f->d_order, sizeof(int) * order.size())) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&f->d_info, sizeof(int) * nb.size())) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&f->d_pool, esz * (size_t)f->pool_elems)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(f->d_loff, loff.data(), sizeof(long long) * loff.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(f->d_npad, npad.data(), sizeof(int) * npad.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(f->d_n, nb.data(), sizeof(int) * nb.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(f->d_order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+
+    int stl = launch_factor(f, st);
+    if (stl == IE_OK) stl = prepare_apply(f);
+    if (stl != IE_OK) { dd_factor_destroy(f); return stl; }
+    std::vector<int> hinfo((size_t)s->nblocks);
+    if ((e = cudaMemcpyAsync(hinfo.data(), f->d_info, sizeof(int) * hinfo.size(), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+    *out = f;
+    for (int i = 0; i < s->nblocks; ++i) {
+        if (hinfo[(size_t)i] >= 0) {
+            if (info) *info = i;
+            ie_set_error("dd_factor: block " + std::to_string(i) + " is not SPD (pivot " +
+                         std::to_string(hinfo[(size_t)i]) + ")");
+            return IE_ERR_NOT_SPD;
+        }
+    }
+    return IE_OK;
+}
+
+extern "C" void dd_factor_destroy(dd_factor_t *f) {
+    if (!f) return;
+    DeviceGuard g(f->device);
+    cudaFree(f->d_loff);
+    cudaFree(f->d_npad);
+    cudaFree(f->d_n);
+    cudaFree(f->d_order);
+    cudaFree(f->d_info);
+    cudaFree(f->d_pool);
+    delete f;
+}
+
+extern "C" int dd_apply(const dd_factor_t *f, const double *r, double *z, int nrhs, long long ld, void *stream) {
+    if (!f) { ie_set_error("dd_apply: NULL factor"); return IE_ERR_ARG; }
+    IE_TRY(check_vec_args("dd_apply", f->prob, r, z, nrhs, ld));
+    const ie_problem *p = f->prob;
+    DeviceGuard g(p->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Staged sr, sz;
+    IE_TRY(stage_in(r, p->N, nrhs, ld, true, s, sr));
+    IE_TRY(stage_in(z, p->N, nrhs, ld, false, s, sz));
+    IE_TRY(launch_apply(f, sr.dev, sr.ld, const_cast<double *>(sz.dev), sz.ld, nrhs, s));
+    IE_TRY(stage_out(z, sz, p->N, nrhs, ld, s));
+    if (sr.buf.ptr || sz.buf.ptr) IE_TRY_CUDA(cudaStreamSynchronize(s));
+    return IE_OK;
+}

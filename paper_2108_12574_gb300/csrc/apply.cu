@@ -1,0 +1,140 @@
+// dd_apply: z = T^{-1} r = sum_i R_i^T L_i^{-T} L_i^{-1} R_i r  (Eq. e:ad).
+//
+// K6 apply_blocks   one CTA of 256 threads per (subdomain, right-hand side): gather R_i r into
+//                   shared memory, forward solve with L_i and backward solve with L_i^T, 32-row
+//                   tiles at a time.  The off-diagonal part of each tile step is a GEMV spread
+//                   over the 8 warps (coalesced reads of L rows); the 32 x 32 diagonal triangle is
+//                   solved by one warp with shuffles.  L_i is read twice (both passes), which is
+//                   the HBM traffic that bounds the step.  The block result goes to a scratch
+//                   vector [rhs][sum n_i].
+// K6b overlap_sum   z_p = sum of the block results of every subdomain containing p, in increasing
+//                   subdomain order (inverse index map), so the sum is deterministic.
+#include <cuda_runtime.h>
+
+#include "iedd_internal.cuh"
+
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+apply_blocks(const T *__restrict__ pool, const long long *__restrict__ loff, const int *__restrict__ npad,
+             const int *__restrict__ nb, const long long *__restrict__ offs, const int *__restrict__ idx,
+             const int *__restrict__ order, const double *__restrict__ r, long long ldr,
+             double *__restrict__ zbuf, long long total) {
+    extern __shared__ unsigned char smem_raw[];
+    T *Y = reinterpret_cast<T *>(smem_raw);
+    __shared__ T D[32][33];
+    __shared__ T red[8][32];
+    const int b = order[blockIdx.x];
+    const int k = blockIdx.y;
+    const int np = npad[b], n = nb[b], nt = np / 32;
+    const T *L = pool + loff[b];
+    const int *id = idx + offs[b];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const double *rk = r + (long long)k * ldr;
+    for (int a = tid; a < np; a += 256) Y[a] = a < n ? (T)rk[id[a]] : T(0);
+    __syncthreads();
+
+    // forward: L y = R_i r
+    for (int t = 0; t < nt; ++t) {
+        const int t0 = t * 32;
+        for (int e = tid; e < 1024; e += 256) D[e >> 5][e & 31] = L[(long long)(t0 + (e >> 5)) * np + t0 + (e & 31)];
+        for (int q = 0; q < 4; ++q) {
+            const int row = t0 + warp + 8 * q;
+            const T *lr = L + (long long)row * np;
+            T s = 0;
+            for (int c = lane; c < t0; c += 32) s += lr[c] * Y[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) red[0][warp + 8 * q] = s;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            T v = Y[t0 + lane] - red[0][lane];
+            for (int j = 0; j < 32; ++j) {
+                const T yj = __shfl_sync(0xffffffffu, v, j) / D[j][j];
+                if (lane == j) v = yj;
+                if (lane > j) v -= D[lane][j] * yj;
+            }
+            Y[t0 + lane] = v;
+        }
+        __syncthreads();
+    }
+    // backward: L^T z = y
+    for (int t = nt - 1; t >= 0; --t) {
+        const int t0 = t * 32;
+        for (int e = tid; e < 1024; e += 256) D[e >> 5][e & 31] = L[(long long)(t0 + (e >> 5)) * np + t0 + (e & 31)];
+        T part = 0;
+        for (int row = t0 + 32 + warp; row < np; row += 8) part += L[(long long)row * np + t0 + lane] * Y[row];
+        red[warp][lane] = part;
+        __syncthreads();
+        if (warp == 0) {
+            T sacc = 0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) sacc += red[w][lane];
+            T v = Y[t0 + lane] - sacc;
+            for (int j = 31; j >= 0; --j) {
+                const T zj = __shfl_sync(0xffffffffu, v, j) / D[j][j];
+                if (lane == j) v = zj;
+                if (lane < j) v -= D[j][lane] * zj;
+            }
+            Y[t0 + lane] = v;
+        }
+        __syncthreads();
+    }
+    double *zk = zbuf + (long long)k * total + offs[b];
+    for (int a = tid; a < n; a += 256) zk[a] = (double)Y[a];
+}
+
+__global__ void overlap_sum(const double *__restrict__ zbuf, long long total, const long long *__restrict__ inv_ptr,
+                            const long long *__restrict__ inv_pos, double *__restrict__ z, long long ldz, long long N) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (i >= N) return;
+    const double *zb = zbuf + (long long)k * total;
+    double s = 0.0;
+    for (long long q = inv_ptr[i]; q < inv_ptr[i + 1]; ++q) s += zb[inv_pos[q]];
+    z[(long long)k * ldz + i] = s;
+}
+
+}  // namespace
+
+// Raise the dynamic shared-memory limit of the apply kernel for large subdomains (done once per
+// factor, outside any stream capture).
+int prepare_apply(const dd_factor_t *f) {
+    if (f->precision == IE_FP64) {
+        size_t sm = sizeof(double) * f->max_pad;
+        if (sm > 48 * 1024)
+            IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    } else {
+        size_t sm = sizeof(float) * f->max_pad;
+        if (sm > 48 * 1024)
+            IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    }
+    return IE_OK;
+}
+
+int launch_apply(const dd_factor_t *f, const double *r, long long ldr, double *z, long long ldz, int nrhs,
+                 cudaStream_t s) {
+    const ie_problem *p = f->prob;
+    const dd_partition_t *part = f->part;
+    DevBuf zbuf;
+    IE_TRY(zbuf.alloc(sizeof(double) * (size_t)std::max<long long>(part->total, 1) * nrhs, s));
+    if (f->nblocks > 0) {
+        dim3 g(f->nblocks, nrhs);
+        if (f->precision == IE_FP64) {
+            size_t sm = sizeof(double) * f->max_pad;
+            apply_blocks<double><<<g, 256, sm, s>>>((const double *)f->d_pool, f->d_loff, f->d_npad, f->d_n, part->d_offs,
+                                                   part->d_idx, f->d_order, r, ldr, zbuf.as<double>(), part->total);
+        } else {
+            size_t sm = sizeof(float) * f->max_pad;
+            apply_blocks<float><<<g, 256, sm, s>>>((const float *)f->d_pool, f->d_loff, f->d_npad, f->d_n, part->d_offs,
+                                                  part->d_idx, f->d_order, r, ldr, zbuf.as<double>(), part->total);
+        }
+        IE_CHECK_LAUNCH();
+    }
+    dim3 g2((unsigned)((p->N + 255) / 256), nrhs);
+    overlap_sum<<<g2, 256, 0, s>>>(zbuf.as<double>(), part->total, part->d_inv_ptr, part->d_inv_pos, z, ldz, p->N);
+    IE_CHECK_LAUNCH();
+    return IE_OK;
+}

@@ -1,0 +1,135 @@
+// Internal declarations shared by the translation units of libiedd (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "iedd.h"
+
+// ---------------------------------------------------------------------------------------------
+// Errors: every entry point returns an ie_status; the message goes to a thread-local string.
+// ---------------------------------------------------------------------------------------------
+void ie_set_error(const std::string &msg);
+
+#define IE_TRY_CUDA(call)                                                                      \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            ie_set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+            return e_ == cudaErrorMemoryAllocation ? IE_ERR_OOM : IE_ERR_CUDA;                 \
+        }                                                                                      \
+    } while (0)
+
+#define IE_CHECK_LAUNCH() IE_TRY_CUDA(cudaGetLastError())
+
+#define IE_TRY(expr)                                                                           \
+    do {                                                                                       \
+        int s_ = (expr);                                                                       \
+        if (s_ != IE_OK) return s_;                                                            \
+    } while (0)
+
+// Scoped device context: makes `dev` current and restores the previous device on exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// ---------------------------------------------------------------------------------------------
+// Handles
+// ---------------------------------------------------------------------------------------------
+struct ie_problem {
+    int dim = 0, n = 0, grid = 0, device = 0;
+    long long N = 0;
+    double h = 0, spacing = 0, weight = 0, diag = 0, a_shift = 0;
+    // Off-diagonal entries in terms of the integer lattice offset D = i - j (r2 = |D|^2 >= 1):
+    //   2D: A_ij = c_const + c_ln * ln(r2) = c_const + c_log2 * log2(r2)
+    //   3D: A_ij = c_r * rsqrt(r2)
+    double c_const = 0, c_ln = 0, c_log2 = 0, c_r = 0;
+    float4 *d_coord = nullptr;     // integer lattice coordinates of every point (x, y, z, 0)
+    float2 *d_table = nullptr;     // entry per |offset| (n^dim), split hi + lo; [0] = A_ii
+    double *d_table64 = nullptr;   // same table in FP64
+    int sm_count = 0;
+};
+
+struct dd_partition_t {
+    const ie_problem *prob = nullptr;
+    int device = 0;
+    int kind = 0, m = 0, delta = 0;
+    int nblocks = 0, max_block = 0;
+    long long total = 0;
+    std::vector<long long> offs;   // CSR offsets, nblocks + 1
+    std::vector<int> idx;          // ascending global indices per block
+    // device copies
+    long long *d_offs = nullptr;
+    int *d_idx = nullptr;
+    // inverse map for the deterministic overlap sum: for point p the positions (into idx) of
+    // every occurrence, in increasing block order
+    long long *d_inv_ptr = nullptr;  // N + 1
+    long long *d_inv_pos = nullptr;  // total
+};
+
+struct dd_factor_t {
+    const ie_problem *prob = nullptr;
+    int device = 0;
+    const dd_partition_t *part = nullptr;
+    int precision = 0;             // IE_FP64 or IE_MIXED
+    int nblocks = 0, max_pad = 0;
+    long long *d_loff = nullptr;   // offset (elements) of each padded block in the pool
+    int *d_npad = nullptr;         // padded (multiple of 32) size of each block
+    int *d_n = nullptr;            // true size of each block
+    int *d_order = nullptr;        // schedule order: blocks by decreasing size
+    void *d_pool = nullptr;        // padded row-major lower factors (float or double)
+    long long pool_elems = 0;
+    int *d_info = nullptr;         // per-block first bad pivot (-1 ok)
+};
+
+// ---------------------------------------------------------------------------------------------
+// Device vector helpers: host / device pointer detection and staging
+// ---------------------------------------------------------------------------------------------
+bool ie_is_device_ptr(const void *p);
+
+// RAII stream-ordered device buffer.
+struct DevBuf {
+    void *ptr = nullptr;
+    cudaStream_t s = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    int alloc(size_t b, cudaStream_t st);
+    ~DevBuf();
+    template <class T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// ---------------------------------------------------------------------------------------------
+// Kernel launchers (matvec.cu, factor.cu, apply.cu, pcg.cu)
+// ---------------------------------------------------------------------------------------------
+// y = A x for device FP64 x (leading dimension ldx) and y (ldy), nrhs columns.
+// precision: IE_FP64, IE_MIXED or IE_ACCURATE.
+int launch_matvec(const ie_problem *p, const double *x, long long ldx, double *y, long long ldy,
+                  int nrhs, int precision, cudaStream_t s);
+// As launch_matvec, and, if dot_out != nullptr, dot_out[k] = x_k^T y_k (FP64, deterministic).
+int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, double *y, long long ldy,
+                      int nrhs, int precision, double *dot_out, cudaStream_t s);
+int build_problem_tables(ie_problem *p);
+
+int launch_factor(dd_factor_t *f, cudaStream_t s);
+int prepare_apply(const dd_factor_t *f);
+// z = T^{-1} r for device FP64 r (ldr) and z (ldz).
+int launch_apply(const dd_factor_t *f, const double *r, long long ldr, double *z, long long ldz,
+                 int nrhs, cudaStream_t s);
+
+// Deterministic FP64 column dot products: out[k] = sum_i a[k*lda+i] * b[k*ldb+i] (device).
+int launch_dots(const double *a, long long lda, const double *b, long long ldb, long long N,
+                int nrhs, double *out, cudaStream_t s);

@@ -1,0 +1,433 @@
+// Matrix-free matvec y = A x for the collocation matrix of Sec. 2.1 (Eqs. e:a_2d, e:a_3d).
+//
+// All kernels work on the integer lattice offset D = i - j of two grid points (the points are
+// x_j = offset + s * j, so x_i - x_j = s * D):
+//   2D  A_ij = w K(s D) = c_const + c_ln ln|D|^2,    3D  A_ij = c_r / |D|,     i != j,
+// and A_ii = the self-cell integral.  |D|^2 is an exact small integer in FP32 (|D|^2 < 2^24
+// for n <= 2048 in 2D and n <= 2364 in 3D), so the only rounding in an FP32 entry is that of
+// the SFU log2 / rsqrt, and the large constant c_const is kept out of the FP32 sums.
+//
+// K1  k1_matvec_f32      FP32, one right-hand side.  Source points are staged through shared
+//                        memory 256 at a time as float4 {D-coords, x_j}; each thread keeps R
+//                        target rows in registers; per pair: 2-3 FADD, FMUL + 1-2 FFMA for
+//                        |D|^2, FMNMX, one SFU op (MUFU.LG2 / MUFU.RSQ), one FFMA.  The i = j
+//                        pair is neutralised branch-free by clamping |D|^2 to >= 1 (log2 1 = 0;
+//                        in 3D the spurious rsqrt(1) x_i is subtracted in the combine).  Work
+//                        is split over (row tile, column split) so the grid fills the GPU;
+//                        partial sums go to a [split][N] FP32 scratch and are combined in FP64.
+// Kd  kd_matvec_f64      the same in FP64 with the natural log / rsqrt of double (plain FP64).
+// K2  k2_accurate_{2d,3d} FP64-class y = A x from the per-|offset| entry table (translation
+//                        invariance of A on the uniform grid): entry hi/lo FP32 pairs, products
+//                        split exactly with FMA, sums as double-float (TwoSum) per 256-column
+//                        tile, flushed to FP64 per tile.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "iedd_internal.cuh"
+#include "reduce.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------------------------
+// Problem tables
+// ---------------------------------------------------------------------------------------------
+__global__ void coord_kernel(float4 *coord, int dim, int n, long long N) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    long long t = i;
+    float c[3] = {0.f, 0.f, 0.f};
+    for (int d = dim - 1; d >= 0; --d) { c[d] = (float)(t % n); t /= n; }
+    coord[i] = make_float4(c[0], c[1], c[2], 0.f);
+}
+
+// Entry for every |offset| (d_1, ..., d_dim) in [0, n)^dim, FP64, and its hi/lo FP32 split.
+__global__ void table_kernel(float2 *t32, double *t64, int dim, int n, long long T, double diag,
+                             double c_const, double c_ln, double c_r) {
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= T) return;
+    long long t = q;
+    double r2 = 0.0;
+    for (int d = 0; d < dim; ++d) { double v = (double)(t % n); r2 += v * v; t /= n; }
+    double e;
+    if (r2 == 0.0) e = diag;
+    else if (dim == 2) e = c_const + c_ln * log(r2);
+    else e = c_r / sqrt(r2);
+    float hi = (float)e;
+    float lo = (float)(e - (double)hi);
+    t32[q] = make_float2(hi, lo);
+    t64[q] = e;
+}
+
+// ---------------------------------------------------------------------------------------------
+// K1: FP32 SFU matvec, one right-hand side
+// ---------------------------------------------------------------------------------------------
+template <int DIM, int R>
+__global__ void __launch_bounds__(kThreads)
+k1_matvec_f32(const float4 *__restrict__ coord, const double *__restrict__ x, long long N,
+              int tiles_per_split, int ntiles, float *__restrict__ partial) {
+    __shared__ float4 sc[kThreads];
+    const long long row0 = (long long)blockIdx.x * (kThreads * R) + threadIdx.x;
+    float px[R], py[R], pz[R], acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        long long i = row0 + (long long)r * kThreads;
+        float4 c = i < N ? coord[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        px[r] = c.x; py[r] = c.y; pz[r] = c.z; acc[r] = 0.f;
+    }
+    const int t0 = blockIdx.y * tiles_per_split;
+    const int t1 = min(t0 + tiles_per_split, ntiles);
+    for (int t = t0; t < t1; ++t) {
+        long long j = (long long)t * kThreads + threadIdx.x;
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);  // padding source: x = 0 contributes nothing
+        if (j < N) { c = coord[j]; c.w = (float)x[j]; }
+        __syncthreads();
+        sc[threadIdx.x] = c;
+        __syncthreads();
+#pragma unroll 8
+        for (int jj = 0; jj < kThreads; ++jj) {
+            const float4 s = sc[jj];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float dx = px[r] - s.x, dy = py[r] - s.y;
+                float r2;
+                if (DIM == 2) {
+                    r2 = fmaf(dx, dx, dy * dy);
+                } else {
+                    float dz = pz[r] - s.z;
+                    r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                }
+                r2 = fmaxf(r2, 1.0f);
+                const float k = DIM == 2 ? __log2f(r2) : rsqrtf(r2);
+                acc[r] = fmaf(k, s.w, acc[r]);
+            }
+        }
+    }
+    float *out = partial + (long long)blockIdx.y * N;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        long long i = row0 + (long long)r * kThreads;
+        if (i < N) out[i] = acc[r];
+    }
+}
+
+// y_i = diag x_i + off-diagonal part from the split partials (FP64 combine).
+template <typename TP>
+__global__ void combine_kernel(const TP *__restrict__ partial, int nsplit, const double *__restrict__ x,
+                               double *__restrict__ y, long long N, int dim, int mode, double diag,
+                               double c_const, double c_sum, const double *__restrict__ xsum) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double s = 0.0;
+    for (int k = 0; k < nsplit; ++k) s += (double)partial[(long long)k * N + i];
+    const double xi = x[i];
+    double y0;
+    if (dim == 2) {
+        // mode 0 (FP32 sums of log2 |D|^2): c_sum = c_log2; mode 1 (FP64 ln): c_sum = c_ln
+        y0 = diag * xi + c_const * (xsum[0] - xi) + c_sum * s;
+    } else {
+        // the clamped i = j pair added rsqrt(1) * x_i (rounded as the kernel saw it)
+        const double xi_k = mode == 0 ? (double)(float)xi : xi;
+        y0 = diag * xi + c_sum * (s - xi_k);
+    }
+    y[i] = y0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Kd: FP64 matvec with entries regenerated in FP64 (plain FP64 mode)
+// ---------------------------------------------------------------------------------------------
+template <int DIM, int R>
+__global__ void __launch_bounds__(kThreads)
+kd_matvec_f64(const float4 *__restrict__ coord, const double *__restrict__ x, long long N,
+              int tiles_per_split, int ntiles, double *__restrict__ partial) {
+    __shared__ double4 sc[kThreads];
+    const long long row0 = (long long)blockIdx.x * (kThreads * R) + threadIdx.x;
+    double px[R], py[R], pz[R], acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        long long i = row0 + (long long)r * kThreads;
+        float4 c = i < N ? coord[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        px[r] = c.x; py[r] = c.y; pz[r] = c.z; acc[r] = 0.0;
+    }
+    const int t0 = blockIdx.y * tiles_per_split;
+    const int t1 = min(t0 + tiles_per_split, ntiles);
+    for (int t = t0; t < t1; ++t) {
+        long long j = (long long)t * kThreads + threadIdx.x;
+        double4 c = make_double4(0.0, 0.0, 0.0, 0.0);
+        if (j < N) { float4 f = coord[j]; c = make_double4(f.x, f.y, f.z, x[j]); }
+        __syncthreads();
+        sc[threadIdx.x] = c;
+        __syncthreads();
+#pragma unroll 4
+        for (int jj = 0; jj < kThreads; ++jj) {
+            const double4 s = sc[jj];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                double dx = px[r] - s.x, dy = py[r] - s.y;
+                double r2 = DIM == 2 ? fma(dx, dx, dy * dy) : fma(dx, dx, fma(dy, dy, (pz[r] - s.z) * (pz[r] - s.z)));
+                r2 = fmax(r2, 1.0);
+                const double k = DIM == 2 ? log(r2) : rsqrt(r2);
+                acc[r] = fma(k, s.w, acc[r]);
+            }
+        }
+    }
+    double *out = partial + (long long)blockIdx.y * N;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        long long i = row0 + (long long)r * kThreads;
+        if (i < N) out[i] = acc[r];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// K2: accurate (double-float) matvec from the per-|offset| entry table
+// ---------------------------------------------------------------------------------------------
+struct DF {
+    float hi, lo;
+};
+
+// (sh, sl) += t * x  with t = th + tl, x = xh + xl: exact product split by FMA, TwoSum for the
+// high parts (intrinsics keep the compiler from contracting the rounded product into an FMA).
+__device__ __forceinline__ void df_fma(float th, float tl, float xh, float xl, float &sh, float &sl) {
+    const float p = __fmul_rn(th, xh);
+    float e = fmaf(th, xh, -p);
+    e = fmaf(th, xl, e);
+    e = fmaf(tl, xh, e);
+    const float s = __fadd_rn(sh, p);
+    const float bp = __fsub_rn(s, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+// 2D: a CTA owns a 16 x 16 patch of target points; each step stages a 16 x 16 patch of source
+// points (x as hi/lo) and the 31 x 31 window of table entries their offsets can reach.
+__global__ void __launch_bounds__(kThreads)
+k2_accurate_2d(const float2 *__restrict__ table, const double *__restrict__ x, int n,
+               int patches_per_split, double *__restrict__ partial) {
+    __shared__ float2 W[31][32];
+    __shared__ float2 X[16][16];
+    const int np = (n + 15) / 16;
+    const int I1 = (blockIdx.x / np) * 16, I2 = (blockIdx.x % np) * 16;
+    const int r1 = threadIdx.x >> 4, r2 = threadIdx.x & 15;
+    const int i1 = I1 + r1, i2 = I2 + r2;
+    const long long N = (long long)n * n;
+    double acc = 0.0;
+    const int q0 = blockIdx.y * patches_per_split;
+    const int q1 = min(q0 + patches_per_split, np * np);
+    for (int q = q0; q < q1; ++q) {
+        const int J1 = (q / np) * 16, J2 = (q % np) * 16;
+        __syncthreads();
+        {
+            const int j1 = J1 + r1, j2 = J2 + r2;
+            double v = (j1 < n && j2 < n) ? x[(long long)j1 * n + j2] : 0.0;
+            float h = (float)v;
+            X[r1][r2] = make_float2(h, (float)(v - (double)h));
+        }
+        for (int e = threadIdx.x; e < 31 * 31; e += kThreads) {
+            const int a = e / 31, b = e % 31;
+            int d1 = abs(I1 - J1 + a - 15), d2 = abs(I2 - J2 + b - 15);
+            d1 = min(d1, n - 1);
+            d2 = min(d2, n - 1);
+            W[a][b] = table[(long long)d1 * n + d2];
+        }
+        __syncthreads();
+        float sh = 0.f, sl = 0.f;
+#pragma unroll 4
+        for (int c1 = 0; c1 < 16; ++c1) {
+#pragma unroll
+            for (int c2 = 0; c2 < 16; ++c2) {
+                const float2 t = W[r1 - c1 + 15][r2 - c2 + 15];
+                const float2 v = X[c1][c2];
+                df_fma(t.x, t.y, v.x, v.y, sh, sl);
+            }
+        }
+        acc += (double)sh + (double)sl;
+    }
+    if (i1 < n && i2 < n) partial[(long long)blockIdx.y * N + (long long)i1 * n + i2] = acc;
+}
+
+// 3D: 4 x 8 x 8 patches; the offset window is 7 x 15 x 15.
+__global__ void __launch_bounds__(kThreads)
+k2_accurate_3d(const float2 *__restrict__ table, const double *__restrict__ x, int n,
+               int patches_per_split, double *__restrict__ partial) {
+    __shared__ float2 W[7][15][16];
+    __shared__ float2 X[4][8][8];
+    const int n1 = (n + 3) / 4, n2 = (n + 7) / 8;  // patches along dim 0 and along dims 1, 2
+    const int npatch = n1 * n2 * n2;
+    const int b = blockIdx.x;
+    const int I1 = (b / (n2 * n2)) * 4, I2 = ((b / n2) % n2) * 8, I3 = (b % n2) * 8;
+    const int r1 = threadIdx.x >> 6, r2 = (threadIdx.x >> 3) & 7, r3 = threadIdx.x & 7;
+    const int i1 = I1 + r1, i2 = I2 + r2, i3 = I3 + r3;
+    const long long N = (long long)n * n * n;
+    double acc = 0.0;
+    const int q0 = blockIdx.y * patches_per_split;
+    const int q1 = min(q0 + patches_per_split, npatch);
+    for (int q = q0; q < q1; ++q) {
+        const int J1 = (q / (n2 * n2)) * 4, J2 = ((q / n2) % n2) * 8, J3 = (q % n2) * 8;
+        __syncthreads();
+        {
+            const int j1 = J1 + r1, j2 = J2 + r2, j3 = J3 + r3;
+            double v = (j1 < n && j2 < n && j3 < n) ? x[((long long)j1 * n + j2) * n + j3] : 0.0;
+            float h = (float)v;
+            X[r1][r2][r3] = make_float2(h, (float)(v - (double)h));
+        }
+        for (int e = threadIdx.x; e < 7 * 15 * 15; e += kThreads) {
+            const int a = e / 225, bb = (e / 15) % 15, c = e % 15;
+            int d1 = min(abs(I1 - J1 + a - 3), n - 1);
+            int d2 = min(abs(I2 - J2 + bb - 7), n - 1);
+            int d3 = min(abs(I3 - J3 + c - 7), n - 1);
+            W[a][bb][c] = table[((long long)d1 * n + d2) * n + d3];
+        }
+        __syncthreads();
+        float sh = 0.f, sl = 0.f;
+        for (int c1 = 0; c1 < 4; ++c1) {
+#pragma unroll 2
+            for (int c2 = 0; c2 < 8; ++c2) {
+#pragma unroll
+                for (int c3 = 0; c3 < 8; ++c3) {
+                    const float2 t = W[r1 - c1 + 3][r2 - c2 + 7][r3 - c3 + 7];
+                    const float2 v = X[c1][c2][c3];
+                    df_fma(t.x, t.y, v.x, v.y, sh, sl);
+                }
+            }
+        }
+        acc += (double)sh + (double)sl;
+    }
+    if (i1 < n && i2 < n && i3 < n) partial[(long long)blockIdx.y * N + ((long long)i1 * n + i2) * n + i3] = acc;
+}
+
+__global__ void sum_splits_kernel(const double *__restrict__ partial, int nsplit, double *__restrict__ y,
+                                  long long N) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double s = 0.0;
+    for (int k = 0; k < nsplit; ++k) s += partial[(long long)k * N + i];
+    y[i] = s;
+}
+
+int splits_for(long long items, long long work_units, int sm_count, int per_sm) {
+    long long target = (long long)sm_count * per_sm * 8;
+    long long s = (target + items - 1) / items;
+    s = std::max<long long>(1, std::min<long long>(s, work_units));
+    return (int)s;
+}
+
+}  // namespace
+
+int build_problem_tables(ie_problem *p) {
+    IE_TRY_CUDA(cudaMalloc(&p->d_coord, sizeof(float4) * p->N));
+    long long T = p->N;  // n^dim offsets
+    IE_TRY_CUDA(cudaMalloc(&p->d_table, sizeof(float2) * T));
+    IE_TRY_CUDA(cudaMalloc(&p->d_table64, sizeof(double) * T));
+    coord_kernel<<<(unsigned)((p->N + 255) / 256), 256>>>(p->d_coord, p->dim, p->n, p->N);
+    IE_CHECK_LAUNCH();
+    table_kernel<<<(unsigned)((T + 255) / 256), 256>>>(p->d_table, p->d_table64, p->dim, p->n, T, p->diag,
+                                                      p->c_const, p->c_ln, p->c_r);
+    IE_CHECK_LAUNCH();
+    IE_TRY_CUDA(cudaDeviceSynchronize());
+    return IE_OK;
+}
+
+int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, double *y, long long ldy,
+                      int nrhs, int precision, double *dot_out, cudaStream_t s) {
+    const long long N = p->N;
+    const int ntiles = (int)((N + kThreads - 1) / kThreads);
+    DevBuf xsum;
+    if (p->dim == 2 && precision != IE_ACCURATE) {
+        DevBuf part;
+        IE_TRY(part.alloc(sizeof(double) * iedd::kRedBlocks * nrhs, s));
+        IE_TRY(xsum.alloc(sizeof(double) * nrhs, s));
+        iedd::dot_partial_kernel<<<dim3(iedd::kRedBlocks, nrhs), iedd::kRedThreads, 0, s>>>(
+            x, ldx, nullptr, 0, N, part.as<double>());
+        IE_CHECK_LAUNCH();
+        iedd::dot_final_kernel<<<nrhs, iedd::kRedBlocks, 0, s>>>(part.as<double>(), xsum.as<double>());
+        IE_CHECK_LAUNCH();
+    }
+    for (int k = 0; k < nrhs; ++k) {
+        const double *xk = x + (long long)k * ldx;
+        double *yk = y + (long long)k * ldy;
+        const double *xs = xsum.ptr ? xsum.as<double>() + k : nullptr;
+        if (precision == IE_MIXED) {
+            constexpr int R = 4;
+            const int rt = (int)((N + kThreads * R - 1) / (kThreads * R));
+            const int S = splits_for(rt, ntiles, p->sm_count, 6);
+            const int tps = (ntiles + S - 1) / S;
+            const int Se = (ntiles + tps - 1) / tps;
+            DevBuf part;
+            IE_TRY(part.alloc(sizeof(float) * N * Se, s));
+            if (p->dim == 2)
+                k1_matvec_f32<2, R><<<dim3(rt, Se), kThreads, 0, s>>>(p->d_coord, xk, N, tps, ntiles, part.as<float>());
+            else
+                k1_matvec_f32<3, R><<<dim3(rt, Se), kThreads, 0, s>>>(p->d_coord, xk, N, tps, ntiles, part.as<float>());
+            IE_CHECK_LAUNCH();
+            combine_kernel<float><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
+                part.as<float>(), Se, xk, yk, N, p->dim, 0, p->diag, p->c_const,
+                p->dim == 2 ? p->c_log2 : p->c_r, xs);
+            IE_CHECK_LAUNCH();
+        } else if (precision == IE_FP64) {
+            constexpr int R = 2;
+            const int rt = (int)((N + kThreads * R - 1) / (kThreads * R));
+            const int S = splits_for(rt, ntiles, p->sm_count, 4);
+            const int tps = (ntiles + S - 1) / S;
+            const int Se = (ntiles + tps - 1) / tps;
+            DevBuf part;
+            IE_TRY(part.alloc(sizeof(double) * N * Se, s));
+            if (p->dim == 2)
+                kd_matvec_f64<2, R><<<dim3(rt, Se), kThreads, 0, s>>>(p->d_coord, xk, N, tps, ntiles, part.as<double>());
+            else
+                kd_matvec_f64<3, R><<<dim3(rt, Se), kThreads, 0, s>>>(p->d_coord, xk, N, tps, ntiles, part.as<double>());
+            IE_CHECK_LAUNCH();
+            combine_kernel<double><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
+                part.as<double>(), Se, xk, yk, N, p->dim, 1, p->diag, p->c_const,
+                p->dim == 2 ? p->c_ln : p->c_r, xs);
+            IE_CHECK_LAUNCH();
+        } else {
+            const int n = p->n;
+            int npatch, rowpatch;
+            if (p->dim == 2) {
+                const int np = (n + 15) / 16;
+                npatch = np * np;
+                rowpatch = npatch;
+            } else {
+                const int n1 = (n + 3) / 4, n2 = (n + 7) / 8;
+                npatch = n1 * n2 * n2;
+                rowpatch = npatch;
+            }
+            const int S = splits_for(rowpatch, npatch, p->sm_count, 4);
+            const int pps = (npatch + S - 1) / S;
+            const int Se = (npatch + pps - 1) / pps;
+            DevBuf part;
+            IE_TRY(part.alloc(sizeof(double) * N * Se, s));
+            if (p->dim == 2)
+                k2_accurate_2d<<<dim3(rowpatch, Se), kThreads, 0, s>>>(p->d_table, xk, n, pps, part.as<double>());
+            else
+                k2_accurate_3d<<<dim3(rowpatch, Se), kThreads, 0, s>>>(p->d_table, xk, n, pps, part.as<double>());
+            IE_CHECK_LAUNCH();
+            sum_splits_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(part.as<double>(), Se, yk, N);
+            IE_CHECK_LAUNCH();
+        }
+    }
+    if (dot_out) IE_TRY(launch_dots(x, ldx, y, ldy, N, nrhs, dot_out, s));
+    return IE_OK;
+}
+
+int launch_matvec(const ie_problem *p, const double *x, long long ldx, double *y, long long ldy,
+                  int nrhs, int precision, cudaStream_t s) {
+    return launch_matvec_dot(p, x, ldx, y, ldy, nrhs, precision, nullptr, s);
+}
+
+int launch_dots(const double *a, long long lda, const double *b, long long ldb, long long N, int nrhs,
+                double *out, cudaStream_t s) {
+    DevBuf part;
+    IE_TRY(part.alloc(sizeof(double) * iedd::kRedBlocks * nrhs, s));
+    iedd::dot_partial_kernel<<<dim3(iedd::kRedBlocks, nrhs), iedd::kRedThreads, 0, s>>>(a, lda, b, ldb, N,
+                                                                                       part.as<double>());
+    IE_CHECK_LAUNCH();
+    iedd::dot_final_kernel<<<nrhs, iedd::kRedBlocks, 0, s>>>(part.as<double>(), out);
+    IE_CHECK_LAUNCH();
+    return IE_OK;
+}

@@ -1,0 +1,276 @@
+"""Thin ctypes binding of libiedd (include/iedd.h): argument marshalling only.
+
+Every compute step runs in the library's CUDA kernels.  The binding loads the in-tree
+``_lib/libiedd.so`` and raises ``ImportError`` if it is missing -- there is no CPU fallback.
+
+Vectors are torch tensors (CUDA or CPU) or numpy arrays, FP64, of shape (N,) or (nrhs, N)
+with unit stride along N; a (nrhs, N) batch is the library's column-major N x nrhs layout
+with ld = stride(0).  Host arrays are staged to the device by the library itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+IE_OK, IE_ERR_ARG, IE_ERR_CUDA, IE_ERR_OOM, IE_ERR_NOT_SPD = 0, -1, -2, -3, -4
+IE_ERR_BREAKDOWN, IE_ERR_MAXIT, IE_ERR_STAGNATION, IE_ERR_TIMEOUT = -5, -6, -7, -8
+IE_FP64, IE_MIXED, IE_ACCURATE = 0, 1, 3
+DD_JACOBI, DD_SCHWARZ, DD_CBD = 0, 1, 2
+IE_GRID_TEXT, IE_GRID_TABLE = 0, 1
+
+STATUS_NAMES = {0: "IE_OK", -1: "IE_ERR_ARG", -2: "IE_ERR_CUDA", -3: "IE_ERR_OOM", -4: "IE_ERR_NOT_SPD",
+                -5: "IE_ERR_BREAKDOWN", -6: "IE_ERR_MAXIT", -7: "IE_ERR_STAGNATION", -8: "IE_ERR_TIMEOUT"}
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libiedd.so")
+
+# Every C-ABI symbol declared in include/iedd.h.
+EXPORTS = ("ie_last_error", "ie_version", "ie_discretize", "ie_problem_info", "ie_destroy", "ie_matvec",
+           "dd_partition", "dd_partition_info", "dd_partition_export", "dd_partition_destroy", "dd_factor",
+           "dd_factor_destroy", "dd_apply", "pcg_default_opts", "pcg_solve")
+
+
+class IEError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class PcgOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_it", ctypes.c_int), ("precision", ctypes.c_int),
+                ("replace_every", ctypes.c_int), ("use_x0", ctypes.c_int), ("timeout_s", ctypes.c_double),
+                ("check_every", ctypes.c_int), ("verify", ctypes.c_int)]
+
+
+class PcgReport(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("replacements", ctypes.c_int), ("status", ctypes.c_int),
+                ("pad_", ctypes.c_int), ("recursive_relres", ctypes.c_double), ("true_relres", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"iterations": self.iterations, "replacements": self.replacements, "status": self.status,
+                "recursive_relres": self.recursive_relres, "true_relres": self.true_relres}
+
+
+_LIB = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libiedd.so; raises ImportError if it was not built (build with __graft_entry__.build())."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libiedd.so not found at {path}: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, i, ll, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "ie_last_error": (ctypes.c_char_p, []),
+        "ie_version": (ctypes.c_char_p, []),
+        "ie_discretize": (i, [i, i, d, i, i, P(vp)]),
+        "ie_problem_info": (i, [vp, P(i), P(i), P(ll), P(d), P(d)]),
+        "ie_destroy": (None, [vp]),
+        "ie_matvec": (i, [vp, vp, vp, i, ll, i, vp]),
+        "dd_partition": (i, [vp, i, i, i, P(vp)]),
+        "dd_partition_info": (i, [vp, P(i), P(ll), P(i)]),
+        "dd_partition_export": (i, [vp, vp, vp]),
+        "dd_partition_destroy": (None, [vp]),
+        "dd_factor": (i, [vp, vp, i, P(vp), P(i), vp]),
+        "dd_factor_destroy": (None, [vp]),
+        "dd_apply": (i, [vp, vp, vp, i, ll, vp]),
+        "pcg_default_opts": (None, [P(PcgOpts)]),
+        "pcg_solve": (i, [vp, vp, vp, vp, i, ll, P(PcgOpts), P(PcgReport), vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(st: int):
+    if st != IE_OK:
+        raise IEError(st, load_library().ie_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return ctypes.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _vec(x, N: int, writable: bool = False):
+    """(pointer, nrhs, ld, keepalive) of an FP64 vector / batch."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64:
+            raise TypeError("vectors must be float64")
+        if writable and not x.flags.writeable:
+            raise ValueError("output array is read-only")
+        if x.ndim == 1:
+            if x.shape[0] != N or x.strides[0] != 8:
+                raise ValueError("expected a contiguous vector of length N")
+            return ctypes.c_void_p(x.ctypes.data), 1, N, x
+        if x.ndim == 2 and x.shape[1] == N and x.strides[1] == 8 and x.strides[0] % 8 == 0:
+            return ctypes.c_void_p(x.ctypes.data), x.shape[0], x.strides[0] // 8, x
+        raise ValueError("expected shape (N,) or (nrhs, N) with unit stride along N")
+    import torch
+    if not isinstance(x, torch.Tensor):
+        raise TypeError("vectors must be torch tensors or numpy arrays")
+    if x.dtype != torch.float64:
+        raise TypeError("vectors must be float64")
+    if x.dim() == 1:
+        if x.shape[0] != N or x.stride(0) != 1:
+            raise ValueError("expected a contiguous vector of length N")
+        return ctypes.c_void_p(x.data_ptr()), 1, N, x
+    if x.dim() == 2 and x.shape[1] == N and x.stride(1) == 1:
+        return ctypes.c_void_p(x.data_ptr()), x.shape[0], x.stride(0), x
+    raise ValueError("expected shape (N,) or (nrhs, N) with unit stride along N")
+
+
+class _Handle:
+    _destroy = None
+
+    def __init__(self, ptr):
+        self._ptr = ptr
+
+    @property
+    def ptr(self):
+        if self._ptr is None:
+            raise ValueError("handle already destroyed")
+        return self._ptr
+
+    def close(self):
+        if getattr(self, "_ptr", None) is not None and _LIB is not None:
+            getattr(_LIB, self._destroy)(self._ptr)
+        self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Problem(_Handle):
+    _destroy = "ie_destroy"
+
+    def __init__(self, ptr):
+        super().__init__(ptr)
+        dim, n, N, h, diag = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+        _check(load_library().ie_problem_info(ptr, ctypes.byref(dim), ctypes.byref(n), ctypes.byref(N),
+                                              ctypes.byref(h), ctypes.byref(diag)))
+        self.dim, self.n, self.N, self.h, self.diag = dim.value, n.value, N.value, h.value, diag.value
+
+
+class Partition(_Handle):
+    _destroy = "dd_partition_destroy"
+
+    def __init__(self, ptr, problem):
+        super().__init__(ptr)
+        self.problem = problem  # keep the problem alive
+        nb, tot, mx = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_int()
+        _check(load_library().dd_partition_info(ptr, ctypes.byref(nb), ctypes.byref(tot), ctypes.byref(mx)))
+        self.nblocks, self.total, self.max_block = nb.value, tot.value, mx.value
+
+    def export(self):
+        """List of index arrays (ascending global indices), one per subdomain."""
+        offs = np.zeros(self.nblocks + 1, dtype=np.int64)
+        idx = np.zeros(max(self.total, 1), dtype=np.int32)
+        _check(load_library().dd_partition_export(self.ptr, offs.ctypes.data, idx.ctypes.data))
+        return [idx[offs[i]:offs[i + 1]].astype(np.int64) for i in range(self.nblocks)]
+
+
+class Factor(_Handle):
+    _destroy = "dd_factor_destroy"
+
+    def __init__(self, ptr, problem, partition, precision):
+        super().__init__(ptr)
+        self.problem, self.partition, self.precision = problem, partition, precision
+
+    def close(self):  # the factor must go before its problem and partition
+        super().close()
+
+
+def ie_version() -> str:
+    return load_library().ie_version().decode()
+
+
+def ie_discretize(dim: int, n: int, a_shift: float = 0.0, grid: int = IE_GRID_TEXT, device: int = 0) -> Problem:
+    out = ctypes.c_void_p()
+    _check(load_library().ie_discretize(dim, n, a_shift, grid, device, ctypes.byref(out)))
+    return Problem(out)
+
+
+def ie_matvec(prob: Problem, x, y, precision: int = IE_MIXED, stream=None):
+    px, k, ld, _kx = _vec(x, prob.N)
+    py, k2, ld2, _ky = _vec(y, prob.N, writable=True)
+    if k != k2 or ld != ld2:
+        raise ValueError("x and y must have the same shape and stride")
+    _check(load_library().ie_matvec(prob.ptr, px, py, k, ld, precision, _stream(stream)))
+    return y
+
+
+def dd_partition(prob: Problem, m: int, delta: int, kind: int = DD_SCHWARZ) -> Partition:
+    out = ctypes.c_void_p()
+    _check(load_library().dd_partition(prob.ptr, m, delta, kind, ctypes.byref(out)))
+    return Partition(out, prob)
+
+
+def dd_factor(prob: Problem, part: Partition, precision: int = IE_MIXED, stream=None) -> Factor:
+    out = ctypes.c_void_p()
+    info = ctypes.c_int(-1)
+    st = load_library().dd_factor(prob.ptr, part.ptr, precision, ctypes.byref(out), ctypes.byref(info),
+                                  _stream(stream))
+    fac = Factor(out, prob, part, precision) if out.value else None
+    if st != IE_OK:
+        err = IEError(st, load_library().ie_last_error().decode())
+        err.info = info.value
+        if fac is not None:
+            fac.close()
+        raise err
+    return fac
+
+
+def dd_apply(fac: Factor, r, z, stream=None):
+    pr, k, ld, _kr = _vec(r, fac.problem.N)
+    pz, k2, ld2, _kz = _vec(z, fac.problem.N, writable=True)
+    if k != k2 or ld != ld2:
+        raise ValueError("r and z must have the same shape and stride")
+    _check(load_library().dd_apply(fac.ptr, pr, pz, k, ld, _stream(stream)))
+    return z
+
+
+def pcg_default_opts() -> PcgOpts:
+    o = PcgOpts()
+    load_library().pcg_default_opts(ctypes.byref(o))
+    return o
+
+
+def pcg_solve(prob: Problem, fac: Factor, f, u, opts: PcgOpts | None = None, stream=None, check=True, **kw):
+    """Solve A u = f; returns the list of per-column reports.  ``kw`` overrides option fields."""
+    o = opts if opts is not None else pcg_default_opts()
+    for key, val in kw.items():
+        setattr(o, key, val)
+    pf, k, ld, _kf = _vec(f, prob.N)
+    pu, k2, ld2, _ku = _vec(u, prob.N, writable=True)
+    if k != k2 or ld != ld2:
+        raise ValueError("f and u must have the same shape and stride")
+    reps = (PcgReport * k)()
+    st = load_library().pcg_solve(prob.ptr, fac.ptr, pf, pu, k, ld, ctypes.byref(o), reps, _stream(stream))
+    out = [r.as_dict() for r in reps]
+    if check and st != IE_OK:
+        err = IEError(st, load_library().ie_last_error().decode())
+        err.reports = out
+        raise err
+    return out

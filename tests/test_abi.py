@@ -1,0 +1,104 @@
+"""The C-ABI library builds, loads and exports every symbol include/iedd.h declares (no GPU).
+
+Also checks the boundary's host-side argument validation, which returns before any device
+work, and that the product path refuses to run without its CUDA library.
+"""
+import ctypes
+import os
+import re
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "iedd.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2108_12574_gb300 import iedd
+    return iedd.load_library()
+
+
+def _declared():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^IEDD_API\s+[\w\s\*]*?\b(\w+)\s*\(", text, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("ie_discretize", "ie_matvec", "dd_partition", "dd_factor", "dd_apply", "pcg_solve"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib._name], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (\w+)$", out, re.M))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+    for n in _declared():
+        assert hasattr(lib, n)
+
+
+def test_binding_covers_header():
+    from paper_2108_12574_gb300 import iedd
+    assert sorted(iedd.EXPORTS) == _declared()
+
+
+def test_version_and_no_error(lib):
+    assert b"sm_103a" in lib.ie_version()
+    assert lib.ie_last_error() == b""
+
+
+def test_library_is_built_for_sm_103a(lib):
+    out = subprocess.run(["cuobjdump", "--list-elf", lib._name], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def test_null_arguments_rejected_without_gpu(lib):
+    from paper_2108_12574_gb300 import iedd
+    # argument checks run before any CUDA call
+    assert lib.ie_discretize(4, 8, 0.0, 0, 0, None) == iedd.IE_ERR_ARG
+    assert lib.ie_matvec(None, None, None, 1, 1, 1, None) == iedd.IE_ERR_ARG
+    assert b"NULL" in lib.ie_last_error()
+    assert lib.dd_partition(None, 2, 1, 1, None) == iedd.IE_ERR_ARG
+    assert lib.dd_apply(None, None, None, 1, 1, None) == iedd.IE_ERR_ARG
+    assert lib.pcg_solve(None, None, None, None, 1, 1, None, None, None) == iedd.IE_ERR_ARG
+    lib.ie_destroy(None)
+    lib.dd_partition_destroy(None)
+    lib.dd_factor_destroy(None)
+
+
+def test_default_opts(lib):
+    from paper_2108_12574_gb300 import iedd
+    o = iedd.pcg_default_opts()
+    assert o.tol == 1e-8 and o.max_it == 1000 and o.precision == iedd.IE_MIXED
+    assert o.replace_every == 50 and o.check_every == 8 and o.verify == 1
+    assert ctypes.sizeof(iedd.PcgReport) == 32
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2108_12574_gb300 import iedd\n"
+            "iedd._LIB = None\n"
+            "try:\n"
+            "    iedd.load_library(%r)\n"
+            "except ImportError as e:\n"
+            "    print('IMPORTERROR', e)\n") % (ROOT, str(tmp_path / "nope.so"))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+    assert "IMPORTERROR" in r.stdout
+
+
+def test_product_path_never_imports_oracle():
+    pkg = os.path.join(ROOT, "paper_2108_12574_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "ie_oracle" not in text and "direct_sum" not in text, f

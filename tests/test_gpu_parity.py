@@ -1,0 +1,374 @@
+"""GPU path vs the FP64 CPU oracle, through the C ABI (needs a GB300).
+
+Tolerances (derived in the design notes):
+  * FP64 matvec, accurate (double-float) matvec: |y - y_ref|_inf <= 1e-12 * ||A||_inf ||x||_inf
+  * FP32 (IE_MIXED) matvec: <= 4e-6 * ||A||_inf ||x||_inf (FP32 entries and sums)
+  * FP64 apply: relative 2-norm error <= 1e-11; FP32 apply: <= 2e-3 (cond(A_i) * eps_fp32)
+  * partitions: bit-exact index sets
+  * PCG FP64: iterations within +-1 of the oracle; solution within 1e-10 (relative L2) of the
+    oracle run for the same number of iterations
+  * PCG mixed: true relative residual <= tol checked by the oracle, solution within 1e-6 of
+    the oracle's solution at the same tolerance, iterations within +-2
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import ie_oracle as O  # noqa: E402
+from paper_2108_12574_gb300 import iedd  # noqa: E402
+from paper_2108_12574_gb300 import inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+    torch.cuda.init()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def _scale(dim, n, x, conv):
+    # ||A||_inf ||x||_inf, with ||A||_inf from the oracle's row sums of |A| (A >= 0 except for
+    # far 2D pairs, so |A| 1 is bounded by A 1 + 2 * (negative part); a factor 2 covers it)
+    rows = O.matvec_direct(dim, n, np.ones(n ** dim), rows=np.array([0, (n ** dim) // 2]), convention=conv)
+    return 2.0 * float(np.max(np.abs(rows))) * float(np.max(np.abs(x)))
+
+
+MATVEC_CASES = [(2, 64, O.GRID_TEXT), (2, 37, O.GRID_TEXT), (2, 16, O.GRID_TABLE), (2, 150, O.GRID_TEXT),
+                (3, 16, O.GRID_TEXT), (3, 11, O.GRID_TEXT), (3, 9, O.GRID_TABLE)]
+
+
+@pytest.mark.parametrize("dim,n,conv", MATVEC_CASES)
+@pytest.mark.parametrize("prec,tol", [(iedd.IE_FP64, 1e-12), (iedd.IE_ACCURATE, 1e-12), (iedd.IE_MIXED, 4e-6)])
+def test_matvec_parity(dim, n, conv, prec, tol):
+    N = n ** dim
+    x = I.uniform_rhs(N, 1)
+    prob = iedd.ie_discretize(dim, n, grid=conv)
+    y = torch.zeros(N, dtype=torch.float64, device="cuda")
+    iedd.ie_matvec(prob, dev(x), y, prec)
+    ref = O.matvec_direct(dim, n, x, convention=conv)
+    err = np.max(np.abs(host(y) - ref))
+    assert err <= tol * _scale(dim, n, x, conv), err
+
+
+def test_matvec_multi_rhs_and_shift():
+    dim, n = 2, 40
+    N = n * n
+    X = I.uniform_rhs_batch(N, [3, 4, 5]).T.copy()  # (nrhs, N)
+    prob = iedd.ie_discretize(dim, n, a_shift=0.3)
+    for prec, tol in ((iedd.IE_FP64, 1e-12), (iedd.IE_ACCURATE, 1e-12), (iedd.IE_MIXED, 4e-6)):
+        Y = torch.zeros((3, N), dtype=torch.float64, device="cuda")
+        iedd.ie_matvec(prob, dev(X), Y, prec)
+        ref = O.matvec_direct(dim, n, X.T, a_shift=0.3).T
+        assert np.max(np.abs(host(Y) - ref)) <= tol * _scale(dim, n, X, O.GRID_TEXT) + 1e-15 * 0.3
+
+
+def test_matvec_host_pointers_match_device():
+    n = 48
+    x = I.uniform_rhs(n * n, 9)
+    prob = iedd.ie_discretize(2, n)
+    y_h = np.zeros(n * n)
+    iedd.ie_matvec(prob, x, y_h, iedd.IE_MIXED)
+    y_d = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    iedd.ie_matvec(prob, dev(x), y_d, iedd.IE_MIXED)
+    torch.cuda.synchronize()
+    assert np.array_equal(y_h, host(y_d))
+
+
+@pytest.mark.parametrize("n,rows_seed", [(512, 0), (1024, 1)])
+def test_matvec_full_size_sampled_rows(n, rows_seed):
+    # the workloads' full sizes: sampled rows against the oracle's direct sum
+    N = n * n
+    x = I.grf(2, n, 0.1, 2)
+    rng = np.random.default_rng(rows_seed)
+    rows = np.unique(np.concatenate([[0, N - 1, N // 2 + n // 2], rng.integers(0, N, 29)]))
+    ref = O.matvec_direct(2, n, x, rows=rows)
+    prob = iedd.ie_discretize(2, n)
+    scale = _scale(2, n, x, O.GRID_TEXT)
+    for prec, tol in ((iedd.IE_MIXED, 4e-6), (iedd.IE_ACCURATE, 1e-12)):
+        y = torch.zeros(N, dtype=torch.float64, device="cuda")
+        iedd.ie_matvec(prob, dev(x), y, prec)
+        err = np.max(np.abs(host(y)[rows] - ref))
+        assert err <= tol * scale, (prec, err)
+
+
+def test_accurate_matvec_3d_full_size_sampled_rows():
+    n = 32
+    N = n ** 3
+    X = I.uniform_rhs_batch(N, [0, 1]).T.copy()
+    rows = np.array([0, 1, 33, N // 2, N - 1, 12345])
+    prob = iedd.ie_discretize(3, n)
+    for prec, tol in ((iedd.IE_MIXED, 4e-6), (iedd.IE_ACCURATE, 1e-12), (iedd.IE_FP64, 1e-12)):
+        Y = torch.zeros((2, N), dtype=torch.float64, device="cuda")
+        iedd.ie_matvec(prob, dev(X), Y, prec)
+        ref = O.matvec_direct(3, n, X.T, rows=rows)
+        assert np.max(np.abs(host(Y)[:, rows].T - ref)) <= tol * _scale(3, n, X, O.GRID_TEXT)
+
+
+PART_CASES = [(2, 64, 4, 1, O.SCHWARZ), (2, 512, 32, 2, O.SCHWARZ), (3, 32, 4, 1, O.SCHWARZ),
+              (2, 12, 3, 1, O.CBD), (3, 8, 4, 1, O.CBD), (2, 30, 5, 2, O.JACOBI), (2, 20, 4, 3, O.SCHWARZ),
+              (2, 24, 3, 5, O.CBD)]
+
+
+@pytest.mark.parametrize("dim,n,m,delta,kind", PART_CASES)
+def test_partition_bit_exact(dim, n, m, delta, kind):
+    prob = iedd.ie_discretize(dim, n)
+    part = iedd.dd_partition(prob, m, delta, kind)
+    got = part.export()
+    ref = O.partition(dim, n, m, delta, kind)
+    assert len(got) == len(ref)
+    for g, r in zip(got, ref):
+        assert np.array_equal(g, r)
+
+
+def test_partition_rejects_bad_sizes():
+    prob = iedd.ie_discretize(2, 30)
+    with pytest.raises(iedd.IEError) as e:
+        iedd.dd_partition(prob, 7, 1, iedd.DD_SCHWARZ)
+    assert e.value.status == iedd.IE_ERR_ARG
+
+
+APPLY_CASES = [(2, 64, 4, 1, O.SCHWARZ), (2, 40, 5, 2, O.SCHWARZ), (3, 16, 2, 1, O.SCHWARZ),
+               (2, 32, 8, 1, O.CBD), (2, 30, 3, 0, O.JACOBI), (3, 12, 3, 1, O.CBD)]
+
+
+@pytest.mark.parametrize("dim,n,m,delta,kind", APPLY_CASES)
+def test_apply_parity(dim, n, m, delta, kind):
+    N = n ** dim
+    blocks = O.partition(dim, n, m, delta, kind)
+    F = O.factor(dim, n, blocks)
+    R = I.uniform_rhs_batch(N, [7, 8]).T.copy()
+    ref = O.apply(F, blocks, R.T).T
+    prob = iedd.ie_discretize(dim, n)
+    part = iedd.dd_partition(prob, m, delta, kind)
+    for prec, tol in ((iedd.IE_FP64, 1e-11), (iedd.IE_MIXED, 2e-3)):
+        fac = iedd.dd_factor(prob, part, prec)
+        Z = torch.zeros((2, N), dtype=torch.float64, device="cuda")
+        iedd.dd_apply(fac, dev(R), Z)
+        err = np.linalg.norm(host(Z) - ref) / np.linalg.norm(ref)
+        assert err <= tol, (prec, err)
+        fac.close()
+
+
+def test_apply_is_deterministic():
+    n = 64
+    prob = iedd.ie_discretize(2, n)
+    part = iedd.dd_partition(prob, 4, 1, iedd.DD_SCHWARZ)
+    fac = iedd.dd_factor(prob, part, iedd.IE_FP64)
+    r = dev(I.uniform_rhs(n * n, 3))
+    z1 = torch.zeros_like(r)
+    z2 = torch.zeros_like(r)
+    iedd.dd_apply(fac, r, z1)
+    iedd.dd_apply(fac, r, z2)
+    assert torch.equal(z1, z2)
+
+
+def test_factor_reports_non_spd_block():
+    prob = iedd.ie_discretize(2, 32, a_shift=-1.0)
+    part = iedd.dd_partition(prob, 4, 1, iedd.DD_SCHWARZ)
+    with pytest.raises(iedd.IEError) as e:
+        iedd.dd_factor(prob, part, iedd.IE_FP64)
+    assert e.value.status == iedd.IE_ERR_NOT_SPD
+    assert e.value.info == 0
+
+
+def _oracle_problem(dim, n, m, delta, kind=O.SCHWARZ, matvec="dense"):
+    return O.Problem(dim, n, m, delta, kind, matvec=matvec)
+
+
+@pytest.mark.parametrize("dim,n,m,delta", [(2, 64, 4, 1), (3, 16, 2, 1), (2, 45, 5, 2)])
+def test_pcg_fp64_parity(dim, n, m, delta):
+    N = n ** dim
+    f = I.uniform_rhs(N, 0)
+    prob = iedd.ie_discretize(dim, n)
+    part = iedd.dd_partition(prob, m, delta, iedd.DD_SCHWARZ)
+    fac = iedd.dd_factor(prob, part, iedd.IE_FP64)
+    u = torch.zeros(N, dtype=torch.float64, device="cuda")
+    rep = iedd.pcg_solve(prob, fac, dev(f), u, tol=1e-8, precision=iedd.IE_FP64)[0]
+    P = _oracle_problem(dim, n, m, delta, matvec="dense" if N <= 4096 else "fft")
+    _, it_ref, _ = P.solve(f, 1e-8)
+    assert abs(rep["iterations"] - it_ref) <= 1, (rep, it_ref)
+    u_same, _, _ = P.solve(f, 0.0, max_it=rep["iterations"])
+    err = np.linalg.norm(host(u) - u_same) / np.linalg.norm(u_same)
+    assert err <= 1e-10, err
+    assert rep["true_relres"] <= 1e-8 * 1.05
+
+
+@pytest.mark.parametrize("dim,n,m,delta", [(2, 64, 4, 1), (3, 16, 2, 1), (2, 96, 6, 2)])
+def test_pcg_mixed_parity(dim, n, m, delta):
+    N = n ** dim
+    f = I.uniform_rhs(N, 0) if dim == 3 else I.grf(2, n, 0.1, 0)
+    prob = iedd.ie_discretize(dim, n)
+    part = iedd.dd_partition(prob, m, delta, iedd.DD_SCHWARZ)
+    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
+    u = torch.zeros(N, dtype=torch.float64, device="cuda")
+    rep = iedd.pcg_solve(prob, fac, dev(f), u, tol=1e-8, precision=iedd.IE_MIXED, replace_every=50)[0]
+    assert rep["status"] == 0 and rep["true_relres"] <= 1e-8
+    P = _oracle_problem(dim, n, m, delta, matvec="fft")
+    true_rel = O.true_relative_residual(dim, n, f, host(u))
+    assert true_rel <= 1e-8 * 1.01, true_rel
+    u_ref, it_ref, _ = P.solve(f, 1e-8)
+    assert abs(rep["iterations"] - it_ref) <= 2, (rep, it_ref)
+    assert np.linalg.norm(host(u) - u_ref) / np.linalg.norm(u_ref) <= 1e-6
+
+
+def test_pcg_multi_rhs_columns_match_single_solves():
+    n = 32
+    N = n * n
+    F = I.uniform_rhs_batch(N, [0, 1, 2]).T.copy()
+    F[2] *= 1e-3
+    prob = iedd.ie_discretize(2, n)
+    part = iedd.dd_partition(prob, 4, 1, iedd.DD_SCHWARZ)
+    for prec in (iedd.IE_FP64, iedd.IE_MIXED):
+        fac = iedd.dd_factor(prob, part, prec)
+        U = torch.zeros((3, N), dtype=torch.float64, device="cuda")
+        reps = iedd.pcg_solve(prob, fac, dev(F), U, tol=1e-8, precision=prec)
+        for k in range(3):
+            u = torch.zeros(N, dtype=torch.float64, device="cuda")
+            rep = iedd.pcg_solve(prob, fac, dev(F[k]), u, tol=1e-8, precision=prec)[0]
+            assert rep["iterations"] == reps[k]["iterations"]
+            assert torch.allclose(u, U[k], rtol=0, atol=1e-12 * float(u.abs().max()))
+            assert reps[k]["true_relres"] <= 1e-8 * 1.05
+
+
+def test_pcg_host_buffers_match_device_buffers():
+    n = 40
+    f = I.uniform_rhs(n * n, 4)
+    prob = iedd.ie_discretize(2, n)
+    part = iedd.dd_partition(prob, 4, 2, iedd.DD_SCHWARZ)
+    fac = iedd.dd_factor(prob, part, iedd.IE_FP64)
+    u_h = np.zeros(n * n)
+    iedd.pcg_solve(prob, fac, f, u_h, precision=iedd.IE_FP64)
+    u_d = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    iedd.pcg_solve(prob, fac, dev(f), u_d, precision=iedd.IE_FP64)
+    assert np.array_equal(u_h, host(u_d))
+
+
+def test_pcg_warm_start_x0():
+    n = 32
+    f = I.uniform_rhs(n * n, 5)
+    prob = iedd.ie_discretize(2, n)
+    part = iedd.dd_partition(prob, 4, 1, iedd.DD_SCHWARZ)
+    fac = iedd.dd_factor(prob, part, iedd.IE_FP64)
+    u = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    r0 = iedd.pcg_solve(prob, fac, dev(f), u, tol=1e-10, precision=iedd.IE_FP64)[0]
+    u2 = u.clone()
+    r1 = iedd.pcg_solve(prob, fac, dev(f), u2, tol=1e-8, precision=iedd.IE_FP64, use_x0=1)[0]
+    assert r1["iterations"] == 0 and r1["status"] == 0
+    assert torch.equal(u, u2)
+    # a perturbed warm start converges in fewer iterations than zero start
+    u3 = u + 1e-6 * dev(I.uniform_rhs(n * n, 6))
+    r2 = iedd.pcg_solve(prob, fac, dev(f), u3, tol=1e-8, precision=iedd.IE_FP64, use_x0=1)[0]
+    assert 0 < r2["iterations"] < r0["iterations"]
+
+
+def test_pcg_nan_rhs_reports_breakdown():
+    n = 16
+    f = I.uniform_rhs(n * n, 0)
+    f[7] = np.nan
+    prob = iedd.ie_discretize(2, n)
+    part = iedd.dd_partition(prob, 2, 1, iedd.DD_SCHWARZ)
+    fac = iedd.dd_factor(prob, part, iedd.IE_FP64)
+    u = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    with pytest.raises(iedd.IEError) as e:
+        iedd.pcg_solve(prob, fac, dev(f), u, precision=iedd.IE_FP64)
+    assert e.value.status == iedd.IE_ERR_BREAKDOWN
+
+
+def test_pcg_timeout_is_reported_without_hanging():
+    n = 64
+    f = I.uniform_rhs(n * n, 0)
+    prob = iedd.ie_discretize(2, n)
+    part = iedd.dd_partition(prob, 4, 1, iedd.DD_SCHWARZ)
+    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
+    u = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    with pytest.raises(iedd.IEError) as e:
+        iedd.pcg_solve(prob, fac, dev(f), u, timeout_s=1e-9)
+    assert e.value.status == iedd.IE_ERR_TIMEOUT
+
+
+def test_pcg_max_it_reported():
+    n = 32
+    f = I.uniform_rhs(n * n, 0)
+    prob = iedd.ie_discretize(2, n)
+    part = iedd.dd_partition(prob, 4, 1, iedd.DD_SCHWARZ)
+    fac = iedd.dd_factor(prob, part, iedd.IE_FP64)
+    u = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    reps = iedd.pcg_solve(prob, fac, dev(f), u, max_it=3, precision=iedd.IE_FP64, check=False)
+    assert reps[0]["status"] == iedd.IE_ERR_MAXIT and reps[0]["iterations"] == 3
+
+
+def test_pcg_zero_rhs():
+    n = 16
+    prob = iedd.ie_discretize(2, n)
+    part = iedd.dd_partition(prob, 2, 1, iedd.DD_SCHWARZ)
+    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
+    u = torch.ones(n * n, dtype=torch.float64, device="cuda")
+    rep = iedd.pcg_solve(prob, fac, torch.zeros_like(u), u)[0]
+    assert rep["iterations"] == 0 and rep["status"] == 0 and float(u.abs().max()) == 0.0
+
+
+def test_pcg_cbd_and_jacobi_iteration_counts():
+    # t:it_m48 style (2D, table grid): Jacobi / Schwarz (D = 4) / CBD (M = N/16), tol 1e-12
+    n = 32
+    f = I.gaussian_noise(n * n, 0)
+    prob = iedd.ie_discretize(2, n, grid=iedd.IE_GRID_TABLE)
+    for kind, m, delta in ((iedd.DD_JACOBI, 2, 0), (iedd.DD_SCHWARZ, 2, 1), (iedd.DD_CBD, 8, 1)):
+        part = iedd.dd_partition(prob, m, delta, kind)
+        fac = iedd.dd_factor(prob, part, iedd.IE_FP64)
+        u = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+        rep = iedd.pcg_solve(prob, fac, dev(f), u, tol=1e-12, precision=iedd.IE_FP64)[0]
+        P = O.Problem(2, n, m, delta, kind, O.GRID_TABLE, matvec="dense")
+        _, it_ref, _ = P.solve(f, 1e-12)
+        assert abs(rep["iterations"] - it_ref) <= 1, (kind, rep, it_ref)
+
+
+def test_pcg_full_size_512_mixed():
+    # 512^2, GRF l = 0.1, Schwarz 32 x 32 partitions, 2-cell overlap, FP32 matvec and factors,
+    # FP64 residual replacement every 50 iterations, tol 1e-8 on the true residual
+    n, m, delta = 512, 32, 2
+    N = n * n
+    f = I.grf(2, n, 0.1, 0)
+    prob = iedd.ie_discretize(2, n)
+    part = iedd.dd_partition(prob, m, delta, iedd.DD_SCHWARZ)
+    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
+    u = torch.zeros(N, dtype=torch.float64, device="cuda")
+    rep = iedd.pcg_solve(prob, fac, dev(f), u, tol=1e-8, precision=iedd.IE_MIXED, replace_every=50)[0]
+    assert rep["status"] == 0
+    assert O.true_relative_residual(2, n, f, host(u)) <= 1e-8 * 1.01
+    P = O.Problem(2, n, m, delta, O.SCHWARZ, matvec="fft")
+    u_ref, it_ref, _ = P.solve(f, 1e-8)
+    assert abs(rep["iterations"] - it_ref) <= 2, (rep, it_ref)
+    assert np.linalg.norm(host(u) - u_ref) / np.linalg.norm(u_ref) <= 1e-6
+
+
+def test_pcg_full_size_3d_batched_mixed():
+    # 32^3, Schwarz 4 x 4 x 4 partitions (blocks of 729-1000 points), 1-cell overlap, 8 of the
+    # 64 uniform right-hand sides (seeds 0..7), FP32 factors, FP64 scalars
+    n, m, delta = 32, 4, 1
+    N = n ** 3
+    F = I.uniform_rhs_batch(N, range(8)).T.copy()
+    prob = iedd.ie_discretize(3, n)
+    part = iedd.dd_partition(prob, m, delta, iedd.DD_SCHWARZ)
+    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
+    U = torch.zeros((8, N), dtype=torch.float64, device="cuda")
+    reps = iedd.pcg_solve(prob, fac, dev(F), U, tol=1e-8)
+    Uh = host(U)
+    rel = O.true_relative_residual(3, n, F.T, Uh.T)
+    assert np.all(rel <= 1e-8 * 1.01), rel
+    P = O.Problem(3, n, m, delta, O.SCHWARZ, matvec="fft")
+    U_ref, its, _ = P.solve(F[:2].T, 1e-8)
+    for k in range(2):
+        assert abs(reps[k]["iterations"] - its[k]) <= 2
+        assert np.linalg.norm(Uh[k] - U_ref[:, k]) / np.linalg.norm(U_ref[:, k]) <= 1e-6
