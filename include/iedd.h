@@ -171,6 +171,9 @@ typedef struct {
     double timeout_s;    /* wall-clock budget (0: none); exceeded -> IE_ERR_TIMEOUT                */
     int check_every;     /* IE_FP64: iterations per CUDA-graph launch between host checks (>= 1)  */
     int verify;          /* IE_FP64: 1 = compute the true residual at the end (one more matvec)    */
+    int inner;           /* IE_MIXED: matvec inside the iteration: IE_MIXED (FP32 SFU entries,
+                            compensated FP32 sums), IE_ACCURATE (double-float table sums on the
+                            FP32 pipes), or 0 = choose (IE_ACCURATE in 2D, IE_MIXED in 3D)       */
 } pcg_opts;
 
 typedef struct {
@@ -180,7 +183,19 @@ typedef struct {
     int pad_;
     double recursive_relres; /* ||r_k||_2 / ||f||_2 of the recurrence                             */
     double true_relres;      /* ||f - A u||_2 / ||f||_2 with the accurate matvec (-1 if not run)  */
+    /* per-solve device timing (CUDA events around each launch; the same in every column)     */
+    int matvecs;             /* inner matvecs q = A p (one launch covers all columns)           */
+    int applies;             /* preconditioner applications z = T^{-1} r                        */
+    double matvec_ms;        /* summed device time of the inner matvecs                         */
+    double apply_ms;         /* summed device time of the applications                          */
+    int accurate_matvecs;    /* accurate f - A u evaluations (replacement, verification)        */
+    int pad2_;
+    double accurate_ms;      /* summed device time of those                                     */
 } pcg_report;
+
+/* Instrumentation: number of kernels this library has launched in this process (a CUDA-graph
+ * replay counts the kernel nodes of the graph); reset != 0 returns the count and zeroes it. */
+IEDD_API long long ie_kernel_launches(int reset);
 
 /* Fills *o with the defaults: tol 1e-8, max_it 1000, IE_MIXED, replace_every 50, use_x0 0,
  * timeout_s 0, check_every 8, verify 1. */

@@ -12,7 +12,19 @@
 
 #include "iedd_internal.cuh"
 
+#include <atomic>
+
 static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+static thread_local bool g_capturing = false;
+
+void ie_count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+bool ie_capturing() { return g_capturing; }
+void ie_set_capturing(bool on) { g_capturing = on; }
+
+extern "C" long long ie_kernel_launches(int reset) {
+    return reset ? g_launches.exchange(0) : g_launches.load();
+}
 
 void ie_set_error(const std::string &msg) { g_last_error = msg; }
 

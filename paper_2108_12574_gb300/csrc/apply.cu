@@ -126,15 +126,16 @@ int launch_apply(const dd_factor_t *f, const double *r, long long ldr, double *z
             size_t sm = sizeof(double) * f->max_pad;
             apply_blocks<double><<<g, 256, sm, s>>>((const double *)f->d_pool, f->d_loff, f->d_npad, f->d_n, part->d_offs,
                                                    part->d_idx, f->d_order, r, ldr, zbuf.as<double>(), part->total);
+            IE_LAUNCHED();
         } else {
             size_t sm = sizeof(float) * f->max_pad;
             apply_blocks<float><<<g, 256, sm, s>>>((const float *)f->d_pool, f->d_loff, f->d_npad, f->d_n, part->d_offs,
                                                   part->d_idx, f->d_order, r, ldr, zbuf.as<double>(), part->total);
+            IE_LAUNCHED();
         }
-        IE_CHECK_LAUNCH();
     }
     dim3 g2((unsigned)((p->N + 255) / 256), nrhs);
     overlap_sum<<<g2, 256, 0, s>>>(zbuf.as<double>(), part->total, part->d_inv_ptr, part->d_inv_pos, z, ldz, p->N);
-    IE_CHECK_LAUNCH();
+    IE_LAUNCHED();
     return IE_OK;
 }

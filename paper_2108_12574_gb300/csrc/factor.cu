@@ -154,17 +154,18 @@ int launch_factor(dd_factor_t *f, cudaStream_t s) {
         gather_blocks<double><<<g, 256, 0, s>>>((double *)f->d_pool, f->d_loff, f->d_npad, f->d_n, part->d_offs,
                                                 part->d_idx, p->d_coord, p->dim, p->diag, p->c_const, p->c_ln,
                                                 p->c_log2, p->c_r);
-        IE_CHECK_LAUNCH();
+        IE_LAUNCHED();
         chol_blocked<double><<<f->nblocks, 256, 0, s>>>((double *)f->d_pool, f->d_loff, f->d_npad, f->d_order,
                                                        f->d_info);
+        IE_LAUNCHED();
     } else {
         gather_blocks<float><<<g, 256, 0, s>>>((float *)f->d_pool, f->d_loff, f->d_npad, f->d_n, part->d_offs,
                                                part->d_idx, p->d_coord, p->dim, p->diag, p->c_const, p->c_ln,
                                                p->c_log2, p->c_r);
-        IE_CHECK_LAUNCH();
+        IE_LAUNCHED();
         chol_blocked<float><<<f->nblocks, 256, 0, s>>>((float *)f->d_pool, f->d_loff, f->d_npad, f->d_order,
                                                       f->d_info);
+        IE_LAUNCHED();
     }
-    IE_CHECK_LAUNCH();
     return IE_OK;
 }

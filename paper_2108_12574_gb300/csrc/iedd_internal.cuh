@@ -25,6 +25,18 @@ void ie_set_error(const std::string &msg);
 
 #define IE_CHECK_LAUNCH() IE_TRY_CUDA(cudaGetLastError())
 
+// Kernel-launch accounting (ie_kernel_launches): every launch site is followed by IE_LAUNCHED(),
+// which counts the launch unless the thread is capturing a graph (graph replays add the number
+// of kernel nodes of the graph instead) and checks the launch error.
+void ie_count_launches(long long k);
+bool ie_capturing();
+void ie_set_capturing(bool on);
+#define IE_LAUNCHED()                                                                          \
+    do {                                                                                       \
+        if (!ie_capturing()) ie_count_launches(1);                                             \
+        IE_CHECK_LAUNCH();                                                                     \
+    } while (0)
+
 #define IE_TRY(expr)                                                                           \
     do {                                                                                       \
         int s_ = (expr);                                                                       \

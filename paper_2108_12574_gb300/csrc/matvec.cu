@@ -7,14 +7,14 @@
 // for n <= 2048 in 2D and n <= 2364 in 3D), so the only rounding in an FP32 entry is that of
 // the SFU log2 / rsqrt, and the large constant c_const is kept out of the FP32 sums.
 //
-// K1  k1_matvec_f32      FP32, one right-hand side.  Source points are staged through shared
-//                        memory 256 at a time as float4 {D-coords, x_j}; each thread keeps R
-//                        target rows in registers; per pair: 2-3 FADD, FMUL + 1-2 FFMA for
-//                        |D|^2, FMNMX, one SFU op (MUFU.LG2 / MUFU.RSQ), one FFMA.  The i = j
-//                        pair is neutralised branch-free by clamping |D|^2 to >= 1 (log2 1 = 0;
-//                        in 3D the spurious rsqrt(1) x_i is subtracted in the combine).  Work
-//                        is split over (row tile, column split) so the grid fills the GPU;
-//                        partial sums go to a [split][N] FP32 scratch and are combined in FP64.
+// K1  k1_matvec_f32      FP32 entries, one right-hand side.  Source points are staged through
+//                        shared memory 256 at a time as float4 {D-coords, x_j}; each thread keeps
+//                        R target rows in registers; per pair (2D): 2 FADD + 2 FFMA for
+//                        |D|^2 + 2^-30, one SFU op (MUFU.LG2; MUFU.RSQ in 3D), FMUL, and a
+//                        Kahan-compensated FP32 add (4 FADD).  Work is split over (row tile,
+//                        column split) so the grid fills the GPU; each split's compensated sum
+//                        goes to a [split][N] FP64 scratch and the splits are combined in FP64
+//                        with the FP64 diagonal and constant terms.
 // Kd  kd_matvec_f64      the same in FP64 with the natural log / rsqrt of double (plain FP64).
 // K2  k2_accurate_{2d,3d} FP64-class y = A x from the per-|offset| entry table (translation
 //                        invariance of A on the uniform grid): entry hi/lo FP32 pairs, products
@@ -65,18 +65,27 @@ __global__ void table_kernel(float2 *t32, double *t64, int dim, int n, long long
 // ---------------------------------------------------------------------------------------------
 // K1: FP32 SFU matvec, one right-hand side
 // ---------------------------------------------------------------------------------------------
+// 2D: the i = j pair is made harmless without a branch or a clamp: |D|^2 + 2^-30 equals |D|^2
+// exactly for every |D|^2 >= 1, and is 2^-30 for i = j, whose term log2(2^-30) x_i the combine
+// removes again (with the same SFU value).  3D clamps |D|^2 to >= 1 and removes rsqrt(1) x_i.
+// The sums are compensated (Kahan): a plain FP32 running sum over thousands of terms of nearly
+// equal magnitude loses the small result that the oscillatory search directions of PCG produce
+// (their A p is ~1/cond(A) of ||A|| ||p||), which costs many iterations; the compensation keeps
+// the sum at FP32-entry accuracy.  Intrinsics keep the compiler from re-associating it.
+constexpr float kTiny2D = 0x1p-30f;
+
 template <int DIM, int R>
 __global__ void __launch_bounds__(kThreads)
 k1_matvec_f32(const float4 *__restrict__ coord, const double *__restrict__ x, long long N,
-              int tiles_per_split, int ntiles, float *__restrict__ partial) {
+              int tiles_per_split, int ntiles, double *__restrict__ partial) {
     __shared__ float4 sc[kThreads];
     const long long row0 = (long long)blockIdx.x * (kThreads * R) + threadIdx.x;
-    float px[R], py[R], pz[R], acc[R];
+    float px[R], py[R], pz[R], acc[R], cmp[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         long long i = row0 + (long long)r * kThreads;
         float4 c = i < N ? coord[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        px[r] = c.x; py[r] = c.y; pz[r] = c.z; acc[r] = 0.f;
+        px[r] = c.x; py[r] = c.y; pz[r] = c.z; acc[r] = 0.f; cmp[r] = 0.f;
     }
     const int t0 = blockIdx.y * tiles_per_split;
     const int t1 = min(t0 + tiles_per_split, ntiles);
@@ -93,24 +102,26 @@ k1_matvec_f32(const float4 *__restrict__ coord, const double *__restrict__ x, lo
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 float dx = px[r] - s.x, dy = py[r] - s.y;
-                float r2;
+                float k;
                 if (DIM == 2) {
-                    r2 = fmaf(dx, dx, dy * dy);
+                    k = __log2f(fmaf(dx, dx, fmaf(dy, dy, kTiny2D)));
                 } else {
                     float dz = pz[r] - s.z;
-                    r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    k = rsqrtf(fmaxf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), 1.0f));
                 }
-                r2 = fmaxf(r2, 1.0f);
-                const float k = DIM == 2 ? __log2f(r2) : rsqrtf(r2);
-                acc[r] = fmaf(k, s.w, acc[r]);
+                const float term = __fmul_rn(k, s.w);
+                const float y = __fsub_rn(term, cmp[r]);
+                const float tt = __fadd_rn(acc[r], y);
+                cmp[r] = __fsub_rn(__fsub_rn(tt, acc[r]), y);
+                acc[r] = tt;
             }
         }
     }
-    float *out = partial + (long long)blockIdx.y * N;
+    double *out = partial + (long long)blockIdx.y * N;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         long long i = row0 + (long long)r * kThreads;
-        if (i < N) out[i] = acc[r];
+        if (i < N) out[i] = (double)acc[r] - (double)cmp[r];
     }
 }
 
@@ -126,8 +137,10 @@ __global__ void combine_kernel(const TP *__restrict__ partial, int nsplit, const
     const double xi = x[i];
     double y0;
     if (dim == 2) {
-        // mode 0 (FP32 sums of log2 |D|^2): c_sum = c_log2; mode 1 (FP64 ln): c_sum = c_ln
-        y0 = diag * xi + c_const * (xsum[0] - xi) + c_sum * s;
+        // mode 0 (FP32 sums of log2(|D|^2 + 2^-30)): c_sum = c_log2, the i = j pair added
+        // log2(2^-30) x_i; mode 1 (FP64 ln of max(|D|^2, 1)): c_sum = c_ln, the pair added 0
+        const double self = mode == 0 ? (double)__fmul_rn(__log2f(kTiny2D), (float)xi) : 0.0;
+        y0 = diag * xi + c_const * (xsum[0] - xi) + c_sum * (s - self);
     } else {
         // the clamped i = j pair added rsqrt(1) * x_i (rounded as the kernel saw it)
         const double xi_k = mode == 0 ? (double)(float)xi : xi;
@@ -203,51 +216,74 @@ __device__ __forceinline__ void df_fma(float th, float tl, float xh, float xl, f
     sl = __fadd_rn(sl, __fadd_rn(err, e));
 }
 
-// 2D: a CTA owns a 16 x 16 patch of target points; each step stages a 16 x 16 patch of source
-// points (x as hi/lo) and the 31 x 31 window of table entries their offsets can reach.
+// 2D: a CTA owns a 16 x 64 patch of target points and walks over 16 x 64 patches of source
+// points.  Per source patch it stages x (hi/lo) and the 31 x 127 window of table entries that
+// the offsets between the two patches can reach.  Thread (t1, t2) owns the rows (t1, t2 + 16 k),
+// k = 0..3.  Because the entry depends only on the offset, the entries that row k needs for
+// source column c0 + 16 m are the window values at (t2 - c0) + 16 (k - m): for each (c1, c0)
+// the thread loads 7 window values and 4 x values and does 16 pairs (Toeplitz register reuse),
+// so shared-memory traffic stays well below the 12 FP32 operations of each double-float pair.
+constexpr int kP1 = 16, kP2 = 64;
+
 __global__ void __launch_bounds__(kThreads)
 k2_accurate_2d(const float2 *__restrict__ table, const double *__restrict__ x, int n,
                int patches_per_split, double *__restrict__ partial) {
-    __shared__ float2 W[31][32];
-    __shared__ float2 X[16][16];
-    const int np = (n + 15) / 16;
-    const int I1 = (blockIdx.x / np) * 16, I2 = (blockIdx.x % np) * 16;
-    const int r1 = threadIdx.x >> 4, r2 = threadIdx.x & 15;
-    const int i1 = I1 + r1, i2 = I2 + r2;
+    __shared__ float2 W[2 * kP1 - 1][2 * kP2];
+    __shared__ float2 X[kP1][kP2];
+    const int np1 = (n + kP1 - 1) / kP1, np2 = (n + kP2 - 1) / kP2;
+    const int I1 = (blockIdx.x / np2) * kP1, I2 = (blockIdx.x % np2) * kP2;
+    const int t1 = threadIdx.x >> 4, t2 = threadIdx.x & 15;
     const long long N = (long long)n * n;
-    double acc = 0.0;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
     const int q0 = blockIdx.y * patches_per_split;
-    const int q1 = min(q0 + patches_per_split, np * np);
+    const int q1 = min(q0 + patches_per_split, np1 * np2);
     for (int q = q0; q < q1; ++q) {
-        const int J1 = (q / np) * 16, J2 = (q % np) * 16;
+        const int J1 = (q / np2) * kP1, J2 = (q % np2) * kP2;
         __syncthreads();
-        {
-            const int j1 = J1 + r1, j2 = J2 + r2;
-            double v = (j1 < n && j2 < n) ? x[(long long)j1 * n + j2] : 0.0;
-            float h = (float)v;
-            X[r1][r2] = make_float2(h, (float)(v - (double)h));
+        for (int e = threadIdx.x; e < kP1 * kP2; e += kThreads) {
+            const int c1 = e / kP2, c2 = e % kP2;
+            const int j1 = J1 + c1, j2 = J2 + c2;
+            const double v = (j1 < n && j2 < n) ? x[(long long)j1 * n + j2] : 0.0;
+            const float h = (float)v;
+            X[c1][c2] = make_float2(h, (float)(v - (double)h));
         }
-        for (int e = threadIdx.x; e < 31 * 31; e += kThreads) {
-            const int a = e / 31, b = e % 31;
-            int d1 = abs(I1 - J1 + a - 15), d2 = abs(I2 - J2 + b - 15);
-            d1 = min(d1, n - 1);
-            d2 = min(d2, n - 1);
+        for (int e = threadIdx.x; e < (2 * kP1 - 1) * (2 * kP2 - 1); e += kThreads) {
+            const int a = e / (2 * kP2 - 1), b = e % (2 * kP2 - 1);
+            const int d1 = min(abs(I1 - J1 + a - (kP1 - 1)), n - 1);
+            const int d2 = min(abs(I2 - J2 + b - (kP2 - 1)), n - 1);
             W[a][b] = table[(long long)d1 * n + d2];
         }
         __syncthreads();
-        float sh = 0.f, sl = 0.f;
-#pragma unroll 4
-        for (int c1 = 0; c1 < 16; ++c1) {
+        float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int c1 = 0; c1 < kP1; ++c1) {
+            const float2 *Wa = W[t1 - c1 + kP1 - 1];
+            const float2 *Xc = X[c1];
+#pragma unroll 2
+            for (int c0 = 0; c0 < 16; ++c0) {
+                const int base = t2 - c0 + kP2 - 1;
+                float2 w[7], xv[4];
 #pragma unroll
-            for (int c2 = 0; c2 < 16; ++c2) {
-                const float2 t = W[r1 - c1 + 15][r2 - c2 + 15];
-                const float2 v = X[c1][c2];
-                df_fma(t.x, t.y, v.x, v.y, sh, sl);
+                for (int d = 0; d < 7; ++d) w[d] = Wa[base + 16 * (d - 3)];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) xv[m] = Xc[c0 + 16 * m];
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        df_fma(w[k - m + 3].x, w[k - m + 3].y, xv[m].x, xv[m].y, sh[k], sl[k]);
             }
         }
-        acc += (double)sh + (double)sl;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k] += (double)sh[k] + (double)sl[k];
     }
-    if (i1 < n && i2 < n) partial[(long long)blockIdx.y * N + (long long)i1 * n + i2] = acc;
+    const int i1 = I1 + t1;
+    if (i1 < n) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i2 = I2 + t2 + 16 * k;
+            if (i2 < n) partial[(long long)blockIdx.y * N + (long long)i1 * n + i2] = acc[k];
+        }
+    }
 }
 
 // 3D: 4 x 8 x 8 patches; the offset window is 7 x 15 x 15.
@@ -324,10 +360,10 @@ int build_problem_tables(ie_problem *p) {
     IE_TRY_CUDA(cudaMalloc(&p->d_table, sizeof(float2) * T));
     IE_TRY_CUDA(cudaMalloc(&p->d_table64, sizeof(double) * T));
     coord_kernel<<<(unsigned)((p->N + 255) / 256), 256>>>(p->d_coord, p->dim, p->n, p->N);
-    IE_CHECK_LAUNCH();
+    IE_LAUNCHED();
     table_kernel<<<(unsigned)((T + 255) / 256), 256>>>(p->d_table, p->d_table64, p->dim, p->n, T, p->diag,
                                                       p->c_const, p->c_ln, p->c_r);
-    IE_CHECK_LAUNCH();
+    IE_LAUNCHED();
     IE_TRY_CUDA(cudaDeviceSynchronize());
     return IE_OK;
 }
@@ -343,9 +379,9 @@ int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, doubl
         IE_TRY(xsum.alloc(sizeof(double) * nrhs, s));
         iedd::dot_partial_kernel<<<dim3(iedd::kRedBlocks, nrhs), iedd::kRedThreads, 0, s>>>(
             x, ldx, nullptr, 0, N, part.as<double>());
-        IE_CHECK_LAUNCH();
+        IE_LAUNCHED();
         iedd::dot_final_kernel<<<nrhs, iedd::kRedBlocks, 0, s>>>(part.as<double>(), xsum.as<double>());
-        IE_CHECK_LAUNCH();
+        IE_LAUNCHED();
     }
     for (int k = 0; k < nrhs; ++k) {
         const double *xk = x + (long long)k * ldx;
@@ -358,16 +394,16 @@ int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, doubl
             const int tps = (ntiles + S - 1) / S;
             const int Se = (ntiles + tps - 1) / tps;
             DevBuf part;
-            IE_TRY(part.alloc(sizeof(float) * N * Se, s));
+            IE_TRY(part.alloc(sizeof(double) * N * Se, s));
             if (p->dim == 2)
-                k1_matvec_f32<2, R><<<dim3(rt, Se), kThreads, 0, s>>>(p->d_coord, xk, N, tps, ntiles, part.as<float>());
+                k1_matvec_f32<2, R><<<dim3(rt, Se), kThreads, 0, s>>>(p->d_coord, xk, N, tps, ntiles, part.as<double>());
             else
-                k1_matvec_f32<3, R><<<dim3(rt, Se), kThreads, 0, s>>>(p->d_coord, xk, N, tps, ntiles, part.as<float>());
-            IE_CHECK_LAUNCH();
-            combine_kernel<float><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
-                part.as<float>(), Se, xk, yk, N, p->dim, 0, p->diag, p->c_const,
+                k1_matvec_f32<3, R><<<dim3(rt, Se), kThreads, 0, s>>>(p->d_coord, xk, N, tps, ntiles, part.as<double>());
+            IE_LAUNCHED();
+            combine_kernel<double><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
+                part.as<double>(), Se, xk, yk, N, p->dim, 0, p->diag, p->c_const,
                 p->dim == 2 ? p->c_log2 : p->c_r, xs);
-            IE_CHECK_LAUNCH();
+            IE_LAUNCHED();
         } else if (precision == IE_FP64) {
             constexpr int R = 2;
             const int rt = (int)((N + kThreads * R - 1) / (kThreads * R));
@@ -380,17 +416,16 @@ int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, doubl
                 kd_matvec_f64<2, R><<<dim3(rt, Se), kThreads, 0, s>>>(p->d_coord, xk, N, tps, ntiles, part.as<double>());
             else
                 kd_matvec_f64<3, R><<<dim3(rt, Se), kThreads, 0, s>>>(p->d_coord, xk, N, tps, ntiles, part.as<double>());
-            IE_CHECK_LAUNCH();
+            IE_LAUNCHED();
             combine_kernel<double><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
                 part.as<double>(), Se, xk, yk, N, p->dim, 1, p->diag, p->c_const,
                 p->dim == 2 ? p->c_ln : p->c_r, xs);
-            IE_CHECK_LAUNCH();
+            IE_LAUNCHED();
         } else {
             const int n = p->n;
             int npatch, rowpatch;
             if (p->dim == 2) {
-                const int np = (n + 15) / 16;
-                npatch = np * np;
+                npatch = ((n + kP1 - 1) / kP1) * ((n + kP2 - 1) / kP2);
                 rowpatch = npatch;
             } else {
                 const int n1 = (n + 3) / 4, n2 = (n + 7) / 8;
@@ -406,9 +441,9 @@ int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, doubl
                 k2_accurate_2d<<<dim3(rowpatch, Se), kThreads, 0, s>>>(p->d_table, xk, n, pps, part.as<double>());
             else
                 k2_accurate_3d<<<dim3(rowpatch, Se), kThreads, 0, s>>>(p->d_table, xk, n, pps, part.as<double>());
-            IE_CHECK_LAUNCH();
+            IE_LAUNCHED();
             sum_splits_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(part.as<double>(), Se, yk, N);
-            IE_CHECK_LAUNCH();
+            IE_LAUNCHED();
         }
     }
     if (dot_out) IE_TRY(launch_dots(x, ldx, y, ldy, N, nrhs, dot_out, s));
@@ -426,8 +461,8 @@ int launch_dots(const double *a, long long lda, const double *b, long long ldb, 
     IE_TRY(part.alloc(sizeof(double) * iedd::kRedBlocks * nrhs, s));
     iedd::dot_partial_kernel<<<dim3(iedd::kRedBlocks, nrhs), iedd::kRedThreads, 0, s>>>(a, lda, b, ldb, N,
                                                                                        part.as<double>());
-    IE_CHECK_LAUNCH();
+    IE_LAUNCHED();
     iedd::dot_final_kernel<<<nrhs, iedd::kRedBlocks, 0, s>>>(part.as<double>(), out);
-    IE_CHECK_LAUNCH();
+    IE_LAUNCHED();
     return IE_OK;
 }

@@ -142,6 +142,7 @@ struct PrivateStream {
 struct Graph {
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t g = nullptr;
+    long long kernels = 0;  // kernel nodes, for the launch accounting
     ~Graph() {
         if (exec) cudaGraphExecDestroy(exec);
         if (g) cudaGraphDestroy(g);
@@ -161,6 +162,7 @@ extern "C" void pcg_default_opts(pcg_opts *o) {
     o->timeout_s = 0;
     o->check_every = 8;
     o->verify = 1;
+    o->inner = 0;
 }
 
 namespace {
@@ -178,6 +180,47 @@ struct Solver {
     PcgCol *st;
     double *pq, *rr, *rz, *ff;
 
+    // CUDA events around every inner matvec / apply / accurate matvec; recorded as external
+    // event nodes inside graphs, read after the host synchronizes
+    std::vector<cudaEvent_t> ev_mv, ev_ap;
+    cudaEvent_t ev_acc[2] = {nullptr, nullptr};
+    int n_mv = 0, n_ap = 0, n_acc = 0;
+    double t_mv = 0, t_ap = 0, t_acc = 0;
+    int pend_mv = 0, pend_ap = 0;  // recorded pairs not yet read
+    ~Solver() {
+        for (auto e : ev_mv) cudaEventDestroy(e);
+        for (auto e : ev_ap) cudaEventDestroy(e);
+        for (auto e : ev_acc) if (e) cudaEventDestroy(e);
+    }
+    int make_events(int pairs) {
+        ev_mv.resize(2 * pairs);
+        ev_ap.resize(2 * pairs);
+        for (auto &e : ev_mv) IE_TRY_CUDA(cudaEventCreate(&e));
+        for (auto &e : ev_ap) IE_TRY_CUDA(cudaEventCreate(&e));
+        for (auto &e : ev_acc) IE_TRY_CUDA(cudaEventCreate(&e));
+        return IE_OK;
+    }
+    int record(cudaEvent_t e) {
+        if (ie_capturing()) IE_TRY_CUDA(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+        else IE_TRY_CUDA(cudaEventRecord(e, s));
+        return IE_OK;
+    }
+    // after a synchronize: add the device time of the pending recorded pairs
+    void harvest() {
+        for (int i = 0; i < pend_mv; ++i) {
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, ev_mv[2 * i], ev_mv[2 * i + 1]) == cudaSuccess) t_mv += ms;
+        }
+        for (int i = 0; i < pend_ap; ++i) {
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, ev_ap[2 * i], ev_ap[2 * i + 1]) == cudaSuccess) t_ap += ms;
+        }
+        cudaGetLastError();
+        n_mv += pend_mv;
+        n_ap += pend_ap;
+        pend_mv = pend_ap = 0;
+    }
+
     int alloc() {
         size_t v = sizeof(double) * (size_t)N * nrhs;
         IE_TRY(bf.alloc(v, s)); IE_TRY(bu.alloc(v, s)); IE_TRY(br.alloc(v, s));
@@ -190,51 +233,85 @@ struct Solver {
         vgrid = (int)std::min<long long>((N + 255) / 256, (long long)p->sm_count * 8);
         return IE_OK;
     }
-    int mv_precision() const { return o.precision == IE_FP64 ? IE_FP64 : IE_MIXED; }
+    int mv_precision() const {
+        if (o.precision == IE_FP64) return IE_FP64;
+        if (o.inner == IE_MIXED || o.inner == IE_ACCURATE) return o.inner;
+        return p->dim == 2 ? IE_ACCURATE : IE_MIXED;
+    }
     int acc_precision() const { return o.precision == IE_FP64 ? IE_FP64 : IE_ACCURATE; }
     dim3 vg() const { return dim3(vgrid, nrhs); }
 
-    int head() {
+    int head(int slot) {
+        IE_TRY(record(ev_mv[2 * slot]));
         IE_TRY(launch_matvec_dot(p, pp, N, q, N, nrhs, mv_precision(), pq, s));
+        IE_TRY(record(ev_mv[2 * slot + 1]));
         k_alpha<<<(nrhs + 63) / 64, 64, 0, s>>>(st, pq, nrhs);
+        IE_LAUNCHED();
         k_update<<<vg(), 256, 0, s>>>(u, r, pp, q, N, st);
+        IE_LAUNCHED();
         IE_TRY(launch_dots(r, N, r, N, N, nrhs, rr, s));
         k_check<<<(nrhs + 63) / 64, 64, 0, s>>>(st, rr, o.tol * o.tol, o.max_it, nrhs);
-        IE_CHECK_LAUNCH();
+        IE_LAUNCHED();
         return IE_OK;
     }
-    int tail(int first) {
+    int tail(int first, int slot) {
+        IE_TRY(record(ev_ap[2 * slot]));
         IE_TRY(launch_apply(fac, r, N, z, N, nrhs, s));
+        IE_TRY(record(ev_ap[2 * slot + 1]));
         IE_TRY(launch_dots(r, N, z, N, N, nrhs, rz, s));
         k_beta<<<(nrhs + 63) / 64, 64, 0, s>>>(st, rz, nrhs, first);
+        IE_LAUNCHED();
         k_pupdate<<<vg(), 256, 0, s>>>(pp, z, N, st, first);
-        IE_CHECK_LAUNCH();
+        IE_LAUNCHED();
         return IE_OK;
     }
     // accurate residual of column k into r[:, k]; returns ||r_k||^2 (synchronizes)
     int accurate_residual(int k, double *rr_host) {
         const long long off = (long long)k * N;
+        IE_TRY(record(ev_acc[0]));
         IE_TRY(launch_matvec(p, u + off, N, q + off, N, 1, acc_precision(), s));
+        IE_TRY(record(ev_acc[1]));
         k_residual<<<dim3(vgrid, 1), 256, 0, s>>>(r + off, f + off, q + off, N);
-        IE_CHECK_LAUNCH();
+        IE_LAUNCHED();
         IE_TRY(launch_dots(r + off, N, r + off, N, N, 1, rr + k, s));
         IE_TRY_CUDA(cudaMemcpyAsync(rr_host, rr + k, sizeof(double), cudaMemcpyDeviceToHost, s));
         IE_TRY_CUDA(cudaStreamSynchronize(s));
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, ev_acc[0], ev_acc[1]) == cudaSuccess) t_acc += ms;
+        cudaGetLastError();
+        n_acc += 1;
         return IE_OK;
     }
     int capture(Graph &gr, int which, int reps) {
         IE_TRY_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        ie_set_capturing(true);
         int rc = IE_OK;
         for (int i = 0; i < reps && rc == IE_OK; ++i) {
-            if (which & 1) rc = head();
-            if (rc == IE_OK && (which & 2)) rc = tail(0);
+            if (which & 1) rc = head(i);
+            if (rc == IE_OK && (which & 2)) rc = tail(0, i);
         }
+        ie_set_capturing(false);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(s, &g);
         if (rc != IE_OK) { if (g) cudaGraphDestroy(g); return rc; }
         if (e != cudaSuccess) { ie_set_error(std::string("graph capture: ") + cudaGetErrorString(e)); return IE_ERR_CUDA; }
         gr.g = g;
+        size_t nn = 0;
+        IE_TRY_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        IE_TRY_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+        for (auto nd : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) gr.kernels++;
+        }
         IE_TRY_CUDA(cudaGraphInstantiate(&gr.exec, g, 0));
+        return IE_OK;
+    }
+    int launch(const Graph &gr, int mv_pairs, int ap_pairs) {
+        IE_TRY_CUDA(cudaGraphLaunch(gr.exec, s));
+        ie_count_launches(gr.kernels);
+        pend_mv += mv_pairs;
+        pend_ap += ap_pairs;
         return IE_OK;
     }
 };
@@ -250,7 +327,8 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
     pcg_opts o;
     if (opts) o = *opts; else pcg_default_opts(&o);
     if (!(o.tol >= 0.0) || o.max_it < 1 || (o.precision != IE_FP64 && o.precision != IE_MIXED) ||
-        o.replace_every < 0 || o.check_every < 0) {
+        o.replace_every < 0 || o.check_every < 0 ||
+        (o.inner != 0 && o.inner != IE_MIXED && o.inner != IE_ACCURATE)) {
         ie_set_error("pcg_solve: invalid options"); return IE_ERR_ARG;
     }
     if (o.check_every < 1) o.check_every = 1;
@@ -260,6 +338,7 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
     IE_TRY(ps.init(static_cast<cudaStream_t>(stream)));
     Solver S{p, fac, nrhs, p->N, o, ps.s};
     IE_TRY(S.alloc());
+    IE_TRY(S.make_events(std::max(o.check_every, 1)));
     const long long N = p->N;
     const size_t rowb = sizeof(double) * N, ldb = sizeof(double) * ld;
     const cudaMemcpyKind kin = ie_is_device_ptr(rhs) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -271,7 +350,7 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
                                       u_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
         IE_TRY(launch_matvec(p, S.u, N, S.q, N, nrhs, S.acc_precision(), s));
         k_residual<<<S.vg(), 256, 0, s>>>(S.r, S.f, S.q, N);
-        IE_CHECK_LAUNCH();
+        IE_LAUNCHED();
     } else {
         IE_TRY_CUDA(cudaMemsetAsync(S.u, 0, sizeof(double) * N * nrhs, s));
         IE_TRY_CUDA(cudaMemcpyAsync(S.r, S.f, sizeof(double) * N * nrhs, cudaMemcpyDeviceToDevice, s));
@@ -280,14 +359,16 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
     IE_TRY(launch_dots(S.f, N, S.f, N, N, nrhs, S.ff, s));
     IE_TRY(launch_dots(S.r, N, S.r, N, N, nrhs, S.rr, s));
     k_init_state<<<(nrhs + 63) / 64, 64, 0, s>>>(S.st, S.ff, S.rr, o.tol * o.tol, nrhs);
-    IE_CHECK_LAUNCH();
-    IE_TRY(S.tail(1));
+    IE_LAUNCHED();
+    IE_TRY(S.tail(1, 0));
+    S.pend_ap = 1;
 
     std::vector<PcgCol> hs((size_t)nrhs);
     std::vector<double> last_true((size_t)nrhs, INFINITY), relres_at_replace((size_t)nrhs, 1.0);
     auto read_states = [&]() -> int {
         IE_TRY_CUDA(cudaMemcpyAsync(hs.data(), S.st, sizeof(PcgCol) * nrhs, cudaMemcpyDeviceToHost, s));
         IE_TRY_CUDA(cudaStreamSynchronize(s));
+        S.harvest();
         return IE_OK;
     };
     auto write_states = [&]() -> int {
@@ -316,7 +397,7 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
                 for (auto &c : hs) if (c.active == 1) { c.active = 0; c.flag = IE_ERR_TIMEOUT; }
                 break;
             }
-            IE_TRY_CUDA(cudaGraphLaunch(gr.exec, s));
+            IE_TRY(S.launch(gr, o.check_every, o.check_every));
             IE_TRY(read_states());
         }
         IE_TRY(write_states());
@@ -374,8 +455,8 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
                 IE_TRY(write_states());
                 break;
             }
-            if (need_tail) IE_TRY_CUDA(cudaGraphLaunch(gt.exec, s));  // z = T^{-1} r, beta, p
-            IE_TRY_CUDA(cudaGraphLaunch(gh.exec, s));                 // q = A p, alpha, u/r, check
+            if (need_tail) IE_TRY(S.launch(gt, 0, 1));  // z = T^{-1} r, beta, p
+            IE_TRY(S.launch(gh, 1, 0));                 // q = A p, alpha, u/r, check
             IE_TRY(read_states());
             IE_TRY(replace());
             need_tail = true;
@@ -407,6 +488,13 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
             rep[k].pad_ = 0;
             rep[k].recursive_relres = c.ff > 0 ? std::sqrt(c.rr / c.ff) : 0.0;
             rep[k].true_relres = c.true_relres;
+            rep[k].matvecs = S.n_mv;
+            rep[k].applies = S.n_ap;
+            rep[k].matvec_ms = S.t_mv;
+            rep[k].apply_ms = S.t_ap;
+            rep[k].accurate_matvecs = S.n_acc;
+            rep[k].pad2_ = 0;
+            rep[k].accurate_ms = S.t_acc;
         }
     }
     return ret;

@@ -11,7 +11,6 @@ from __future__ import annotations
 
 import ctypes
 import os
-from dataclasses import dataclass
 
 import numpy as np
 
@@ -29,7 +28,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "lib
 # Every C-ABI symbol declared in include/iedd.h.
 EXPORTS = ("ie_last_error", "ie_version", "ie_discretize", "ie_problem_info", "ie_destroy", "ie_matvec",
            "dd_partition", "dd_partition_info", "dd_partition_export", "dd_partition_destroy", "dd_factor",
-           "dd_factor_destroy", "dd_apply", "pcg_default_opts", "pcg_solve")
+           "dd_factor_destroy", "dd_apply", "ie_kernel_launches", "pcg_default_opts", "pcg_solve")
 
 
 class IEError(RuntimeError):
@@ -41,16 +40,18 @@ class IEError(RuntimeError):
 class PcgOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_it", ctypes.c_int), ("precision", ctypes.c_int),
                 ("replace_every", ctypes.c_int), ("use_x0", ctypes.c_int), ("timeout_s", ctypes.c_double),
-                ("check_every", ctypes.c_int), ("verify", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("verify", ctypes.c_int), ("inner", ctypes.c_int)]
 
 
 class PcgReport(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("replacements", ctypes.c_int), ("status", ctypes.c_int),
-                ("pad_", ctypes.c_int), ("recursive_relres", ctypes.c_double), ("true_relres", ctypes.c_double)]
+                ("pad_", ctypes.c_int), ("recursive_relres", ctypes.c_double), ("true_relres", ctypes.c_double),
+                ("matvecs", ctypes.c_int), ("applies", ctypes.c_int), ("matvec_ms", ctypes.c_double),
+                ("apply_ms", ctypes.c_double), ("accurate_matvecs", ctypes.c_int), ("pad2_", ctypes.c_int),
+                ("accurate_ms", ctypes.c_double)]
 
     def as_dict(self):
-        return {"iterations": self.iterations, "replacements": self.replacements, "status": self.status,
-                "recursive_relres": self.recursive_relres, "true_relres": self.true_relres}
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}
 
 
 _LIB = None
@@ -80,6 +81,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dd_factor": (i, [vp, vp, i, P(vp), P(i), vp]),
         "dd_factor_destroy": (None, [vp]),
         "dd_apply": (i, [vp, vp, vp, i, ll, vp]),
+        "ie_kernel_launches": (ll, [i]),
         "pcg_default_opts": (None, [P(PcgOpts)]),
         "pcg_solve": (i, [vp, vp, vp, vp, i, ll, P(PcgOpts), P(PcgReport), vp]),
     }
@@ -249,6 +251,10 @@ def dd_apply(fac: Factor, r, z, stream=None):
         raise ValueError("r and z must have the same shape and stride")
     _check(load_library().dd_apply(fac.ptr, pr, pz, k, ld, _stream(stream)))
     return z
+
+
+def ie_kernel_launches(reset: bool = False) -> int:
+    return load_library().ie_kernel_launches(1 if reset else 0)
 
 
 def pcg_default_opts() -> PcgOpts:

@@ -72,6 +72,7 @@ def test_null_arguments_rejected_without_gpu(lib):
     lib.ie_destroy(None)
     lib.dd_partition_destroy(None)
     lib.dd_factor_destroy(None)
+    assert lib.ie_kernel_launches(0) >= 0
 
 
 def test_default_opts(lib):
