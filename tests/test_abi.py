@@ -80,7 +80,7 @@ def test_default_opts(lib):
     o = iedd.pcg_default_opts()
     assert o.tol == 1e-8 and o.max_it == 1000 and o.precision == iedd.IE_MIXED
     assert o.replace_every == 50 and o.check_every == 8 and o.verify == 1
-    assert ctypes.sizeof(iedd.PcgReport) == 32
+    assert ctypes.sizeof(iedd.PcgReport) == 72
 
 
 def test_missing_library_fails_loudly(tmp_path):
