@@ -15,9 +15,12 @@
 
 namespace {
 
-template <typename T>
+// TL: storage type of the factor; T: arithmetic type of the solves.  FP32 factors are solved in
+// FP64 arithmetic: FP32 substitution is not symmetric to working accuracy (its error grows with
+// cond(A_i) ~ 1e3), and an operator T^{-1} that is not symmetric slows PCG down measurably.
+template <typename TL, typename T>
 __global__ void __launch_bounds__(256)
-apply_blocks(const T *__restrict__ pool, const long long *__restrict__ loff, const int *__restrict__ npad,
+apply_blocks(const TL *__restrict__ pool, const long long *__restrict__ loff, const int *__restrict__ npad,
              const int *__restrict__ nb, const long long *__restrict__ offs, const int *__restrict__ idx,
              const int *__restrict__ order, const double *__restrict__ r, long long ldr,
              double *__restrict__ zbuf, long long total) {
@@ -28,7 +31,7 @@ apply_blocks(const T *__restrict__ pool, const long long *__restrict__ loff, con
     const int b = order[blockIdx.x];
     const int k = blockIdx.y;
     const int np = npad[b], n = nb[b], nt = np / 32;
-    const T *L = pool + loff[b];
+    const TL *L = pool + loff[b];
     const int *id = idx + offs[b];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double *rk = r + (long long)k * ldr;
@@ -38,12 +41,12 @@ apply_blocks(const T *__restrict__ pool, const long long *__restrict__ loff, con
     // forward: L y = R_i r
     for (int t = 0; t < nt; ++t) {
         const int t0 = t * 32;
-        for (int e = tid; e < 1024; e += 256) D[e >> 5][e & 31] = L[(long long)(t0 + (e >> 5)) * np + t0 + (e & 31)];
+        for (int e = tid; e < 1024; e += 256) D[e >> 5][e & 31] = (T)L[(long long)(t0 + (e >> 5)) * np + t0 + (e & 31)];
         for (int q = 0; q < 4; ++q) {
             const int row = t0 + warp + 8 * q;
-            const T *lr = L + (long long)row * np;
+            const TL *lr = L + (long long)row * np;
             T s = 0;
-            for (int c = lane; c < t0; c += 32) s += lr[c] * Y[c];
+            for (int c = lane; c < t0; c += 32) s += (T)lr[c] * Y[c];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
             if (lane == 0) red[0][warp + 8 * q] = s;
@@ -63,9 +66,9 @@ apply_blocks(const T *__restrict__ pool, const long long *__restrict__ loff, con
     // backward: L^T z = y
     for (int t = nt - 1; t >= 0; --t) {
         const int t0 = t * 32;
-        for (int e = tid; e < 1024; e += 256) D[e >> 5][e & 31] = L[(long long)(t0 + (e >> 5)) * np + t0 + (e & 31)];
+        for (int e = tid; e < 1024; e += 256) D[e >> 5][e & 31] = (T)L[(long long)(t0 + (e >> 5)) * np + t0 + (e & 31)];
         T part = 0;
-        for (int row = t0 + 32 + warp; row < np; row += 8) part += L[(long long)row * np + t0 + lane] * Y[row];
+        for (int row = t0 + 32 + warp; row < np; row += 8) part += (T)L[(long long)row * np + t0 + lane] * Y[row];
         red[warp][lane] = part;
         __syncthreads();
         if (warp == 0) {
@@ -102,14 +105,12 @@ __global__ void overlap_sum(const double *__restrict__ zbuf, long long total, co
 // Raise the dynamic shared-memory limit of the apply kernel for large subdomains (done once per
 // factor, outside any stream capture).
 int prepare_apply(const dd_factor_t *f) {
-    if (f->precision == IE_FP64) {
-        size_t sm = sizeof(double) * f->max_pad;
-        if (sm > 48 * 1024)
-            IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    } else {
-        size_t sm = sizeof(float) * f->max_pad;
-        if (sm > 48 * 1024)
-            IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const size_t sm = sizeof(double) * f->max_pad;
+    if (sm > 48 * 1024) {
+        if (f->precision == IE_FP64)
+            IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        else
+            IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     }
     return IE_OK;
 }
@@ -122,14 +123,13 @@ int launch_apply(const dd_factor_t *f, const double *r, long long ldr, double *z
     IE_TRY(zbuf.alloc(sizeof(double) * (size_t)std::max<long long>(part->total, 1) * nrhs, s));
     if (f->nblocks > 0) {
         dim3 g(f->nblocks, nrhs);
+        const size_t sm = sizeof(double) * f->max_pad;
         if (f->precision == IE_FP64) {
-            size_t sm = sizeof(double) * f->max_pad;
-            apply_blocks<double><<<g, 256, sm, s>>>((const double *)f->d_pool, f->d_loff, f->d_npad, f->d_n, part->d_offs,
+            apply_blocks<double, double><<<g, 256, sm, s>>>((const double *)f->d_pool, f->d_loff, f->d_npad, f->d_n, part->d_offs,
                                                    part->d_idx, f->d_order, r, ldr, zbuf.as<double>(), part->total);
             IE_LAUNCHED();
         } else {
-            size_t sm = sizeof(float) * f->max_pad;
-            apply_blocks<float><<<g, 256, sm, s>>>((const float *)f->d_pool, f->d_loff, f->d_npad, f->d_n, part->d_offs,
+            apply_blocks<float, double><<<g, 256, sm, s>>>((const float *)f->d_pool, f->d_loff, f->d_npad, f->d_n, part->d_offs,
                                                   part->d_idx, f->d_order, r, ldr, zbuf.as<double>(), part->total);
             IE_LAUNCHED();
         }

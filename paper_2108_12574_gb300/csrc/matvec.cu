@@ -125,6 +125,127 @@ k1_matvec_f32(const float4 *__restrict__ coord, const double *__restrict__ x, lo
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// K1m: FP32 SFU matvec for a batch of right-hand sides (GEMM-shaped)
+// ---------------------------------------------------------------------------------------------
+// A CTA owns 128 target rows and NR right-hand sides.  For every chunk of 32 source points it
+// evaluates the 128 x 32 entry tile once (one SFU op per entry, spread over the CTA) into shared
+// memory, stages the 32 x NR slice of x, and each thread accumulates an 8 x (NR/16) block of the
+// product with FFMA -- the entry cost is amortised over NR right-hand sides.  FP32 partial sums
+// are flushed every 8 chunks (256 source points) into FP64 accumulators kept in (dynamic)
+// shared memory, so registers hold only the FP32 block.  Same entry conventions as K1.
+constexpr int kMBM = 128, kMBK = 32;
+
+template <int DIM, int NR>
+__global__ void __launch_bounds__(kThreads)
+k1m_matvec_f32(const float4 *__restrict__ coord, const double *__restrict__ x, long long ldx, int nrhs,
+               long long N, int chunks_per_split, int nchunks, double *__restrict__ partial) {
+    constexpr int TN = NR / 16;
+    __shared__ float4 rc[kMBM];
+    __shared__ float4 cc[kMBK];
+    __shared__ __align__(16) float E[kMBK][kMBM];
+    __shared__ __align__(16) float Xs[kMBK][NR];
+    const long long row0 = (long long)blockIdx.x * kMBM;
+    const int rhs0 = blockIdx.z * NR;
+    const int tid = threadIdx.x, tm = tid >> 4, tn = tid & 15;
+    if (tid < kMBM) {
+        const long long i = row0 + tid;
+        rc[tid] = i < N ? coord[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    extern __shared__ double dacc_s[];  // [8 * TN][kThreads]
+    float acc[8][TN];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) { acc[a][b] = 0.f; dacc_s[(a * TN + b) * kThreads + tid] = 0.0; }
+    const int k0 = blockIdx.y * chunks_per_split;
+    const int k1 = min(k0 + chunks_per_split, nchunks);
+    for (int ch = k0; ch < k1; ++ch) {
+        const long long j0 = (long long)ch * kMBK;
+        __syncthreads();
+        if (tid < kMBK) {
+            const long long j = j0 + tid;
+            cc[tid] = j < N ? coord[j] : make_float4(1e6f, 1e6f, 1e6f, 0.f);
+        }
+        // x slice: Xs[c][r] = x[(rhs0 + r) * ldx + j0 + c]  (zero outside)
+        for (int e = tid; e < kMBK * NR; e += kThreads) {
+            const int r = e / kMBK, c = e % kMBK;
+            const long long j = j0 + c;
+            Xs[c][r] = (j < N && rhs0 + r < nrhs) ? (float)x[(long long)(rhs0 + r) * ldx + j] : 0.f;
+        }
+        __syncthreads();
+        // entry tile E[c][m]
+        for (int e = tid; e < kMBK * kMBM; e += kThreads) {
+            const int m = e % kMBM, c = e / kMBM;
+            const float4 a = rc[m], b = cc[c];
+            const float dx = a.x - b.x, dy = a.y - b.y;
+            float k;
+            if (DIM == 2) {
+                k = __log2f(fmaf(dx, dx, fmaf(dy, dy, kTiny2D)));
+            } else {
+                const float dz = a.z - b.z;
+                k = rsqrtf(fmaxf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), 1.0f));
+            }
+            E[c][m] = k;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int c = 0; c < kMBK; ++c) {
+            const float4 e0 = *reinterpret_cast<const float4 *>(&E[c][tm * 8]);
+            const float4 e1 = *reinterpret_cast<const float4 *>(&E[c][tm * 8 + 4]);
+            const float ev[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+            float xv[TN];
+#pragma unroll
+            for (int b = 0; b < TN; ++b) xv[b] = Xs[c][tn * TN + b];
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < TN; ++b) acc[a][b] = fmaf(ev[a], xv[b], acc[a][b]);
+        }
+        if (((ch - k0) & 7) == 7 || ch == k1 - 1) {
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < TN; ++b) {
+                    dacc_s[(a * TN + b) * kThreads + tid] += (double)acc[a][b];
+                    acc[a][b] = 0.f;
+                }
+        }
+    }
+    // partial layout: [split][rhs][N]
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const long long i = row0 + tm * 8 + a;
+        if (i >= N) continue;
+#pragma unroll
+        for (int b = 0; b < TN; ++b) {
+            const int r = rhs0 + tn * TN + b;
+            if (r < nrhs) partial[((long long)blockIdx.y * nrhs + r) * N + i] = dacc_s[(a * TN + b) * kThreads + tid];
+        }
+    }
+}
+
+// Combine for K1m: column r of y from the [split][rhs][N] partials.
+__global__ void combine_multi_kernel(const double *__restrict__ partial, int nsplit, int nrhs,
+                                     const double *__restrict__ x, long long ldx, double *__restrict__ y,
+                                     long long ldy, long long N, int dim, double diag, double c_const,
+                                     double c_sum, const double *__restrict__ xsum) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (i >= N) return;
+    double s = 0.0;
+    for (int k = 0; k < nsplit; ++k) s += partial[((long long)k * nrhs + r) * N + i];
+    const double xi = x[(long long)r * ldx + i];
+    double y0;
+    if (dim == 2) {
+        const double self = (double)__log2f(kTiny2D) * (double)(float)xi;
+        y0 = diag * xi + c_const * (xsum[r] - xi) + c_sum * (s - self);
+    } else {
+        y0 = diag * xi + c_sum * (s - (double)(float)xi);
+    }
+    y[(long long)r * ldy + i] = y0;
+}
+
 // y_i = diag x_i + off-diagonal part from the split partials (FP64 combine).
 template <typename TP>
 __global__ void combine_kernel(const TP *__restrict__ partial, int nsplit, const double *__restrict__ x,
@@ -254,10 +375,10 @@ k2_accurate_2d(const float2 *__restrict__ table, const double *__restrict__ x, i
             W[a][b] = table[(long long)d1 * n + d2];
         }
         __syncthreads();
-        float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
         for (int c1 = 0; c1 < kP1; ++c1) {
             const float2 *Wa = W[t1 - c1 + kP1 - 1];
             const float2 *Xc = X[c1];
+            float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 2
             for (int c0 = 0; c0 < 16; ++c0) {
                 const int base = t2 - c0 + kP2 - 1;
@@ -271,10 +392,18 @@ k2_accurate_2d(const float2 *__restrict__ table, const double *__restrict__ x, i
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
                         df_fma(w[k - m + 3].x, w[k - m + 3].y, xv[m].x, xv[m].y, sh[k], sl[k]);
-            }
-        }
+                // renormalise (Fast2Sum) so the low word stays below an ulp of the high word
 #pragma unroll
-        for (int k = 0; k < 4; ++k) acc[k] += (double)sh[k] + (double)sl[k];
+                for (int k = 0; k < 4; ++k) {
+                    const float t = __fadd_rn(sh[k], sl[k]);
+                    sl[k] = __fsub_rn(sl[k], __fsub_rn(t, sh[k]));
+                    sh[k] = t;
+                }
+            }
+            // flush the 64-term double-float partial sums to FP64
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[k] += (double)sh[k] + (double)sl[k];
+        }
     }
     const int i1 = I1 + t1;
     if (i1 < n) {
@@ -355,6 +484,10 @@ int splits_for(long long items, long long work_units, int sm_count, int per_sm) 
 }  // namespace
 
 int build_problem_tables(ie_problem *p) {
+    // dynamic shared memory of the batched matvec (set outside any stream capture)
+    const int dsm64 = (int)(sizeof(double) * 8 * 4 * kThreads);
+    IE_TRY_CUDA(cudaFuncSetAttribute(k1m_matvec_f32<2, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm64));
+    IE_TRY_CUDA(cudaFuncSetAttribute(k1m_matvec_f32<3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm64));
     IE_TRY_CUDA(cudaMalloc(&p->d_coord, sizeof(float4) * p->N));
     long long T = p->N;  // n^dim offsets
     IE_TRY_CUDA(cudaMalloc(&p->d_table, sizeof(float2) * T));
@@ -382,6 +515,34 @@ int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, doubl
         IE_LAUNCHED();
         iedd::dot_final_kernel<<<nrhs, iedd::kRedBlocks, 0, s>>>(part.as<double>(), xsum.as<double>());
         IE_LAUNCHED();
+    }
+    if (precision == IE_MIXED && nrhs >= 4) {
+        const int NR = nrhs > 16 ? 64 : 16;
+        const int rt = (int)((N + kMBM - 1) / kMBM);
+        const int nchunks = (int)((N + kMBK - 1) / kMBK);
+        const int groups = (nrhs + NR - 1) / NR;
+        int S = splits_for((long long)rt * groups, nchunks, p->sm_count, 3);
+        S = std::min(S, 16);
+        const int cps = (nchunks + S - 1) / S;
+        const int Se = (nchunks + cps - 1) / cps;
+        DevBuf part;
+        IE_TRY(part.alloc(sizeof(double) * N * nrhs * Se, s));
+        const dim3 g(rt, Se, groups);
+        const size_t dsm = sizeof(double) * 8 * (NR / 16) * kThreads;
+        if (p->dim == 2) {
+            if (NR == 64) k1m_matvec_f32<2, 64><<<g, kThreads, dsm, s>>>(p->d_coord, x, ldx, nrhs, N, cps, nchunks, part.as<double>());
+            else k1m_matvec_f32<2, 16><<<g, kThreads, dsm, s>>>(p->d_coord, x, ldx, nrhs, N, cps, nchunks, part.as<double>());
+        } else {
+            if (NR == 64) k1m_matvec_f32<3, 64><<<g, kThreads, dsm, s>>>(p->d_coord, x, ldx, nrhs, N, cps, nchunks, part.as<double>());
+            else k1m_matvec_f32<3, 16><<<g, kThreads, dsm, s>>>(p->d_coord, x, ldx, nrhs, N, cps, nchunks, part.as<double>());
+        }
+        IE_LAUNCHED();
+        combine_multi_kernel<<<dim3((unsigned)((N + 255) / 256), nrhs), 256, 0, s>>>(
+            part.as<double>(), Se, nrhs, x, ldx, y, ldy, N, p->dim, p->diag, p->c_const,
+            p->dim == 2 ? p->c_log2 : p->c_r, xsum.ptr ? xsum.as<double>() : nullptr);
+        IE_LAUNCHED();
+        if (dot_out) IE_TRY(launch_dots(x, ldx, y, ldy, N, nrhs, dot_out, s));
+        return IE_OK;
     }
     for (int k = 0; k < nrhs; ++k) {
         const double *xk = x + (long long)k * ldx;

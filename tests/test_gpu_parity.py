@@ -38,10 +38,11 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def _scale(dim, n, x, conv):
+def _scale(dim, n, x, conv, a_shift=0.0):
     # ||A||_inf ||x||_inf, with ||A||_inf from the oracle's row sums of |A| (A >= 0 except for
     # far 2D pairs, so |A| 1 is bounded by A 1 + 2 * (negative part); a factor 2 covers it)
-    rows = O.matvec_direct(dim, n, np.ones(n ** dim), rows=np.array([0, (n ** dim) // 2]), convention=conv)
+    rows = O.matvec_direct(dim, n, np.ones(n ** dim), rows=np.array([0, (n ** dim) // 2]), convention=conv,
+                           a_shift=abs(a_shift))
     return 2.0 * float(np.max(np.abs(rows))) * float(np.max(np.abs(x)))
 
 
@@ -62,16 +63,32 @@ def test_matvec_parity(dim, n, conv, prec, tol):
     assert err <= tol * _scale(dim, n, x, conv), err
 
 
-def test_matvec_multi_rhs_and_shift():
-    dim, n = 2, 40
-    N = n * n
-    X = I.uniform_rhs_batch(N, [3, 4, 5]).T.copy()  # (nrhs, N)
+@pytest.mark.parametrize("dim,n,nrhs", [(2, 40, 3), (2, 40, 5), (3, 12, 20), (3, 10, 70), (2, 33, 17)])
+def test_matvec_multi_rhs_and_shift(dim, n, nrhs):
+    # nrhs >= 4 takes the batched FP32 kernel (16 or 64 right-hand sides per CTA)
+    N = n ** dim
+    X = I.uniform_rhs_batch(N, list(range(3, 3 + nrhs))).T.copy()  # (nrhs, N)
     prob = iedd.ie_discretize(dim, n, a_shift=0.3)
+    scale = _scale(dim, n, X, O.GRID_TEXT, 0.3)
+    ref = O.matvec_direct(dim, n, X.T, a_shift=0.3).T
     for prec, tol in ((iedd.IE_FP64, 1e-12), (iedd.IE_ACCURATE, 1e-12), (iedd.IE_MIXED, 4e-6)):
-        Y = torch.zeros((3, N), dtype=torch.float64, device="cuda")
+        Y = torch.zeros((nrhs, N), dtype=torch.float64, device="cuda")
         iedd.ie_matvec(prob, dev(X), Y, prec)
-        ref = O.matvec_direct(dim, n, X.T, a_shift=0.3).T
-        assert np.max(np.abs(host(Y) - ref)) <= tol * _scale(dim, n, X, O.GRID_TEXT) + 1e-15 * 0.3
+        assert np.max(np.abs(host(Y) - ref)) <= tol * scale, prec
+
+
+def test_matvec_strided_batch():
+    n = 20
+    N = n * n
+    X = torch.zeros((6, N + 7), dtype=torch.float64, device="cuda")
+    Xh = I.uniform_rhs_batch(N, range(6)).T.copy()
+    X[:, :N] = dev(Xh)
+    Y = torch.zeros((6, N + 7), dtype=torch.float64, device="cuda")
+    prob = iedd.ie_discretize(2, n)
+    iedd.ie_matvec(prob, X[:, :N], Y[:, :N], iedd.IE_MIXED)
+    ref = O.matvec_direct(2, n, Xh.T).T
+    assert np.max(np.abs(host(Y[:, :N]) - ref)) <= 4e-6 * _scale(2, n, Xh, O.GRID_TEXT)
+    assert float(Y[:, N:].abs().max()) == 0.0
 
 
 def test_matvec_host_pointers_match_device():
