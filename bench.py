@@ -4,8 +4,9 @@
 Workload (synthetic stand-in for the paper's uniform-grid problems): 2D Laplace first-kind
 IE, 512 x 512 cell-centred grid (N = 262144), f a Gaussian random field (squared-exponential
 covariance, length scale 0.1, seed = rank), Schwarz preconditioner with 32 x 32 partitions of
-16 x 16 cells extended by 2 cells, FP32 factors, double-float (FP32-pipe) matvec, FP64 CG
-scalars and residual replacement; tolerance 1e-8 on the true residual.
+16 x 16 cells extended by 2 cells, FP32 factors (FP64 solves), FP32 SFU matvec with compensated
+sums, FP64 CG scalars and residual replacement by the double-float accurate matvec; tolerance
+1e-8 on the true residual.
 
 One step = the whole hot path for one right-hand side: ie_discretize, dd_partition, dd_factor,
 pcg_solve (inputs already in HBM).  N > 1 GPUs run independent replicas (weak scaling).
@@ -31,8 +32,10 @@ WORKLOAD = "ie2d_n512_schwarz_m32_d2"
 DIM, NGRID, MPART, DELTA, ELL, TOL, REPLACE_EVERY = 2, 512, 32, 2, 0.1, 1e-8, 50
 METRIC = "PCG time-to-1e-8 true relative residual (s)"
 L2_FLUSH_BYTES = 512 << 20
-FP32_OPS_PER_PAIR_K2 = 12   # double-float pair: FMUL + 3 FFMA (exact product) + 6 (TwoSum) + 2
+FP32_OPS_PER_PAIR_K1 = 9    # 2 FADD + 2 FFMA (|D|^2 + 2^-30), FMUL, 4 FADD (Kahan)
+SFU_OPS_PER_PAIR_K1 = 1     # MUFU.LG2
 FP32_LANES_PER_SM = 128
+SFU_LANES_PER_SM = 16
 
 # DRAM traffic per launch of the dominant kernel from an ncu capture, valid only for the
 # source it was measured on (hash of matvec.cu); otherwise the bench reports null.
@@ -52,7 +55,8 @@ def parse():
 def config_dict():
     return {"workload": WORKLOAD, "dim": DIM, "n": NGRID, "N": NGRID ** DIM, "m": MPART, "delta": DELTA,
             "rhs": f"GRF l={ELL} seed=rank", "tol": TOL, "decomposition": "schwarz",
-            "precision": "mixed (FP32 factors, double-float matvec, FP64 scalars)",
+            "precision": "mixed (FP32 SFU matvec with compensated sums, FP32 factors with FP64 solves, "
+                         "FP64 scalars, double-float residual replacement)",
             "l2": "flushed between timed steps (512 MiB write)"}
 
 
@@ -266,20 +270,22 @@ def main():
     e2e = {"value": reduce_max(statistics.mean(e2e_times)), "unit": "s",
            "h2d_bytes_per_step": int(f_host.nbytes), "d2h_bytes_per_step": int(u_host.nbytes)}
 
-    # roofline of the dominant kernel: the inner matvec (double-float table sum, K2)
+    # roofline of the dominant kernel: the inner matvec (FP32 SFU entries, compensated sums, K1)
     pairs = float(N) * (N - 1)
     mv_launch_s = last["matvec_ms"] / max(last["matvecs"], 1) / 1e3
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     f_mhz = clocks.get("sm_mhz") or 2070.0
-    peak = sms * FP32_LANES_PER_SM / FP32_OPS_PER_PAIR_K2 * f_mhz * 1e6
+    per_clk = min(FP32_LANES_PER_SM / FP32_OPS_PER_PAIR_K1, SFU_LANES_PER_SM / SFU_OPS_PER_PAIR_K1)
+    peak = sms * per_clk * f_mhz * 1e6
     achieved = pairs / mv_launch_s
     src_hash = hashlib.sha256(open(os.path.join(ROOT, "paper_2108_12574_gb300", "csrc", "matvec.cu"), "rb")
                               .read()).hexdigest()[:16]
     traffic = NCU_TRAFFIC.get(src_hash)
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpairs/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "k2_accurate_2d",
-                "peak_basis": (f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes/clk / {FP32_OPS_PER_PAIR_K2} FP32 ops per "
-                               f"double-float pair x {f_mhz:.0f} MHz (median SM clock sampled in the timed region)")}
+                "frac": achieved / peak, "traffic": traffic, "kernel": "k1_matvec_f32",
+                "peak_basis": (f"{sms} SMs x min({FP32_LANES_PER_SM} FP32 lanes / {FP32_OPS_PER_PAIR_K1} FP32 ops, "
+                               f"{SFU_LANES_PER_SM} SFU lanes / {SFU_OPS_PER_PAIR_K1} SFU op) pairs/clk x {f_mhz:.0f} MHz "
+                               f"(median SM clock sampled in the timed region)")}
 
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",

@@ -173,7 +173,7 @@ typedef struct {
     int verify;          /* IE_FP64: 1 = compute the true residual at the end (one more matvec)    */
     int inner;           /* IE_MIXED: matvec inside the iteration: IE_MIXED (FP32 SFU entries,
                             compensated FP32 sums), IE_ACCURATE (double-float table sums on the
-                            FP32 pipes), or 0 = choose (IE_ACCURATE in 2D, IE_MIXED in 3D)       */
+                            FP32 pipes), or 0 = the library's choice (IE_MIXED)       */
 } pcg_opts;
 
 typedef struct {

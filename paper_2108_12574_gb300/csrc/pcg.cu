@@ -236,7 +236,7 @@ struct Solver {
     int mv_precision() const {
         if (o.precision == IE_FP64) return IE_FP64;
         if (o.inner == IE_MIXED || o.inner == IE_ACCURATE) return o.inner;
-        return p->dim == 2 ? IE_ACCURATE : IE_MIXED;
+        return IE_MIXED;
     }
     int acc_precision() const { return o.precision == IE_FP64 ? IE_FP64 : IE_ACCURATE; }
     dim3 vg() const { return dim3(vgrid, nrhs); }

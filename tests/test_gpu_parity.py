@@ -285,7 +285,7 @@ def test_pcg_warm_start_x0():
     assert r1["iterations"] == 0 and r1["status"] == 0
     assert torch.equal(u, u2)
     # a perturbed warm start converges in fewer iterations than zero start
-    u3 = u + 1e-6 * dev(I.uniform_rhs(n * n, 6))
+    u3 = u + 1e-3 * float(u.abs().max()) * dev(I.uniform_rhs(n * n, 6))
     r2 = iedd.pcg_solve(prob, fac, dev(f), u3, tol=1e-8, precision=iedd.IE_FP64, use_x0=1)[0]
     assert 0 < r2["iterations"] < r0["iterations"]
 
