@@ -173,7 +173,9 @@ typedef struct {
     int verify;          /* IE_FP64: 1 = compute the true residual at the end (one more matvec)    */
     int inner;           /* IE_MIXED: matvec inside the iteration: IE_MIXED (FP32 SFU entries,
                             compensated FP32 sums), IE_ACCURATE (double-float table sums on the
-                            FP32 pipes), or 0 = the library's choice (IE_MIXED)       */
+                            FP32 pipes; the search directions are then rounded to
+                            FP32), or 0 = the library's choice (IE_ACCURATE in 2D, IE_MIXED
+                            in 3D)       */
 } pcg_opts;
 
 typedef struct {

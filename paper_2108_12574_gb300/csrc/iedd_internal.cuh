@@ -127,8 +127,12 @@ struct DevBuf {
 // ---------------------------------------------------------------------------------------------
 // Kernel launchers (matvec.cu, factor.cu, apply.cu, pcg.cu)
 // ---------------------------------------------------------------------------------------------
+// Internal matvec mode: the accurate (double-float) sum for an x whose entries are exactly
+// representable in FP32 (PCG rounds its search directions so), which saves one FFMA per pair.
+constexpr int IE_ACCURATE_X32 = 4;
+
 // y = A x for device FP64 x (leading dimension ldx) and y (ldy), nrhs columns.
-// precision: IE_FP64, IE_MIXED or IE_ACCURATE.
+// precision: IE_FP64, IE_MIXED, IE_ACCURATE or IE_ACCURATE_X32.
 int launch_matvec(const ie_problem *p, const double *x, long long ldx, double *y, long long ldy,
                   int nrhs, int precision, cudaStream_t s);
 // As launch_matvec, and, if dot_out != nullptr, dot_out[k] = x_k^T y_k (FP64, deterministic).

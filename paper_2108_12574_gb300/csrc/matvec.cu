@@ -74,16 +74,30 @@ __global__ void table_kernel(float2 *t32, double *t64, int dim, int n, long long
 // the sum at FP32-entry accuracy.  Intrinsics keep the compiler from re-associating it.
 constexpr float kTiny2D = 0x1p-30f;
 
-template <int DIM, int R>
+// Kahan step with the product fused into the compensated term: y = k x - c in one FFMA.
+__device__ __forceinline__ void kahan_fma(float k, float xv, float &acc, float &cmp) {
+    const float y = __fmaf_rn(k, xv, -cmp);
+    const float t = __fadd_rn(acc, y);
+    cmp = __fsub_rn(__fsub_rn(t, acc), y);
+    acc = t;
+}
+
+// CONSEC: the R rows of a thread are consecutive points of one grid line (n % R == 0), so the
+// offsets along the slow axes are shared by the R pairs of a source point:
+//   2D per pair: FADD (dy), FFMA (dy^2 + dx^2 + 2^-30), MUFU.LG2, FFMA + 3 FADD (Kahan).
+template <int DIM, int R, bool CONSEC>
 __global__ void __launch_bounds__(kThreads)
 k1_matvec_f32(const float4 *__restrict__ coord, const double *__restrict__ x, long long N,
               int tiles_per_split, int ntiles, double *__restrict__ partial) {
     __shared__ float4 sc[kThreads];
-    const long long row0 = (long long)blockIdx.x * (kThreads * R) + threadIdx.x;
+    const long long row0 = (long long)blockIdx.x * (kThreads * R);
+    auto row_of = [&](int r) -> long long {
+        return CONSEC ? row0 + (long long)threadIdx.x * R + r : row0 + threadIdx.x + (long long)r * kThreads;
+    };
     float px[R], py[R], pz[R], acc[R], cmp[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        long long i = row0 + (long long)r * kThreads;
+        const long long i = row_of(r);
         float4 c = i < N ? coord[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         px[r] = c.x; py[r] = c.y; pz[r] = c.z; acc[r] = 0.f; cmp[r] = 0.f;
     }
@@ -99,28 +113,44 @@ k1_matvec_f32(const float4 *__restrict__ coord, const double *__restrict__ x, lo
 #pragma unroll 8
         for (int jj = 0; jj < kThreads; ++jj) {
             const float4 s = sc[jj];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float dx = px[r] - s.x, dy = py[r] - s.y;
-                float k;
+            if (CONSEC) {
                 if (DIM == 2) {
-                    k = __log2f(fmaf(dx, dx, fmaf(dy, dy, kTiny2D)));
+                    const float dx = px[0] - s.x;
+                    const float dxx = __fmaf_rn(dx, dx, kTiny2D);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float dy = py[r] - s.y;
+                        kahan_fma(__log2f(__fmaf_rn(dy, dy, dxx)), s.w, acc[r], cmp[r]);
+                    }
                 } else {
-                    float dz = pz[r] - s.z;
-                    k = rsqrtf(fmaxf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), 1.0f));
+                    const float dx = px[0] - s.x, dy = py[0] - s.y;
+                    const float dxy = __fmaf_rn(dx, dx, dy * dy);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float dz = pz[r] - s.z;
+                        kahan_fma(rsqrtf(fmaxf(__fmaf_rn(dz, dz, dxy), 1.0f)), s.w, acc[r], cmp[r]);
+                    }
                 }
-                const float term = __fmul_rn(k, s.w);
-                const float y = __fsub_rn(term, cmp[r]);
-                const float tt = __fadd_rn(acc[r], y);
-                cmp[r] = __fsub_rn(__fsub_rn(tt, acc[r]), y);
-                acc[r] = tt;
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float dx = px[r] - s.x, dy = py[r] - s.y;
+                    float k;
+                    if (DIM == 2) {
+                        k = __log2f(fmaf(dx, dx, fmaf(dy, dy, kTiny2D)));
+                    } else {
+                        const float dz = pz[r] - s.z;
+                        k = rsqrtf(fmaxf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), 1.0f));
+                    }
+                    kahan_fma(k, s.w, acc[r], cmp[r]);
+                }
             }
         }
     }
     double *out = partial + (long long)blockIdx.y * N;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        long long i = row0 + (long long)r * kThreads;
+        const long long i = row_of(r);
         if (i < N) out[i] = (double)acc[r] - (double)cmp[r];
     }
 }
@@ -260,7 +290,7 @@ __global__ void combine_kernel(const TP *__restrict__ partial, int nsplit, const
     if (dim == 2) {
         // mode 0 (FP32 sums of log2(|D|^2 + 2^-30)): c_sum = c_log2, the i = j pair added
         // log2(2^-30) x_i; mode 1 (FP64 ln of max(|D|^2, 1)): c_sum = c_ln, the pair added 0
-        const double self = mode == 0 ? (double)__fmul_rn(__log2f(kTiny2D), (float)xi) : 0.0;
+        const double self = mode == 0 ? (double)__log2f(kTiny2D) * (double)(float)xi : 0.0;
         y0 = diag * xi + c_const * (xsum[0] - xi) + c_sum * (s - self);
     } else {
         // the clamped i = j pair added rsqrt(1) * x_i (rounded as the kernel saw it)
@@ -338,22 +368,34 @@ __device__ __forceinline__ void df_fma(float th, float tl, float xh, float xl, f
 }
 
 // 2D: a CTA owns a 16 x 64 patch of target points and walks over 16 x 64 patches of source
-// points.  Per source patch it stages x (hi/lo) and the 31 x 127 window of table entries that
-// the offsets between the two patches can reach.  Thread (t1, t2) owns the rows (t1, t2 + 16 k),
+// points.  Per source patch it stages x and the 31 x 127 window of table entries that the
+// offsets between the two patches can reach.  Thread (t1, t2) owns the rows (t1, t2 + 16 k),
 // k = 0..3.  Because the entry depends only on the offset, the entries that row k needs for
 // source column c0 + 16 m are the window values at (t2 - c0) + 16 (k - m): for each (c1, c0)
-// the thread loads 7 window values and 4 x values and does 16 pairs (Toeplitz register reuse),
-// so shared-memory traffic stays well below the 12 FP32 operations of each double-float pair.
+// the thread loads 7 window values and 4 x values and does 16 pairs (Toeplitz register reuse).
+//
+// Exact accumulation in 6 FP32 operations per pair.  Each 64-term window of a row starts its
+// high word at a power of two M >= 2 * (64 max|t_hi| max|x_hi| over the window), so |high| >=
+// |product| holds throughout and Fast2Sum is exact: with p = fl(t_hi x_hi), s = fl(high + p),
+// z = s - high (exact), the rounding errors of both the product and the sum are
+// t_hi x_hi - z, which one FMA returns.  The low word collects that, t_lo x_hi (and t_hi x_lo
+// when x carries a low part) and is renormalised into the high word every RENORM steps; the
+// window is flushed to FP64 as (high - M) + low (exact subtraction by Sterbenz).
+// XSPLIT = false is used inside PCG, whose search directions are rounded to FP32.
 constexpr int kP1 = 16, kP2 = 64;
 
+template <bool XSPLIT, int RENORM>
 __global__ void __launch_bounds__(kThreads)
 k2_accurate_2d(const float2 *__restrict__ table, const double *__restrict__ x, int n,
                int patches_per_split, double *__restrict__ partial) {
     __shared__ float2 W[2 * kP1 - 1][2 * kP2];
     __shared__ float2 X[kP1][kP2];
+    __shared__ float wmax[2 * kP1 - 1];
+    __shared__ float xmax[kP1];
     const int np1 = (n + kP1 - 1) / kP1, np2 = (n + kP2 - 1) / kP2;
     const int I1 = (blockIdx.x / np2) * kP1, I2 = (blockIdx.x % np2) * kP2;
     const int t1 = threadIdx.x >> 4, t2 = threadIdx.x & 15;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long N = (long long)n * n;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     const int q0 = blockIdx.y * patches_per_split;
@@ -366,7 +408,7 @@ k2_accurate_2d(const float2 *__restrict__ table, const double *__restrict__ x, i
             const int j1 = J1 + c1, j2 = J2 + c2;
             const double v = (j1 < n && j2 < n) ? x[(long long)j1 * n + j2] : 0.0;
             const float h = (float)v;
-            X[c1][c2] = make_float2(h, (float)(v - (double)h));
+            X[c1][c2] = make_float2(h, XSPLIT ? (float)(v - (double)h) : 0.f);
         }
         for (int e = threadIdx.x; e < (2 * kP1 - 1) * (2 * kP2 - 1); e += kThreads) {
             const int a = e / (2 * kP2 - 1), b = e % (2 * kP2 - 1);
@@ -375,10 +417,29 @@ k2_accurate_2d(const float2 *__restrict__ table, const double *__restrict__ x, i
             W[a][b] = table[(long long)d1 * n + d2];
         }
         __syncthreads();
+        // per-row maxima of |x_hi| (16 rows of 64) and |t_hi| (31 rows of 127)
+        for (int r = warp; r < kP1; r += kThreads / 32) {
+            float v = fmaxf(fabsf(X[r][lane].x), fabsf(X[r][lane + 32].x));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (lane == 0) xmax[r] = v;
+        }
+        for (int r = warp; r < 2 * kP1 - 1; r += kThreads / 32) {
+            float v = 0.f;
+            for (int b = lane; b < 2 * kP2 - 1; b += 32) v = fmaxf(v, fabsf(W[r][b].x));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (lane == 0) wmax[r] = v;
+        }
+        __syncthreads();
         for (int c1 = 0; c1 < kP1; ++c1) {
-            const float2 *Wa = W[t1 - c1 + kP1 - 1];
+            const int a = t1 - c1 + kP1 - 1;
+            const float2 *Wa = W[a];
             const float2 *Xc = X[c1];
-            float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+            int ex;
+            frexpf(64.f * wmax[a] * xmax[c1], &ex);
+            const float M = ldexpf(1.f, ex + 1);  // >= 2 * bound, a power of two
+            float sh[4] = {M, M, M, M}, sl[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 2
             for (int c0 = 0; c0 < 16; ++c0) {
                 const int base = t2 - c0 + kP2 - 1;
@@ -388,21 +449,31 @@ k2_accurate_2d(const float2 *__restrict__ table, const double *__restrict__ x, i
 #pragma unroll
                 for (int m = 0; m < 4; ++m) xv[m] = Xc[c0 + 16 * m];
 #pragma unroll
-                for (int m = 0; m < 4; ++m)
+                for (int m = 0; m < 4; ++m) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        df_fma(w[k - m + 3].x, w[k - m + 3].y, xv[m].x, xv[m].y, sh[k], sl[k]);
-                // renormalise (Fast2Sum) so the low word stays below an ulp of the high word
+                    for (int k = 0; k < 4; ++k) {
+                        const float th = w[k - m + 3].x, tl = w[k - m + 3].y, xh = xv[m].x;
+                        const float pr = __fmul_rn(th, xh);
+                        const float sn = __fadd_rn(sh[k], pr);
+                        const float z = __fsub_rn(sn, sh[k]);
+                        const float d = __fmaf_rn(th, xh, -z);
+                        float lo = __fmaf_rn(tl, xh, sl[k]);
+                        if (XSPLIT) lo = __fmaf_rn(th, xv[m].y, lo);
+                        sl[k] = __fadd_rn(lo, d);
+                        sh[k] = sn;
+                    }
+                }
+                if ((c0 + 1) % RENORM == 0) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float t = __fadd_rn(sh[k], sl[k]);
-                    sl[k] = __fsub_rn(sl[k], __fsub_rn(t, sh[k]));
-                    sh[k] = t;
+                    for (int k = 0; k < 4; ++k) {
+                        const float t = __fadd_rn(sh[k], sl[k]);
+                        sl[k] = __fsub_rn(sl[k], __fsub_rn(t, sh[k]));
+                        sh[k] = t;
+                    }
                 }
             }
-            // flush the 64-term double-float partial sums to FP64
 #pragma unroll
-            for (int k = 0; k < 4; ++k) acc[k] += (double)sh[k] + (double)sl[k];
+            for (int k = 0; k < 4; ++k) acc[k] += (double)__fsub_rn(sh[k], M) + (double)sl[k];
         }
     }
     const int i1 = I1 + t1;
@@ -506,7 +577,7 @@ int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, doubl
     const long long N = p->N;
     const int ntiles = (int)((N + kThreads - 1) / kThreads);
     DevBuf xsum;
-    if (p->dim == 2 && precision != IE_ACCURATE) {
+    if (p->dim == 2 && (precision == IE_MIXED || precision == IE_FP64)) {
         DevBuf part;
         IE_TRY(part.alloc(sizeof(double) * iedd::kRedBlocks * nrhs, s));
         IE_TRY(xsum.alloc(sizeof(double) * nrhs, s));
@@ -556,10 +627,15 @@ int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, doubl
             const int Se = (ntiles + tps - 1) / tps;
             DevBuf part;
             IE_TRY(part.alloc(sizeof(double) * N * Se, s));
-            if (p->dim == 2)
-                k1_matvec_f32<2, R><<<dim3(rt, Se), kThreads, 0, s>>>(p->d_coord, xk, N, tps, ntiles, part.as<double>());
+            const bool consec = p->n % R == 0;
+            if (p->dim == 2 && consec)
+                k1_matvec_f32<2, R, true><<<dim3(rt, Se), kThreads, 0, s>>>(p->d_coord, xk, N, tps, ntiles, part.as<double>());
+            else if (p->dim == 2)
+                k1_matvec_f32<2, R, false><<<dim3(rt, Se), kThreads, 0, s>>>(p->d_coord, xk, N, tps, ntiles, part.as<double>());
+            else if (consec)
+                k1_matvec_f32<3, R, true><<<dim3(rt, Se), kThreads, 0, s>>>(p->d_coord, xk, N, tps, ntiles, part.as<double>());
             else
-                k1_matvec_f32<3, R><<<dim3(rt, Se), kThreads, 0, s>>>(p->d_coord, xk, N, tps, ntiles, part.as<double>());
+                k1_matvec_f32<3, R, false><<<dim3(rt, Se), kThreads, 0, s>>>(p->d_coord, xk, N, tps, ntiles, part.as<double>());
             IE_LAUNCHED();
             combine_kernel<double><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(
                 part.as<double>(), Se, xk, yk, N, p->dim, 0, p->diag, p->c_const,
@@ -598,8 +674,10 @@ int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, doubl
             const int Se = (npatch + pps - 1) / pps;
             DevBuf part;
             IE_TRY(part.alloc(sizeof(double) * N * Se, s));
-            if (p->dim == 2)
-                k2_accurate_2d<<<dim3(rowpatch, Se), kThreads, 0, s>>>(p->d_table, xk, n, pps, part.as<double>());
+            if (p->dim == 2 && precision == IE_ACCURATE)
+                k2_accurate_2d<true, 1><<<dim3(rowpatch, Se), kThreads, 0, s>>>(p->d_table, xk, n, pps, part.as<double>());
+            else if (p->dim == 2)
+                k2_accurate_2d<false, 2><<<dim3(rowpatch, Se), kThreads, 0, s>>>(p->d_table, xk, n, pps, part.as<double>());
             else
                 k2_accurate_3d<<<dim3(rowpatch, Se), kThreads, 0, s>>>(p->d_table, xk, n, pps, part.as<double>());
             IE_LAUNCHED();

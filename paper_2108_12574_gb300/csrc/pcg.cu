@@ -104,14 +104,18 @@ __global__ void k_beta(PcgCol *st, const double *rz_new, int nrhs, int first) {
     st[k].rz = v;
 }
 
-// p = z + beta p  (active columns); first: p = z
-__global__ void k_pupdate(double *p, const double *z, long long N, const PcgCol *st, int first) {
+// p = z + beta p  (active columns); first: p = z.  round32: the direction is rounded to FP32
+// (the exact double-float inner matvec then needs no low word for it; a rounded search
+// direction is still a valid direction for the u and r updates, which stay in FP64).
+__global__ void k_pupdate(double *p, const double *z, long long N, const PcgCol *st, int first, int round32) {
     const int k = blockIdx.y;
     if (st[k].active != 1) return;
     const double b = st[k].beta;
     const long long off = (long long)k * N;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-        p[off + i] = first ? z[off + i] : fma(b, p[off + i], z[off + i]);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const double v = first ? z[off + i] : fma(b, p[off + i], z[off + i]);
+        p[off + i] = round32 ? (double)__double2float_rn(v) : v;
+    }
 }
 
 // r = f - q for one column (or all columns when k < 0)
@@ -235,9 +239,11 @@ struct Solver {
     }
     int mv_precision() const {
         if (o.precision == IE_FP64) return IE_FP64;
-        if (o.inner == IE_MIXED || o.inner == IE_ACCURATE) return o.inner;
-        return IE_MIXED;
+        if (o.inner == IE_MIXED) return IE_MIXED;
+        if (o.inner == IE_ACCURATE) return IE_ACCURATE_X32;
+        return p->dim == 2 ? IE_ACCURATE_X32 : IE_MIXED;
     }
+    bool exact_inner() const { return mv_precision() == IE_ACCURATE_X32 || mv_precision() == IE_FP64; }
     int acc_precision() const { return o.precision == IE_FP64 ? IE_FP64 : IE_ACCURATE; }
     dim3 vg() const { return dim3(vgrid, nrhs); }
 
@@ -261,7 +267,7 @@ struct Solver {
         IE_TRY(launch_dots(r, N, z, N, N, nrhs, rz, s));
         k_beta<<<(nrhs + 63) / 64, 64, 0, s>>>(st, rz, nrhs, first);
         IE_LAUNCHED();
-        k_pupdate<<<vg(), 256, 0, s>>>(pp, z, N, st, first);
+        k_pupdate<<<vg(), 256, 0, s>>>(pp, z, N, st, first, mv_precision() == IE_ACCURATE_X32 ? 1 : 0);
         IE_LAUNCHED();
         return IE_OK;
     }
@@ -416,7 +422,7 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
                 bool pending = c.flag == 1;
                 bool due = c.active == 1 &&
                            ((o.replace_every > 0 && c.it > 0 && c.it % o.replace_every == 0) ||
-                            relres <= kReplaceDrop * relres_at_replace[(size_t)k]);
+                            (!S.exact_inner() && relres <= kReplaceDrop * relres_at_replace[(size_t)k]));
                 if (!pending && !due) continue;
                 double rr_true = 0;
                 IE_TRY(S.accurate_residual(k, &rr_true));
