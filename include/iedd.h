@@ -171,11 +171,15 @@ typedef struct {
     double timeout_s;    /* wall-clock budget (0: none); exceeded -> IE_ERR_TIMEOUT                */
     int check_every;     /* IE_FP64: iterations per CUDA-graph launch between host checks (>= 1)  */
     int verify;          /* IE_FP64: 1 = compute the true residual at the end (one more matvec)    */
-    int inner;           /* IE_MIXED: matvec inside the iteration: IE_MIXED (FP32 SFU entries,
-                            compensated FP32 sums), IE_ACCURATE (double-float table sums on the
-                            FP32 pipes; the search directions are then rounded to
-                            FP32), or 0 = the library's choice (IE_ACCURATE in 2D, IE_MIXED
-                            in 3D)       */
+    int inner;           /* matvec inside the iteration (q = A p):
+                              0            the library's choice: IE_FP64 precision -> the FP64
+                                           regenerated matvec; IE_MIXED -> IE_ACCURATE in 2D,
+                                           IE_MIXED in 3D
+                              IE_MIXED     FP32 SFU entries with compensated FP32 sums
+                              IE_ACCURATE  double-float table sums on the FP32 pipes
+                              4            as IE_ACCURATE with the search directions rounded to
+                                           FP32 (one FFMA less per pair, more iterations)
+                              16           the FP64 regenerated matvec in either precision */
 } pcg_opts;
 
 typedef struct {

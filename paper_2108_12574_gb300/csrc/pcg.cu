@@ -238,12 +238,12 @@ struct Solver {
         return IE_OK;
     }
     int mv_precision() const {
+        if (o.inner == IE_FP64 + 16) return IE_FP64;
+        if (o.inner == IE_MIXED || o.inner == IE_ACCURATE || o.inner == IE_ACCURATE_X32) return o.inner;
         if (o.precision == IE_FP64) return IE_FP64;
-        if (o.inner == IE_MIXED) return IE_MIXED;
-        if (o.inner == IE_ACCURATE) return IE_ACCURATE_X32;
-        return p->dim == 2 ? IE_ACCURATE_X32 : IE_MIXED;
+        return p->dim == 2 ? IE_ACCURATE : IE_MIXED;
     }
-    bool exact_inner() const { return mv_precision() == IE_ACCURATE_X32 || mv_precision() == IE_FP64; }
+    bool exact_inner() const { return mv_precision() != IE_MIXED; }
     int acc_precision() const { return o.precision == IE_FP64 ? IE_FP64 : IE_ACCURATE; }
     dim3 vg() const { return dim3(vgrid, nrhs); }
 
@@ -334,7 +334,8 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
     if (opts) o = *opts; else pcg_default_opts(&o);
     if (!(o.tol >= 0.0) || o.max_it < 1 || (o.precision != IE_FP64 && o.precision != IE_MIXED) ||
         o.replace_every < 0 || o.check_every < 0 ||
-        (o.inner != 0 && o.inner != IE_MIXED && o.inner != IE_ACCURATE)) {
+        (o.inner != 0 && o.inner != IE_MIXED && o.inner != IE_ACCURATE && o.inner != IE_ACCURATE_X32 &&
+         o.inner != IE_FP64 + 16)) {
         ie_set_error("pcg_solve: invalid options"); return IE_ERR_ARG;
     }
     if (o.check_every < 1) o.check_every = 1;
