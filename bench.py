@@ -49,7 +49,40 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64-plain and CPU-baseline legs")
+    ap.add_argument("--kernel", choices=["k1", "k2", "kd", "apply", "factor"], default=None,
+                    help="profiling case: run one hot operation twice on a --dim/--n/--nrhs problem and exit")
+    ap.add_argument("--dim", type=int, default=DIM)
+    ap.add_argument("--n", type=int, default=NGRID)
+    ap.add_argument("--nrhs", type=int, default=1)
     return ap.parse_args()
+
+
+def kernel_case(args):
+    """A single hot operation, launched twice (warm-up + the one to capture with ncu -s/-c)."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2108_12574_gb300 import iedd
+    from paper_2108_12574_gb300 import inputs as I
+
+    N = args.n ** args.dim
+    prob = iedd.ie_discretize(args.dim, args.n)
+    X = torch.from_numpy(I.uniform_rhs_batch(N, range(args.nrhs)).T.copy()).cuda()
+    Y = torch.zeros_like(X)
+    m = args.n // 16 if args.dim == 2 else args.n // 8
+    for _ in range(2):
+        if args.kernel in ("k1", "k2", "kd"):
+            prec = {"k1": iedd.IE_MIXED, "k2": iedd.IE_ACCURATE, "kd": iedd.IE_FP64}[args.kernel]
+            iedd.ie_matvec(prob, X, Y, prec)
+        else:
+            part = iedd.dd_partition(prob, m, 2 if args.dim == 2 else 1, iedd.DD_SCHWARZ)
+            fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
+            if args.kernel == "apply":
+                iedd.dd_apply(fac, X, Y)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": args.kernel, "dim": args.dim, "n": args.n, "nrhs": args.nrhs, "ok": True}))
+    return 0
 
 
 def config_dict():
@@ -179,6 +212,8 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------
 def main():
     args = parse()
+    if args.kernel:
+        return kernel_case(args)
     if args.impl == "reference":
         return run_reference(args)
     import numpy as np
