@@ -199,6 +199,29 @@ typedef struct {
     double accurate_ms;      /* summed device time of those                                     */
 } pcg_report;
 
+/*
+ * ie_matvec_noalloc -- y = A x with the FP32 SFU matvec (the kernel ie_matvec runs for IE_MIXED,
+ * same accuracy), for callers that cannot allocate device memory: code that runs where
+ * cudaMalloc is forbidden or unsafe (inside an allocator or a memory-capped host framework,
+ * or after all memory was reserved up front).  The paper has no counterpart of this call.
+ *   dim, n, a_shift, grid   as ie_discretize (no problem handle is needed: the point
+ *                           coordinates are derived from the grid index); N = n^dim must be
+ *                           <= IE_NOALLOC_MAX_N, else IE_ERR_ARG with a message
+ *   x, y                    device FP64 vectors of length N (one right-hand side); host pointers
+ *                           are rejected with IE_ERR_ARG (staging them would allocate)
+ *   stream                  cudaStream_t (NULL: legacy default stream); the call is asynchronous
+ * It allocates nothing: no cudaMalloc, cudaFree or allocating library routine.  Its scratch is one
+ * file-scope device array of IE_NOALLOC_SCRATCH_BYTES, present on every GPU that loads the
+ * library until the process exits.  The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress, with that device current); make that first call before any stream
+ * capture.  All calls share the array: calls whose GPU work overlaps (other streams, other
+ * threads) race and must be ordered by the caller.
+ */
+#define IE_NOALLOC_SCRATCH_BYTES (32LL << 20)
+#define IE_NOALLOC_MAX_N (4194304LL - 1024LL)
+IEDD_API int ie_matvec_noalloc(int dim, int n, double a_shift, int grid, const double *x, double *y,
+                               void *stream);
+
 /* Instrumentation: number of kernels this library has launched in this process (a CUDA-graph
  * replay counts the kernel nodes of the graph); reset != 0 returns the count and zeroes it. */
 IEDD_API long long ie_kernel_launches(int reset);

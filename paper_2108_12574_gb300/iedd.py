@@ -28,7 +28,9 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "lib
 # Every C-ABI symbol declared in include/iedd.h.
 EXPORTS = ("ie_last_error", "ie_version", "ie_discretize", "ie_problem_info", "ie_destroy", "ie_matvec",
            "dd_partition", "dd_partition_info", "dd_partition_export", "dd_partition_destroy", "dd_factor",
-           "dd_factor_destroy", "dd_apply", "ie_kernel_launches", "pcg_default_opts", "pcg_solve")
+           "dd_factor_destroy", "dd_apply", "ie_kernel_launches", "pcg_default_opts", "pcg_solve",
+           "ie_matvec_noalloc")
+IE_NOALLOC_MAX_N = 4194304 - 1024
 
 
 class IEError(RuntimeError):
@@ -82,6 +84,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dd_factor_destroy": (None, [vp]),
         "dd_apply": (i, [vp, vp, vp, i, ll, vp]),
         "ie_kernel_launches": (ll, [i]),
+        "ie_matvec_noalloc": (i, [i, i, d, i, vp, vp, vp]),
         "pcg_default_opts": (None, [P(PcgOpts)]),
         "pcg_solve": (i, [vp, vp, vp, vp, i, ll, P(PcgOpts), P(PcgReport), vp]),
     }
@@ -251,6 +254,17 @@ def dd_apply(fac: Factor, r, z, stream=None):
         raise ValueError("r and z must have the same shape and stride")
     _check(load_library().dd_apply(fac.ptr, pr, pz, k, ld, _stream(stream)))
     return z
+
+
+def ie_matvec_noalloc(dim: int, n: int, x, y, a_shift: float = 0.0, grid: int = IE_GRID_TEXT, stream=None):
+    """y = A x (FP32 SFU kernel) with no device allocation; x, y: CUDA FP64 vectors of length n^dim."""
+    N = n ** dim
+    px, k, _, _kx = _vec(x, N)
+    py, k2, _, _ky = _vec(y, N, writable=True)
+    if k != 1 or k2 != 1:
+        raise ValueError("ie_matvec_noalloc takes one right-hand side")
+    _check(load_library().ie_matvec_noalloc(dim, n, a_shift, grid, px, py, _stream(stream)))
+    return y
 
 
 def ie_kernel_launches(reset: bool = False) -> int:
