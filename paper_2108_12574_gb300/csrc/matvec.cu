@@ -44,7 +44,8 @@ __global__ void coord_kernel(float4 *coord, int dim, int n, long long N) {
     coord[i] = make_float4(c[0], c[1], c[2], 0.f);
 }
 
-// Entry for every |offset| (d_1, ..., d_dim) in [0, n)^dim, FP64, and its hi/lo FP32 split.
+// Entry for every |offset| (d_1, ..., d_dim) in [0, n)^dim, FP64, and its hi/lo FP32 split
+// (zero at offset 0: see below).
 __global__ void table_kernel(float2 *t32, double *t64, int dim, int n, long long T, double diag,
                              double c_const, double c_ln, double c_r) {
     long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -58,7 +59,9 @@ __global__ void table_kernel(float2 *t32, double *t64, int dim, int n, long long
     else e = c_r / sqrt(r2);
     float hi = (float)e;
     float lo = (float)(e - (double)hi);
-    t32[q] = make_float2(hi, lo);
+    // the double-float table leaves the diagonal out (it is added in FP64 by the final sum), so a
+    // large diagonal (second-kind shift) does not coarsen the accumulation windows
+    t32[q] = r2 == 0.0 ? make_float2(0.f, 0.f) : make_float2(hi, lo);
     t64[q] = e;
 }
 
@@ -380,7 +383,9 @@ __device__ __forceinline__ void df_fma(float th, float tl, float xh, float xl, f
 // z = s - high (exact), the rounding errors of both the product and the sum are
 // t_hi x_hi - z, which one FMA returns.  The low word collects that, t_lo x_hi (and t_hi x_lo
 // when x carries a low part) and is renormalised into the high word every RENORM steps; the
-// window is flushed to FP64 as (high - M) + low (exact subtraction by Sterbenz).
+// window's value (high - M) + low (exact subtraction by Sterbenz) is added to a double-float
+// patch sum with TwoSum, and the patch sum to FP64 once per source patch (1024 columns).
+// The diagonal is not in the table (added in FP64 afterwards), so the offsets M stay small.
 // XSPLIT = false is used inside PCG, whose search directions are rounded to FP32.
 constexpr int kP1 = 16, kP2 = 64;
 
@@ -402,6 +407,7 @@ k2_accurate_2d(const float2 *__restrict__ table, const double *__restrict__ x, i
     const int q1 = min(q0 + patches_per_split, np1 * np2);
     for (int q = q0; q < q1; ++q) {
         const int J1 = (q / np2) * kP1, J2 = (q % np2) * kP2;
+        float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};  // patch sums (double-float)
         __syncthreads();
         for (int e = threadIdx.x; e < kP1 * kP2; e += kThreads) {
             const int c1 = e / kP2, c2 = e % kP2;
@@ -472,9 +478,19 @@ k2_accurate_2d(const float2 *__restrict__ table, const double *__restrict__ x, i
                     }
                 }
             }
+            // add the window ((high - M) exactly, + low) to the patch sum with TwoSum
 #pragma unroll
-            for (int k = 0; k < 4; ++k) acc[k] += (double)__fsub_rn(sh[k], M) + (double)sl[k];
+            for (int k = 0; k < 4; ++k) {
+                const float wv = __fsub_rn(sh[k], M);
+                const float sn = __fadd_rn(ah[k], wv);
+                const float bp = __fsub_rn(sn, ah[k]);
+                const float er = __fadd_rn(__fsub_rn(ah[k], __fsub_rn(sn, bp)), __fsub_rn(wv, bp));
+                al[k] = __fadd_rn(al[k], __fadd_rn(er, sl[k]));
+                ah[k] = sn;
+            }
         }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k] += (double)ah[k] + (double)al[k];
     }
     const int i1 = I1 + t1;
     if (i1 < n) {
@@ -536,13 +552,14 @@ k2_accurate_3d(const float2 *__restrict__ table, const double *__restrict__ x, i
     if (i1 < n && i2 < n && i3 < n) partial[(long long)blockIdx.y * N + ((long long)i1 * n + i2) * n + i3] = acc;
 }
 
-__global__ void sum_splits_kernel(const double *__restrict__ partial, int nsplit, double *__restrict__ y,
-                                  long long N) {
+// y_i = diag x_i + the split partial sums of the off-diagonal pairs (FP64).
+__global__ void sum_splits_kernel(const double *__restrict__ partial, int nsplit, const double *__restrict__ x,
+                                  double diag, double *__restrict__ y, long long N) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     double s = 0.0;
     for (int k = 0; k < nsplit; ++k) s += partial[(long long)k * N + i];
-    y[i] = s;
+    y[i] = fma(diag, x[i], s);
 }
 
 int splits_for(long long items, long long work_units, int sm_count, int per_sm) {
@@ -681,7 +698,7 @@ int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, doubl
             else
                 k2_accurate_3d<<<dim3(rowpatch, Se), kThreads, 0, s>>>(p->d_table, xk, n, pps, part.as<double>());
             IE_LAUNCHED();
-            sum_splits_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(part.as<double>(), Se, yk, N);
+            sum_splits_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(part.as<double>(), Se, xk, p->diag, yk, N);
             IE_LAUNCHED();
         }
     }

