@@ -242,11 +242,7 @@ def main():
         torch.cuda.synchronize(dev)
 
     def reduce_max(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(v, dist, dev)
 
     N = NGRID ** DIM
     f_host = I.grf(DIM, NGRID, ELL, rank)
@@ -337,6 +333,16 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def max_over_ranks(v: float, dist=None, device=None) -> float:
+    """Largest value over the ranks of the default process group (v itself without one)."""
+    if dist is None or not dist.is_initialized():
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def extras(torch, iedd, I, dev, stream, iterations):
