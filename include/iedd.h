@@ -167,7 +167,9 @@ typedef struct {
     int max_it;          /* iteration cap per right-hand side (products q = A p)                  */
     int precision;       /* IE_FP64 or IE_MIXED (the factor may have either precision)            */
     int replace_every;   /* IE_MIXED: replace r by the accurate f - A u every k iterations (0: off) */
-    int use_x0;          /* 1: u holds the initial iterate on entry; 0: start from u = 0           */
+    int use_x0;          /* 1: u holds the initial iterate on entry; 0: start from u = 0;
+                            2: as 1, but a column whose initial residual ||f - A u|| is not
+                            below ||f|| starts from u = 0 instead (warm-start fallback)          */
     double timeout_s;    /* wall-clock budget (0: none); exceeded -> IE_ERR_TIMEOUT                */
     int check_every;     /* IE_FP64: iterations per CUDA-graph launch between host checks (>= 1)  */
     int verify;          /* IE_FP64: 1 = compute the true residual at the end (one more matvec)    */
@@ -186,7 +188,7 @@ typedef struct {
     int iterations;          /* products q = A p for this right-hand side                       */
     int replacements;        /* accurate residual recomputations (IE_MIXED)                       */
     int status;              /* ie_status of this right-hand side                                 */
-    int pad_;
+    int x0_used;             /* 1 if the column started from the caller's u, 0 if from zero        */
     double recursive_relres; /* ||r_k||_2 / ||f||_2 of the recurrence                             */
     double true_relres;      /* ||f - A u||_2 / ||f||_2 with the accurate matvec (-1 if not run)  */
     /* per-solve device timing (CUDA events around each launch; the same in every column)     */
@@ -221,6 +223,40 @@ typedef struct {
 #define IE_NOALLOC_MAX_N (4194304LL - 1024LL)
 IEDD_API int ie_matvec_noalloc(int dim, int n, double a_shift, int grid, const double *x, double *y,
                                void *stream);
+
+/*
+ * Learned warm start (not in the paper: a production layer on top of the method).  A 4-level
+ * U-Net (encoder 12/24/48/96 channels, 2x2 average pooling, nearest upsampling with skip
+ * concatenation, ReLU, 1x1 output; 274,213 parameters; NHWC; BF16 weights and activations with
+ * FP32 accumulation; FP32 master weights and Adam) maps a 2D right-hand side f to an initial
+ * iterate u0 for pcg_solve (use_x0 = 1).  Inputs: f / rms(f) and the normalised 5-point
+ * Laplacian of f; output scale rms(Laplacian f) / h^2 (u is close to -Laplace(f) inside the
+ * domain).  The grid side must be a multiple of 16.  Parameter vector layout (FP32): for each
+ * layer in order, W[Cout][3][3][Cin] (W[Cout][Cin] for the 1x1) followed by b[Cout].
+ *
+ * ws_create       He-normal initial weights from SplitMix64 (seed), zero biases.
+ * ws_get_params / ws_set_params   copy the FP32 master weights (host arrays of ws_num_params).
+ * ws_forward_raw  in: [B][n][n][2] FP32 (host or device), out: [B][n][n] FP32; B <= 16.
+ * ws_backward_raw gradient of sum(dout * out) with respect to the parameters (FP32, nparams),
+ *                 for the input `in`; no update.
+ * ws_train_step   one Adam step (lr; beta 0.9 / 0.999) on the MSE between the network output and
+ *                 the scaled target u, for `batch` <= 16 device columns of f and u (ld >= N) of a
+ *                 2D problem; *loss (host, may be NULL) receives the loss before the step.
+ * ws_predict      u0 for nrhs device columns of f (ld >= N).  Asynchronous.
+ */
+typedef struct ws_model ws_model;
+IEDD_API int ws_create(int device, unsigned long long seed, ws_model **out);
+IEDD_API void ws_destroy(ws_model *w);
+IEDD_API long long ws_num_params(const ws_model *w);
+IEDD_API int ws_get_params(const ws_model *w, float *host);
+IEDD_API int ws_set_params(ws_model *w, const float *host);
+IEDD_API int ws_forward_raw(ws_model *w, const float *in, float *out, int B, int n, void *stream);
+IEDD_API int ws_backward_raw(ws_model *w, const float *in, const float *dout, float *grad, int B, int n,
+                             void *stream);
+IEDD_API int ws_train_step(ws_model *w, const ie_problem *p, const double *f, const double *u, int batch,
+                           long long ld, float lr, double *loss, void *stream);
+IEDD_API int ws_predict(ws_model *w, const ie_problem *p, const double *f, double *u0, int nrhs, long long ld,
+                        void *stream);
 
 /* Instrumentation: number of kernels this library has launched in this process (a CUDA-graph
  * replay counts the kernel nodes of the graph); reset != 0 returns the count and zeroes it. */

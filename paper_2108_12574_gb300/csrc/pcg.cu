@@ -118,6 +118,22 @@ __global__ void k_pupdate(double *p, const double *z, long long N, const PcgCol 
     }
 }
 
+// Warm-start fallback: a column whose initial residual is not below ||f|| restarts from u = 0
+// (r = f).  rr and ff hold the squared norms of r and f per column.
+__global__ void k_fallback(double *u, double *r, const double *f, double *rr, const double *ff, long long N,
+                           int *used) {
+    const int k = blockIdx.y;
+    const bool bad = !(rr[k] < ff[k]);
+    const long long off = (long long)k * N;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        if (bad) { u[off + i] = 0.0; r[off + i] = f[off + i]; }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        used[k] = bad ? 0 : 1;
+        if (bad) rr[k] = ff[k];
+    }
+}
+
 // r = f - q for one column (or all columns when k < 0)
 __global__ void k_residual(double *r, const double *f, const double *q, long long N) {
     const long long off = (long long)blockIdx.y * N;
@@ -333,7 +349,7 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
     pcg_opts o;
     if (opts) o = *opts; else pcg_default_opts(&o);
     if (!(o.tol >= 0.0) || o.max_it < 1 || (o.precision != IE_FP64 && o.precision != IE_MIXED) ||
-        o.replace_every < 0 || o.check_every < 0 ||
+        o.replace_every < 0 || o.check_every < 0 || o.use_x0 < 0 || o.use_x0 > 2 ||
         (o.inner != 0 && o.inner != IE_MIXED && o.inner != IE_ACCURATE && o.inner != IE_ACCURATE_X32 &&
          o.inner != IE_FP64 + 16)) {
         ie_set_error("pcg_solve: invalid options"); return IE_ERR_ARG;
@@ -365,6 +381,15 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
     IE_TRY_CUDA(cudaMemsetAsync(S.pp, 0, sizeof(double) * N * nrhs, s));
     IE_TRY(launch_dots(S.f, N, S.f, N, N, nrhs, S.ff, s));
     IE_TRY(launch_dots(S.r, N, S.r, N, N, nrhs, S.rr, s));
+    DevBuf used;
+    IE_TRY(used.alloc(sizeof(int) * nrhs, s));
+    if (o.use_x0 == 2) {
+        k_fallback<<<S.vg(), 256, 0, s>>>(S.u, S.r, S.f, S.rr, S.ff, N, used.as<int>());
+        IE_LAUNCHED();
+    } else {
+        IE_TRY_CUDA(cudaMemsetAsync(used.ptr, o.use_x0 ? 0x01 : 0, sizeof(int) * nrhs, s));
+    }
+    std::vector<int> x0_used((size_t)nrhs, 0);
     k_init_state<<<(nrhs + 63) / 64, 64, 0, s>>>(S.st, S.ff, S.rr, o.tol * o.tol, nrhs);
     IE_LAUNCHED();
     IE_TRY(S.tail(1, 0));
@@ -479,6 +504,7 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
     }
     IE_TRY_CUDA(cudaMemcpy2DAsync(u_out, ldb, S.u, rowb, rowb, nrhs,
                                   u_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    IE_TRY_CUDA(cudaMemcpyAsync(x0_used.data(), used.ptr, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
     IE_TRY_CUDA(cudaStreamSynchronize(s));
     int ret = IE_OK;
     for (int k = 0; k < nrhs; ++k) {
@@ -492,7 +518,7 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
             rep[k].iterations = c.it;
             rep[k].replacements = c.replacements;
             rep[k].status = stk;
-            rep[k].pad_ = 0;
+            rep[k].x0_used = o.use_x0 == 2 ? (x0_used[(size_t)k] != 0) : (o.use_x0 ? 1 : 0);
             rep[k].recursive_relres = c.ff > 0 ? std::sqrt(c.rr / c.ff) : 0.0;
             rep[k].true_relres = c.true_relres;
             rep[k].matvecs = S.n_mv;

@@ -29,7 +29,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "lib
 EXPORTS = ("ie_last_error", "ie_version", "ie_discretize", "ie_problem_info", "ie_destroy", "ie_matvec",
            "dd_partition", "dd_partition_info", "dd_partition_export", "dd_partition_destroy", "dd_factor",
            "dd_factor_destroy", "dd_apply", "ie_kernel_launches", "pcg_default_opts", "pcg_solve",
-           "ie_matvec_noalloc")
+           "ie_matvec_noalloc", "ws_create", "ws_destroy", "ws_num_params", "ws_get_params", "ws_set_params",
+           "ws_forward_raw", "ws_backward_raw", "ws_train_step", "ws_predict")
 IE_NOALLOC_MAX_N = 4194304 - 1024
 
 
@@ -47,7 +48,7 @@ class PcgOpts(ctypes.Structure):
 
 class PcgReport(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("replacements", ctypes.c_int), ("status", ctypes.c_int),
-                ("pad_", ctypes.c_int), ("recursive_relres", ctypes.c_double), ("true_relres", ctypes.c_double),
+                ("x0_used", ctypes.c_int), ("recursive_relres", ctypes.c_double), ("true_relres", ctypes.c_double),
                 ("matvecs", ctypes.c_int), ("applies", ctypes.c_int), ("matvec_ms", ctypes.c_double),
                 ("apply_ms", ctypes.c_double), ("accurate_matvecs", ctypes.c_int), ("pad2_", ctypes.c_int),
                 ("accurate_ms", ctypes.c_double)]
@@ -85,6 +86,15 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dd_apply": (i, [vp, vp, vp, i, ll, vp]),
         "ie_kernel_launches": (ll, [i]),
         "ie_matvec_noalloc": (i, [i, i, d, i, vp, vp, vp]),
+        "ws_create": (i, [i, ctypes.c_ulonglong, P(vp)]),
+        "ws_destroy": (None, [vp]),
+        "ws_num_params": (ll, [vp]),
+        "ws_get_params": (i, [vp, vp]),
+        "ws_set_params": (i, [vp, vp]),
+        "ws_forward_raw": (i, [vp, vp, vp, i, i, vp]),
+        "ws_backward_raw": (i, [vp, vp, vp, vp, i, i, vp]),
+        "ws_train_step": (i, [vp, vp, vp, vp, i, ll, ctypes.c_float, P(d), vp]),
+        "ws_predict": (i, [vp, vp, vp, vp, i, ll, vp]),
         "pcg_default_opts": (None, [P(PcgOpts)]),
         "pcg_solve": (i, [vp, vp, vp, vp, i, ll, P(PcgOpts), P(PcgReport), vp]),
     }
@@ -265,6 +275,66 @@ def ie_matvec_noalloc(dim: int, n: int, x, y, a_shift: float = 0.0, grid: int = 
         raise ValueError("ie_matvec_noalloc takes one right-hand side")
     _check(load_library().ie_matvec_noalloc(dim, n, a_shift, grid, px, py, _stream(stream)))
     return y
+
+
+class WarmStartModel(_Handle):
+    """The warm-start U-Net (ws_* calls)."""
+    _destroy = "ws_destroy"
+
+    @property
+    def nparams(self) -> int:
+        return int(load_library().ws_num_params(self.ptr))
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.nparams, dtype=np.float32)
+        _check(load_library().ws_get_params(self.ptr, out.ctypes.data))
+        return out
+
+    def set_params(self, theta) -> None:
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        if theta.size != self.nparams:
+            raise ValueError("wrong parameter count")
+        _check(load_library().ws_set_params(self.ptr, theta.ctypes.data))
+
+    def forward_raw(self, x: np.ndarray, stream=None) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        B, n = x.shape[0], x.shape[1]
+        out = np.zeros((B, n, n), dtype=np.float32)
+        _check(load_library().ws_forward_raw(self.ptr, x.ctypes.data, out.ctypes.data, B, n, _stream(stream)))
+        return out
+
+    def backward_raw(self, x: np.ndarray, dout: np.ndarray, stream=None) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        dout = np.ascontiguousarray(dout, dtype=np.float32)
+        B, n = x.shape[0], x.shape[1]
+        g = np.zeros(self.nparams, dtype=np.float32)
+        _check(load_library().ws_backward_raw(self.ptr, x.ctypes.data, dout.ctypes.data, g.ctypes.data, B, n,
+                                              _stream(stream)))
+        return g
+
+    def train_step(self, prob: Problem, f, u, lr: float, stream=None) -> float:
+        pf, k, ld, _kf = _vec(f, prob.N)
+        pu, k2, ld2, _ku = _vec(u, prob.N)
+        if k != k2 or ld != ld2:
+            raise ValueError("f and u must have the same shape and stride")
+        loss = ctypes.c_double(0.0)
+        _check(load_library().ws_train_step(self.ptr, prob.ptr, pf, pu, k, ld, lr, ctypes.byref(loss),
+                                            _stream(stream)))
+        return loss.value
+
+    def predict(self, prob: Problem, f, u0, stream=None):
+        pf, k, ld, _kf = _vec(f, prob.N)
+        pu, k2, ld2, _ku = _vec(u0, prob.N, writable=True)
+        if k != k2 or ld != ld2:
+            raise ValueError("f and u0 must have the same shape and stride")
+        _check(load_library().ws_predict(self.ptr, prob.ptr, pf, pu, k, ld, _stream(stream)))
+        return u0
+
+
+def ws_create(device: int = 0, seed: int = 0) -> WarmStartModel:
+    out = ctypes.c_void_p()
+    _check(load_library().ws_create(device, seed, ctypes.byref(out)))
+    return WarmStartModel(out)
 
 
 def ie_kernel_launches(reset: bool = False) -> int:

@@ -1,0 +1,83 @@
+"""Pins of the FP64 U-Net oracle (no GPU): the convolution's orientation against shifted
+inputs, pooling/upsampling identities, and every gradient against central finite differences."""
+import numpy as np
+import pytest
+
+from oracle import unet_oracle as U
+
+
+def test_parameter_count():
+    assert U.num_params() == 274213
+
+
+def test_conv3x3_orientation_by_shifts():
+    # a kernel with a single 1 at (dy, dx) copies the input shifted by (dy-1, dx-1)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((1, 6, 7, 1))
+    for dy in range(3):
+        for dx in range(3):
+            W = np.zeros((1, 3, 3, 1))
+            W[0, dy, dx, 0] = 1.0
+            y = U.conv3x3(x, W, np.zeros(1))
+            xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (0, 0)))
+            assert np.array_equal(y, xp[:, dy:dy + 6, dx:dx + 7, :])
+
+
+def test_conv3x3_channel_mixing():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((2, 4, 4, 3))
+    W = np.zeros((2, 3, 3, 3))
+    W[1, 1, 1, 2] = 2.0  # output 1 = 2 * input channel 2, output 0 = bias
+    y = U.conv3x3(x, W, np.array([0.5, -1.0]))
+    assert np.allclose(y[..., 0], 0.5) and np.allclose(y[..., 1], 2 * x[..., 2] - 1.0)
+
+
+def test_pool_upsample_identities():
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((2, 8, 8, 3))
+    assert np.allclose(U.avgpool2(U.upsample2(x)), x)
+    c = np.full((1, 4, 4, 2), 3.5)
+    assert np.allclose(U.avgpool2(c), 3.5)
+
+
+def test_bf16_rounding():
+    assert U.bf16_round(1.0) == 1.0
+    assert U.bf16_round(1.0 + 2 ** -9) == 1.0            # tie -> even
+    assert U.bf16_round(1.0 + 3 * 2 ** -9) == 1.0 + 2 ** -7
+    assert U.bf16_round(-2.5) == -2.5
+
+
+def _loss(theta, x, dout):
+    out, _ = U.forward(theta, x)
+    return float(np.sum(out * dout))
+
+
+def test_gradient_matches_central_differences():
+    rng = np.random.default_rng(3)
+    # He-scaled weights keep activations O(1), so a small step rarely crosses a ReLU kink
+    theta = np.concatenate([np.concatenate([rng.standard_normal(co * k * k * ci) * np.sqrt(2.0 / (k * k * ci)),
+                                            rng.standard_normal(co) * 0.1]) for ci, co, k in U.SPEC])
+    x = rng.standard_normal((1, 16, 16, 2))
+    dout = rng.standard_normal((1, 16, 16))
+    g = U.backward(theta, x, dout)
+    idx = rng.choice(theta.size, 40, replace=False)
+    # make sure every layer's weights and the biases are probed
+    offs = np.cumsum([0] + [co * k * k * ci + co for ci, co, k in U.SPEC])
+    idx = np.concatenate([idx, offs[:-1], offs[1:] - 1])
+    eps = 1e-6
+    gmax = float(np.max(np.abs(g)))
+    for i in idx:
+        t1, t2 = theta.copy(), theta.copy()
+        t1[i] += eps
+        t2[i] -= eps
+        fd = (_loss(t1, x, dout) - _loss(t2, x, dout)) / (2 * eps)
+        assert abs(fd - g[i]) <= 1e-5 * abs(fd) + 1e-8 * gmax, (i, fd, g[i])
+
+
+def test_features_scale_invariant():
+    rng = np.random.default_rng(4)
+    f = rng.standard_normal(16 * 16)
+    a, rl = U.features(f, 16)
+    b, rl2 = U.features(7.0 * f, 16)
+    assert np.allclose(a, b) and np.isclose(rl2, 7.0 * rl)
+    assert np.isclose(np.sqrt(np.mean(a[..., 0] ** 2)), 1.0)
