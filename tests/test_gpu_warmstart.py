@@ -96,7 +96,7 @@ def test_warm_start_fallback_keeps_tolerance():
     assert rep["x0_used"] == 0 and rep["status"] == 0 and rep["true_relres"] <= 1e-8
     # a good one (the solution itself) is used and needs no iteration
     u1 = u0.clone().zero_()
-    iedd.pcg_solve(prob, fac, f, u1, tol=1e-12)
+    iedd.pcg_solve(prob, fac, f, u1, tol=1e-11, precision=iedd.IE_FP64)
     rep = iedd.pcg_solve(prob, fac, f, u1, tol=1e-8, use_x0=2)[0]
     assert rep["x0_used"] == 1 and rep["iterations"] == 0
     assert O.true_relative_residual(2, n, f.cpu().numpy(), u1.cpu().numpy()) <= 1e-8
