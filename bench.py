@@ -327,12 +327,28 @@ def main():
 
     if not args.no_extras and rank == 0:
         line.update(extras(torch, iedd, I, dev, stream, last["iterations"]))
+        line["warm_start"] = warm_start_leg()
         line["cpu_baseline"] = cpu_baseline(last["iterations"], 0)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def warm_start_leg(fields: int = 16):
+    """The learned warm start on its own workload (2D 256^2, Schwarz 16 x 16 partitions, 2-cell
+    overlap): zero-start PCG against U-Net start (ws_predict + pcg_solve with the fallback
+    start) on held-out GRF fields (seeds 0..fields-1), both to a 1e-8 true residual."""
+    from paper_2108_12574_gb300 import warmstart as WS
+    if not os.path.exists(WS.WEIGHTS):
+        return {"unavailable": "trained weights not present"}
+    prob, part, fac = WS.setup()
+    model = WS.load_model()
+    WS.evaluate(model, prob, fac, [fields])  # warm-up
+    s = WS.summarize(WS.evaluate(model, prob, fac, list(range(fields))))
+    s["workload"] = "ie2d_n256_schwarz_m16_d2"
+    return s
 
 
 def max_over_ranks(v: float, dist=None, device=None) -> float:
