@@ -89,6 +89,113 @@ apply_blocks(const TL *__restrict__ pool, const long long *__restrict__ loff, co
     for (int a = tid; a < n; a += 256) zk[a] = (double)Y[a];
 }
 
+// K6m apply_blocks_multi: one CTA per (subdomain, group of R right-hand sides).  The factor is
+// read once per group instead of once per right-hand side: each 32-row step stages 32 x 32
+// tiles of L in shared memory and applies them to all R columns held in shared memory (GEMM
+// updates, thread (row, column group) accumulating 4 columns), then solves the 32 x 32
+// triangle for the R columns (R / 8 columns per warp).  Arithmetic type T: FP64 (R = 16) for
+// FP64 factors and for 2D, FP32 (R = 32) for FP32 factors of 3D problems, whose blocks and
+// operator are well conditioned (cond(A) = O(N^{2/3})) so that FP32 substitution does not slow PCG.
+constexpr int kRM = 16;  // right-hand sides per CTA (FP64 arithmetic); 32 in FP32
+
+template <typename TL, typename T, int R>
+__global__ void __launch_bounds__(256)
+apply_blocks_multi(const TL *__restrict__ pool, const long long *__restrict__ loff, const int *__restrict__ npad,
+                   const int *__restrict__ nb, const long long *__restrict__ offs, const int *__restrict__ idx,
+                   const int *__restrict__ order, const double *__restrict__ r, long long ldr, int nrhs,
+                   double *__restrict__ zbuf, long long total) {
+    extern __shared__ __align__(16) unsigned char ysm_raw[];
+    T *Ysm = reinterpret_cast<T *>(ysm_raw);  // [npad][R]
+    __shared__ T Lt[32][33];
+    constexpr int JQ = R / 8;  // columns per thread in the updates
+    const int b = order[blockIdx.x];
+    const int g0 = blockIdx.y * R;
+    const int np = npad[b], n = nb[b], nt = np / 32;
+    const TL *L = pool + loff[b];
+    const int *id = idx + offs[b];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int e = tid; e < np * R; e += 256) {
+        const int a = e / R, j = e % R;
+        Ysm[e] = (a < n && g0 + j < nrhs) ? (T)r[(long long)(g0 + j) * ldr + id[a]] : T(0);
+    }
+    __syncthreads();
+    // thread layout for the updates: rr = tid / 8 (tile row 0..31), jq = tid % 8 -> columns JQ jq + q
+    const int rr = tid >> 3, jq = tid & 7;
+    // forward: L y = R_i r
+    for (int t = 0; t < nt; ++t) {
+        const int t0 = t * 32;
+        T acc[JQ];
+#pragma unroll
+        for (int q = 0; q < JQ; ++q) acc[q] = T(0);
+        for (int c0 = 0; c0 < t0; c0 += 32) {
+            __syncthreads();
+            for (int e = tid; e < 1024; e += 256) Lt[e >> 5][e & 31] = (T)L[(long long)(t0 + (e >> 5)) * np + c0 + (e & 31)];
+            __syncthreads();
+#pragma unroll 8
+            for (int c = 0; c < 32; ++c) {
+                const T l = Lt[rr][c];
+#pragma unroll
+                for (int q = 0; q < JQ; ++q) acc[q] = fma(l, Ysm[(c0 + c) * R + JQ * jq + q], acc[q]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < JQ; ++q) Ysm[(t0 + rr) * R + JQ * jq + q] -= acc[q];
+        for (int e = tid; e < 1024; e += 256) Lt[e >> 5][e & 31] = (T)L[(long long)(t0 + (e >> 5)) * np + t0 + (e & 31)];
+        __syncthreads();
+        // triangle: warp w solves columns w R/8 .. (w+1) R/8 - 1 (lanes = rows)
+        for (int q = 0; q < JQ; ++q) {
+            const int j = JQ * warp + q;
+            T v = Ysm[(t0 + lane) * R + j];
+            for (int i = 0; i < 32; ++i) {
+                const T yi = __shfl_sync(0xffffffffu, v, i) / Lt[i][i];
+                if (lane == i) v = yi;
+                if (lane > i) v -= Lt[lane][i] * yi;
+            }
+            Ysm[(t0 + lane) * R + j] = v;
+        }
+        __syncthreads();
+    }
+    // backward: L^T z = y
+    for (int t = nt - 1; t >= 0; --t) {
+        const int t0 = t * 32;
+        T acc[JQ];
+#pragma unroll
+        for (int q = 0; q < JQ; ++q) acc[q] = T(0);
+        for (int r0 = t0 + 32; r0 < np; r0 += 32) {
+            __syncthreads();
+            for (int e = tid; e < 1024; e += 256) Lt[e >> 5][e & 31] = (T)L[(long long)(r0 + (e >> 5)) * np + t0 + (e & 31)];
+            __syncthreads();
+#pragma unroll 8
+            for (int qq = 0; qq < 32; ++qq) {
+                const T l = Lt[qq][rr];  // L[r0 + qq][t0 + rr]
+#pragma unroll
+                for (int q = 0; q < JQ; ++q) acc[q] = fma(l, Ysm[(r0 + qq) * R + JQ * jq + q], acc[q]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < JQ; ++q) Ysm[(t0 + rr) * R + JQ * jq + q] -= acc[q];
+        for (int e = tid; e < 1024; e += 256) Lt[e >> 5][e & 31] = (T)L[(long long)(t0 + (e >> 5)) * np + t0 + (e & 31)];
+        __syncthreads();
+        for (int q = 0; q < JQ; ++q) {
+            const int j = JQ * warp + q;
+            T v = Ysm[(t0 + lane) * R + j];
+            for (int i = 31; i >= 0; --i) {
+                const T zi = __shfl_sync(0xffffffffu, v, i) / Lt[i][i];
+                if (lane == i) v = zi;
+                if (lane < i) v -= Lt[i][lane] * zi;
+            }
+            Ysm[(t0 + lane) * R + j] = v;
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < n * R; e += 256) {
+        const int a = e / R, j = e % R;
+        if (g0 + j < nrhs) zbuf[(long long)(g0 + j) * total + offs[b] + a] = (double)Ysm[e];
+    }
+}
+
 __global__ void overlap_sum(const double *__restrict__ zbuf, long long total, const long long *__restrict__ inv_ptr,
                             const long long *__restrict__ inv_pos, double *__restrict__ z, long long ldz, long long N) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -105,6 +212,12 @@ __global__ void overlap_sum(const double *__restrict__ zbuf, long long total, co
 // Raise the dynamic shared-memory limit of the apply kernel for large subdomains (done once per
 // factor, outside any stream capture).
 int prepare_apply(const dd_factor_t *f) {
+    const size_t smm = sizeof(double) * f->max_pad * kRM;  // = 4 * max_pad * 32 for the FP32 variant
+    if (smm > 48 * 1024 && smm <= 200 * 1024) {
+        IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks_multi<double, double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
+        IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks_multi<float, double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
+        IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks_multi<float, float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
+    }
     const size_t sm = sizeof(double) * f->max_pad;
     if (sm > 48 * 1024) {
         if (f->precision == IE_FP64)
@@ -121,7 +234,26 @@ int launch_apply(const dd_factor_t *f, const double *r, long long ldr, double *z
     const dd_partition_t *part = f->part;
     DevBuf zbuf;
     IE_TRY(zbuf.alloc(sizeof(double) * (size_t)std::max<long long>(part->total, 1) * nrhs, s));
-    if (f->nblocks > 0) {
+    const size_t smm = sizeof(double) * f->max_pad * kRM;
+    if (f->nblocks > 0 && nrhs >= 4 && smm <= 200 * 1024) {
+        if (f->precision == IE_FP64) {
+            dim3 g(f->nblocks, (nrhs + 15) / 16);
+            apply_blocks_multi<double, double, 16><<<g, 256, smm, s>>>((const double *)f->d_pool, f->d_loff, f->d_npad,
+                                                                       f->d_n, part->d_offs, part->d_idx, f->d_order, r,
+                                                                       ldr, nrhs, zbuf.as<double>(), part->total);
+        } else if (p->dim == 2) {
+            dim3 g(f->nblocks, (nrhs + 15) / 16);
+            apply_blocks_multi<float, double, 16><<<g, 256, smm, s>>>((const float *)f->d_pool, f->d_loff, f->d_npad,
+                                                                      f->d_n, part->d_offs, part->d_idx, f->d_order, r,
+                                                                      ldr, nrhs, zbuf.as<double>(), part->total);
+        } else {
+            dim3 g(f->nblocks, (nrhs + 31) / 32);
+            apply_blocks_multi<float, float, 32><<<g, 256, smm, s>>>((const float *)f->d_pool, f->d_loff, f->d_npad,
+                                                                     f->d_n, part->d_offs, part->d_idx, f->d_order, r,
+                                                                     ldr, nrhs, zbuf.as<double>(), part->total);
+        }
+        IE_LAUNCHED();
+    } else if (f->nblocks > 0) {
         dim3 g(f->nblocks, nrhs);
         const size_t sm = sizeof(double) * f->max_pad;
         if (f->precision == IE_FP64) {

@@ -160,18 +160,20 @@ APPLY_CASES = [(2, 64, 4, 1, O.SCHWARZ), (2, 40, 5, 2, O.SCHWARZ), (3, 16, 2, 1,
                (2, 32, 8, 1, O.CBD), (2, 30, 3, 0, O.JACOBI), (3, 12, 3, 1, O.CBD)]
 
 
+@pytest.mark.parametrize("nrhs", [2, 20])
 @pytest.mark.parametrize("dim,n,m,delta,kind", APPLY_CASES)
-def test_apply_parity(dim, n, m, delta, kind):
+def test_apply_parity(dim, n, m, delta, kind, nrhs):
+    # nrhs >= 4 takes the batched kernel (factor tiles shared by 16 or 32 right-hand sides)
     N = n ** dim
     blocks = O.partition(dim, n, m, delta, kind)
     F = O.factor(dim, n, blocks)
-    R = I.uniform_rhs_batch(N, [7, 8]).T.copy()
+    R = I.uniform_rhs_batch(N, list(range(7, 7 + nrhs))).T.copy()
     ref = O.apply(F, blocks, R.T).T
     prob = iedd.ie_discretize(dim, n)
     part = iedd.dd_partition(prob, m, delta, kind)
     for prec, tol in ((iedd.IE_FP64, 1e-11), (iedd.IE_MIXED, 2e-3)):
         fac = iedd.dd_factor(prob, part, prec)
-        Z = torch.zeros((2, N), dtype=torch.float64, device="cuda")
+        Z = torch.zeros((nrhs, N), dtype=torch.float64, device="cuda")
         iedd.dd_apply(fac, dev(R), Z)
         err = np.linalg.norm(host(Z) - ref) / np.linalg.norm(ref)
         assert err <= tol, (prec, err)
