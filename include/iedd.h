@@ -116,6 +116,17 @@ IEDD_API void ie_destroy(ie_problem *p);
 IEDD_API int ie_matvec(const ie_problem *p, const double *x, double *y, int nrhs, long long ld,
               int precision, void *stream);
 #define IE_ACCURATE 3
+#define IE_STORED 5   /* ie_matvec from the stored FP32 matrix (ie_store_matrix); HBM-bound */
+
+/*
+ * ie_store_matrix -- stored-matrix fallback: materialise the off-diagonal part of A densely in
+ * device memory (FP32, row-major N x N, 4 N^2 bytes; entries from the FP64 per-offset table,
+ * rounded once) so that ie_matvec(..., IE_STORED, ...) streams it instead of regenerating entries
+ * (the diagonal stays FP64).  Returns IE_ERR_OOM when 4 N^2 bytes exceed 90 % of the free device
+ * memory (N <= ~2.5e5 on a GB300).  Synchronizes the stream.  ie_release_matrix frees it.
+ */
+IEDD_API int ie_store_matrix(ie_problem *p, void *stream);
+IEDD_API int ie_release_matrix(ie_problem *p);
 
 /*
  * dd_partition -- index sets of the subdomains (Sec. 2.2-2.3, Eqs. e:dd, e:first, e:cbd).

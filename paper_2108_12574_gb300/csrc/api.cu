@@ -124,6 +124,7 @@ extern "C" void ie_destroy(ie_problem *p) {
     cudaFree(p->d_coord);
     cudaFree(p->d_table);
     cudaFree(p->d_table64);
+    cudaFree(p->d_stored);
     delete p;
 }
 
@@ -174,15 +175,21 @@ int check_vec_args(const char *who, const ie_problem *p, const void *a, const vo
 extern "C" int ie_matvec(const ie_problem *p, const double *x, double *y, int nrhs, long long ld,
                          int precision, void *stream) {
     IE_TRY(check_vec_args("ie_matvec", p, x, y, nrhs, ld));
-    if (precision != IE_FP64 && precision != IE_MIXED && precision != IE_ACCURATE) {
+    if (precision != IE_FP64 && precision != IE_MIXED && precision != IE_ACCURATE && precision != IE_STORED) {
         ie_set_error("ie_matvec: unknown precision"); return IE_ERR_ARG;
+    }
+    if (precision == IE_STORED && !p->d_stored) {
+        ie_set_error("ie_matvec: IE_STORED needs ie_store_matrix first"); return IE_ERR_ARG;
     }
     DeviceGuard g(p->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Staged sx, sy;
     IE_TRY(stage_in(x, p->N, nrhs, ld, true, s, sx));
     IE_TRY(stage_in(y, p->N, nrhs, ld, false, s, sy));
-    IE_TRY(launch_matvec(p, sx.dev, sx.ld, const_cast<double *>(sy.dev), sy.ld, nrhs, precision, s));
+    if (precision == IE_STORED)
+        IE_TRY(launch_matvec_stored(p, sx.dev, sx.ld, const_cast<double *>(sy.dev), sy.ld, nrhs, s));
+    else
+        IE_TRY(launch_matvec(p, sx.dev, sx.ld, const_cast<double *>(sy.dev), sy.ld, nrhs, precision, s));
     IE_TRY(stage_out(y, sy, p->N, nrhs, ld, s));
     if (sx.buf.ptr || sy.buf.ptr) IE_TRY_CUDA(cudaStreamSynchronize(s));
     return IE_OK;

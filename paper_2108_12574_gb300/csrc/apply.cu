@@ -209,22 +209,18 @@ __global__ void overlap_sum(const double *__restrict__ zbuf, long long total, co
 
 }  // namespace
 
-// Raise the dynamic shared-memory limit of the apply kernel for large subdomains (done once per
-// factor, outside any stream capture).
+// Raise the dynamic shared-memory limit of the apply kernels (outside any stream capture).  The
+// opt-in is needed whenever static + dynamic shared memory exceeds 48 KB, and the attribute is
+// per kernel for the whole process, so it is set to one fixed ceiling that covers every factor.
+constexpr int kApplySmemCeiling = 200 * 1024;
+
 int prepare_apply(const dd_factor_t *f) {
-    const size_t smm = sizeof(double) * f->max_pad * kRM;  // = 4 * max_pad * 32 for the FP32 variant
-    if (smm > 48 * 1024 && smm <= 200 * 1024) {
-        IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks_multi<double, double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
-        IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks_multi<float, double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
-        IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks_multi<float, float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm));
-    }
-    const size_t sm = sizeof(double) * f->max_pad;
-    if (sm > 48 * 1024) {
-        if (f->precision == IE_FP64)
-            IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        else
-            IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    }
+    (void)f;
+    IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks_multi<double, double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmemCeiling));
+    IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks_multi<float, double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmemCeiling));
+    IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks_multi<float, float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmemCeiling));
+    IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmemCeiling));
+    IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmemCeiling));
     return IE_OK;
 }
 
@@ -235,7 +231,7 @@ int launch_apply(const dd_factor_t *f, const double *r, long long ldr, double *z
     DevBuf zbuf;
     IE_TRY(zbuf.alloc(sizeof(double) * (size_t)std::max<long long>(part->total, 1) * nrhs, s));
     const size_t smm = sizeof(double) * f->max_pad * kRM;
-    if (f->nblocks > 0 && nrhs >= 4 && smm <= 200 * 1024) {
+    if (f->nblocks > 0 && nrhs >= 4 && smm <= (size_t)kApplySmemCeiling) {
         if (f->precision == IE_FP64) {
             dim3 g(f->nblocks, (nrhs + 15) / 16);
             apply_blocks_multi<double, double, 16><<<g, 256, smm, s>>>((const double *)f->d_pool, f->d_loff, f->d_npad,

@@ -71,6 +71,7 @@ struct ie_problem {
     float4 *d_coord = nullptr;     // integer lattice coordinates of every point (x, y, z, 0)
     float2 *d_table = nullptr;     // entry per |offset| (n^dim), split hi + lo; [0] = A_ii
     double *d_table64 = nullptr;   // same table in FP64
+    float *d_stored = nullptr;     // optional dense FP32 copy of A (zero diagonal), ie_store_matrix
     int sm_count = 0;
 };
 
@@ -139,6 +140,8 @@ int launch_matvec(const ie_problem *p, const double *x, long long ldx, double *y
 int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, double *y, long long ldy,
                       int nrhs, int precision, double *dot_out, cudaStream_t s);
 int build_problem_tables(ie_problem *p);
+int launch_matvec_stored(const ie_problem *p, const double *x, long long ldx, double *y, long long ldy, int nrhs,
+                         cudaStream_t s);
 
 int launch_factor(dd_factor_t *f, cudaStream_t s);
 int prepare_apply(const dd_factor_t *f);

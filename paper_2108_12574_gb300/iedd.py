@@ -16,7 +16,7 @@ import numpy as np
 
 IE_OK, IE_ERR_ARG, IE_ERR_CUDA, IE_ERR_OOM, IE_ERR_NOT_SPD = 0, -1, -2, -3, -4
 IE_ERR_BREAKDOWN, IE_ERR_MAXIT, IE_ERR_STAGNATION, IE_ERR_TIMEOUT = -5, -6, -7, -8
-IE_FP64, IE_MIXED, IE_ACCURATE = 0, 1, 3
+IE_FP64, IE_MIXED, IE_ACCURATE, IE_STORED = 0, 1, 3, 5
 DD_JACOBI, DD_SCHWARZ, DD_CBD = 0, 1, 2
 IE_GRID_TEXT, IE_GRID_TABLE = 0, 1
 
@@ -30,7 +30,8 @@ EXPORTS = ("ie_last_error", "ie_version", "ie_discretize", "ie_problem_info", "i
            "dd_partition", "dd_partition_info", "dd_partition_export", "dd_partition_destroy", "dd_factor",
            "dd_factor_destroy", "dd_apply", "ie_kernel_launches", "pcg_default_opts", "pcg_solve",
            "ie_matvec_noalloc", "ws_create", "ws_destroy", "ws_num_params", "ws_get_params", "ws_set_params",
-           "ws_forward_raw", "ws_backward_raw", "ws_train_step", "ws_predict")
+           "ws_forward_raw", "ws_backward_raw", "ws_train_step", "ws_predict", "ie_store_matrix",
+           "ie_release_matrix")
 IE_NOALLOC_MAX_N = 4194304 - 1024
 
 
@@ -85,6 +86,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dd_factor_destroy": (None, [vp]),
         "dd_apply": (i, [vp, vp, vp, i, ll, vp]),
         "ie_kernel_launches": (ll, [i]),
+        "ie_store_matrix": (i, [vp, vp]),
+        "ie_release_matrix": (i, [vp]),
         "ie_matvec_noalloc": (i, [i, i, d, i, vp, vp, vp]),
         "ws_create": (i, [i, ctypes.c_ulonglong, P(vp)]),
         "ws_destroy": (None, [vp]),
@@ -234,6 +237,14 @@ def ie_matvec(prob: Problem, x, y, precision: int = IE_MIXED, stream=None):
         raise ValueError("x and y must have the same shape and stride")
     _check(load_library().ie_matvec(prob.ptr, px, py, k, ld, precision, _stream(stream)))
     return y
+
+
+def ie_store_matrix(prob: Problem, stream=None):
+    _check(load_library().ie_store_matrix(prob.ptr, _stream(stream)))
+
+
+def ie_release_matrix(prob: Problem):
+    _check(load_library().ie_release_matrix(prob.ptr))
 
 
 def dd_partition(prob: Problem, m: int, delta: int, kind: int = DD_SCHWARZ) -> Partition:

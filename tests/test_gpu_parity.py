@@ -133,6 +133,28 @@ def test_accurate_matvec_3d_full_size_sampled_rows():
         assert np.max(np.abs(host(Y)[:, rows].T - ref)) <= tol * _scale(3, n, X, O.GRID_TEXT)
 
 
+@pytest.mark.parametrize("dim,n", [(2, 64), (3, 16), (2, 30)])
+def test_stored_matrix_matvec(dim, n):
+    N = n ** dim
+    X = I.uniform_rhs_batch(N, [2, 3]).T.copy()
+    prob = iedd.ie_discretize(dim, n)
+    iedd.ie_store_matrix(prob)
+    Y = torch.zeros((2, N), dtype=torch.float64, device="cuda")
+    iedd.ie_matvec(prob, dev(X), Y, iedd.IE_STORED)
+    ref = O.matvec_direct(dim, n, X.T).T
+    assert np.max(np.abs(host(Y) - ref)) <= 4e-6 * _scale(dim, n, X, O.GRID_TEXT)
+    iedd.ie_release_matrix(prob)
+    with pytest.raises(iedd.IEError):
+        iedd.ie_matvec(prob, dev(X), Y, iedd.IE_STORED)
+
+
+def test_stored_matrix_too_large_is_refused():
+    prob = iedd.ie_discretize(2, 1024)  # 4 N^2 = 4.4 TB
+    with pytest.raises(iedd.IEError) as e:
+        iedd.ie_store_matrix(prob)
+    assert e.value.status == iedd.IE_ERR_OOM
+
+
 PART_CASES = [(2, 64, 4, 1, O.SCHWARZ), (2, 512, 32, 2, O.SCHWARZ), (3, 32, 4, 1, O.SCHWARZ),
               (2, 12, 3, 1, O.CBD), (3, 8, 4, 1, O.CBD), (2, 30, 5, 2, O.JACOBI), (2, 20, 4, 3, O.SCHWARZ),
               (2, 24, 3, 5, O.CBD)]
