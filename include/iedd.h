@@ -117,6 +117,10 @@ IEDD_API int ie_matvec(const ie_problem *p, const double *x, double *y, int nrhs
               int precision, void *stream);
 #define IE_ACCURATE 3
 #define IE_STORED 5   /* ie_matvec from the stored FP32 matrix (ie_store_matrix); HBM-bound */
+#define IE_TENSOR 6   /* FP32 SFU entries contracted with x on the tcgen05 tensor cores (3xTF32
+                         split, FP32 accumulation in tensor memory), 64 right-hand sides per CTA;
+                         same accuracy class as IE_MIXED.  Returns IE_ERR_TIMEOUT if a CTA gave
+                         up waiting for its MMAs (bounded waits; the call then synchronizes). */
 
 /*
  * ie_store_matrix -- stored-matrix fallback: materialise the off-diagonal part of A densely in
@@ -192,6 +196,7 @@ typedef struct {
                               IE_ACCURATE  double-float table sums on the FP32 pipes
                               4            as IE_ACCURATE with the search directions rounded to
                                            FP32 (one FFMA less per pair, more iterations)
+                              IE_TENSOR    the tcgen05 batched kernel (many right-hand sides)
                               16           the FP64 regenerated matvec in either precision */
 } pcg_opts;
 

@@ -125,6 +125,7 @@ extern "C" void ie_destroy(ie_problem *p) {
     cudaFree(p->d_table);
     cudaFree(p->d_table64);
     cudaFree(p->d_stored);
+    cudaFree(p->d_err);
     delete p;
 }
 
@@ -175,7 +176,8 @@ int check_vec_args(const char *who, const ie_problem *p, const void *a, const vo
 extern "C" int ie_matvec(const ie_problem *p, const double *x, double *y, int nrhs, long long ld,
                          int precision, void *stream) {
     IE_TRY(check_vec_args("ie_matvec", p, x, y, nrhs, ld));
-    if (precision != IE_FP64 && precision != IE_MIXED && precision != IE_ACCURATE && precision != IE_STORED) {
+    if (precision != IE_FP64 && precision != IE_MIXED && precision != IE_ACCURATE && precision != IE_STORED &&
+        precision != IE_TENSOR) {
         ie_set_error("ie_matvec: unknown precision"); return IE_ERR_ARG;
     }
     if (precision == IE_STORED && !p->d_stored) {
@@ -191,6 +193,13 @@ extern "C" int ie_matvec(const ie_problem *p, const double *x, double *y, int nr
     else
         IE_TRY(launch_matvec(p, sx.dev, sx.ld, const_cast<double *>(sy.dev), sy.ld, nrhs, precision, s));
     IE_TRY(stage_out(y, sy, p->N, nrhs, ld, s));
+    if (precision == IE_TENSOR) {
+        // the tensor-core kernel reports a CTA that gave up waiting for its MMAs
+        int err = 0;
+        IE_TRY_CUDA(cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        IE_TRY_CUDA(cudaStreamSynchronize(s));
+        if (err) { ie_set_error("ie_matvec: tensor-core matvec timed out waiting for its MMAs"); return IE_ERR_TIMEOUT; }
+    }
     if (sx.buf.ptr || sy.buf.ptr) IE_TRY_CUDA(cudaStreamSynchronize(s));
     return IE_OK;
 }

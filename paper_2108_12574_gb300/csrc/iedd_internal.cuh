@@ -72,6 +72,7 @@ struct ie_problem {
     float2 *d_table = nullptr;     // entry per |offset| (n^dim), split hi + lo; [0] = A_ii
     double *d_table64 = nullptr;   // same table in FP64
     float *d_stored = nullptr;     // optional dense FP32 copy of A (zero diagonal), ie_store_matrix
+    int *d_err = nullptr;          // device error word of the tensor-core matvec (bounded waits)
     int sm_count = 0;
 };
 
@@ -140,6 +141,12 @@ int launch_matvec(const ie_problem *p, const double *x, long long ldx, double *y
 int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, double *y, long long ldy,
                       int nrhs, int precision, double *dot_out, cudaStream_t s);
 int build_problem_tables(ie_problem *p);
+int launch_matvec_tc(const ie_problem *p, const double *x, long long ldx, int nrhs, double *partial, int S, int cps,
+                     int nchunks, int *d_err, cudaStream_t s);
+int prepare_tc();
+int tc_chunk();
+int tc_rows();
+int tc_cols();
 int launch_matvec_stored(const ie_problem *p, const double *x, long long ldx, double *y, long long ldy, int nrhs,
                          cudaStream_t s);
 

@@ -572,6 +572,9 @@ int splits_for(long long items, long long work_units, int sm_count, int per_sm) 
 }  // namespace
 
 int build_problem_tables(ie_problem *p) {
+    IE_TRY(prepare_tc());
+    IE_TRY_CUDA(cudaMalloc(&p->d_err, sizeof(int)));
+    IE_TRY_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
     // dynamic shared memory of the batched matvec (set outside any stream capture)
     const int dsm64 = (int)(sizeof(double) * 8 * 4 * kThreads);
     IE_TRY_CUDA(cudaFuncSetAttribute(k1m_matvec_f32<2, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm64));
@@ -594,7 +597,7 @@ int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, doubl
     const long long N = p->N;
     const int ntiles = (int)((N + kThreads - 1) / kThreads);
     DevBuf xsum;
-    if (p->dim == 2 && (precision == IE_MIXED || precision == IE_FP64)) {
+    if (p->dim == 2 && (precision == IE_MIXED || precision == IE_FP64 || precision == IE_TENSOR)) {
         DevBuf part;
         IE_TRY(part.alloc(sizeof(double) * iedd::kRedBlocks * nrhs, s));
         IE_TRY(xsum.alloc(sizeof(double) * nrhs, s));
@@ -603,6 +606,24 @@ int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, doubl
         IE_LAUNCHED();
         iedd::dot_final_kernel<<<nrhs, iedd::kRedBlocks, 0, s>>>(part.as<double>(), xsum.as<double>());
         IE_LAUNCHED();
+    }
+    if (precision == IE_TENSOR) {
+        const int rt = (int)((N + tc_rows() - 1) / tc_rows());
+        const int nchunks = (int)((N + tc_chunk() - 1) / tc_chunk());
+        const int groups = (nrhs + tc_cols() - 1) / tc_cols();
+        int S = splits_for((long long)rt * groups, nchunks, p->sm_count, 3);
+        S = std::min(S, 16);
+        const int cps = (nchunks + S - 1) / S;
+        const int Se = (nchunks + cps - 1) / cps;
+        DevBuf part;
+        IE_TRY(part.alloc(sizeof(double) * N * nrhs * Se, s));
+        IE_TRY(launch_matvec_tc(p, x, ldx, nrhs, part.as<double>(), Se, cps, nchunks, p->d_err, s));
+        combine_multi_kernel<<<dim3((unsigned)((N + 255) / 256), nrhs), 256, 0, s>>>(
+            part.as<double>(), Se, nrhs, x, ldx, y, ldy, N, p->dim, p->diag, p->c_const,
+            p->dim == 2 ? p->c_log2 : p->c_r, xsum.ptr ? xsum.as<double>() : nullptr);
+        IE_LAUNCHED();
+        if (dot_out) IE_TRY(launch_dots(x, ldx, y, ldy, N, nrhs, dot_out, s));
+        return IE_OK;
     }
     if (precision == IE_MIXED && nrhs >= 4) {
         const int NR = nrhs > 16 ? 64 : 16;

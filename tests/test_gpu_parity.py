@@ -77,6 +77,18 @@ def test_matvec_multi_rhs_and_shift(dim, n, nrhs):
         assert np.max(np.abs(host(Y) - ref)) <= tol * scale, prec
 
 
+@pytest.mark.parametrize("dim,n,nrhs", [(3, 16, 64), (3, 12, 70), (2, 40, 20), (3, 10, 1)])
+def test_tensor_core_matvec(dim, n, nrhs):
+    # tcgen05 3xTF32 contraction of SFU entries: FP32-class accuracy, like IE_MIXED
+    N = n ** dim
+    X = I.uniform_rhs_batch(N, list(range(nrhs))).T.copy()
+    prob = iedd.ie_discretize(dim, n)
+    Y = torch.zeros((nrhs, N), dtype=torch.float64, device="cuda")
+    iedd.ie_matvec(prob, dev(X), Y, iedd.IE_TENSOR)
+    ref = O.matvec_direct(dim, n, X.T).T
+    assert np.max(np.abs(host(Y) - ref)) <= 4e-6 * _scale(dim, n, X, O.GRID_TEXT)
+
+
 def test_matvec_strided_batch():
     n = 20
     N = n * n
