@@ -23,7 +23,7 @@ namespace {
 
 constexpr int kTM = 128, kTN = 64, kTK = 32;
 constexpr uint32_t kLBO = 128, kSBO = (kTK / 4) * 128;
-constexpr long long kSpinLimit = 1LL << 26;  // mbarrier polls before giving up
+constexpr long long kSpinLimit = 1LL << 24;  // non-blocking mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -56,10 +56,10 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t phase) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
         : "r"(bar), "r"(phase)
@@ -70,7 +70,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
 // bounded wait for the given phase of the barrier; false if the limit ran out
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
     for (long long i = 0; i < kSpinLimit; ++i)
-        if (mbar_try_wait(bar, phase)) return true;
+        if (mbar_test(bar, phase)) return true;
     return false;
 }
 
