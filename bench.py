@@ -30,6 +30,19 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "ie2d_n512_schwarz_m32_d2"
 DIM, NGRID, MPART, DELTA, ELL, TOL, REPLACE_EVERY = 2, 512, 32, 2, 0.1, 1e-8, 50
+# every workload the benchmark can time (--workload); the default is the 512^2 one
+WORKLOADS = {
+    "ie2d_n64_schwarz_m4_d1": dict(dim=2, n=64, m=4, delta=1, rhs="uniform", seeds=1, precision="fp64",
+                                   factor="fp64"),
+    "ie2d_n512_schwarz_m32_d2": dict(dim=2, n=512, m=32, delta=2, rhs="grf", ell=0.1, seeds=1, precision="mixed",
+                                     factor="mixed"),
+    "ie3d_n32_schwarz_m4_d1_rhs64": dict(dim=3, n=32, m=4, delta=1, rhs="uniform", seeds=64, precision="mixed",
+                                         factor="mixed"),
+    "ie2d_n1024_schwarz_m64_d2": dict(dim=2, n=1024, m=64, delta=2, rhs="grf", ell=0.05, seeds=1, precision="mixed",
+                                      factor="mixed"),
+    "ie2d_n256_schwarz_m16_d2": dict(dim=2, n=256, m=16, delta=2, rhs="grf", ell=0.1, seeds=1, precision="mixed",
+                                     factor="mixed"),
+}
 METRIC = "PCG time-to-1e-8 true relative residual (s)"
 L2_FLUSH_BYTES = 512 << 20
 # FP32-pipe operations per pair of the exact double-float matvec (k2_accurate_2d, x split hi/lo):
@@ -48,8 +61,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=WORKLOAD)
     ap.add_argument("--no-extras", action="store_true", help="skip FP64-plain and CPU-baseline legs")
-    ap.add_argument("--kernel", choices=["k1", "k2", "kd", "apply", "factor"], default=None,
+    ap.add_argument("--kernel", choices=["k1", "k2", "kd", "tc", "stored", "apply", "factor"], default=None,
                     help="profiling case: run one hot operation twice on a --dim/--n/--nrhs problem and exit")
     ap.add_argument("--dim", type=int, default=DIM)
     ap.add_argument("--n", type=int, default=NGRID)
@@ -72,8 +86,11 @@ def kernel_case(args):
     Y = torch.zeros_like(X)
     m = args.n // 16 if args.dim == 2 else args.n // 8
     for _ in range(2):
-        if args.kernel in ("k1", "k2", "kd"):
-            prec = {"k1": iedd.IE_MIXED, "k2": iedd.IE_ACCURATE, "kd": iedd.IE_FP64}[args.kernel]
+        if args.kernel in ("k1", "k2", "kd", "tc", "stored"):
+            prec = {"k1": iedd.IE_MIXED, "k2": iedd.IE_ACCURATE, "kd": iedd.IE_FP64, "tc": iedd.IE_TENSOR,
+                    "stored": iedd.IE_STORED}[args.kernel]
+            if args.kernel == "stored":
+                iedd.ie_store_matrix(prob)
             iedd.ie_matvec(prob, X, Y, prec)
         else:
             part = iedd.dd_partition(prob, m, 2 if args.dim == 2 else 1, iedd.DD_SCHWARZ)
@@ -244,20 +261,31 @@ def main():
     def reduce_max(v: float) -> float:
         return max_over_ranks(v, dist, dev)
 
-    N = NGRID ** DIM
-    f_host = I.grf(DIM, NGRID, ELL, rank)
+    W = WORKLOADS[args.workload]
+    dim_w, n_w = W["dim"], W["n"]
+    N = n_w ** dim_w
+    nr = W["seeds"]
+    prec = iedd.IE_FP64 if W["precision"] == "fp64" else iedd.IE_MIXED
+    fprec = iedd.IE_FP64 if W["factor"] == "fp64" else iedd.IE_MIXED
+    seeds = [rank * nr + k for k in range(nr)]
+    if W["rhs"] == "grf":
+        f_host = np.stack([I.grf(dim_w, n_w, W["ell"], s_) for s_ in seeds])
+    else:
+        f_host = np.stack([I.uniform_rhs(N, s_) for s_ in seeds])
+    if nr == 1:
+        f_host = f_host[0]
     f = torch.from_numpy(f_host).to(dev)
     u = torch.zeros_like(f)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step(fv, uv):
-        prob = iedd.ie_discretize(DIM, NGRID, device=local)
-        part = iedd.dd_partition(prob, MPART, DELTA, iedd.DD_SCHWARZ)
-        fac = iedd.dd_factor(prob, part, iedd.IE_MIXED, stream=stream)
-        reps = iedd.pcg_solve(prob, fac, fv, uv, tol=TOL, precision=iedd.IE_MIXED, replace_every=REPLACE_EVERY,
+        prob = iedd.ie_discretize(dim_w, n_w, device=local)
+        part = iedd.dd_partition(prob, W["m"], W["delta"], iedd.DD_SCHWARZ)
+        fac = iedd.dd_factor(prob, part, fprec, stream=stream)
+        reps = iedd.pcg_solve(prob, fac, fv, uv, tol=TOL, precision=prec, replace_every=REPLACE_EVERY,
                               stream=stream)
         fac.close(); part.close(); prob.close()
-        return reps[0]
+        return reps
 
     for _ in range(args.warmup):
         u.zero_()
@@ -287,11 +315,12 @@ def main():
     value = ms_per_step / 1e3
 
     # correctness of what was timed: the true residual reported by the accurate matvec
-    last = reps[-1]
-    ok = all(r["status"] == 0 and 0 <= r["true_relres"] <= TOL for r in reps)
+    ok = all(r["status"] == 0 and 0 <= r["true_relres"] <= TOL for rs in reps for r in rs)
+    last = reps[-1][0]
+    its_all = [r["iterations"] for r in reps[-1]]
 
     # end to end through the public API with HOST buffers (copies inside the timed region)
-    u_host = np.zeros(N)
+    u_host = np.zeros_like(f_host)
     e2e_times = []
     for _ in range(max(1, args.steps)):
         barrier()
@@ -301,31 +330,46 @@ def main():
     e2e = {"value": reduce_max(statistics.mean(e2e_times)), "unit": "s",
            "h2d_bytes_per_step": int(f_host.nbytes), "d2h_bytes_per_step": int(u_host.nbytes)}
 
-    # roofline of the dominant kernel: the inner matvec (exact double-float table sums, K2)
+    # roofline of the dominant kernel: the inner matvec
     pairs = float(N) * (N - 1)
     mv_launch_s = last["matvec_ms"] / max(last["matvecs"], 1) / 1e3
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     f_mhz = clocks.get("sm_mhz") or 2070.0
-    per_clk = FP32_LANES_PER_SM / FP32_OPS_PER_PAIR_K2
-    peak = sms * per_clk * f_mhz * 1e6
-    achieved = pairs / mv_launch_s
     src_hash = hashlib.sha256(open(os.path.join(ROOT, "paper_2108_12574_gb300", "csrc", "matvec.cu"), "rb")
                               .read()).hexdigest()[:16]
-    traffic = NCU_TRAFFIC.get(src_hash)
-    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpairs/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "k2_accurate_2d<true,1>",
-                "peak_basis": (f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes / {FP32_OPS_PER_PAIR_K2} FP32 ops per pair "
-                               f"x {f_mhz:.0f} MHz (median SM clock sampled in the timed region)")}
+    if prec == iedd.IE_MIXED and dim_w == 2:
+        per_clk = FP32_LANES_PER_SM / FP32_OPS_PER_PAIR_K2
+        peak = sms * per_clk * f_mhz * 1e6
+        achieved = pairs * nr / mv_launch_s
+        roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpairs/s",
+                    "frac": achieved / peak, "traffic": NCU_TRAFFIC.get(src_hash) if args.workload == WORKLOAD else None,
+                    "kernel": "k2_accurate_2d<true,1>",
+                    "peak_basis": (f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes / {FP32_OPS_PER_PAIR_K2} FP32 ops per "
+                                   f"pair x {f_mhz:.0f} MHz (median SM clock sampled in the timed region)")}
+    elif prec == iedd.IE_MIXED:
+        # batched FP32 kernel: one FFMA per pair and right-hand side dominates (entries amortised)
+        peak = sms * FP32_LANES_PER_SM * f_mhz * 1e6
+        achieved = pairs * nr / mv_launch_s
+        roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair-rhs/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": "k1m_matvec_f32<3,64>",
+                    "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FFMA/clk x {f_mhz:.0f} MHz (one FFMA per pair per RHS)"}
+    else:
+        achieved = pairs * nr / mv_launch_s
+        roofline = {"bound": "fp64", "achieved": achieved / 1e9, "peak": None, "unit": "Gpairs/s", "frac": None,
+                    "traffic": None, "kernel": "kd_matvec_f64",
+                    "peak_basis": "FP64 log per pair; no measured FP64 peak on this pool"}
 
+    cfg = config_dict() if args.workload == WORKLOAD else {"workload": args.workload, **W, "tol": TOL}
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 (double-float sums) + f64", "data": "synthetic",
-            "config": config_dict(), "iterations": last["iterations"], "true_relres": last["true_relres"],
+            "vs_baseline": None, "dtype": "f32 (double-float sums) + f64" if prec == iedd.IE_MIXED else "f64",
+            "data": "synthetic", "config": cfg, "iterations": last["iterations"],
+            "iterations_max": max(its_all), "true_relres": max(r["true_relres"] for r in reps[-1]),
             "replacements": last["replacements"], "converged": ok,
             "t_solve_matvec_s": last["matvec_ms"] / 1e3, "t_solve_apply_s": last["apply_ms"] / 1e3,
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks}
 
-    if not args.no_extras and rank == 0:
+    if not args.no_extras and rank == 0 and args.workload == WORKLOAD:
         line.update(extras(torch, iedd, I, dev, stream, last["iterations"]))
         line["warm_start"] = warm_start_leg()
         line["cpu_baseline"] = cpu_baseline(last["iterations"], 0)
