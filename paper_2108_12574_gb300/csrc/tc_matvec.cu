@@ -2,13 +2,15 @@
 //
 // For a batch of right-hand sides the matvec is a dense contraction: a CTA owns 128 target rows
 // and 64 right-hand sides; for each chunk of 32 source points it evaluates the 128 x 32 entry
-// tile E (SFU rsqrt / log2, as K1) and stages the 64 x 32 slice of x, both split into TF32
-// high and low parts (3xTF32: E_hi x_hi + E_hi x_lo + E_lo x_hi, FP32-class accuracy), and one
-// thread issues 12 tcgen05.mma.kind::tf32 (M = 128, N = 64, K = 8) into an FP32 accumulator in
-// tensor memory (64 TMEM columns).  Completion is tracked with tcgen05.commit on an mbarrier,
-// with a bounded wait: a CTA that waits too long records an error code, still drains its own
-// MMAs (bounded again), frees its TMEM and returns.  The epilogue reads the accumulator with
-// tcgen05.ld (32x32b) and writes the same [split][rhs][N] FP64 partials as the CUDA-core kernel.
+// tile E (SFU rsqrt / log2, as K1), split into TF32 high and low parts, while a bulk
+// asynchronous copy (cp.async.bulk, mbarrier complete_tx) brings the matching 64 x 32 slice of
+// x, split once per matvec by xsplit_kernel.  One thread issues 12 tcgen05.mma.kind::tf32
+// (M = 128, N = 64, K = 8; 3xTF32: E_hi x_hi + E_hi x_lo + E_lo x_hi) into an FP32 accumulator in
+// tensor memory (64 TMEM columns).  Two operand stages let the CTA build chunk c + 1 while the
+// MMAs of chunk c run; every 8 chunks the accumulator is read (tcgen05.ld 32x32b) and added to a
+// compensated (TwoSum) FP32 pair per output, which keeps the sum at FP32-entry accuracy.
+// Completion is tracked with tcgen05.commit on per-stage mbarriers, with bounded waits: a CTA
+// that waits too long records an error code, frees its TMEM and returns.
 //
 // Shared-memory operands use the canonical no-swizzle K-major layout: 8-row x 16-byte core
 // matrices, element (r, k) at (r / 8) * SBO + (k / 4) * LBO + (r % 8) * 16 + (k % 4) * 4 bytes,
@@ -78,22 +80,64 @@ __device__ __forceinline__ uint32_t op_off(int r, int k) {
     return (uint32_t)((r >> 3) * kSBO + (k >> 2) * kLBO + (r & 7) * 16 + (k & 3) * 4);
 }
 
+// x pre-split for the tensor-core matvec: for right-hand-side group g (64 columns) and source
+// chunk c (32 points) one 16 KB record: the 64 x 32 TF32 high parts, then the low parts, both
+// in the core-matrix layout of a K-major B operand.  One pass over x per matvec.
+__global__ void xsplit_kernel(const double *__restrict__ x, long long ldx, int nrhs, long long N, int nchunks,
+                              uint32_t *__restrict__ out) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // one thread per (g, c, slot)
+    const long long per = (long long)kTN * kTK;
+    const long long rec = e / per;
+    if (rec >= (long long)nchunks * ((nrhs + kTN - 1) / kTN)) return;
+    const int slot = (int)(e % per);
+    const int g = (int)(rec / nchunks), c = (int)(rec % nchunks);
+    // slot -> core matrix cm and position l inside it (the layout order of the record)
+    const int cm = slot >> 5, l = slot & 31;
+    const int col = (cm / (kTK / 4)) * 8 + (l >> 2);   // right-hand side within the group
+    const int k = (cm % (kTK / 4)) * 4 + (l & 3);       // source within the chunk
+    const long long j = (long long)c * kTK + k;
+    const int r = g * kTN + col;
+    const float v = (j < N && r < nrhs) ? (float)x[(long long)r * ldx + j] : 0.f;
+    const uint32_t hi = to_tf32(v);
+    const uint32_t lo = to_tf32(v - __uint_as_float(hi));
+    uint32_t *o = out + rec * 2 * per;
+    o[slot] = hi;
+    o[per + slot] = lo;
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void two_sum_acc(float v, float &hi, float &lo) {
+    const float s = __fadd_rn(hi, v);
+    const float bp = __fsub_rn(s, hi);
+    const float er = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(v, bp));
+    hi = s;
+    lo = __fadd_rn(lo, er);
+}
+
+constexpr int kStage = 2 * kTM * kTK + 2 * kTN * kTK;  // uint32 words per operand stage (48 KB)
+constexpr int kFlush = 8;                              // chunks accumulated in TMEM between flushes
+
 template <int DIM>
 __global__ void __launch_bounds__(256)
-k1t_matvec_tc(const float4 *__restrict__ coord, const double *__restrict__ x, long long ldx, int nrhs, long long N,
+k1t_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsplit, int nrhs, long long N,
               int chunks_per_split, int nchunks, double *__restrict__ partial, int *__restrict__ err) {
-    extern __shared__ __align__(128) uint32_t opnd[];  // A hi | A lo | B hi | B lo (48 KB)
-    uint32_t *Ahi = opnd, *Alo = opnd + kTM * kTK, *Bhi = opnd + 2 * kTM * kTK, *Blo = Bhi + kTN * kTK;
+    extern __shared__ __align__(128) uint32_t opnd[];  // 2 stages of [A hi | A lo | B hi | B lo]
     __shared__ float4 rc[kTM];
-    __shared__ float4 cc[kTK];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar_mma[2];
+    __shared__ __align__(8) uint64_t mbar_ld[2];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long row0 = (long long)blockIdx.x * kTM;
-    const int rhs0 = blockIdx.z * kTN;
-    const uint32_t bar = smem_u32(&mbar);
+    const int grp = blockIdx.z;
+    const int rhs0 = grp * kTN;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -101,7 +145,10 @@ k1t_matvec_tc(const float4 *__restrict__ coord, const double *__restrict__ x, lo
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1u));
+        for (int st = 0; st < 2; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar_mma[st])), "r"(1u));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar_ld[st])), "r"(1u));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
     }
@@ -114,77 +161,21 @@ k1t_matvec_tc(const float4 *__restrict__ coord, const double *__restrict__ x, lo
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
 
+    // epilogue ownership: warp w reads TMEM lanes 32 (w % 4) .., columns 32 (w / 4) ..
+    const int q = warp & 3, h = warp >> 2;
+    float ahi[32], alo[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) { ahi[c] = 0.f; alo[c] = 0.f; }
+
     const int k0 = blockIdx.y * chunks_per_split;
     const int k1 = min(k0 + chunks_per_split, nchunks);
-    uint32_t phase = 0;
-    bool issued_any = false;
-    for (int ch = k0; ch < k1; ++ch) {
-        const long long j0 = (long long)ch * kTK;
-        if (tid < kTK) {
-            const long long j = j0 + tid;
-            cc[tid] = j < N ? coord[j] : make_float4(1e6f, 1e6f, 1e6f, 0.f);
-        }
-        __syncthreads();
-        // entry tile: A[r][k] = K(row r, source k), split into TF32 high and low parts
-        for (int e = tid; e < kTM * kTK; e += 256) {
-            const int r = e / kTK, k = e % kTK;
-            const float4 a = rc[r], b = cc[k];
-            const float dx = a.x - b.x, dy = a.y - b.y;
-            float v;
-            if (DIM == 2) {
-                v = __log2f(fmaf(dx, dx, fmaf(dy, dy, 0x1p-30f)));
-            } else {
-                const float dz = a.z - b.z;
-                v = rsqrtf(fmaxf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), 1.0f));
-            }
-            const uint32_t hi = to_tf32(v);
-            const uint32_t lo = to_tf32(v - __uint_as_float(hi));
-            const uint32_t o = op_off(r, k) >> 2;
-            Ahi[o] = hi;
-            Alo[o] = lo;
-        }
-        // x slice: B[c][k] = x[rhs0 + c][j0 + k]
-        for (int e = tid; e < kTN * kTK; e += 256) {
-            const int c = e / kTK, k = e % kTK;
-            const long long j = j0 + k;
-            const float v = (j < N && rhs0 + c < nrhs) ? (float)x[(long long)(rhs0 + c) * ldx + j] : 0.f;
-            const uint32_t hi = to_tf32(v);
-            const uint32_t lo = to_tf32(v - __uint_as_float(hi));
-            const uint32_t o = op_off(c, k) >> 2;
-            Bhi[o] = hi;
-            Blo[o] = lo;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo), bhi = smem_u32(Bhi), blo = smem_u32(Blo);
-#pragma unroll
-            for (int s = 0; s < kTK / 8; ++s) {
-                const uint32_t koff = (uint32_t)s * 2 * kLBO;  // 8 TF32 elements = two K core matrices
-                mma_tf32(tmem, make_desc(ahi + koff), make_desc(bhi + koff), (issued_any || s > 0) ? 1u : 0u);
-                mma_tf32(tmem, make_desc(ahi + koff), make_desc(blo + koff), 1u);
-                mma_tf32(tmem, make_desc(alo + koff), make_desc(bhi + koff), 1u);
-            }
-            mma_commit(bar);
-        }
-        issued_any = true;
-        // the operands may be overwritten only after the MMAs that read them complete
-        const bool ok = mbar_wait(bar, phase);
-        if (!ok) {
-            abort_flag = 1;
-            // drain our own MMAs before freeing tensor memory (bounded again)
-            if (tid == 0) (void)mbar_wait(bar, phase);
-        }
-        phase ^= 1u;
-        __syncthreads();
-        if (abort_flag) break;
-    }
+    uint32_t ph_mma[2] = {0u, 0u}, ph_ld[2] = {0u, 0u};
+    int pending[2] = {0, 0};   // stage has MMAs in flight
+    int since_flush = 0;
 
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!abort_flag && issued_any) {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, columns 32 (w / 4) .. + 31
-        const int q = warp & 3, h = warp >> 2;
+    auto flush = [&](void) {
+        // all MMAs issued so far have completed (caller waited); read and add to (hi, lo)
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         uint32_t v[32];
         const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h);
         asm volatile(
@@ -196,16 +187,108 @@ k1t_matvec_tc(const float4 *__restrict__ coord, const double *__restrict__ x, lo
               "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int c = 0; c < 32; ++c) two_sum_acc(__uint_as_float(v[c]), ahi[c], alo[c]);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    };
+
+    for (int ch = k0; ch < k1; ++ch) {  // abort_flag is acted on only after a barrier (uniform exit)
+        const int st = (ch - k0) & 1;
+        uint32_t *Ahi = opnd + st * kStage, *Alo = Ahi + kTM * kTK, *Bv = Ahi + 2 * kTM * kTK;
+        // the stage's previous MMAs must be done before its operands are overwritten
+        if (pending[st]) {
+            const bool ok = mbar_wait(smem_u32(&mbar_mma[st]), ph_mma[st]);
+            if (!ok) abort_flag = 1;
+            ph_mma[st] ^= 1u;
+            pending[st] = 0;
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        if (since_flush == kFlush) {
+            // the other stage's MMAs (the newest) must also be done before reading TMEM
+            if (pending[st ^ 1]) {
+                const bool ok = mbar_wait(smem_u32(&mbar_mma[st ^ 1]), ph_mma[st ^ 1]);
+                if (!ok) abort_flag = 1;
+                ph_mma[st ^ 1] ^= 1u;
+                pending[st ^ 1] = 0;
+            }
+            __syncthreads();
+            if (abort_flag) break;
+            flush();
+            __syncthreads();
+            since_flush = 0;
+        }
+        // B operand (pre-split x) by a bulk asynchronous copy
+        if (tid == 0) {
+            const uint32_t *src = xsplit + ((long long)grp * nchunks + ch) * (2LL * kTN * kTK);
+            bulk_g2s(smem_u32(Bv), src, (uint32_t)(2 * kTN * kTK * sizeof(uint32_t)), smem_u32(&mbar_ld[st]));
+        }
+        // A operand: entries of 128 rows x 32 sources; one warp writes one 8 x 4 core matrix
+        const long long j0 = (long long)ch * kTK;
+        for (int e = tid; e < kTM * kTK; e += 256) {
+            const int cm = e >> 5, l = e & 31;
+            const int r = (cm / (kTK / 4)) * 8 + (l >> 2);
+            const int k = (cm % (kTK / 4)) * 4 + (l & 3);
+            const long long j = j0 + k;
+            const float4 a = rc[r];
+            const float4 b = j < N ? coord[j] : make_float4(1e6f, 1e6f, 1e6f, 0.f);
+            const float dx = a.x - b.x, dy = a.y - b.y;
+            float v;
+            if (DIM == 2) {
+                v = __log2f(fmaf(dx, dx, fmaf(dy, dy, 0x1p-30f)));
+            } else {
+                const float dz = a.z - b.z;
+                v = rsqrtf(fmaxf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), 1.0f));
+            }
+            const uint32_t hi = to_tf32(v);
+            Ahi[e] = hi;
+            Alo[e] = to_tf32(v - __uint_as_float(hi));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            const bool ok = mbar_wait(smem_u32(&mbar_ld[st]), ph_ld[st]);
+            ph_ld[st] ^= 1u;
+            if (!ok) {
+                abort_flag = 1;
+            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo);
+                const uint32_t bhi = smem_u32(Bv), blo = bhi + kTN * kTK * 4;
+#pragma unroll
+                for (int s = 0; s < kTK / 8; ++s) {
+                    const uint32_t koff = (uint32_t)s * 2 * kLBO;
+                    mma_tf32(tmem, make_desc(ahi + koff), make_desc(bhi + koff), (since_flush > 0 || s > 0) ? 1u : 0u);
+                    mma_tf32(tmem, make_desc(ahi + koff), make_desc(blo + koff), 1u);
+                    mma_tf32(tmem, make_desc(alo + koff), make_desc(bhi + koff), 1u);
+                }
+                mma_commit(smem_u32(&mbar_mma[st]));
+            }
+        }
+        pending[st] = 1;
+        ++since_flush;
+    }
+    // drain both stages (bounded), then the final flush
+    for (int st = 0; st < 2; ++st) {
+        if (pending[st]) {
+            const bool ok = mbar_wait(smem_u32(&mbar_mma[st]), ph_mma[st]);
+            if (!ok) abort_flag = 1;
+            pending[st] = 0;
+        }
+    }
+    __syncthreads();
+    if (!abort_flag && since_flush > 0) flush();
+    if (!abort_flag) {
         const long long i = row0 + 32 * q + lane;
         if (i < N) {
 #pragma unroll
             for (int c = 0; c < 32; ++c) {
                 const int r = rhs0 + 32 * h + c;
-                if (r < nrhs) partial[((long long)blockIdx.y * nrhs + r) * N + i] = (double)__uint_as_float(v[c]);
+                if (r < nrhs) partial[((long long)blockIdx.y * nrhs + r) * N + i] = (double)ahi[c] + (double)alo[c];
             }
         }
-    } else if (abort_flag) {
-        if (tid == 0) atomicExch(err, 1);
+    } else if (tid == 0) {
+        atomicExch(err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -223,12 +306,17 @@ int launch_matvec_tc(const ie_problem *p, const double *x, long long ldx, int nr
                      int nchunks, int *d_err, cudaStream_t s) {
     const int rt = (int)((p->N + kTM - 1) / kTM);
     const int groups = (nrhs + kTN - 1) / kTN;
+    DevBuf xs;
+    const long long words = (long long)groups * nchunks * 2 * kTN * kTK;
+    IE_TRY(xs.alloc(sizeof(uint32_t) * words, s));
+    xsplit_kernel<<<(unsigned)((words / 2 + 255) / 256), 256, 0, s>>>(x, ldx, nrhs, p->N, nchunks, xs.as<uint32_t>());
+    IE_LAUNCHED();
     const dim3 g(rt, S, groups);
-    const size_t dsm = sizeof(uint32_t) * (2 * kTM * kTK + 2 * kTN * kTK);
+    const size_t dsm = sizeof(uint32_t) * 2 * kStage;
     if (p->dim == 2)
-        k1t_matvec_tc<2><<<g, 256, dsm, s>>>(p->d_coord, x, ldx, nrhs, p->N, cps, nchunks, partial, d_err);
+        k1t_matvec_tc<2><<<g, 256, dsm, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial, d_err);
     else
-        k1t_matvec_tc<3><<<g, 256, dsm, s>>>(p->d_coord, x, ldx, nrhs, p->N, cps, nchunks, partial, d_err);
+        k1t_matvec_tc<3><<<g, 256, dsm, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial, d_err);
     IE_LAUNCHED();
     return IE_OK;
 }
@@ -238,7 +326,7 @@ int tc_rows() { return kTM; }
 int tc_cols() { return kTN; }
 
 int prepare_tc() {
-    const int dsm = (int)(sizeof(uint32_t) * (2 * kTM * kTK + 2 * kTN * kTK));
+    const int dsm = (int)(sizeof(uint32_t) * 2 * kStage);
     IE_TRY_CUDA(cudaFuncSetAttribute(k1t_matvec_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
     IE_TRY_CUDA(cudaFuncSetAttribute(k1t_matvec_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
     return IE_OK;
