@@ -132,6 +132,11 @@ struct DevBuf {
 // Internal matvec mode: the accurate (double-float) sum for an x whose entries are exactly
 // representable in FP32 (PCG rounds its search directions so), which saves one FFMA per pair.
 constexpr int IE_ACCURATE_X32 = 4;
+// Internal matvec modes of the exact kernel for the PCG inner product q = A p: the low word is
+// renormalised every 4 (mode 7) or 16 (mode 8) source steps instead of every step.  The error
+// stays many orders below what slows PCG; the true residual always uses IE_ACCURATE.
+constexpr int IE_ACCURATE_R4 = 7;
+constexpr int IE_ACCURATE_R16 = 8;
 
 // y = A x for device FP64 x (leading dimension ldx) and y (ldy), nrhs columns.
 // precision: IE_FP64, IE_MIXED, IE_ACCURATE or IE_ACCURATE_X32.

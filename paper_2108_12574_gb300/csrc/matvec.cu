@@ -714,6 +714,10 @@ int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, doubl
             IE_TRY(part.alloc(sizeof(double) * N * Se, s));
             if (p->dim == 2 && precision == IE_ACCURATE)
                 k2_accurate_2d<true, 1><<<dim3(rowpatch, Se), kThreads, 0, s>>>(p->d_table, xk, n, pps, part.as<double>());
+            else if (p->dim == 2 && precision == IE_ACCURATE_R4)
+                k2_accurate_2d<true, 4><<<dim3(rowpatch, Se), kThreads, 0, s>>>(p->d_table, xk, n, pps, part.as<double>());
+            else if (p->dim == 2 && precision == IE_ACCURATE_R16)
+                k2_accurate_2d<true, 16><<<dim3(rowpatch, Se), kThreads, 0, s>>>(p->d_table, xk, n, pps, part.as<double>());
             else if (p->dim == 2)
                 k2_accurate_2d<false, 2><<<dim3(rowpatch, Se), kThreads, 0, s>>>(p->d_table, xk, n, pps, part.as<double>());
             else

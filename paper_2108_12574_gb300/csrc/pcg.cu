@@ -255,7 +255,8 @@ struct Solver {
     }
     int mv_precision() const {
         if (o.inner == IE_FP64 + 16) return IE_FP64;
-        if (o.inner == IE_MIXED || o.inner == IE_ACCURATE || o.inner == IE_ACCURATE_X32 || o.inner == IE_TENSOR)
+        if (o.inner == IE_MIXED || o.inner == IE_ACCURATE || o.inner == IE_ACCURATE_X32 || o.inner == IE_TENSOR ||
+            o.inner == IE_ACCURATE_R4 || o.inner == IE_ACCURATE_R16)
             return o.inner;
         if (o.precision == IE_FP64) return IE_FP64;
         return p->dim == 2 ? IE_ACCURATE : IE_MIXED;
@@ -352,7 +353,7 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
     if (!(o.tol >= 0.0) || o.max_it < 1 || (o.precision != IE_FP64 && o.precision != IE_MIXED) ||
         o.replace_every < 0 || o.check_every < 0 || o.use_x0 < 0 || o.use_x0 > 2 ||
         (o.inner != 0 && o.inner != IE_MIXED && o.inner != IE_ACCURATE && o.inner != IE_ACCURATE_X32 &&
-         o.inner != IE_TENSOR &&
+         o.inner != IE_TENSOR && o.inner != IE_ACCURATE_R4 && o.inner != IE_ACCURATE_R16 &&
          o.inner != IE_FP64 + 16)) {
         ie_set_error("pcg_solve: invalid options"); return IE_ERR_ARG;
     }
