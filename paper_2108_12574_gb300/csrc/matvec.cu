@@ -502,17 +502,22 @@ k2_accurate_2d(const float2 *__restrict__ table, const double *__restrict__ x, i
     }
 }
 
-// 3D: 4 x 8 x 8 patches; the offset window is 7 x 15 x 15.
+// 3D: 4 x 8 x 8 patches; the offset window is 7 x 15 x 15.  Same exact accumulation as the 2D
+// kernel (power-of-two offset per 64-term window, Fast2Sum + one FMA for both rounding errors,
+// renormalisation every 8 terms), one target row per thread.
 __global__ void __launch_bounds__(kThreads)
 k2_accurate_3d(const float2 *__restrict__ table, const double *__restrict__ x, int n,
                int patches_per_split, double *__restrict__ partial) {
     __shared__ float2 W[7][15][16];
     __shared__ float2 X[4][8][8];
+    __shared__ float wmax[7];
+    __shared__ float xmax[4];
     const int n1 = (n + 3) / 4, n2 = (n + 7) / 8;  // patches along dim 0 and along dims 1, 2
     const int npatch = n1 * n2 * n2;
     const int b = blockIdx.x;
     const int I1 = (b / (n2 * n2)) * 4, I2 = ((b / n2) % n2) * 8, I3 = (b % n2) * 8;
     const int r1 = threadIdx.x >> 6, r2 = (threadIdx.x >> 3) & 7, r3 = threadIdx.x & 7;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i1 = I1 + r1, i2 = I2 + r2, i3 = I3 + r3;
     const long long N = (long long)n * n * n;
     double acc = 0.0;
@@ -535,19 +540,57 @@ k2_accurate_3d(const float2 *__restrict__ table, const double *__restrict__ x, i
             W[a][bb][c] = table[((long long)d1 * n + d2) * n + d3];
         }
         __syncthreads();
-        float sh = 0.f, sl = 0.f;
+        // maxima of |x_hi| per c1 plane (64 values) and of |t_hi| per a plane (225 values)
+        if (warp < 4) {
+            const float* xp = &X[warp][0][0].x;
+            float v = fmaxf(fabsf(xp[2 * lane]), fabsf(xp[2 * (lane + 32)]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (lane == 0) xmax[warp] = v;
+        } else {
+            for (int a = warp - 4; a < 7; a += 4) {
+                float v = 0.f;
+                for (int e = lane; e < 225; e += 32) v = fmaxf(v, fabsf(W[a][e / 15][e % 15].x));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+                if (lane == 0) wmax[a] = v;
+            }
+        }
+        __syncthreads();
+        float ah = 0.f, al = 0.f;
         for (int c1 = 0; c1 < 4; ++c1) {
+            const int a = r1 - c1 + 3;
+            int ex;
+            frexpf(64.f * wmax[a] * xmax[c1], &ex);
+            const float M = ldexpf(1.f, ex + 1);
+            float sh = M, sl = 0.f;
 #pragma unroll 2
             for (int c2 = 0; c2 < 8; ++c2) {
 #pragma unroll
                 for (int c3 = 0; c3 < 8; ++c3) {
-                    const float2 t = W[r1 - c1 + 3][r2 - c2 + 7][r3 - c3 + 7];
+                    const float2 t = W[a][r2 - c2 + 7][r3 - c3 + 7];
                     const float2 v = X[c1][c2][c3];
-                    df_fma(t.x, t.y, v.x, v.y, sh, sl);
+                    const float pr = __fmul_rn(t.x, v.x);
+                    const float sn = __fadd_rn(sh, pr);
+                    const float z = __fsub_rn(sn, sh);
+                    const float d = __fmaf_rn(t.x, v.x, -z);
+                    float lo = __fmaf_rn(t.y, v.x, sl);
+                    lo = __fmaf_rn(t.x, v.y, lo);
+                    sl = __fadd_rn(lo, d);
+                    sh = sn;
                 }
+                const float tt = __fadd_rn(sh, sl);
+                sl = __fsub_rn(sl, __fsub_rn(tt, sh));
+                sh = tt;
             }
+            const float wv = __fsub_rn(sh, M);
+            const float sn = __fadd_rn(ah, wv);
+            const float bp = __fsub_rn(sn, ah);
+            const float er = __fadd_rn(__fsub_rn(ah, __fsub_rn(sn, bp)), __fsub_rn(wv, bp));
+            al = __fadd_rn(al, __fadd_rn(er, sl));
+            ah = sn;
         }
-        acc += (double)sh + (double)sl;
+        acc += (double)ah + (double)al;
     }
     if (i1 < n && i2 < n && i3 < n) partial[(long long)blockIdx.y * N + ((long long)i1 * n + i2) * n + i3] = acc;
 }

@@ -10,7 +10,7 @@
 //     iterations back to back between host checks.  IE_MIXED checks after each head so that
 //     the accurate residual f - A u (FP64-class, ie_matvec IE_ACCURATE) can replace r between
 //     head and tail (residual replacement: when the recursive residual has dropped by
-//     `kReplaceDrop` since the last replacement, every replace_every iterations, and when it
+//     a set factor since the last replacement, every replace_every iterations, and when it
 //     reaches tol -- a column is done only when the replaced (true) residual meets tol).
 #include <cuda_runtime.h>
 
@@ -23,7 +23,12 @@
 
 namespace {
 
-constexpr double kReplaceDrop = 1e-3;  // replace when relres fell by this factor since last time
+// Replace r by the accurate residual when the recursive residual fell by this factor since the
+// last replacement (FP32 inner matvecs only).  The gap an FP32 matvec opens per cycle is about
+// its error times cond(A): 1e-3 in 2D (cond ~1e5) needs a replacement every 1e3 of decrease;
+// in 3D (cond ~1e3) every 1e4 suffices.
+constexpr double kReplaceDrop2D = 1e-3;
+constexpr double kReplaceDrop3D = 1e-4;
 
 struct PcgCol {
     double ff;       // ||f||^2
@@ -451,7 +456,8 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
                 bool pending = c.flag == 1;
                 bool due = c.active == 1 &&
                            ((o.replace_every > 0 && c.it > 0 && c.it % o.replace_every == 0) ||
-                            (!S.exact_inner() && relres <= kReplaceDrop * relres_at_replace[(size_t)k]));
+                            (!S.exact_inner() &&
+                             relres <= (p->dim == 2 ? kReplaceDrop2D : kReplaceDrop3D) * relres_at_replace[(size_t)k]));
                 if (!pending && !due) continue;
                 double rr_true = 0;
                 IE_TRY(S.accurate_residual(k, &rr_true));
