@@ -105,8 +105,8 @@ def kernel_case(args):
 def config_dict():
     return {"workload": WORKLOAD, "dim": DIM, "n": NGRID, "N": NGRID ** DIM, "m": MPART, "delta": DELTA,
             "rhs": f"GRF l={ELL} seed=rank", "tol": TOL, "decomposition": "schwarz",
-            "precision": "mixed (double-float table matvec on FP32 pipes, FP32 factors with FP64 solves, "
-                         "FP64 scalars and vectors)",
+            "precision": "mixed (double-float table matvec on FP32 pipes, FP32 explicit subdomain inverses "
+                         "with double-float products, FP64 scalars and vectors)",
             "l2": "flushed between timed steps (512 MiB write)"}
 
 

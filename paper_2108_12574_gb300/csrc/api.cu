@@ -377,6 +377,23 @@ extern "C" int dd_factor(const ie_problem *p, const dd_partition_t *s, int preci
     if ((e = cudaMalloc(&f->d_order, sizeof(int) * order.size())) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&f->d_info, sizeof(int) * nb.size())) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&f->d_pool, esz * (size_t)f->pool_elems)) != cudaSuccess) return fail(e);
+    f->inverse = precision == IE_MIXED && f->max_pad <= kInvMaxPad;
+    if (f->inverse) {
+        if ((e = cudaMalloc(&f->d_inv_pool, esz * (size_t)f->pool_elems)) != cudaSuccess) return fail(e);
+        std::vector<long long> xoff((size_t)s->nblocks + 1, 0);
+        std::vector<int2> chunks;
+        for (int i = 0; i < s->nblocks; ++i) xoff[(size_t)i + 1] = xoff[(size_t)i] + npad[(size_t)i];
+        for (int i : order)  // largest blocks first
+            for (int r0 = 0; r0 < nb[(size_t)i]; r0 += kApplyRows) chunks.push_back(make_int2(i, r0));
+        f->xtotal = xoff.back();
+        f->nchunks = (int)chunks.size();
+        if ((e = cudaMalloc(&f->d_xoff, sizeof(long long) * xoff.size())) != cudaSuccess) return fail(e);
+        if ((e = cudaMalloc(&f->d_chunks, sizeof(int2) * std::max<size_t>(chunks.size(), 1))) != cudaSuccess) return fail(e);
+        if ((e = cudaMemcpy(f->d_xoff, xoff.data(), sizeof(long long) * xoff.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+        if (!chunks.empty() &&
+            (e = cudaMemcpy(f->d_chunks, chunks.data(), sizeof(int2) * chunks.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return fail(e);
+    }
     if ((e = cudaMemcpy(f->d_loff, loff.data(), sizeof(long long) * loff.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpy(f->d_npad, npad.data(), sizeof(int) * npad.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpy(f->d_n, nb.data(), sizeof(int) * nb.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
@@ -388,6 +405,11 @@ extern "C" int dd_factor(const ie_problem *p, const dd_partition_t *s, int preci
     std::vector<int> hinfo((size_t)s->nblocks);
     if ((e = cudaMemcpyAsync(hinfo.data(), f->d_info, sizeof(int) * hinfo.size(), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return fail(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+    if (f->inverse) {  // the factors were only the way to the inverses
+        if ((e = cudaFree(f->d_pool)) != cudaSuccess) return fail(e);
+        f->d_pool = f->d_inv_pool;
+        f->d_inv_pool = nullptr;
+    }
     *out = f;
     for (int i = 0; i < s->nblocks; ++i) {
         if (hinfo[(size_t)i] >= 0) {
@@ -409,6 +431,9 @@ extern "C" void dd_factor_destroy(dd_factor_t *f) {
     cudaFree(f->d_order);
     cudaFree(f->d_info);
     cudaFree(f->d_pool);
+    cudaFree(f->d_inv_pool);
+    cudaFree(f->d_xoff);
+    cudaFree(f->d_chunks);
     delete f;
 }
 

@@ -7,6 +7,17 @@
 //                   solved by one warp with shuffles.  L_i is read twice (both passes), which is
 //                   the HBM traffic that bounds the step.  The block result goes to a scratch
 //                   vector [rhs][sum n_i].
+// K6s apply_split   (FP32 explicit inverses) per (subdomain, right-hand side): R_i r scaled by a
+//                   power of two and split into FP32 hi/lo words, once per apply.
+// K6i apply_inverse one CTA of 256 threads per (64 rows of a subdomain, group of R right-hand
+//                   sides): z_i = M_i (R_i r) with the symmetric M_i = A_i^{-1} stored in FP32, a
+//                   batched GEMV (R = 1) or GEMM (R = 4, 8) streaming M_i once per group, every row
+//                   independent.  Products and sums are double-float (~2^-48 of the
+//                   partial sums), so the operator applied is the fixed symmetric matrix M_i to
+//                   working accuracy.  FP32 sums would not be: their error acts like a
+//                   preconditioner that changes from one iteration to the next, and PCG slows
+//                   down (by 2 iterations at 128^2 already with sums good to 2^-48 of the
+//                   largest row sum instead of the partial sums).
 // K6b overlap_sum   z_p = sum of the block results of every subdomain containing p, in increasing
 //                   subdomain order (inverse index map), so the sum is deterministic.
 #include <cuda_runtime.h>
@@ -196,6 +207,200 @@ apply_blocks_multi(const TL *__restrict__ pool, const long long *__restrict__ lo
     }
 }
 
+// Double-float accumulation of one term m (h + l) into (s, c): p = m h rounded (kept out of any
+// FMA contraction), its exact error and m l go to c together with the exact TwoSum error of
+// s + p.  11 FP32 operations; the sum is good to ~2^-48 of the partial sums' magnitudes.
+__device__ __forceinline__ void df_fma(float &s, float &c, float m, float h, float l) {
+    const float p = __fmul_rn(m, h);
+    const float pe = fmaf(m, l, fmaf(m, h, -p));
+    const float t = s + p;
+    const float bp = t - s;
+    const float err = (s - (t - bp)) + (p - bp);
+    s = t;
+    c += err + pe;
+}
+
+// Butterfly sum of the (hi, lo) pairs of a group of kLPR lanes with exact TwoSum errors; every
+// lane of the group ends with the same pair (the exact error of hi_a + hi_b does not depend on
+// the order of the operands).
+__device__ __forceinline__ void df_group_sum(float &hi, float &lo) {
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        const float hs = __shfl_xor_sync(0xffffffffu, hi, o), ls = __shfl_xor_sync(0xffffffffu, lo, o);
+        const float t = hi + hs;
+        const float bp = t - hi;
+        const float err = (hi - (t - bp)) + (hs - bp);
+        hi = t;
+        lo = (lo + ls) + err;
+    }
+}
+
+// x 2^e, exact whenever the result is a normal double: two multiplies by powers of two built
+// from their bits (each half of e stays in the normal exponent range), instead of ldexp.
+__device__ __forceinline__ double pow2_bits(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+__device__ __forceinline__ double scale2(double x, int e) {
+    const int e1 = e / 2;
+    return (x * pow2_bits(e1)) * pow2_bits(e - e1);
+}
+
+// K6s: x = r 2^-e per (subdomain, right-hand side), e the exponent with max_a |r_a| < 2^e (an exact
+// scaling: the FP32 words of x neither overflow nor lose bits to underflow whatever the scale of
+// r), split into FP32 hi and (LO) lo words, padded with zeros to the block's padded size.
+template <bool LO>
+__global__ void __launch_bounds__(256)
+apply_split(const int *__restrict__ npad, const int *__restrict__ nb, const long long *__restrict__ offs,
+            const int *__restrict__ idx, const long long *__restrict__ xoff, const double *__restrict__ r,
+            long long ldr, long long xtotal, int nblocks, float *__restrict__ xh, float *__restrict__ xl,
+            int *__restrict__ xexp) {
+    __shared__ double wmax[8];
+    __shared__ int se;
+    const int b = blockIdx.x, k = blockIdx.y;
+    const int np = npad[b], n = nb[b];
+    const int *id = idx + offs[b];
+    const double *rk = r + (long long)k * ldr;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double m = 0.0;
+    for (int a = tid; a < n; a += 256) m = fmax(m, fabs(rk[id[a]]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) wmax[warp] = m;
+    __syncthreads();
+    if (tid == 0) {
+        double mm = 0.0;
+        for (int w = 0; w < 8; ++w) mm = fmax(mm, wmax[w]);
+        int e = 0;
+        frexp(mm, &e);  // mm = f 2^e, f in [0.5, 1)
+        se = e;
+        xexp[(long long)k * nblocks + b] = e;
+    }
+    __syncthreads();
+    const long long base = (long long)k * xtotal + xoff[b];
+    for (int a = tid; a < np; a += 256) {
+        const double x = a < n ? scale2(rk[id[a]], -se) : 0.0;
+        const float h = (float)x;
+        xh[base + a] = h;
+        if (LO) xl[base + a] = (float)(x - (double)h);
+    }
+}
+
+// K6i: one CTA per (chunk of kApplyRows rows of one subdomain, group of R right-hand sides).  The
+// CTA stages the block's split x for its R columns in shared memory.  A row is taken by LPR = 8
+// lanes (the padded size is a multiple of 32, so every lane has the same np/32 float4 columns:
+// lane c of the group reads float4 columns c, c + 8, ...); a warp covers 4 x RW rows per pass,
+// the 4 row groups reading the same x words (shared-memory broadcast), U float4 loads per lane
+// and row issued before any arithmetic.  The column order of every sum is the same for every R,
+// so a column's result does not depend on how many right-hand sides share the pass.  EXACT:
+// double-float products and sums (df_fma); otherwise FP32 FMAs on the hi words.  The FP64
+// conversion of each result runs in one lane only (FP64 is 1/64 of the FP32 rate).
+constexpr int kLPR = 8;
+
+template <int R, int RW, int U, bool EXACT>
+__device__ __forceinline__ void inverse_chunk(float (&s)[RW][R], float (&c)[RW][R], const float4 *const (&mrow)[RW],
+                                              int u, int cl, int np4, const float4 *xh4, const float4 *xl4) {
+    float4 m4[RW][U];
+#pragma unroll
+    for (int uu = 0; uu < U; ++uu)
+#pragma unroll
+        for (int q = 0; q < RW; ++q) m4[q][uu] = __ldg(mrow[q] + (u + uu) * kLPR);
+#pragma unroll
+    for (int uu = 0; uu < U; ++uu) {
+        const int c4 = cl + (u + uu) * kLPR;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const float4 h = xh4[j * np4 + c4];
+            if (EXACT) {
+                const float4 l = xl4[j * np4 + c4];
+#pragma unroll
+                for (int q = 0; q < RW; ++q) {
+                    df_fma(s[q][j], c[q][j], m4[q][uu].x, h.x, l.x);
+                    df_fma(s[q][j], c[q][j], m4[q][uu].y, h.y, l.y);
+                    df_fma(s[q][j], c[q][j], m4[q][uu].z, h.z, l.z);
+                    df_fma(s[q][j], c[q][j], m4[q][uu].w, h.w, l.w);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < RW; ++q) {
+                    s[q][j] = fmaf(m4[q][uu].x, h.x, s[q][j]);
+                    s[q][j] = fmaf(m4[q][uu].y, h.y, s[q][j]);
+                    s[q][j] = fmaf(m4[q][uu].z, h.z, s[q][j]);
+                    s[q][j] = fmaf(m4[q][uu].w, h.w, s[q][j]);
+                }
+            }
+        }
+    }
+}
+
+template <int R, int RW, int U, bool EXACT>
+__global__ void __launch_bounds__(256)
+apply_inverse(const float *__restrict__ pool, const long long *__restrict__ loff, const int *__restrict__ npad,
+              const int *__restrict__ nb, const long long *__restrict__ offs, const int2 *__restrict__ chunks,
+              const long long *__restrict__ xoff, const float *__restrict__ xh_g, const float *__restrict__ xl_g,
+              const int *__restrict__ xexp, long long xtotal, int nblocks, int nrhs, double *__restrict__ zbuf,
+              long long total) {
+    constexpr int SUB = 32 / kLPR;                  // row groups per warp
+    constexpr int K = (RW * R + kLPR - 1) / kLPR;   // results per lane and pass
+    extern __shared__ __align__(16) float xs[];     // x hi words [R][np], then (EXACT) lo words [R][np]
+    const int2 ch = chunks[blockIdx.x];
+    const int b = ch.x, row0 = ch.y;
+    const int g0 = blockIdx.y * R;
+    const int np = npad[b], n = nb[b];
+    const int rend = min(row0 + kApplyRows, n);
+    const float *M = pool + loff[b];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int sub = lane / kLPR, cl = lane % kLPR;
+    const int np4 = np >> 2, cnt = np4 / kLPR;
+    float4 *xh4 = reinterpret_cast<float4 *>(xs), *xl4 = xh4 + R * np4;
+    for (int e = tid; e < R * np4; e += 256) {
+        const int j = e / np4, c4 = e - j * np4;
+        const long long src = ((long long)(g0 + j) * xtotal + xoff[b]) / 4 + c4;
+        const bool ok = g0 + j < nrhs;
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        xh4[e] = ok ? reinterpret_cast<const float4 *>(xh_g)[src] : zero;
+        if (EXACT) xl4[e] = ok ? reinterpret_cast<const float4 *>(xl_g)[src] : zero;
+    }
+    __syncthreads();
+    for (int a0 = row0 + warp * SUB * RW; a0 < rend; a0 += 8 * SUB * RW) {
+        const int ab = a0 + sub * RW;  // first row of this lane's group
+        const float4 *mrow[RW];
+#pragma unroll
+        for (int q = 0; q < RW; ++q)
+            mrow[q] = reinterpret_cast<const float4 *>(M + (long long)min(ab + q, n - 1) * np) + cl;
+        float s[RW][R], c[RW][R];
+#pragma unroll
+        for (int q = 0; q < RW; ++q)
+#pragma unroll
+            for (int j = 0; j < R; ++j) { s[q][j] = 0.f; c[q][j] = 0.f; }
+        int u = 0;
+        for (; u + U <= cnt; u += U) inverse_chunk<R, RW, U, EXACT>(s, c, mrow, u, cl, np4, xh4, xl4);
+        for (; u < cnt; ++u) inverse_chunk<R, RW, 1, EXACT>(s, c, mrow, u, cl, np4, xh4, xl4);
+        float oh[K], ol[K];
+#pragma unroll
+        for (int t = 0; t < K; ++t) { oh[t] = 0.f; ol[t] = 0.f; }
+#pragma unroll
+        for (int q = 0; q < RW; ++q) {
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                float hi = s[q][j], lo = c[q][j];
+                if (EXACT) {
+                    df_group_sum(hi, lo);
+                } else {
+#pragma unroll
+                    for (int o = kLPR / 2; o > 0; o >>= 1) hi += __shfl_xor_sync(0xffffffffu, hi, o);
+                }
+                const int k = q * R + j;
+                if (cl == k % kLPR) { oh[k / kLPR] = hi; ol[k / kLPR] = lo; }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            const int k = t * kLPR + cl, q = k / R, j = k % R;
+            if (k < RW * R && ab + q < rend && g0 + j < nrhs)
+                zbuf[(long long)(g0 + j) * total + offs[b] + ab + q] =
+                    scale2((double)oh[t] + (double)ol[t], xexp[(long long)(g0 + j) * nblocks + b]);
+        }
+    }
+}
+
 __global__ void overlap_sum(const double *__restrict__ zbuf, long long total, const long long *__restrict__ inv_ptr,
                             const long long *__restrict__ inv_pos, double *__restrict__ z, long long ldz, long long N) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -216,6 +421,9 @@ constexpr int kApplySmemCeiling = 200 * 1024;
 
 int prepare_apply(const dd_factor_t *f) {
     (void)f;
+    IE_TRY_CUDA(cudaFuncSetAttribute(apply_inverse<8, 2, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmemCeiling));
+    IE_TRY_CUDA(cudaFuncSetAttribute(apply_inverse<4, 2, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmemCeiling));
+    IE_TRY_CUDA(cudaFuncSetAttribute(apply_inverse<1, 2, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmemCeiling));
     IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks_multi<double, double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmemCeiling));
     IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks_multi<float, double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmemCeiling));
     IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks_multi<float, float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmemCeiling));
@@ -231,7 +439,36 @@ int launch_apply(const dd_factor_t *f, const double *r, long long ldr, double *z
     DevBuf zbuf;
     IE_TRY(zbuf.alloc(sizeof(double) * (size_t)std::max<long long>(part->total, 1) * nrhs, s));
     const size_t smm = sizeof(double) * f->max_pad * kRM;
-    if (f->nblocks > 0 && nrhs >= 4 && smm <= (size_t)kApplySmemCeiling) {
+    if (f->nblocks > 0 && f->inverse) {
+        // 2D blocks, and single columns, get the double-float sums; batches of 3D columns FP32
+        const bool exact = p->dim == 2 || nrhs < 4;
+        DevBuf xb, xe;
+        IE_TRY(xb.alloc(sizeof(float) * (size_t)f->xtotal * nrhs * (exact ? 2 : 1), s));
+        IE_TRY(xe.alloc(sizeof(int) * (size_t)f->nblocks * nrhs, s));
+        float *xh = xb.as<float>(), *xl = exact ? xh + f->xtotal * nrhs : nullptr;
+        const float *M = (const float *)f->d_pool;
+        dim3 gs(f->nblocks, nrhs);
+        if (exact) {
+            apply_split<true><<<gs, 256, 0, s>>>(f->d_npad, f->d_n, part->d_offs, part->d_idx, f->d_xoff, r, ldr,
+                                                 f->xtotal, f->nblocks, xh, xl, xe.as<int>());
+        } else {
+            apply_split<false><<<gs, 256, 0, s>>>(f->d_npad, f->d_n, part->d_offs, part->d_idx, f->d_xoff, r, ldr,
+                                                  f->xtotal, f->nblocks, xh, xl, xe.as<int>());
+        }
+        IE_LAUNCHED();
+#define IE_APPLY_INV(R_, RW_, U_, EX_)                                                                   \
+    apply_inverse<R_, RW_, U_, EX_><<<dim3(f->nchunks, (nrhs + R_ - 1) / R_), 256,                       \
+                                      sizeof(float) * (EX_ ? 2 : 1) * R_ * f->max_pad, s>>>(              \
+        M, f->d_loff, f->d_npad, f->d_n, part->d_offs, f->d_chunks, f->d_xoff, xh, xl, xe.as<int>(),     \
+        f->xtotal, f->nblocks, nrhs, zbuf.as<double>(), part->total)
+        if (f->nchunks > 0) {
+            if (!exact) IE_APPLY_INV(8, 2, 4, false);
+            else if (nrhs >= 4) IE_APPLY_INV(4, 2, 2, true);
+            else IE_APPLY_INV(1, 2, 4, true);
+            IE_LAUNCHED();
+        }
+#undef IE_APPLY_INV
+    } else if (f->nblocks > 0 && nrhs >= 4 && smm <= (size_t)kApplySmemCeiling) {
         if (f->precision == IE_FP64) {
             dim3 g(f->nblocks, (nrhs + 15) / 16);
             apply_blocks_multi<double, double, 16><<<g, 256, smm, s>>>((const double *)f->d_pool, f->d_loff, f->d_npad,

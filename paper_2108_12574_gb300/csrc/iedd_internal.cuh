@@ -103,10 +103,23 @@ struct dd_factor_t {
     int *d_npad = nullptr;         // padded (multiple of 32) size of each block
     int *d_n = nullptr;            // true size of each block
     int *d_order = nullptr;        // schedule order: blocks by decreasing size
-    void *d_pool = nullptr;        // padded row-major lower factors (float or double)
+    void *d_pool = nullptr;        // padded row-major lower factors (float or double), or the
+                                   // symmetric inverses M_i = A_i^{-1} when inverse != 0
     long long pool_elems = 0;
     int *d_info = nullptr;         // per-block first bad pivot (-1 ok)
+    int inverse = 0;               // FP32 explicit inverses (IE_MIXED, max_pad <= kInvMaxPad)
+    void *d_inv_pool = nullptr;    // inverses while the factor runs (moved to d_pool afterwards)
+    long long *d_xoff = nullptr;   // per block: offset of its padded slice of the apply's split x
+    long long xtotal = 0;          // sum of the padded block sizes
+    int nchunks = 0;               // apply work items: (block, first row) per kApplyRows rows
+    int2 *d_chunks = nullptr;
 };
+
+// Largest padded block whose inverse strip (max_pad x 33 FP32) fits one CTA's shared memory.
+constexpr int kInvMaxPad = 1536;
+// Rows of one subdomain handled by one CTA of the explicit-inverse apply.
+constexpr int kApplyRows = 64;
+size_t inverse_strip_smem(int max_pad);
 
 // ---------------------------------------------------------------------------------------------
 // Device vector helpers: host / device pointer detection and staging

@@ -191,7 +191,10 @@ def test_partition_rejects_bad_sizes():
 
 
 APPLY_CASES = [(2, 64, 4, 1, O.SCHWARZ), (2, 40, 5, 2, O.SCHWARZ), (3, 16, 2, 1, O.SCHWARZ),
-               (2, 32, 8, 1, O.CBD), (2, 30, 3, 0, O.JACOBI), (3, 12, 3, 1, O.CBD)]
+               (2, 32, 8, 1, O.CBD), (2, 30, 3, 0, O.JACOBI), (3, 12, 3, 1, O.CBD),
+               # colour blocks of 1600 points: beyond the explicit-inverse limit, FP32 factors
+               # are applied by triangular solves instead
+               (2, 64, 4, 2, O.CBD)]
 
 
 @pytest.mark.parametrize("nrhs", [2, 20])
@@ -212,6 +215,40 @@ def test_apply_parity(dim, n, m, delta, kind, nrhs):
         err = np.linalg.norm(host(Z) - ref) / np.linalg.norm(ref)
         assert err <= tol, (prec, err)
         fac.close()
+
+
+@pytest.mark.parametrize("dim,n,m,delta", [(2, 64, 4, 2), (3, 16, 2, 1), (2, 40, 5, 2)])
+def test_mixed_apply_is_a_fixed_symmetric_operator(dim, n, m, delta):
+    # FP32 explicit inverses applied with double-float sums: the operator is the fixed
+    # symmetric matrix sum_i R_i^T M_i R_i to ~1e-12, where FP32 sums would leave ~1e-7
+    N = n ** dim
+    prob = iedd.ie_discretize(dim, n)
+    part = iedd.dd_partition(prob, m, delta, iedd.DD_SCHWARZ)
+    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
+    U = I.uniform_rhs_batch(N, [31, 32]).T.copy()
+    Z = torch.zeros((2, N), dtype=torch.float64, device="cuda")
+    iedd.dd_apply(fac, dev(U), Z)
+    Zh = host(Z)
+    a, b = float(U[0] @ Zh[1]), float(U[1] @ Zh[0])
+    scale = np.linalg.norm(U[0]) * np.linalg.norm(Zh[1])
+    assert abs(a - b) <= 1e-10 * scale, (a, b, abs(a - b) / scale)
+    # linearity under a scaling that is not a power of two
+    Z3 = torch.zeros_like(Z)
+    iedd.dd_apply(fac, dev(3.0 * U), Z3)
+    err = np.linalg.norm(host(Z3) - 3.0 * Zh) / np.linalg.norm(3.0 * Zh)
+    assert err <= 1e-10, err
+    # a batch of 8 columns (one pass over M_i per 4 columns) gives each column bit for bit as
+    # alone in 2D; 3D batches take FP32 sums (their blocks are well conditioned), good to ~1e-6
+    R = I.uniform_rhs_batch(N, list(range(40, 48))).T.copy()
+    Z8 = torch.zeros((8, N), dtype=torch.float64, device="cuda")
+    iedd.dd_apply(fac, dev(R), Z8)
+    for k in (0, 5, 7):
+        z = torch.zeros(N, dtype=torch.float64, device="cuda")
+        iedd.dd_apply(fac, dev(R[k]), z)
+        if dim == 2:
+            assert torch.equal(z, Z8[k]), k
+        else:
+            assert float(torch.linalg.norm(z - Z8[k]) / torch.linalg.norm(z)) <= 1e-6, k
 
 
 def test_apply_is_deterministic():
@@ -402,9 +439,11 @@ def test_pcg_full_size_512_mixed():
     assert O.true_relative_residual(2, n, f, host(u)) <= 1e-8 * 1.01
     P = O.Problem(2, n, m, delta, O.SCHWARZ, matvec="fft")
     u_ref, it_ref, _ = P.solve(f, 1e-8)
-    # mixed mode: FP32 factors and a double-float matvec change the rounding of CG; at
-    # cond(A) ~ 2e5 that moves the count by a few iterations (FP64 mode matches exactly)
-    assert abs(rep["iterations"] - it_ref) <= 3, (rep, it_ref)
+    # mixed mode: an FP32-stored preconditioner is a slightly different SPD operator (its
+    # smallest eigenvalues move by ~eps_fp32 cond(A_i)): with an exact matvec and exact products,
+    # every FP32 rounding of A_i^{-1} or L_i takes 46 to 48 iterations where FP64 takes 44, and
+    # the double-float matvec and the residual replacement move the count by one or two more
+    assert it_ref - 1 <= rep["iterations"] <= it_ref + 5, (rep, it_ref)
     assert np.linalg.norm(host(u) - u_ref) / np.linalg.norm(u_ref) <= 1e-6
 
 
