@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=WORKLOAD)
     ap.add_argument("--no-extras", action="store_true", help="skip FP64-plain and CPU-baseline legs")
-    ap.add_argument("--kernel", choices=["k1", "k2", "kd", "tc", "stored", "apply", "factor"], default=None,
+    ap.add_argument("--kernel", choices=["k1", "k2", "kd", "tc", "stored", "fft", "apply", "factor"], default=None,
                     help="profiling case: run one hot operation twice on a --dim/--n/--nrhs problem and exit")
     ap.add_argument("--dim", type=int, default=DIM)
     ap.add_argument("--n", type=int, default=NGRID)
@@ -86,9 +86,9 @@ def kernel_case(args):
     Y = torch.zeros_like(X)
     m = args.n // 16 if args.dim == 2 else args.n // 8
     for _ in range(2):
-        if args.kernel in ("k1", "k2", "kd", "tc", "stored"):
+        if args.kernel in ("k1", "k2", "kd", "tc", "stored", "fft"):
             prec = {"k1": iedd.IE_MIXED, "k2": iedd.IE_ACCURATE, "kd": iedd.IE_FP64, "tc": iedd.IE_TENSOR,
-                    "stored": iedd.IE_STORED}[args.kernel]
+                    "stored": iedd.IE_STORED, "fft": iedd.IE_FFT}[args.kernel]
             if args.kernel == "stored":
                 iedd.ie_store_matrix(prob)
             iedd.ie_matvec(prob, X, Y, prec)

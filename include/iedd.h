@@ -121,6 +121,14 @@ IEDD_API int ie_matvec(const ie_problem *p, const double *x, double *y, int nrhs
                          split, FP32 accumulation in tensor memory), 64 right-hand sides per CTA;
                          same accuracy class as IE_MIXED.  Returns IE_ERR_TIMEOUT if a CTA gave
                          up waiting for its MMAs (bounded waits; the call then synchronizes). */
+#define IE_FFT 9      /* the paper's FFT matvec (Sec. 6): A is Toeplitz in every coordinate on the
+                         uniform grid, so A x is a convolution, computed in FP64 on the periodic
+                         grid of L^d points (L the power of two >= 2n - 1; pairs of columns share
+                         one complex transform).  FP64-class result.  n <= 4096 (IE_ERR_ARG
+                         otherwise).  The first IE_FFT call on a problem builds the kernel's
+                         spectrum (8 L^d bytes, kept until ie_destroy) and synchronizes; it must
+                         not be inside a stream capture and must not run concurrently with another
+                         call on the same problem.  Scratch: 16 L^d bytes per pair of columns. */
 
 /*
  * ie_store_matrix -- stored-matrix fallback: materialise the off-diagonal part of A densely in
@@ -197,6 +205,8 @@ typedef struct {
                               4            as IE_ACCURATE with the search directions rounded to
                                            FP32 (one FFMA less per pair, more iterations)
                               IE_TENSOR    the tcgen05 batched kernel (many right-hand sides)
+                              IE_FFT       the FP64 FFT matvec (Sec. 6), also used for the
+                                           accurate residual; the first use builds its plan
                               16           the FP64 regenerated matvec in either precision */
 } pcg_opts;
 

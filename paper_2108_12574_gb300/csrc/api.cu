@@ -126,6 +126,8 @@ extern "C" void ie_destroy(ie_problem *p) {
     cudaFree(p->d_table64);
     cudaFree(p->d_stored);
     cudaFree(p->d_err);
+    cudaFree(p->d_fft_tw);
+    cudaFree(p->d_fft_chat);
     delete p;
 }
 
@@ -177,7 +179,7 @@ extern "C" int ie_matvec(const ie_problem *p, const double *x, double *y, int nr
                          int precision, void *stream) {
     IE_TRY(check_vec_args("ie_matvec", p, x, y, nrhs, ld));
     if (precision != IE_FP64 && precision != IE_MIXED && precision != IE_ACCURATE && precision != IE_STORED &&
-        precision != IE_TENSOR) {
+        precision != IE_TENSOR && precision != IE_FFT) {
         ie_set_error("ie_matvec: unknown precision"); return IE_ERR_ARG;
     }
     if (precision == IE_STORED && !p->d_stored) {
@@ -185,6 +187,15 @@ extern "C" int ie_matvec(const ie_problem *p, const double *x, double *y, int nr
     }
     DeviceGuard g(p->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (precision == IE_FFT && !p->d_fft_chat) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        IE_TRY_CUDA(cudaStreamIsCapturing(s, &cs));
+        if (cs != cudaStreamCaptureStatusNone) {
+            ie_set_error("ie_matvec: the first IE_FFT call on a problem builds its FFT plan and must not be captured");
+            return IE_ERR_ARG;
+        }
+        IE_TRY(prepare_fft(p));
+    }
     Staged sx, sy;
     IE_TRY(stage_in(x, p->N, nrhs, ld, true, s, sx));
     IE_TRY(stage_in(y, p->N, nrhs, ld, false, s, sy));

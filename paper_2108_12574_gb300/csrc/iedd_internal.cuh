@@ -74,6 +74,11 @@ struct ie_problem {
     float *d_stored = nullptr;     // optional dense FP32 copy of A (zero diagonal), ie_store_matrix
     int *d_err = nullptr;          // device error word of the tensor-core matvec (bounded waits)
     int sm_count = 0;
+    // FFT matvec (built on first use): periodic grid of L = 2^fft_lg points per axis, twiddles
+    // exp(-2 pi i k / L) (k < L / 2) and the kernel's spectrum (FP64, L^d, forward-pass order)
+    int fft_lg = 0;
+    double2 *d_fft_tw = nullptr;
+    double *d_fft_chat = nullptr;
 };
 
 struct dd_partition_t {
@@ -167,6 +172,12 @@ int tc_rows();
 int tc_cols();
 int launch_matvec_stored(const ie_problem *p, const double *x, long long ldx, double *y, long long ldy, int nrhs,
                          cudaStream_t s);
+
+// FFT matvec (fft.cu): prepare_fft builds the plan once per problem (synchronizes; not inside a
+// stream capture); launch_matvec_fft then computes y = A x for nrhs columns.
+int prepare_fft(const ie_problem *p);
+int launch_matvec_fft(const ie_problem *p, const double *x, long long ldx, double *y, long long ldy, int nrhs,
+                      cudaStream_t s);
 
 int launch_factor(dd_factor_t *f, cudaStream_t s);
 int prepare_apply(const dd_factor_t *f);

@@ -638,6 +638,11 @@ int build_problem_tables(ie_problem *p) {
 int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, double *y, long long ldy,
                       int nrhs, int precision, double *dot_out, cudaStream_t s) {
     const long long N = p->N;
+    if (precision == IE_FFT) {
+        IE_TRY(launch_matvec_fft(p, x, ldx, y, ldy, nrhs, s));
+        if (dot_out) IE_TRY(launch_dots(x, ldx, y, ldy, N, nrhs, dot_out, s));
+        return IE_OK;
+    }
     const int ntiles = (int)((N + kThreads - 1) / kThreads);
     DevBuf xsum;
     if (p->dim == 2 && (precision == IE_MIXED || precision == IE_FP64 || precision == IE_TENSOR)) {

@@ -261,13 +261,17 @@ struct Solver {
     int mv_precision() const {
         if (o.inner == IE_FP64 + 16) return IE_FP64;
         if (o.inner == IE_MIXED || o.inner == IE_ACCURATE || o.inner == IE_ACCURATE_X32 || o.inner == IE_TENSOR ||
-            o.inner == IE_ACCURATE_R4 || o.inner == IE_ACCURATE_R16)
+            o.inner == IE_ACCURATE_R4 || o.inner == IE_ACCURATE_R16 || o.inner == IE_FFT)
             return o.inner;
         if (o.precision == IE_FP64) return IE_FP64;
         return p->dim == 2 ? IE_ACCURATE : IE_MIXED;
     }
     bool exact_inner() const { return mv_precision() != IE_MIXED && mv_precision() != IE_TENSOR; }
-    int acc_precision() const { return o.precision == IE_FP64 ? IE_FP64 : IE_ACCURATE; }
+    // the accurate residual: the FFT matvec is FP64-class, so an FFT inner matvec serves for both
+    int acc_precision() const {
+        if (o.inner == IE_FFT) return IE_FFT;
+        return o.precision == IE_FP64 ? IE_FP64 : IE_ACCURATE;
+    }
     dim3 vg() const { return dim3(vgrid, nrhs); }
 
     int head(int slot) {
@@ -359,12 +363,13 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
         o.replace_every < 0 || o.check_every < 0 || o.use_x0 < 0 || o.use_x0 > 2 ||
         (o.inner != 0 && o.inner != IE_MIXED && o.inner != IE_ACCURATE && o.inner != IE_ACCURATE_X32 &&
          o.inner != IE_TENSOR && o.inner != IE_ACCURATE_R4 && o.inner != IE_ACCURATE_R16 &&
-         o.inner != IE_FP64 + 16)) {
+         o.inner != IE_FP64 + 16 && o.inner != IE_FFT)) {
         ie_set_error("pcg_solve: invalid options"); return IE_ERR_ARG;
     }
     if (o.check_every < 1) o.check_every = 1;
     const auto t_start = std::chrono::steady_clock::now();
     DeviceGuard g(p->device);
+    if (o.inner == IE_FFT) IE_TRY(prepare_fft(p));  // before any capture
     PrivateStream ps;
     IE_TRY(ps.init(static_cast<cudaStream_t>(stream)));
     Solver S{p, fac, nrhs, p->N, o, ps.s};

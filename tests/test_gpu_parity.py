@@ -132,6 +132,68 @@ def test_matvec_full_size_sampled_rows(n, rows_seed):
         assert err <= tol * scale, (prec, err)
 
 
+@pytest.mark.parametrize("dim,n,conv", MATVEC_CASES + [(2, 5, O.GRID_TEXT), (3, 3, O.GRID_TEXT)])
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_fft_matvec_parity(dim, n, conv, nrhs):
+    # the FFT matvec (circulant embedding, FP64): FP64 accuracy against the direct sum, for odd
+    # and even sizes, both grid conventions, and an odd number of columns (one column's pair
+    # partner is zero)
+    N = n ** dim
+    X = I.uniform_rhs_batch(N, list(range(11, 11 + nrhs))).T.copy()
+    prob = iedd.ie_discretize(dim, n, grid=conv)
+    Y = torch.zeros((nrhs, N), dtype=torch.float64, device="cuda")
+    iedd.ie_matvec(prob, dev(X), Y, iedd.IE_FFT)
+    for k in range(nrhs):
+        ref = O.matvec_direct(dim, n, X[k], convention=conv)
+        err = np.max(np.abs(host(Y[k]) - ref))
+        assert err <= 1e-12 * _scale(dim, n, X[k], conv), (k, err)
+
+
+def test_fft_matvec_full_size_sampled_rows():
+    n = 512
+    N = n * n
+    x = I.grf(2, n, 0.1, 2)
+    rows = np.unique(np.concatenate([[0, N - 1, N // 2 + n // 2], np.random.default_rng(3).integers(0, N, 29)]))
+    ref = O.matvec_direct(2, n, x, rows=rows)
+    prob = iedd.ie_discretize(2, n)
+    y = torch.zeros(N, dtype=torch.float64, device="cuda")
+    iedd.ie_matvec(prob, dev(x), y, iedd.IE_FFT)
+    assert np.max(np.abs(host(y)[rows] - ref)) <= 1e-12 * _scale(2, n, x, O.GRID_TEXT)
+
+
+@pytest.mark.parametrize("dim,n,m,delta", [(2, 64, 4, 1), (3, 16, 2, 1)])
+def test_pcg_fft_inner_fp64_parity(dim, n, m, delta):
+    # PCG with the FFT matvec in FP64: the same iterations as the oracle (+-1) and its solution
+    N = n ** dim
+    f = I.uniform_rhs(N, 0)
+    prob = iedd.ie_discretize(dim, n)
+    part = iedd.dd_partition(prob, m, delta, iedd.DD_SCHWARZ)
+    fac = iedd.dd_factor(prob, part, iedd.IE_FP64)
+    u = torch.zeros(N, dtype=torch.float64, device="cuda")
+    rep = iedd.pcg_solve(prob, fac, dev(f), u, tol=1e-8, precision=iedd.IE_FP64, inner=iedd.IE_FFT)[0]
+    P = _oracle_problem(dim, n, m, delta, matvec="fft")
+    _, it_ref, _ = P.solve(f, 1e-8)
+    assert abs(rep["iterations"] - it_ref) <= 1, (rep, it_ref)
+    u_same, _, _ = P.solve(f, 0.0, max_it=rep["iterations"])
+    assert np.linalg.norm(host(u) - u_same) / np.linalg.norm(u_same) <= 1e-10
+    assert O.true_relative_residual(dim, n, f, host(u)) <= 1e-8 * 1.05
+
+
+def test_pcg_fft_inner_mixed_512():
+    # the 512^2 workload with the FFT inner matvec and FP32 inverses: the true residual meets tol
+    n, m, delta = 512, 32, 2
+    f = I.grf(2, n, 0.1, 0)
+    prob = iedd.ie_discretize(2, n)
+    part = iedd.dd_partition(prob, m, delta, iedd.DD_SCHWARZ)
+    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
+    u = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    rep = iedd.pcg_solve(prob, fac, dev(f), u, tol=1e-8, precision=iedd.IE_MIXED, inner=iedd.IE_FFT)[0]
+    assert rep["status"] == 0 and rep["true_relres"] <= 1e-8
+    assert O.true_relative_residual(2, n, f, host(u)) <= 1e-8 * 1.01
+    _, it_ref, _ = O.Problem(2, n, m, delta, O.SCHWARZ, matvec="fft").solve(f, 1e-8)
+    assert it_ref - 1 <= rep["iterations"] <= it_ref + 5, (rep, it_ref)
+
+
 def test_accurate_matvec_3d_full_size_sampled_rows():
     n = 32
     N = n ** 3
