@@ -51,8 +51,17 @@ FP32_OPS_PER_PAIR_K2 = 7.75
 FP32_LANES_PER_SM = 128
 
 # DRAM traffic per launch of the dominant kernel from an ncu capture, valid only for the
-# source it was measured on (hash of matvec.cu); otherwise the bench reports null.
-NCU_TRAFFIC = {"05d8602d0e0764b2": 4228608}  # k2_accurate_2d<true,1>, n = 512, bytes per launch
+# source it was measured on (k2_source_hash: the 2D exact kernel's source text); otherwise the
+# bench reports null.
+NCU_TRAFFIC = {"24904137a1834c92": 4624128}  # k2_accurate_2d<true,1>, n = 512, bytes per launch
+
+
+def k2_source_hash() -> str:
+    """sha256 (16 hex digits) of the 2D exact kernel's source text (from its patch constants to
+    the 3D kernel's comment), the key under which its ncu DRAM traffic is recorded."""
+    src = open(os.path.join(ROOT, "paper_2108_12574_gb300", "csrc", "matvec.cu")).read()
+    a, b = src.index("constexpr int kP1"), src.index("// 3D: 4 x 8 x 8 patches")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
 def parse():
@@ -335,8 +344,7 @@ def main():
     mv_launch_s = last["matvec_ms"] / max(last["matvecs"], 1) / 1e3
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     f_mhz = clocks.get("sm_mhz") or 2070.0
-    src_hash = hashlib.sha256(open(os.path.join(ROOT, "paper_2108_12574_gb300", "csrc", "matvec.cu"), "rb")
-                              .read()).hexdigest()[:16]
+    src_hash = k2_source_hash()
     if prec == iedd.IE_MIXED and dim_w == 2:
         per_clk = FP32_LANES_PER_SM / FP32_OPS_PER_PAIR_K2
         peak = sms * per_clk * f_mhz * 1e6
@@ -444,15 +452,54 @@ def extras(torch, iedd, I, dev, stream, iterations):
     t_ap = (time.perf_counter() - t0) / 5
     fp64_its = 44  # FP64 PCG iterations of this workload at 1e-8 (the FP64 path's own count)
     stored = stored_matvec_leg(torch, iedd, I, dev, stream)
+    t_fft = t_mv(iedd.IE_FFT, 20)
     return {
         "matvec_gpairs_s": {"k2_double_float_table": pairs / t_k2 / 1e9, "k1_fp32_sfu_compensated": pairs / t_k1 / 1e9,
                             "kd_fp64_regenerated": pairs / t_64 / 1e9},
+        "fft_matvec": {"ms": t_fft * 1e3, "pairs_equivalent_gpairs_s": pairs / t_fft / 1e9,
+                       "basis": "FP64 circulant-embedding FFT on the 1024^2 periodic grid (the paper's matvec)"},
+        "fft_solve": fft_solve_leg(torch, iedd, I, dev, stream),
         "fp64_plain": {"value": t_fac + (fp64_its + 1) * t_64 + fp64_its * t_ap, "unit": "s", "extrapolated": True,
                        "basis": (f"FP64 factor + {fp64_its} x (FP64 regenerated matvec + FP64 apply) + one FP64 "
                                  f"true-residual matvec, each timed on this GPU (a full FP64 solve measured 224.6 s)"),
                        "parts_s": {"factor": t_fac, "matvec": t_64, "apply": t_ap}},
         "stored_matvec": stored,
     }
+
+
+def fft_solve_leg(torch, iedd, I, dev, stream, steps=3):
+    """The same workload and step (discretize + partition + factor + pcg_solve, L2 flushed, CUDA
+    events) with the paper's FFT matvec as the inner product and for the true residual: FP32
+    explicit inverses (IE_MIXED factors) and FP64 factors."""
+    f = torch.from_numpy(I.grf(DIM, NGRID, ELL, 0)).to(dev)
+    u = torch.zeros_like(f)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = {}
+    for name, fprec, prec in (("mixed", iedd.IE_MIXED, iedd.IE_MIXED), ("fp64", iedd.IE_FP64, iedd.IE_FP64)):
+        def step():
+            prob = iedd.ie_discretize(DIM, NGRID, device=dev.index)
+            part = iedd.dd_partition(prob, MPART, DELTA, iedd.DD_SCHWARZ)
+            fac = iedd.dd_factor(prob, part, fprec, stream=stream)
+            rep = iedd.pcg_solve(prob, fac, f, u, tol=TOL, precision=prec, inner=iedd.IE_FFT, stream=stream)[0]
+            fac.close(); part.close(); prob.close()
+            return rep
+        u.zero_()
+        step()
+        ms = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            u.zero_()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rep = step()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        out[name] = {"value": statistics.mean(ms) / 1e3, "unit": "s", "iterations": rep["iterations"],
+                     "true_relres": rep["true_relres"], "t_solve_matvec_s": rep["matvec_ms"] / 1e3,
+                     "t_solve_apply_s": rep["apply_ms"] / 1e3}
+    return out
 
 
 def stored_matvec_leg(torch, iedd, I, dev, stream, n=256):
