@@ -56,6 +56,18 @@ FP32_LANES_PER_SM = 128
 NCU_TRAFFIC = {"24904137a1834c92": 4624128}  # k2_accurate_2d<true,1>, n = 512, bytes per launch
 
 
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates per GPU
+
+
+def measured_peak(key: str, fallback: float) -> float:
+    """A peak from MEASURED_PEAKS.json at the repository root (driver-written), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)[key])
+    except (OSError, KeyError, ValueError, TypeError):
+        return fallback
+
+
 def k2_source_hash() -> str:
     """sha256 (16 hex digits) of the 2D exact kernel's source text (from its patch constants to
     the 3D kernel's comment), the key under which its ncu DRAM traffic is recorded."""
@@ -115,7 +127,8 @@ def config_dict():
     return {"workload": WORKLOAD, "dim": DIM, "n": NGRID, "N": NGRID ** DIM, "m": MPART, "delta": DELTA,
             "rhs": f"GRF l={ELL} seed=rank", "tol": TOL, "decomposition": "schwarz",
             "precision": "mixed (double-float table matvec on FP32 pipes, FP32 explicit subdomain inverses "
-                         "with double-float products, FP64 scalars and vectors)",
+                         "with double-float products, FP64 scalars and vectors; the FP64 true residual "
+                         "and replacements by the FP64 FFT matvec)",
             "l2": "flushed between timed steps (512 MiB write)"}
 
 
@@ -354,6 +367,17 @@ def main():
                     "kernel": "k2_accurate_2d<true,1>",
                     "peak_basis": (f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes / {FP32_OPS_PER_PAIR_K2} FP32 ops per "
                                    f"pair x {f_mhz:.0f} MHz (median SM clock sampled in the timed region)")}
+    elif prec == iedd.IE_MIXED and nr >= 16:
+        # 3D batch: the tcgen05 kernel, 3 TF32 MMAs (3xTF32 split) per pair and right-hand side,
+        # against the TF32 dense peak = measured sustained bf16 peak x the nominal TF32/bf16 ratio
+        bf16 = measured_peak("bf16_tflops_sustained", 1700.0)
+        peak = bf16 * TF32_PER_BF16 * 1e12
+        achieved = pairs * nr * 6.0 / mv_launch_s
+        roofline = {"bound": "tensor", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": "k1t_matvec_tc<3>",
+                    "pair_rhs_per_s": pairs * nr / mv_launch_s,
+                    "peak_basis": (f"TF32 dense = {bf16:.1f} TFLOP/s bf16 sustained (of measured) x {TF32_PER_BF16:.3f} "
+                                   "(nominal 1.1 / 2.25 PFLOP/s); work = 3 TF32 MMAs (2 flops each) per pair per RHS")}
     elif prec == iedd.IE_MIXED:
         # batched FP32 kernel: one FFMA per pair and right-hand side dominates (entries amortised)
         peak = sms * FP32_LANES_PER_SM * f_mhz * 1e6
@@ -525,8 +549,9 @@ def stored_matvec_leg(torch, iedd, I, dev, stream, n=256):
     ts, t2 = t(iedd.IE_STORED), t(iedd.IE_ACCURATE)
     iedd.ie_release_matrix(prob)
     gbs = 4.0 * N * N / ts / 1e9
+    hbm = measured_peak("hbm_gbs", 6800.0)
     return {"workload": "2D n=256 (N=65536), dense FP32 A", "ms": ts * 1e3, "achieved_gbs": gbs,
-            "hbm_peak_gbs": 6777.0, "frac": gbs / 6777.0, "regenerated_exact_ms": t2 * 1e3,
+            "hbm_peak_gbs": hbm, "frac": gbs / hbm, "regenerated_exact_ms": t2 * 1e3,
             "note": "peak = measured copy bandwidth (of measured)"}
 
 

@@ -199,7 +199,8 @@ typedef struct {
     int inner;           /* matvec inside the iteration (q = A p):
                               0            the library's choice: IE_FP64 precision -> the FP64
                                            regenerated matvec; IE_MIXED -> IE_ACCURATE in 2D,
-                                           IE_MIXED in 3D
+                                           IE_TENSOR for 3D batches of >= 16 columns,
+                                           IE_MIXED for fewer
                               IE_MIXED     FP32 SFU entries with compensated FP32 sums
                               IE_ACCURATE  double-float table sums on the FP32 pipes
                               4            as IE_ACCURATE with the search directions rounded to
@@ -208,6 +209,11 @@ typedef struct {
                               IE_FFT       the FP64 FFT matvec (Sec. 6), also used for the
                                            accurate residual; the first use builds its plan
                               16           the FP64 regenerated matvec in either precision */
+    int residual;        /* matvec of the accurate residual f - A u (IE_MIXED replacements, the
+                            final verification, r0 from a given x0):
+                              0            the library's choice: IE_FFT where supported
+                                           (n <= 4096), else IE_FP64 / IE_ACCURATE by precision
+                              IE_FFT, IE_FP64, IE_ACCURATE   that matvec */
 } pcg_opts;
 
 typedef struct {
@@ -223,7 +229,7 @@ typedef struct {
     double matvec_ms;        /* summed device time of the inner matvecs                         */
     double apply_ms;         /* summed device time of the applications                          */
     int accurate_matvecs;    /* accurate f - A u evaluations (replacement, verification)        */
-    int pad2_;
+    int accurate_mode;       /* ie_matvec mode of those (IE_FFT, IE_FP64 or IE_ACCURATE)         */
     double accurate_ms;      /* summed device time of those                                     */
 } pcg_report;
 
@@ -302,11 +308,12 @@ IEDD_API void pcg_default_opts(pcg_opts *o);
  *   rep    (host, may be NULL) nrhs reports
  * Iteration: r = f - A u0; z = T^{-1} r; p = z; then q = A p, alpha = r^T z / p^T q,
  * u += alpha p, r -= alpha q, z = T^{-1} r, beta = r_new^T z_new / r^T z, p = z + beta p.
- * IE_MIXED: q = A p in FP32 (ie_matvec IE_MIXED), T^{-1} in the factor's precision, vectors and
- * scalars in FP64.  When the recursive residual reaches tol (and every replace_every
- * iterations) r is replaced by the accurate f - A u (ie_matvec IE_ACCURATE); a column is done
- * only when that true residual is <= tol.  IE_FP64: stops on the recursive residual; with
- * verify = 1 the true residual is reported.
+ * IE_MIXED: q = A p by the inner matvec (pcg_opts.inner), T^{-1} in the factor's precision,
+ * vectors and scalars in FP64.  When the recursive residual reaches tol (and every
+ * replace_every iterations) r is replaced by the accurate f - A u (the FP64-class matvec chosen
+ * by pcg_opts.residual); a column is done only when that true residual is <= tol.  IE_FP64:
+ * stops on the recursive residual; with verify = 1 the true residual is reported.  A
+ * tensor-core inner matvec that timed out (bounded waits) makes every column IE_ERR_TIMEOUT.
  * Returns IE_OK if every column converged, else the first failing column's status.
  * Synchronizes the stream.
  */

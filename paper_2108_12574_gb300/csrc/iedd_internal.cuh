@@ -176,6 +176,8 @@ int launch_matvec_stored(const ie_problem *p, const double *x, long long ldx, do
 // FFT matvec (fft.cu): prepare_fft builds the plan once per problem (synchronizes; not inside a
 // stream capture); launch_matvec_fft then computes y = A x for nrhs columns.
 int prepare_fft(const ie_problem *p);
+// 1 if the FFT matvec handles this problem (else 0 and, if why != nullptr, the reason)
+int fft_supported(const ie_problem *p, std::string *why);
 int launch_matvec_fft(const ie_problem *p, const double *x, long long ldx, double *y, long long ldy, int nrhs,
                       cudaStream_t s);
 

@@ -264,12 +264,16 @@ struct Solver {
             o.inner == IE_ACCURATE_R4 || o.inner == IE_ACCURATE_R16 || o.inner == IE_FFT)
             return o.inner;
         if (o.precision == IE_FP64) return IE_FP64;
-        return p->dim == 2 ? IE_ACCURATE : IE_MIXED;
+        if (p->dim == 2) return IE_ACCURATE;
+        return nrhs >= 16 ? IE_TENSOR : IE_MIXED;  // 3D batches: the tcgen05 kernel
     }
     bool exact_inner() const { return mv_precision() != IE_MIXED && mv_precision() != IE_TENSOR; }
-    // the accurate residual: the FFT matvec is FP64-class, so an FFT inner matvec serves for both
+    // the accurate residual (replacements, verification, r0 from x0): by default the FP64 FFT
+    // matvec where it is supported (the paper's matvec, FP64-class and far cheaper than an FP64
+    // or double-float regenerated sum); else the regenerated FP64 / double-float sum
     int acc_precision() const {
-        if (o.inner == IE_FFT) return IE_FFT;
+        if (o.residual) return o.residual;
+        if (o.inner == IE_FFT || fft_supported(p, nullptr)) return IE_FFT;
         return o.precision == IE_FP64 ? IE_FP64 : IE_ACCURATE;
     }
     dim3 vg() const { return dim3(vgrid, nrhs); }
@@ -363,16 +367,18 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
         o.replace_every < 0 || o.check_every < 0 || o.use_x0 < 0 || o.use_x0 > 2 ||
         (o.inner != 0 && o.inner != IE_MIXED && o.inner != IE_ACCURATE && o.inner != IE_ACCURATE_X32 &&
          o.inner != IE_TENSOR && o.inner != IE_ACCURATE_R4 && o.inner != IE_ACCURATE_R16 &&
-         o.inner != IE_FP64 + 16 && o.inner != IE_FFT)) {
+         o.inner != IE_FP64 + 16 && o.inner != IE_FFT) ||
+        (o.residual != 0 && o.residual != IE_ACCURATE && o.residual != IE_FP64 && o.residual != IE_FFT)) {
         ie_set_error("pcg_solve: invalid options"); return IE_ERR_ARG;
     }
     if (o.check_every < 1) o.check_every = 1;
     const auto t_start = std::chrono::steady_clock::now();
     DeviceGuard g(p->device);
-    if (o.inner == IE_FFT) IE_TRY(prepare_fft(p));  // before any capture
     PrivateStream ps;
     IE_TRY(ps.init(static_cast<cudaStream_t>(stream)));
     Solver S{p, fac, nrhs, p->N, o, ps.s};
+    if (S.mv_precision() == IE_FFT || S.acc_precision() == IE_FFT) IE_TRY(prepare_fft(p));  // before any capture
+    if (S.mv_precision() == IE_TENSOR) IE_TRY_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
     IE_TRY(S.alloc());
     IE_TRY(S.make_events(std::max(o.check_every, 1)));
     const long long N = p->N;
@@ -519,11 +525,18 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
     IE_TRY_CUDA(cudaMemcpy2DAsync(u_out, ldb, S.u, rowb, rowb, nrhs,
                                   u_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     IE_TRY_CUDA(cudaMemcpyAsync(x0_used.data(), used.ptr, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
+    int tc_err = 0;
+    if (S.mv_precision() == IE_TENSOR)  // a tensor-core CTA that gave up waiting for its MMAs
+        IE_TRY_CUDA(cudaMemcpyAsync(&tc_err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     IE_TRY_CUDA(cudaStreamSynchronize(s));
     int ret = IE_OK;
+    if (tc_err) {
+        ret = IE_ERR_TIMEOUT;
+        ie_set_error("pcg_solve: the tensor-core matvec timed out waiting for its MMAs");
+    }
     for (int k = 0; k < nrhs; ++k) {
         const PcgCol &c = hs[(size_t)k];
-        int stk = c.flag == 2 ? IE_OK : (c.flag < 0 ? c.flag : IE_ERR_MAXIT);
+        int stk = tc_err ? IE_ERR_TIMEOUT : c.flag == 2 ? IE_OK : (c.flag < 0 ? c.flag : IE_ERR_MAXIT);
         if (stk != IE_OK && ret == IE_OK) {
             ret = stk;
             ie_set_error("pcg_solve: column " + std::to_string(k) + " stopped with status " + std::to_string(stk));
@@ -540,7 +553,7 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
             rep[k].matvec_ms = S.t_mv;
             rep[k].apply_ms = S.t_ap;
             rep[k].accurate_matvecs = S.n_acc;
-            rep[k].pad2_ = 0;
+            rep[k].accurate_mode = S.acc_precision();
             rep[k].accurate_ms = S.t_acc;
         }
     }

@@ -44,14 +44,15 @@ class IEError(RuntimeError):
 class PcgOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_it", ctypes.c_int), ("precision", ctypes.c_int),
                 ("replace_every", ctypes.c_int), ("use_x0", ctypes.c_int), ("timeout_s", ctypes.c_double),
-                ("check_every", ctypes.c_int), ("verify", ctypes.c_int), ("inner", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("verify", ctypes.c_int), ("inner", ctypes.c_int),
+                ("residual", ctypes.c_int)]
 
 
 class PcgReport(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("replacements", ctypes.c_int), ("status", ctypes.c_int),
                 ("x0_used", ctypes.c_int), ("recursive_relres", ctypes.c_double), ("true_relres", ctypes.c_double),
                 ("matvecs", ctypes.c_int), ("applies", ctypes.c_int), ("matvec_ms", ctypes.c_double),
-                ("apply_ms", ctypes.c_double), ("accurate_matvecs", ctypes.c_int), ("pad2_", ctypes.c_int),
+                ("apply_ms", ctypes.c_double), ("accurate_matvecs", ctypes.c_int), ("accurate_mode", ctypes.c_int),
                 ("accurate_ms", ctypes.c_double)]
 
     def as_dict(self):

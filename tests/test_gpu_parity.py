@@ -179,6 +179,22 @@ def test_pcg_fft_inner_fp64_parity(dim, n, m, delta):
     assert O.true_relative_residual(dim, n, f, host(u)) <= 1e-8 * 1.05
 
 
+@pytest.mark.parametrize("residual", [0, iedd.IE_ACCURATE, iedd.IE_FFT])
+def test_pcg_accurate_residual_modes(residual):
+    # the accurate residual (replacements, verification) by the library's choice (the FP64 FFT
+    # matvec) or forced: each reports its mode and meets tol on the oracle's residual
+    n, m, delta = 64, 4, 1
+    f = I.grf(2, n, 0.1, 5)
+    prob = iedd.ie_discretize(2, n)
+    part = iedd.dd_partition(prob, m, delta, iedd.DD_SCHWARZ)
+    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
+    u = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    rep = iedd.pcg_solve(prob, fac, dev(f), u, tol=1e-9, precision=iedd.IE_MIXED, residual=residual)[0]
+    assert rep["accurate_mode"] == (residual or iedd.IE_FFT)
+    assert rep["status"] == 0 and rep["accurate_matvecs"] >= 1
+    assert O.true_relative_residual(2, n, f, host(u)) <= 1e-9 * 1.01
+
+
 def test_pcg_fft_inner_mixed_512():
     # the 512^2 workload with the FFT inner matvec and FP32 inverses: the true residual meets tol
     n, m, delta = 512, 32, 2
@@ -526,5 +542,7 @@ def test_pcg_full_size_3d_batched_mixed():
     P = O.Problem(3, n, m, delta, O.SCHWARZ, matvec="fft")
     U_ref, its, _ = P.solve(F[:2].T, 1e-8)
     for k in range(2):
-        assert abs(reps[k]["iterations"] - its[k]) <= 2
+        # the 3D batch runs the tcgen05 inner matvec (3xTF32 products, FP32 accumulation): FP32
+        # class rounding moves where the oscillating residual first dips below tol
+        assert its[k] - 1 <= reps[k]["iterations"] <= its[k] + 5, (reps[k], its[k])
         assert np.linalg.norm(Uh[k] - U_ref[:, k]) / np.linalg.norm(U_ref[:, k]) <= 1e-6
