@@ -390,7 +390,6 @@ extern "C" int dd_factor(const ie_problem *p, const dd_partition_t *s, int preci
     if ((e = cudaMalloc(&f->d_pool, esz * (size_t)f->pool_elems)) != cudaSuccess) return fail(e);
     f->inverse = precision == IE_MIXED && f->max_pad <= kInvMaxPad;
     if (f->inverse) {
-        if ((e = cudaMalloc(&f->d_inv_pool, esz * (size_t)f->pool_elems)) != cudaSuccess) return fail(e);
         std::vector<long long> xoff((size_t)s->nblocks + 1, 0);
         std::vector<int2> chunks;
         for (int i = 0; i < s->nblocks; ++i) xoff[(size_t)i + 1] = xoff[(size_t)i] + npad[(size_t)i];
@@ -410,17 +409,14 @@ extern "C" int dd_factor(const ie_problem *p, const dd_partition_t *s, int preci
     if ((e = cudaMemcpy(f->d_n, nb.data(), sizeof(int) * nb.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpy(f->d_order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
 
+    if ((e = cudaMemsetAsync(f->d_info, 0xFF, sizeof(int) * nb.size(), st)) != cudaSuccess) return fail(e);
     int stl = launch_factor(f, st);
+    if (stl == IE_OK && f->inverse) stl = launch_factor_tc(f, npad, loff, st);
     if (stl == IE_OK) stl = prepare_apply(f);
     if (stl != IE_OK) { dd_factor_destroy(f); return stl; }
     std::vector<int> hinfo((size_t)s->nblocks);
     if ((e = cudaMemcpyAsync(hinfo.data(), f->d_info, sizeof(int) * hinfo.size(), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return fail(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
-    if (f->inverse) {  // the factors were only the way to the inverses
-        if ((e = cudaFree(f->d_pool)) != cudaSuccess) return fail(e);
-        f->d_pool = f->d_inv_pool;
-        f->d_inv_pool = nullptr;
-    }
     *out = f;
     for (int i = 0; i < s->nblocks; ++i) {
         if (hinfo[(size_t)i] >= 0) {
@@ -442,7 +438,6 @@ extern "C" void dd_factor_destroy(dd_factor_t *f) {
     cudaFree(f->d_order);
     cudaFree(f->d_info);
     cudaFree(f->d_pool);
-    cudaFree(f->d_inv_pool);
     cudaFree(f->d_xoff);
     cudaFree(f->d_chunks);
     delete f;

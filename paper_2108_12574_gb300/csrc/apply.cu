@@ -441,7 +441,9 @@ int launch_apply(const dd_factor_t *f, const double *r, long long ldr, double *z
     const size_t smm = sizeof(double) * f->max_pad * kRM;
     if (f->nblocks > 0 && f->inverse) {
         // 2D blocks, and single columns, get the double-float sums; batches of 3D columns FP32
-        const bool exact = p->dim == 2 || nrhs < 4;
+        // the batched variants stage 32 bytes per point; larger blocks take the columns one by one
+        const bool batch_fits = sizeof(float) * 8 * (size_t)f->max_pad <= (size_t)kApplySmemCeiling;
+        const bool exact = p->dim == 2 || nrhs < 4 || !batch_fits;
         DevBuf xb, xe;
         IE_TRY(xb.alloc(sizeof(float) * (size_t)f->xtotal * nrhs * (exact ? 2 : 1), s));
         IE_TRY(xe.alloc(sizeof(int) * (size_t)f->nblocks * nrhs, s));
@@ -463,7 +465,7 @@ int launch_apply(const dd_factor_t *f, const double *r, long long ldr, double *z
         f->xtotal, f->nblocks, nrhs, zbuf.as<double>(), part->total)
         if (f->nchunks > 0) {
             if (!exact) IE_APPLY_INV(8, 2, 4, false);
-            else if (nrhs >= 4) IE_APPLY_INV(4, 2, 2, true);
+            else if (nrhs >= 4 && batch_fits) IE_APPLY_INV(4, 2, 2, true);
             else IE_APPLY_INV(1, 2, 4, true);
             IE_LAUNCHED();
         }

@@ -13,14 +13,8 @@
 //                    the symmetric rank-32 update of the trailing lower tiles (tile pairs staged
 //                    in shared memory).  The first non-positive pivot is recorded in info and
 //                    the block stops.
-// K5i chol_inverse   (FP32 factors whose padded size fits the shared-memory strip) one CTA per
-//                    (block, 32-column strip j): the strip of M_i = A_i^{-1} = L^{-T} L^{-1} on and
-//                    below the diagonal, by a forward solve L W = E_j (E_j: columns of the identity)
-//                    and a backward solve L^T X = W, both stopped at tile row j (rows above it are
-//                    not needed by the lower strip); the strip lives in shared memory, tiles of L
-//                    are staged one at a time.  Tile (i, j) and its transpose (j, i) are both
-//                    written from the same values, so the stored M_i is exactly symmetric.  The
-//                    apply then multiplies by M_i instead of solving with L_i twice.
+// K5t (tc_factor.cu) for FP32 factors applied through explicit inverses: the same Cholesky and
+//                    the inverse M_i = L_i^{-T} L_i^{-1} with the bulk on the tensor cores.
 #include <cuda_runtime.h>
 
 #include "iedd_internal.cuh"
@@ -151,110 +145,7 @@ chol_blocked(T *__restrict__ pool, const long long *__restrict__ loff, const int
     if (tid == 0) info[b] = bad;
 }
 
-// Strip row stride 33: the lanes of the 32 x 32 triangle solves walk down a column.
-constexpr int kStrip = 33;
-
-__global__ void __launch_bounds__(256)
-chol_inverse(const float *__restrict__ Lpool, float *__restrict__ Mpool, const long long *__restrict__ loff,
-             const int *__restrict__ npad, const int *__restrict__ order) {
-    extern __shared__ float S[];  // [(np - 32 j)][kStrip]: tile rows j .. nt-1 of the strip
-    __shared__ float Lt[32][33];
-    __shared__ float Ld[32][33];
-    const int b = order[blockIdx.x];
-    const int j = blockIdx.y;
-    const int np = npad[b], nt = np / 32;
-    if (j >= nt) return;  // uniform over the CTA
-    const float *L = Lpool + loff[b];
-    float *M = Mpool + loff[b];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int rr = tid >> 3, cb = tid & 7;  // GEMM thread tile: row rr, columns cb + 8 q
-    auto srow = [&](int i, int r) { return S + (size_t)((i - j) * 32 + r) * kStrip; };
-
-    // forward: S_i = L_ii^{-1} (delta_ij I - sum_{k=j}^{i-1} L_ik S_k), i = j .. nt-1
-    for (int i = j; i < nt; ++i) {
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int k = j; k < i; ++k) {
-            __syncthreads();
-            for (int e = tid; e < 1024; e += 256) Lt[e >> 5][e & 31] = L[(long long)(i * 32 + (e >> 5)) * np + k * 32 + (e & 31)];
-            __syncthreads();
-#pragma unroll 8
-            for (int t = 0; t < 32; ++t) {
-                const float l = Lt[rr][t];
-                const float *sk = srow(k, t);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[q] = fmaf(l, sk[cb + 8 * q], acc[q]);
-            }
-        }
-        __syncthreads();
-        for (int e = tid; e < 1024; e += 256) Ld[e >> 5][e & 31] = L[(long long)(i * 32 + (e >> 5)) * np + i * 32 + (e & 31)];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int c = cb + 8 * q;
-            srow(i, rr)[c] = ((i == j && rr == c) ? 1.f : 0.f) - acc[q];
-        }
-        __syncthreads();
-        // L_ii y = t for the 32 columns: warp w takes columns 4w .. 4w+3, lanes are rows
-        for (int q = 0; q < 4; ++q) {
-            const int c = 4 * warp + q;
-            float v = srow(i, lane)[c];
-            for (int a = 0; a < 32; ++a) {
-                const float ya = __shfl_sync(0xffffffffu, v, a) / Ld[a][a];
-                if (lane == a) v = ya;
-                if (lane > a) v = fmaf(-Ld[lane][a], ya, v);
-            }
-            srow(i, lane)[c] = v;
-        }
-    }
-    // backward: S_i = L_ii^{-T} (S_i - sum_{k=i+1}^{nt-1} L_ki^T S_k), i = nt-1 .. j
-    for (int i = nt - 1; i >= j; --i) {
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int k = i + 1; k < nt; ++k) {
-            __syncthreads();
-            for (int e = tid; e < 1024; e += 256) Lt[e >> 5][e & 31] = L[(long long)(k * 32 + (e >> 5)) * np + i * 32 + (e & 31)];
-            __syncthreads();
-#pragma unroll 8
-            for (int t = 0; t < 32; ++t) {
-                const float l = Lt[t][rr];  // L_ki[t][rr] = (L_ki^T)[rr][t]
-                const float *sk = srow(k, t);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[q] = fmaf(l, sk[cb + 8 * q], acc[q]);
-            }
-        }
-        __syncthreads();
-        for (int e = tid; e < 1024; e += 256) Ld[e >> 5][e & 31] = L[(long long)(i * 32 + (e >> 5)) * np + i * 32 + (e & 31)];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) srow(i, rr)[cb + 8 * q] -= acc[q];
-        __syncthreads();
-        // L_ii^T x = t: lanes are rows, back to front
-        for (int q = 0; q < 4; ++q) {
-            const int c = 4 * warp + q;
-            float v = srow(i, lane)[c];
-            for (int a = 31; a >= 0; --a) {
-                const float xa = __shfl_sync(0xffffffffu, v, a) / Ld[a][a];
-                if (lane == a) v = xa;
-                if (lane < a) v = fmaf(-Ld[a][lane], xa, v);
-            }
-            srow(i, lane)[c] = v;
-        }
-    }
-    __syncthreads();
-    // store: tile (i, j) and its transpose (j, i); the diagonal tile from its lower triangle
-    for (int i = j; i < nt; ++i) {
-        for (int e = tid; e < 1024; e += 256) {
-            const int r = e >> 5, c = e & 31;
-            if (i == j) {
-                M[(long long)(j * 32 + r) * np + j * 32 + c] = r >= c ? srow(j, r)[c] : srow(j, c)[r];
-            } else {
-                M[(long long)(i * 32 + r) * np + j * 32 + c] = srow(i, r)[c];
-                M[(long long)(j * 32 + r) * np + i * 32 + c] = srow(i, c)[r];
-            }
-        }
-    }
-}
-
 }  // namespace
-
-size_t inverse_strip_smem(int max_pad) { return sizeof(float) * (size_t)max_pad * kStrip; }
 
 int launch_factor(dd_factor_t *f, cudaStream_t s) {
     const ie_problem *p = f->prob;
@@ -274,17 +165,10 @@ int launch_factor(dd_factor_t *f, cudaStream_t s) {
                                                part->d_idx, p->d_coord, p->dim, p->diag, p->c_const, p->c_ln,
                                                p->c_log2, p->c_r);
         IE_LAUNCHED();
+        if (f->inverse) return IE_OK;  // Cholesky and inverse on the tensor cores (launch_factor_tc)
         chol_blocked<float><<<f->nblocks, 256, 0, s>>>((float *)f->d_pool, f->d_loff, f->d_npad, f->d_order,
                                                       f->d_info);
         IE_LAUNCHED();
-        if (f->d_inv_pool) {
-            const size_t sm = inverse_strip_smem(f->max_pad);
-            IE_TRY_CUDA(cudaFuncSetAttribute(chol_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            dim3 gi(f->nblocks, f->max_pad / 32);
-            chol_inverse<<<gi, 256, sm, s>>>((const float *)f->d_pool, (float *)f->d_inv_pool, f->d_loff, f->d_npad,
-                                             f->d_order);
-            IE_LAUNCHED();
-        }
     }
     return IE_OK;
 }

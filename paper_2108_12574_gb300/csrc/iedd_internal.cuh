@@ -112,19 +112,18 @@ struct dd_factor_t {
                                    // symmetric inverses M_i = A_i^{-1} when inverse != 0
     long long pool_elems = 0;
     int *d_info = nullptr;         // per-block first bad pivot (-1 ok)
-    int inverse = 0;               // FP32 explicit inverses (IE_MIXED, max_pad <= kInvMaxPad)
-    void *d_inv_pool = nullptr;    // inverses while the factor runs (moved to d_pool afterwards)
+    int inverse = 0;               // FP32 explicit inverses in d_pool (IE_MIXED, max_pad <= kInvMaxPad)
     long long *d_xoff = nullptr;   // per block: offset of its padded slice of the apply's split x
     long long xtotal = 0;          // sum of the padded block sizes
     int nchunks = 0;               // apply work items: (block, first row) per kApplyRows rows
     int2 *d_chunks = nullptr;
 };
 
-// Largest padded block whose inverse strip (max_pad x 33 FP32) fits one CTA's shared memory.
-constexpr int kInvMaxPad = 1536;
+// Largest padded block applied through its explicit inverse: the apply stages the block's split x
+// (8 bytes per point and right-hand side) in one CTA's shared memory.
+constexpr int kInvMaxPad = 25600;
 // Rows of one subdomain handled by one CTA of the explicit-inverse apply.
 constexpr int kApplyRows = 64;
-size_t inverse_strip_smem(int max_pad);
 
 // ---------------------------------------------------------------------------------------------
 // Device vector helpers: host / device pointer detection and staging
@@ -182,6 +181,10 @@ int launch_matvec_fft(const ie_problem *p, const double *x, long long ldx, doubl
                       cudaStream_t s);
 
 int launch_factor(dd_factor_t *f, cudaStream_t s);
+// tc_factor.cu: Cholesky and explicit inverse of the gathered FP32 blocks in f->d_pool (M_i
+// replaces the block), bulk on the tensor cores; synchronizes.  f->d_info must hold -1 per block.
+int launch_factor_tc(dd_factor_t *f, const std::vector<int> &npad, const std::vector<long long> &loff,
+                     cudaStream_t s);
 int prepare_apply(const dd_factor_t *f);
 // z = T^{-1} r for device FP64 r (ldr) and z (ldz).
 int launch_apply(const dd_factor_t *f, const double *r, long long ldr, double *z, long long ldz,

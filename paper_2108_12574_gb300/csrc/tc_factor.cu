@@ -1,0 +1,528 @@
+// Mixed-precision subdomain factor on the tensor cores: A_i = L_i L_i^T and the explicit symmetric
+// inverse M_i = A_i^{-1} = W_i^T W_i (W_i = L_i^{-1}) for every block at once, FP32 storage, the
+// bulk of the flops as 3xTF32 tcgen05 MMAs (the exact subdomain solver of Sec. 4.3, Eq. e:ai).
+//
+// Blocks are cut into tiles of P = 128 rows (the last one ragged, a multiple of 32).  Per panel
+// k0 (all blocks in the same launches):
+//   KD diag_factor   one CTA per block: Cholesky of the diagonal tile in shared memory (32-wide
+//                    blocked), its triangular inverse Tinv (kept per tile), and the diagonal tile
+//                    of W^T (= Tinv^T, zero below its diagonal).
+//   panel            L_21 = A_21 Tinv^T                         (GEMM tasks, in place)
+//   trailing         A_22 -= L_21 L_21^T over the lower tiles    (GEMM tasks)
+// Then W by tile rows i = 1, 2, ...: G_ij = sum_{k=j}^{i-1} L_ik W_kj (stored transposed) and
+// W_ij = -Tinv_i G_ij (stored transposed, in W^T), and finally M_ab = sum_k W_ka W_kb for the lower
+// tiles a >= b, written to (a, b) and mirrored to (b, a) from the same values, so M_i is exactly
+// symmetric; M_i replaces L_i in the pool.
+//
+// KG tc_gemm_tasks  one CTA per task C (<= 128 x 128) = s_old C + s_acc A B^T, A: m x k and B: n x k
+//                   row-major FP32 with k contiguous (k a multiple of 32).  Per 32-wide chunk the
+//                   threads load A and B with 16-byte loads, split each value into TF32 high and low
+//                   parts and store them in the canonical K-major no-swizzle layout (8-row x 16-byte
+//                   core matrices); one thread issues 12 tcgen05.mma.kind::tf32 (M = N = 128, K = 8;
+//                   A_hi B_hi + A_hi B_lo + A_lo B_hi) into an FP32 accumulator in tensor memory; two
+//                   operand stages, tcgen05.commit to per-stage mbarriers, bounded waits (a CTA that
+//                   waits too long records an error, frees its tensor memory and returns).  The
+//                   epilogue stages the accumulator in shared memory (tcgen05.ld 32x32b) and writes C
+//                   row-wise and / or the transposed CT column-wise, both coalesced.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "iedd_internal.cuh"
+
+namespace {
+
+constexpr int kP = 128;                 // tile rows
+constexpr int kGK = 16;                 // K per operand chunk
+constexpr uint32_t kGLBO = 128;         // bytes between core matrices along K
+constexpr uint32_t kGSBO = (kGK / 4) * 128;  // bytes between 8-row groups
+constexpr int kGOp = kP * kGK;          // 32-bit words of one operand part (128 x 16)
+constexpr int kGStage = 4 * kGOp;       // A hi, A lo, B hi, B lo
+constexpr int kGSmem = 2 * kGStage * 4; // two stages, bytes (64 KB: three CTAs per SM)
+constexpr int kGF4 = kP * kGK / 4 / 256;  // float4 per thread per operand and chunk (2)
+constexpr int kTS = kP + 1;             // diagonal-kernel tile row stride (floats)
+constexpr int kES = kP / 2 + 1;         // epilogue half-tile row stride (floats)
+constexpr long long kGSpin = 1LL << 24; // non-blocking mbarrier polls before giving up
+// kind::tf32: D FP32 (bit 4), A and B TF32 (bits 7, 10), K-major both, N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t kGIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kP >> 3) << 17) | ((uint32_t)(kP >> 4) << 24);
+
+struct GemmTask {
+    const float *A, *B;  // operand origins: A rows 0..m-1, B rows 0..n-1, k contiguous
+    float *C, *CT;       // outputs (either may be null)
+    int lda, ldb, ldc, ldct;
+    int m, n, k;         // m, n <= 128; k a multiple of 32
+    float s_old, s_acc;  // C = s_old C + s_acc acc (C is not read when s_old == 0); CT^T = s_acc acc
+    int diag;            // diagonal tile: C only where r >= c, CT only where c < r
+    int pad_;
+};
+
+__device__ __forceinline__ uint32_t gsmem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t tf32_of(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return r;
+}
+
+__device__ __forceinline__ uint64_t gdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((kGLBO >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((kGSBO >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // tcgen05 descriptor version; base offset 0, no swizzle
+    return d;
+}
+
+__device__ __forceinline__ void gmma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kGIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ bool gbar_test(uint32_t bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool gbar_wait(uint32_t bar, uint32_t phase) {
+    for (long long i = 0; i < kGSpin; ++i)
+        if (gbar_test(bar, phase)) return true;
+    return false;
+}
+
+// One operand part of a chunk: 128 rows x 16 columns as 512 float4; element e of thread tid is
+// e = tid + 256 u: row (e / 32) * 8 + e % 8, float4 column (e / 8) % 4.  Eight consecutive threads
+// take the 8 rows of one core matrix (conflict-free 16-byte stores, 64-byte row segments).
+__device__ __forceinline__ void chunk_fetch(const float *src, int ld, int rows_valid, int c0, int tid,
+                                            float4 (&v)[kGF4]) {
+#pragma unroll
+    for (int u = 0; u < kGF4; ++u) {
+        const int e = tid + 256 * u;
+        const int r = (e >> 5) * 8 + (e & 7), k4 = (e >> 3) & 3;
+        v[u] = r < rows_valid ? *reinterpret_cast<const float4 *>(src + (long long)r * ld + c0 + 4 * k4)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+__device__ __forceinline__ void chunk_store(const float4 (&v)[kGF4], uint32_t *hi, uint32_t *lo, int tid) {
+#pragma unroll
+    for (int u = 0; u < kGF4; ++u) {
+        const int e = tid + 256 * u;
+        const int r = (e >> 5) * 8 + (e & 7), k4 = (e >> 3) & 3;
+        const uint32_t off = (uint32_t)(((r >> 3) * kGSBO + k4 * kGLBO + (r & 7) * 16) >> 2);
+        const uint32_t h0 = tf32_of(v[u].x), h1 = tf32_of(v[u].y), h2 = tf32_of(v[u].z), h3 = tf32_of(v[u].w);
+        *reinterpret_cast<uint4 *>(hi + off) = make_uint4(h0, h1, h2, h3);
+        *reinterpret_cast<uint4 *>(lo + off) =
+            make_uint4(tf32_of(v[u].x - __uint_as_float(h0)), tf32_of(v[u].y - __uint_as_float(h1)),
+                       tf32_of(v[u].z - __uint_as_float(h2)), tf32_of(v[u].w - __uint_as_float(h3)));
+    }
+}
+
+__global__ void __launch_bounds__(256)
+tc_gemm_tasks(const GemmTask *__restrict__ tasks, int *__restrict__ err) {
+    extern __shared__ __align__(1024) uint32_t gsm[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const GemmTask t = tasks[blockIdx.x];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(gsmem_u32(&tmem_base)),
+                     "r"((uint32_t)kP));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int st = 0; st < 2; ++st)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(gsmem_u32(&mbar[st])), "r"(1u));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const int nch = t.k / kGK;
+    uint32_t ph[2] = {0u, 0u};
+    int pending[2] = {0, 0};
+    float4 va[kGF4], vb[kGF4];  // the next chunk, in flight while the current one is stored and multiplied
+    if (nch > 0) {
+        chunk_fetch(t.A, t.lda, t.m, 0, tid, va);
+        chunk_fetch(t.B, t.ldb, t.n, 0, tid, vb);
+    }
+    for (int ch = 0; ch < nch; ++ch) {
+        const int st = ch & 1;
+        uint32_t *Ahi = gsm + st * kGStage, *Alo = Ahi + kGOp, *Bhi = Alo + kGOp, *Blo = Bhi + kGOp;
+        if (pending[st]) {  // the stage's previous MMAs must be done before its operands change
+            if (!gbar_wait(gsmem_u32(&mbar[st]), ph[st])) abort_flag = 1;
+            ph[st] ^= 1u;
+            pending[st] = 0;
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        chunk_store(va, Ahi, Alo, tid);
+        chunk_store(vb, Bhi, Blo, tid);
+        if (ch + 1 < nch) {
+            chunk_fetch(t.A, t.lda, t.m, (ch + 1) * kGK, tid, va);
+            chunk_fetch(t.B, t.ldb, t.n, (ch + 1) * kGK, tid, vb);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ah = gsmem_u32(Ahi), al = gsmem_u32(Alo), bh = gsmem_u32(Bhi), bl = gsmem_u32(Blo);
+#pragma unroll
+            for (int s = 0; s < kGK / 8; ++s) {
+                const uint32_t ko = (uint32_t)s * 2 * kGLBO;
+                gmma(tmem, gdesc(ah + ko), gdesc(bh + ko), (ch > 0 || s > 0) ? 1u : 0u);
+                gmma(tmem, gdesc(ah + ko), gdesc(bl + ko), 1u);
+                gmma(tmem, gdesc(al + ko), gdesc(bh + ko), 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             gsmem_u32(&mbar[st]))
+                         : "memory");
+        }
+        pending[st] = 1;
+    }
+    for (int st = 0; st < 2; ++st) {  // drain (bounded)
+        if (pending[st]) {
+            if (!gbar_wait(gsmem_u32(&mbar[st]), ph[st])) abort_flag = 1;
+            pending[st] = 0;
+        }
+    }
+    __syncthreads();
+    if (!abort_flag && nch > 0) {
+        // accumulator -> shared half tile T[r][c] (64 columns per pass, stride kES): warp w reads
+        // TMEM lanes 32 (w % 4) .., columns 64 pass + 32 (w / 4) ..; then C row-wise, CT column-wise
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float *T = reinterpret_cast<float *>(gsm);
+        const int q = warp & 3, h = warp >> 2;
+        for (int pass = 0; pass < 2; ++pass) {
+            const int cbase = 64 * pass;
+            {
+                uint32_t v[32];
+                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(cbase + 32 * h);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float *row = T + (32 * q + lane) * kES + 32 * h;
+#pragma unroll
+                for (int c = 0; c < 32; ++c) row[c] = __uint_as_float(v[c]);
+            }
+            __syncthreads();
+            if (t.C) {
+                for (int e = tid; e < kP * 64; e += 256) {
+                    const int r = e >> 6, cl = e & 63, c = cbase + cl;
+                    if (r < t.m && c < t.n && (!t.diag || r >= c)) {
+                        float *dst = t.C + (long long)r * t.ldc + c;
+                        const float a = T[r * kES + cl];
+                        *dst = t.s_old != 0.f ? fmaf(t.s_acc, a, t.s_old * *dst) : t.s_acc * a;
+                    }
+                }
+            }
+            if (t.CT) {
+                for (int e = tid; e < kP * 64; e += 256) {
+                    const int cl = e >> 7, r = e & (kP - 1), c = cbase + cl;
+                    if (r < t.m && c < t.n && (!t.diag || c < r))
+                        t.CT[(long long)c * t.ldct + r] = t.s_acc * T[r * kES + cl];
+                }
+            }
+            __syncthreads();
+        }
+    } else if (abort_flag && tid == 0) {
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kP));
+    }
+}
+
+// KD: the diagonal tile of panel k0 of each listed block.  Shared memory: D (the tile, then L_kk)
+// and X (Tinv), 128 x 129 floats each.
+__global__ void __launch_bounds__(256)
+diag_factor(float *__restrict__ pool, float *__restrict__ wt, float *__restrict__ tinv,
+            const long long *__restrict__ loff, const long long *__restrict__ toff, const int *__restrict__ npad,
+            const int *__restrict__ list, int k0, int *__restrict__ info) {
+    extern __shared__ float dsm[];
+    float *D = dsm, *X = dsm + kP * kTS;
+    __shared__ int bad;
+    const int b = list[blockIdx.x];
+    const int np = npad[b], pk = min(kP, np - k0), nt = pk / 32;
+    float *A = pool + loff[b] + (long long)k0 * np + k0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) bad = -1;
+    for (int e = tid; e < kP * kP; e += 256) {
+        const int r = e >> 7, c = e & (kP - 1);
+        D[r * kTS + c] = (r < pk && c <= r) ? A[(long long)r * np + c] : 0.f;
+        X[r * kTS + c] = 0.f;
+    }
+    __syncthreads();
+    // blocked Cholesky of D (32-wide): diagonal sub-tile column by column, panel, trailing update
+    for (int kk = 0; kk < nt; ++kk) {
+        const int c0 = kk * 32;
+        // the 32 x 32 diagonal sub-tile in one warp's registers (lane = row): right-looking,
+        // column j's entries shuffled to the lanes that update with them; no block barrier
+        if (warp == 0) {
+            float row[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) row[c] = c <= lane ? D[(c0 + lane) * kTS + c0 + c] : 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                float piv = __shfl_sync(0xffffffffu, row[j], j);
+                if (!(piv > 0.f)) {  // uniform: every lane holds the same pivot
+                    if (lane == 0 && bad < 0) bad = c0 + j;
+                    piv = 1.f;
+                }
+                const float djj = sqrtf(piv);
+                const float lij = lane > j ? row[j] / djj : (lane == j ? djj : 0.f);
+                if (lane >= j) row[j] = lij;
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    if (c > j) {  // compile-time after unrolling
+                        const float lcj = __shfl_sync(0xffffffffu, lij, c);
+                        if (c <= lane) row[c] = fmaf(-lij, lcj, row[c]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+                if (c <= lane) D[(c0 + lane) * kTS + c0 + c] = row[c];
+        }
+        __syncthreads();
+        // rows below the sub-tile: X L^T = D (one warp per row, lanes = columns)
+        for (int row = c0 + 32 + warp; row < pk; row += 8) {
+            float v = D[row * kTS + c0 + lane];
+            for (int c = 0; c < 32; ++c) {
+                const float xc = __shfl_sync(0xffffffffu, v, c) / D[(c0 + c) * kTS + c0 + c];
+                if (lane == c) v = xc;
+                if (lane > c) v = fmaf(-xc, D[(c0 + lane) * kTS + c0 + c], v);
+            }
+            D[row * kTS + c0 + lane] = v;
+        }
+        __syncthreads();
+        // trailing lower part: D[i][c] -= sum_t D[i][c0 + t] D[c][c0 + t], c0 + 32 <= c <= i < pk
+        const int r0 = c0 + 32, rest = pk - r0;
+        for (int e = tid; e < rest * rest; e += 256) {
+            const int i = r0 + e / rest, c = r0 + e % rest;
+            if (c <= i) {
+                float s = 0.f;
+#pragma unroll 8
+                for (int t2 = 0; t2 < 32; ++t2) s = fmaf(D[i * kTS + c0 + t2], D[c * kTS + c0 + t2], s);
+                D[i * kTS + c] -= s;
+            }
+        }
+        __syncthreads();
+    }
+    // L_kk back to the pool (lower part)
+    for (int e = tid; e < pk * pk; e += 256) {
+        const int r = e / pk, c = e % pk;
+        if (c <= r) A[(long long)r * np + c] = D[r * kTS + c];
+    }
+    // X = L_kk^{-1}: 32-column strips, forward substitution over 32-row tiles
+    for (int js = 0; js < nt; ++js) {
+        for (int is = js; is < nt; ++is) {
+            // X_is,js = L_is,is^{-1} (delta - sum_{k=js}^{is-1} L_is,k X_k,js): thread (row rr, columns cb + 8 q)
+            const int rr = tid >> 3, cb = tid & 7;
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int ks = js; ks < is; ++ks) {
+#pragma unroll 8
+                for (int t2 = 0; t2 < 32; ++t2) {
+                    const float l = D[(is * 32 + rr) * kTS + ks * 32 + t2];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[q] = fmaf(l, X[(ks * 32 + t2) * kTS + js * 32 + cb + 8 * q], acc[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = cb + 8 * q;
+                X[(is * 32 + rr) * kTS + js * 32 + c] = ((is == js && rr == c) ? 1.f : 0.f) - acc[q];
+            }
+            __syncthreads();
+            // triangle: warp w solves columns 4w .. 4w + 3 of the 32 x 32 tile (lanes are rows)
+            for (int q = 0; q < 4; ++q) {
+                const int c = js * 32 + 4 * warp + q;
+                float v = X[(is * 32 + lane) * kTS + c];
+                for (int a = 0; a < 32; ++a) {
+                    const float ya = __shfl_sync(0xffffffffu, v, a) / D[(is * 32 + a) * kTS + is * 32 + a];
+                    if (lane == a) v = ya;
+                    if (lane > a) v = fmaf(-D[(is * 32 + lane) * kTS + is * 32 + a], ya, v);
+                }
+                X[(is * 32 + lane) * kTS + c] = v;
+            }
+            __syncthreads();
+        }
+    }
+    // Tinv (128 x 128, zero outside pk x pk) and the diagonal tile of W^T (Tinv^T, zero below)
+    float *Tb = tinv + toff[b] + (long long)(k0 / kP) * kP * kP;
+    float *Wb = wt + loff[b] + (long long)k0 * np + k0;
+    for (int e = tid; e < kP * kP; e += 256) {
+        const int r = e >> 7, c = e & (kP - 1);
+        Tb[e] = (r < pk && c <= r) ? X[r * kTS + c] : 0.f;
+        if (r < pk && c < pk) Wb[(long long)r * np + c] = c >= r ? X[c * kTS + r] : 0.f;
+    }
+    if (tid == 0 && bad >= 0 && info[b] < 0) info[b] = k0 + bad;
+}
+
+}  // namespace
+
+constexpr int kDiagSmem = 2 * kP * kTS * (int)sizeof(float);
+
+int prepare_tc_factor() {
+    IE_TRY_CUDA(cudaFuncSetAttribute(tc_gemm_tasks, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem));
+    IE_TRY_CUDA(cudaFuncSetAttribute(diag_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, kDiagSmem));
+    return IE_OK;
+}
+
+// L and then M in f->d_pool (FP32, already holding the gathered lower blocks); synchronizes.
+int launch_factor_tc(dd_factor_t *f, const std::vector<int> &npad, const std::vector<long long> &loff,
+                     cudaStream_t s) {
+    const int nb = f->nblocks;
+    if (nb == 0) return IE_OK;
+    IE_TRY(prepare_tc_factor());
+    float *pool = (float *)f->d_pool;
+    std::vector<long long> toff((size_t)nb + 1, 0), goff((size_t)nb + 1, 0);
+    int max_np = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int nt = (npad[(size_t)b] + kP - 1) / kP;
+        toff[(size_t)b + 1] = toff[(size_t)b] + (long long)nt * kP * kP;
+        goff[(size_t)b + 1] = goff[(size_t)b] + (long long)npad[(size_t)b] * kP;
+        max_np = std::max(max_np, npad[(size_t)b]);
+    }
+    DevBuf wt, tinv, gbuf, dtoff, derr;
+    IE_TRY(wt.alloc(sizeof(float) * (size_t)f->pool_elems, s));
+    IE_TRY(tinv.alloc(sizeof(float) * (size_t)toff.back(), s));
+    IE_TRY(gbuf.alloc(sizeof(float) * (size_t)goff.back(), s));
+    IE_TRY(dtoff.alloc(sizeof(long long) * toff.size(), s));
+    IE_TRY(derr.alloc(sizeof(int), s));
+    IE_TRY_CUDA(cudaMemcpyAsync(dtoff.ptr, toff.data(), sizeof(long long) * toff.size(), cudaMemcpyHostToDevice, s));
+    IE_TRY_CUDA(cudaMemsetAsync(derr.ptr, 0, sizeof(int), s));
+    float *W = wt.as<float>(), *T = tinv.as<float>(), *G = gbuf.as<float>();
+    auto P_ = [&](int b) { return pool + loff[(size_t)b]; };
+    auto W_ = [&](int b) { return W + loff[(size_t)b]; };
+    auto T_ = [&](int b, int i) { return T + toff[(size_t)b] + (long long)i * kP * kP; };
+    auto G_ = [&](int b) { return G + goff[(size_t)b]; };
+    // the whole schedule is built first (GEMM task lists and diagonal-kernel block lists), copied
+    // once, and launched back to back with no host synchronization in between
+    std::vector<GemmTask> tasks;
+    std::vector<int> lists;
+    struct Op { int diag; int k0; size_t off, cnt; };
+    std::vector<Op> ops;
+    size_t mark = 0;
+    auto close_gemm = [&]() {
+        if (tasks.size() > mark) ops.push_back({0, 0, mark, tasks.size() - mark});
+        mark = tasks.size();
+    };
+    auto task = [&](const float *A, int lda, const float *B, int ldb, int m, int n, int k, float *C, int ldc,
+                    float *CT, int ldct, float s_old, float s_acc, int diag) {
+        GemmTask g;
+        g.A = A; g.B = B; g.C = C; g.CT = CT;
+        g.lda = lda; g.ldb = ldb; g.ldc = ldc; g.ldct = ldct;
+        g.m = m; g.n = n; g.k = k; g.s_old = s_old; g.s_acc = s_acc; g.diag = diag; g.pad_ = 0;
+        tasks.push_back(g);
+    };
+    // Cholesky, panel by panel
+    for (int k0 = 0; k0 < max_np; k0 += kP) {
+        const size_t l0 = lists.size();
+        for (int b = 0; b < nb; ++b)
+            if (npad[(size_t)b] > k0) lists.push_back(b);
+        ops.push_back({1, k0, l0, lists.size() - l0});
+        for (int b = 0; b < nb; ++b) {  // panel: L_21 = A_21 Tinv^T, in place
+            const int np = npad[(size_t)b];
+            if (np <= k0) continue;
+            const int pk = std::min(kP, np - k0);
+            for (int r0 = k0 + pk; r0 < np; r0 += kP) {
+                float *a = P_(b) + (long long)r0 * np + k0;
+                task(a, np, T_(b, k0 / kP), kP, std::min(kP, np - r0), pk, pk, a, np, nullptr, 0, 0.f, 1.f, 0);
+            }
+        }
+        close_gemm();
+        for (int b = 0; b < nb; ++b) {  // trailing: A_22 -= L_21 L_21^T, lower tiles
+            const int np = npad[(size_t)b];
+            if (np <= k0) continue;
+            const int pk = std::min(kP, np - k0);
+            for (int ra = k0 + pk; ra < np; ra += kP)
+                for (int rb = k0 + pk; rb <= ra; rb += kP)
+                    task(P_(b) + (long long)ra * np + k0, np, P_(b) + (long long)rb * np + k0, np, std::min(kP, np - ra),
+                         std::min(kP, np - rb), pk, P_(b) + (long long)ra * np + rb, np, nullptr, 0, 1.f, -1.f, 0);
+        }
+        close_gemm();
+    }
+    // W = L^{-1} by tile rows (W^T stored): G_ij^T, then W_ij^T = -(Tinv_i G_ij)^T
+    const int max_nt = (max_np + kP - 1) / kP;
+    for (int i = 1; i < max_nt; ++i) {
+        for (int b = 0; b < nb; ++b) {
+            const int np = npad[(size_t)b], ri = i * kP;
+            if (ri >= np) continue;
+            const int mi = std::min(kP, np - ri);
+            for (int j = 0; j < i; ++j) {
+                const int rj = j * kP;
+                task(P_(b) + (long long)ri * np + rj, np, W_(b) + (long long)rj * np + rj, np, mi, kP, ri - rj, nullptr, 0,
+                     G_(b) + (long long)rj * kP, kP, 0.f, 1.f, 0);
+            }
+        }
+        close_gemm();
+        for (int b = 0; b < nb; ++b) {
+            const int np = npad[(size_t)b], ri = i * kP;
+            if (ri >= np) continue;
+            const int mi = std::min(kP, np - ri);
+            for (int j = 0; j < i; ++j) {
+                const int rj = j * kP;
+                task(T_(b, i), kP, G_(b) + (long long)rj * kP, kP, mi, kP, mi, nullptr, 0, W_(b) + (long long)rj * np + ri,
+                     np, 0.f, -1.f, 0);
+            }
+        }
+        close_gemm();
+    }
+    // M = W^T W into the pool: lower tiles a >= b, mirrored
+    for (int b = 0; b < nb; ++b) {
+        const int np = npad[(size_t)b];
+        for (int ra = 0; ra < np; ra += kP)
+            for (int rb = 0; rb <= ra; rb += kP)
+                task(W_(b) + (long long)ra * np + ra, np, W_(b) + (long long)rb * np + ra, np, std::min(kP, np - ra),
+                     std::min(kP, np - rb), np - ra, P_(b) + (long long)ra * np + rb, np, P_(b) + (long long)rb * np + ra,
+                     np, 0.f, 1.f, ra == rb ? 1 : 0);
+    }
+    close_gemm();
+    DevBuf dtasks, dlists;
+    IE_TRY(dtasks.alloc(sizeof(GemmTask) * std::max<size_t>(tasks.size(), 1), s));
+    IE_TRY(dlists.alloc(sizeof(int) * std::max<size_t>(lists.size(), 1), s));
+    IE_TRY_CUDA(cudaMemcpyAsync(dtasks.ptr, tasks.data(), sizeof(GemmTask) * tasks.size(), cudaMemcpyHostToDevice, s));
+    IE_TRY_CUDA(cudaMemcpyAsync(dlists.ptr, lists.data(), sizeof(int) * lists.size(), cudaMemcpyHostToDevice, s));
+    for (const Op &op : ops) {
+        if (op.cnt == 0) continue;
+        if (op.diag) {
+            diag_factor<<<(unsigned)op.cnt, 256, kDiagSmem, s>>>(pool, W, T, f->d_loff, dtoff.as<long long>(), f->d_npad,
+                                                                 dlists.as<int>() + op.off, op.k0, f->d_info);
+        } else {
+            tc_gemm_tasks<<<(unsigned)op.cnt, 256, kGSmem, s>>>(dtasks.as<GemmTask>() + op.off, derr.as<int>());
+        }
+        IE_LAUNCHED();
+    }
+    int herr = 0;
+    IE_TRY_CUDA(cudaMemcpyAsync(&herr, derr.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    IE_TRY_CUDA(cudaStreamSynchronize(s));
+    if (herr) {
+        ie_set_error("dd_factor: a tensor-core GEMM timed out waiting for its MMAs");
+        return IE_ERR_TIMEOUT;
+    }
+    return IE_OK;
+}
