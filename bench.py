@@ -483,6 +483,7 @@ def extras(torch, iedd, I, dev, stream, iterations):
         "fft_matvec": {"ms": t_fft * 1e3, "pairs_equivalent_gpairs_s": pairs / t_fft / 1e9,
                        "basis": "FP64 circulant-embedding FFT on the 1024^2 periodic grid (the paper's matvec)"},
         "fft_solve": fft_solve_leg(torch, iedd, I, dev, stream),
+        "cbd": cbd_leg(torch, iedd, I, dev, stream),
         "fp64_plain": {"value": t_fac + (fp64_its + 1) * t_64 + fp64_its * t_ap, "unit": "s", "extrapolated": True,
                        "basis": (f"FP64 factor + {fp64_its} x (FP64 regenerated matvec + FP64 apply) + one FP64 "
                                  f"true-residual matvec, each timed on this GPU (a full FP64 solve measured 224.6 s)"),
@@ -523,6 +524,42 @@ def fft_solve_leg(torch, iedd, I, dev, stream, steps=3):
         out[name] = {"value": statistics.mean(ms) / 1e3, "unit": "s", "iterations": rep["iterations"],
                      "true_relres": rep["true_relres"], "t_solve_matvec_s": rep["matvec_ms"] / 1e3,
                      "t_solve_apply_s": rep["apply_ms"] / 1e3}
+    return out
+
+
+def cbd_leg(torch, iedd, I, dev, stream, sizes=(128, 256)):
+    """The paper's CBD preconditioner (Sec. 2.3: 2^d colour blocks, each the union of the extended
+    boxes of one parity colour, factored densely) against Schwarz (one block per extended box) on
+    the same 2D grids: boxes of 16 x 16 cells, 2-cell overlap, GRF l = 0.1, tol 1e-8, FFT matvec,
+    FP32 factors and inverses on the tensor cores.  Times: dd_factor and pcg_solve (host clock
+    around each, synchronized)."""
+    out = {}
+    for n in sizes:
+        f = torch.from_numpy(I.grf(2, n, ELL, 0)).to(dev)
+        prob = iedd.ie_discretize(2, n, device=dev.index)
+        row = {}
+        for name, kind in (("schwarz", iedd.DD_SCHWARZ), ("cbd", iedd.DD_CBD)):
+            part = iedd.dd_partition(prob, n // 16, 2, kind)
+            nb, maxb = part.nblocks, part.max_block
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            fac = iedd.dd_factor(prob, part, iedd.IE_MIXED, stream=stream)
+            torch.cuda.synchronize(dev)
+            t_fac = time.perf_counter() - t0
+            u = torch.zeros_like(f)
+            iedd.pcg_solve(prob, fac, f, u, tol=TOL, inner=iedd.IE_FFT, stream=stream)  # warm-up
+            u.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            rep = iedd.pcg_solve(prob, fac, f, u, tol=TOL, inner=iedd.IE_FFT, stream=stream)[0]
+            torch.cuda.synchronize(dev)
+            t_sol = time.perf_counter() - t0
+            row[name] = {"blocks": nb, "max_block": maxb, "factor_s": t_fac, "solve_s": t_sol,
+                         "iterations": rep["iterations"], "true_relres": rep["true_relres"],
+                         "apply_ms_per_iteration": rep["apply_ms"] / max(rep["applies"], 1)}
+            fac.close(); part.close()
+        prob.close()
+        out[f"n{n}"] = row
     return out
 
 

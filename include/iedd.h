@@ -148,7 +148,7 @@ IEDD_API int ie_release_matrix(ie_problem *p);
  *   kind   DD_JACOBI (the boxes), DD_SCHWARZ (the extended boxes, D = M) or DD_CBD (extended
  *          boxes unioned by the parity colour (k_1 mod 2, ..., k_d mod 2), D = 2^dim)
  * Index sets are in ascending global order.  Host-side; the sets are also copied to the device.
- * Errors: IE_ERR_ARG (n % m != 0, delta < 0, a subdomain larger than 16384 points), IE_ERR_OOM.
+ * Errors: IE_ERR_ARG (n % m != 0, delta < 0, a subdomain larger than 25600 points), IE_ERR_OOM.
  */
 IEDD_API int dd_partition(const ie_problem *p, int m, int delta, int kind, dd_partition_t **out);
 
@@ -163,10 +163,15 @@ IEDD_API void dd_partition_destroy(dd_partition_t *s);
 /*
  * dd_factor -- regenerate every A_i = R_i A R_i^T (Eq. e:ai) and factor it, A_i = L_i L_i^T,
  * by dense Cholesky (the exact subdomain solver of Sec. 4.3), all blocks in one launch.
- *   precision  IE_FP64: FP64 entries and factors.  IE_MIXED: FP32 entries and factors.
+ *   precision  IE_FP64: FP64 entries and factors, one CTA per block on the CUDA cores (blocks of
+ *              at most 8192 points, else IE_ERR_ARG).  IE_MIXED: FP32 entries; the Cholesky
+ *              factor and the explicit symmetric inverse M_i = A_i^{-1} of every block are
+ *              computed on the tcgen05 tensor cores (3xTF32 products, FP32 storage), and dd_apply
+ *              multiplies by M_i.
  *   info       (host, may be NULL) receives -1 if every block is SPD, else the first failing
  *              block index; the call then returns IE_ERR_NOT_SPD and *out is still created
- *              (its failing blocks are unusable).
+ *              (its failing blocks are unusable).  IE_ERR_TIMEOUT if a tensor-core task gave up
+ *              waiting for its MMAs (bounded waits).
  * The factor keeps references to p's device data: destroy it before the problem.
  * Synchronizes the stream (to read the per-block status).
  */
@@ -176,11 +181,12 @@ IEDD_API int dd_factor(const ie_problem *p, const dd_partition_t *s, int precisi
 IEDD_API void dd_factor_destroy(dd_factor_t *f);
 
 /*
- * dd_apply -- z = T^{-1} r = sum_i R_i^T L_i^{-T} L_i^{-1} R_i r (Eq. e:ad): gather, forward and
- * backward triangular solves per subdomain, then a plain (unweighted) sum over the overlaps,
- * taken in a fixed order so the result is bitwise reproducible.
+ * dd_apply -- z = T^{-1} r = sum_i R_i^T A_i^{-1} R_i r (Eq. e:ad), then a plain (unweighted) sum
+ * over the overlaps, taken in a fixed order so the result is bitwise reproducible.
  *   r, z  N x nrhs column-major, leading dimension ld (host or device, FP64); must not overlap.
- * Arithmetic is in the factor's precision; z is FP64.
+ * IE_FP64 factors: forward and backward triangular solves with L_i in FP64.  IE_MIXED factors:
+ * z_i = M_i (R_i r) with the FP32 inverse, products and sums in double-float (FP32 sums for
+ * 3D batches of >= 4 columns), so the operator is a fixed symmetric matrix; z is FP64.
  */
 IEDD_API int dd_apply(const dd_factor_t *f, const double *r, double *z, int nrhs, long long ld,
              void *stream);

@@ -218,7 +218,7 @@ extern "C" int ie_matvec(const ie_problem *p, const double *x, double *y, int nr
 // ---------------------------------------------------------------------------------------------
 // Domain decomposition (Sec. 2.2-2.3; Eqs. e:dd, e:first, e:cbd; Table t:dd)
 // ---------------------------------------------------------------------------------------------
-static const int kMaxBlock = 16384;
+static const int kMaxBlock = kInvMaxPad;  // the largest block the mixed factor and apply take
 
 extern "C" int dd_partition(const ie_problem *p, int m, int delta, int kind, dd_partition_t **out) {
     if (!out) { ie_set_error("dd_partition: out is NULL"); return IE_ERR_ARG; }
@@ -287,7 +287,7 @@ extern "C" int dd_partition(const ie_problem *p, int m, int delta, int kind, dd_
     s->total = s->offs.back();
     if (s->max_block > kMaxBlock) {
         delete s;
-        ie_set_error("dd_partition: a subdomain has more than 16384 points");
+        ie_set_error("dd_partition: a subdomain has more than " + std::to_string(kMaxBlock) + " points");
         return IE_ERR_ARG;
     }
     s->idx.reserve((size_t)s->total);
@@ -357,6 +357,11 @@ extern "C" int dd_factor(const ie_problem *p, const dd_partition_t *s, int preci
     if (!p || !s) { ie_set_error("dd_factor: NULL problem or partition"); return IE_ERR_ARG; }
     if (s->prob != p) { ie_set_error("dd_factor: partition belongs to another problem"); return IE_ERR_ARG; }
     if (precision != IE_FP64 && precision != IE_MIXED) { ie_set_error("dd_factor: unknown precision"); return IE_ERR_ARG; }
+    if (precision == IE_FP64 && s->max_block > kFp64MaxBlock) {
+        ie_set_error("dd_factor: IE_FP64 factors take blocks of at most " + std::to_string(kFp64MaxBlock) +
+                     " points (one CTA per block); use IE_MIXED");
+        return IE_ERR_ARG;
+    }
     DeviceGuard g(p->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     dd_factor_t *f = new (std::nothrow) dd_factor_t();

@@ -17,6 +17,8 @@
 //                    the inverse M_i = L_i^{-T} L_i^{-1} with the bulk on the tensor cores.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "iedd_internal.cuh"
 
 namespace {
@@ -151,7 +153,9 @@ int launch_factor(dd_factor_t *f, cudaStream_t s) {
     const ie_problem *p = f->prob;
     const dd_partition_t *part = f->part;
     if (f->nblocks == 0) return IE_OK;
-    dim3 g(f->nblocks, 64);
+    // enough CTAs per block for the largest one (CBD colour blocks hold up to 6.5e8 entries)
+    const long long ent = (long long)f->max_pad * f->max_pad;
+    dim3 g(f->nblocks, (unsigned)std::min<long long>(65535, std::max<long long>(64, ent / (256LL * 1024))));
     if (f->precision == IE_FP64) {
         gather_blocks<double><<<g, 256, 0, s>>>((double *)f->d_pool, f->d_loff, f->d_npad, f->d_n, part->d_offs,
                                                 part->d_idx, p->d_coord, p->dim, p->diag, p->c_const, p->c_ln,

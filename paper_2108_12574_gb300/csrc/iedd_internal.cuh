@@ -122,6 +122,8 @@ struct dd_factor_t {
 // Largest padded block applied through its explicit inverse: the apply stages the block's split x
 // (8 bytes per point and right-hand side) in one CTA's shared memory.
 constexpr int kInvMaxPad = 25600;
+// Largest block of an FP64 factor (one CTA per block factors it on CUDA cores).
+constexpr int kFp64MaxBlock = 8192;
 // Rows of one subdomain handled by one CTA of the explicit-inverse apply.
 constexpr int kApplyRows = 64;
 

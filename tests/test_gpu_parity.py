@@ -195,6 +195,43 @@ def test_pcg_accurate_residual_modes(residual):
     assert O.true_relative_residual(2, n, f, host(u)) <= 1e-9 * 1.01
 
 
+def test_cbd_mixed_matches_oracle_64():
+    # the paper's CBD preconditioner (4 colour blocks of 1444 points) with the tensor-core factor
+    # and explicit inverses: true residual <= tol and the oracle's iteration count (FP64 blocks)
+    n, m, delta = 64, 4, 2
+    f = I.grf(2, n, 0.1, 0)
+    prob = iedd.ie_discretize(2, n)
+    part = iedd.dd_partition(prob, m, delta, iedd.DD_CBD)
+    assert part.nblocks == 4 and part.max_block == 1444
+    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
+    u = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    rep = iedd.pcg_solve(prob, fac, dev(f), u, tol=1e-8, inner=iedd.IE_FFT)[0]
+    assert rep["status"] == 0
+    assert O.true_relative_residual(2, n, f, host(u)) <= 1e-8 * 1.01
+    _, it_ref, _ = O.Problem(2, n, m, delta, O.CBD, matvec="fft").solve(f, 1e-8)
+    assert it_ref - 1 <= rep["iterations"] <= it_ref + 3, (rep, it_ref)
+
+
+def test_cbd_mixed_256_converges_in_fewer_iterations_than_schwarz():
+    # 256^2: colour blocks of 24964 points (four dense FP32 inverses of 2.5 GB each); the true
+    # residual is checked by the oracle's FFT matvec
+    n, m, delta = 256, 16, 2
+    f = I.grf(2, n, 0.1, 1)
+    prob = iedd.ie_discretize(2, n)
+    its = {}
+    for kind in (iedd.DD_SCHWARZ, iedd.DD_CBD):
+        part = iedd.dd_partition(prob, m, delta, kind)
+        fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
+        u = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+        rep = iedd.pcg_solve(prob, fac, dev(f), u, tol=1e-8, inner=iedd.IE_FFT)[0]
+        assert rep["status"] == 0
+        assert O.true_relative_residual(2, n, f, host(u)) <= 1e-8 * 1.01
+        its[kind] = rep["iterations"]
+        fac.close()
+        part.close()
+    assert its[iedd.DD_CBD] < its[iedd.DD_SCHWARZ] / 1.5, its
+
+
 def test_pcg_fft_inner_mixed_512():
     # the 512^2 workload with the FFT inner matvec and FP32 inverses: the true residual meets tol
     n, m, delta = 512, 32, 2
