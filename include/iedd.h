@@ -300,6 +300,21 @@ IEDD_API int ws_predict(ws_model *w, const ie_problem *p, const double *f, doubl
  * replay counts the kernel nodes of the graph); reset != 0 returns the count and zeroes it. */
 IEDD_API long long ie_kernel_launches(int reset);
 
+/*
+ * ie_autotune -- the library's autotuner (not in the paper): launch shapes of the explicit-inverse
+ * apply (rows per work item, rows per warp pass, loads in flight) and of the FFT passes (lines per
+ * CTA) are chosen by timing every candidate once per problem shape, at dd_factor and at the first
+ * IE_FFT use (both synchronous and outside any stream capture), and cached for the process.  All
+ * candidates compute bitwise identical results.  On by default; the environment variable
+ * IEDD_AUTOTUNE=0 starts with it off.
+ *   mode  -1: query; 0: off; 1: on; 2: forget the cached choices (state unchanged)
+ * Returns the state before the call (1 on, 0 off).  Thread-safe.
+ */
+IEDD_API int ie_autotune(int mode);
+/* The cached choices, one line each: "key -> choice (candidate:time ...)"; valid until the next
+ * call from the same thread. */
+IEDD_API const char *ie_autotune_report(void);
+
 /* Fills *o with the defaults: tol 1e-8, max_it 1000, IE_MIXED, replace_every 50, use_x0 0,
  * timeout_s 0, check_every 8, verify 1. */
 IEDD_API void pcg_default_opts(pcg_opts *o);

@@ -8,6 +8,9 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <cstdlib>
+#include <mutex>
+#include <map>
 #include <vector>
 
 #include "iedd_internal.cuh"
@@ -51,6 +54,57 @@ int DevBuf::alloc(size_t b, cudaStream_t st) {
 
 DevBuf::~DevBuf() {
     if (ptr) cudaFreeAsync(ptr, s);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Autotuning: measured choices of launch shapes, cached per problem shape for the process
+// ---------------------------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, std::string>> g_tune;
+int g_tune_on = -1;  // -1: not read yet (IEDD_AUTOTUNE=0 disables)
+bool tune_on_locked() {
+    if (g_tune_on < 0) {
+        const char *e = std::getenv("IEDD_AUTOTUNE");
+        g_tune_on = (e && e[0] == '0') ? 0 : 1;
+    }
+    return g_tune_on == 1;
+}
+}  // namespace
+
+bool autotune_enabled() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return tune_on_locked();
+}
+
+bool tune_get(const std::string &key, int *choice) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it == g_tune.end()) return false;
+    *choice = it->second.first;
+    return true;
+}
+
+void tune_put(const std::string &key, int choice, const std::string &detail) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = {choice, detail};
+}
+
+extern "C" int ie_autotune(int mode) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const int prev = tune_on_locked() ? 1 : 0;
+    if (mode == 0 || mode == 1) g_tune_on = mode;
+    if (mode == 2) g_tune.clear();
+    return prev;
+}
+
+extern "C" const char *ie_autotune_report(void) {
+    static thread_local std::string out;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    out.clear();
+    for (const auto &kv : g_tune)
+        out += kv.first + " -> " + std::to_string(kv.second.first) + " (" + kv.second.second + ")\n";
+    return out.c_str();
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -396,18 +450,20 @@ extern "C" int dd_factor(const ie_problem *p, const dd_partition_t *s, int preci
     f->inverse = precision == IE_MIXED && f->max_pad <= kInvMaxPad;
     if (f->inverse) {
         std::vector<long long> xoff((size_t)s->nblocks + 1, 0);
-        std::vector<int2> chunks;
         for (int i = 0; i < s->nblocks; ++i) xoff[(size_t)i + 1] = xoff[(size_t)i] + npad[(size_t)i];
-        for (int i : order)  // largest blocks first
-            for (int r0 = 0; r0 < nb[(size_t)i]; r0 += kApplyRows) chunks.push_back(make_int2(i, r0));
         f->xtotal = xoff.back();
-        f->nchunks = (int)chunks.size();
         if ((e = cudaMalloc(&f->d_xoff, sizeof(long long) * xoff.size())) != cudaSuccess) return fail(e);
-        if ((e = cudaMalloc(&f->d_chunks, sizeof(int2) * std::max<size_t>(chunks.size(), 1))) != cudaSuccess) return fail(e);
         if ((e = cudaMemcpy(f->d_xoff, xoff.data(), sizeof(long long) * xoff.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
-        if (!chunks.empty() &&
-            (e = cudaMemcpy(f->d_chunks, chunks.data(), sizeof(int2) * chunks.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
-            return fail(e);
+        for (int k = 0; k < 3; ++k) {  // work items of kApplyRowOpts[k] rows, largest blocks first
+            std::vector<int2> chunks;
+            for (int i : order)
+                for (int r0 = 0; r0 < nb[(size_t)i]; r0 += kApplyRowOpts[k]) chunks.push_back(make_int2(i, r0));
+            f->nchunks[k] = (int)chunks.size();
+            if ((e = cudaMalloc(&f->d_chunks[k], sizeof(int2) * std::max<size_t>(chunks.size(), 1))) != cudaSuccess) return fail(e);
+            if (!chunks.empty() && (e = cudaMemcpy(f->d_chunks[k], chunks.data(), sizeof(int2) * chunks.size(),
+                                                   cudaMemcpyHostToDevice)) != cudaSuccess)
+                return fail(e);
+        }
     }
     if ((e = cudaMemcpy(f->d_loff, loff.data(), sizeof(long long) * loff.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpy(f->d_npad, npad.data(), sizeof(int) * npad.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
@@ -418,6 +474,15 @@ extern "C" int dd_factor(const ie_problem *p, const dd_partition_t *s, int preci
     int stl = launch_factor(f, st);
     if (stl == IE_OK && f->inverse) stl = launch_factor_tc(f, npad, loff, st);
     if (stl == IE_OK) stl = prepare_apply(f);
+    if (stl == IE_OK && f->inverse) {
+        // the tuning applies need the factor finished and every block SPD
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+        std::vector<int> hinfo0((size_t)s->nblocks);
+        if ((e = cudaMemcpy(hinfo0.data(), f->d_info, sizeof(int) * hinfo0.size(), cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e);
+        bool spd = true;
+        for (int v : hinfo0) spd = spd && v < 0;
+        if (spd) stl = tune_apply(f, st);
+    }
     if (stl != IE_OK) { dd_factor_destroy(f); return stl; }
     std::vector<int> hinfo((size_t)s->nblocks);
     if ((e = cudaMemcpyAsync(hinfo.data(), f->d_info, sizeof(int) * hinfo.size(), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return fail(e);
@@ -444,7 +509,7 @@ extern "C" void dd_factor_destroy(dd_factor_t *f) {
     cudaFree(f->d_info);
     cudaFree(f->d_pool);
     cudaFree(f->d_xoff);
-    cudaFree(f->d_chunks);
+    for (int k = 0; k < 3; ++k) cudaFree(f->d_chunks[k]);
     delete f;
 }
 

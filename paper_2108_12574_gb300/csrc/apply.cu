@@ -283,7 +283,7 @@ apply_split(const int *__restrict__ npad, const int *__restrict__ nb, const long
     }
 }
 
-// K6i: one CTA per (chunk of kApplyRows rows of one subdomain, group of R right-hand sides).  The
+// K6i: one CTA per (chunk of `rows` rows of one subdomain, group of R right-hand sides).  The
 // CTA stages the block's split x for its R columns in shared memory.  A row is taken by LPR = 8
 // lanes (the padded size is a multiple of 32, so every lane has the same np/32 float4 columns:
 // lane c of the group reads float4 columns c, c + 8, ...); a warp covers 4 x RW rows per pass,
@@ -336,7 +336,7 @@ apply_inverse(const float *__restrict__ pool, const long long *__restrict__ loff
               const int *__restrict__ nb, const long long *__restrict__ offs, const int2 *__restrict__ chunks,
               const long long *__restrict__ xoff, const float *__restrict__ xh_g, const float *__restrict__ xl_g,
               const int *__restrict__ xexp, long long xtotal, int nblocks, int nrhs, double *__restrict__ zbuf,
-              long long total) {
+              long long total, int rows) {
     constexpr int SUB = 32 / kLPR;                  // row groups per warp
     constexpr int K = (RW * R + kLPR - 1) / kLPR;   // results per lane and pass
     extern __shared__ __align__(16) float xs[];     // x hi words [R][np], then (EXACT) lo words [R][np]
@@ -344,7 +344,7 @@ apply_inverse(const float *__restrict__ pool, const long long *__restrict__ loff
     const int b = ch.x, row0 = ch.y;
     const int g0 = blockIdx.y * R;
     const int np = npad[b], n = nb[b];
-    const int rend = min(row0 + kApplyRows, n);
+    const int rend = min(row0 + rows, n);
     const float *M = pool + loff[b];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int sub = lane / kLPR, cl = lane % kLPR;
@@ -419,11 +419,44 @@ __global__ void overlap_sum(const double *__restrict__ zbuf, long long total, co
 // per kernel for the whole process, so it is set to one fixed ceiling that covers every factor.
 constexpr int kApplySmemCeiling = 200 * 1024;
 
+// The explicit-inverse apply's candidate configurations: class (kApplyE1 / E4 / F8) x variant
+// (rows per warp pass RW, float4 loads in flight U) x rows per work item (kApplyRowOpts).  Every
+// candidate sums each row in the same order, so they differ in speed only.
+#define IE_AINV_VARIANTS(X)                                                                         \
+    X(0, 1, 2, 4, true) X(1, 1, 4, 2, true) X(2, 1, 1, 8, true)                                     \
+    X(3, 4, 2, 2, true) X(4, 4, 1, 4, true) X(5, 4, 4, 1, true)                                     \
+    X(6, 8, 2, 4, false) X(7, 8, 1, 4, false) X(8, 8, 4, 2, false)
+
+int launch_apply_inverse(const dd_factor_t *f, int klass, int cfg, const float *xh, const float *xl, const int *xe,
+                         int nrhs, double *zbuf, cudaStream_t s) {
+    const dd_partition_t *part = f->part;
+    const int v = cfg / 3, ri = cfg % 3;
+    const unsigned nch = (unsigned)f->nchunks[ri];
+    const float *M = (const float *)f->d_pool;
+    switch (klass * 3 + v) {
+#define IE_AINV_CASE(ID, R_, RW_, U_, EX_)                                                                     \
+    case ID:                                                                                                  \
+        apply_inverse<R_, RW_, U_, EX_><<<dim3(nch, (nrhs + R_ - 1) / R_), 256,                               \
+                                          sizeof(float) * (EX_ ? 2 : 1) * R_ * f->max_pad, s>>>(              \
+            M, f->d_loff, f->d_npad, f->d_n, part->d_offs, f->d_chunks[ri], f->d_xoff, xh, xl, xe, f->xtotal,  \
+            f->nblocks, nrhs, zbuf, part->total, kApplyRowOpts[ri]);                                          \
+        break;
+        IE_AINV_VARIANTS(IE_AINV_CASE)
+#undef IE_AINV_CASE
+        default:
+            ie_set_error("dd_apply: bad apply configuration");
+            return IE_ERR_ARG;
+    }
+    IE_LAUNCHED();
+    return IE_OK;
+}
+
 int prepare_apply(const dd_factor_t *f) {
     (void)f;
-    IE_TRY_CUDA(cudaFuncSetAttribute(apply_inverse<8, 2, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmemCeiling));
-    IE_TRY_CUDA(cudaFuncSetAttribute(apply_inverse<4, 2, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmemCeiling));
-    IE_TRY_CUDA(cudaFuncSetAttribute(apply_inverse<1, 2, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmemCeiling));
+#define IE_AINV_ATTR(ID, R_, RW_, U_, EX_) \
+    IE_TRY_CUDA(cudaFuncSetAttribute(apply_inverse<R_, RW_, U_, EX_>, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmemCeiling));
+    IE_AINV_VARIANTS(IE_AINV_ATTR)
+#undef IE_AINV_ATTR
     IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks_multi<double, double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmemCeiling));
     IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks_multi<float, double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmemCeiling));
     IE_TRY_CUDA(cudaFuncSetAttribute(apply_blocks_multi<float, float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kApplySmemCeiling));
@@ -448,7 +481,6 @@ int launch_apply(const dd_factor_t *f, const double *r, long long ldr, double *z
         IE_TRY(xb.alloc(sizeof(float) * (size_t)f->xtotal * nrhs * (exact ? 2 : 1), s));
         IE_TRY(xe.alloc(sizeof(int) * (size_t)f->nblocks * nrhs, s));
         float *xh = xb.as<float>(), *xl = exact ? xh + f->xtotal * nrhs : nullptr;
-        const float *M = (const float *)f->d_pool;
         dim3 gs(f->nblocks, nrhs);
         if (exact) {
             apply_split<true><<<gs, 256, 0, s>>>(f->d_npad, f->d_n, part->d_offs, part->d_idx, f->d_xoff, r, ldr,
@@ -458,18 +490,10 @@ int launch_apply(const dd_factor_t *f, const double *r, long long ldr, double *z
                                                   f->xtotal, f->nblocks, xh, xl, xe.as<int>());
         }
         IE_LAUNCHED();
-#define IE_APPLY_INV(R_, RW_, U_, EX_)                                                                   \
-    apply_inverse<R_, RW_, U_, EX_><<<dim3(f->nchunks, (nrhs + R_ - 1) / R_), 256,                       \
-                                      sizeof(float) * (EX_ ? 2 : 1) * R_ * f->max_pad, s>>>(              \
-        M, f->d_loff, f->d_npad, f->d_n, part->d_offs, f->d_chunks, f->d_xoff, xh, xl, xe.as<int>(),     \
-        f->xtotal, f->nblocks, nrhs, zbuf.as<double>(), part->total)
-        if (f->nchunks > 0) {
-            if (!exact) IE_APPLY_INV(8, 2, 4, false);
-            else if (nrhs >= 4 && batch_fits) IE_APPLY_INV(4, 2, 2, true);
-            else IE_APPLY_INV(1, 2, 4, true);
-            IE_LAUNCHED();
+        if (f->nchunks[0] > 0) {
+            const int klass = !exact ? kApplyF8 : (nrhs >= 4 && batch_fits) ? kApplyE4 : kApplyE1;
+            IE_TRY(launch_apply_inverse(f, klass, f->apply_cfg[klass], xh, xl, xe.as<int>(), nrhs, zbuf.as<double>(), s));
         }
-#undef IE_APPLY_INV
     } else if (f->nblocks > 0 && nrhs >= 4 && smm <= (size_t)kApplySmemCeiling) {
         if (f->precision == IE_FP64) {
             dim3 g(f->nblocks, (nrhs + 15) / 16);
@@ -505,4 +529,58 @@ int launch_apply(const dd_factor_t *f, const double *r, long long ldr, double *z
     overlap_sum<<<g2, 256, 0, s>>>(zbuf.as<double>(), part->total, part->d_inv_ptr, part->d_inv_pos, z, ldz, p->N);
     IE_LAUNCHED();
     return IE_OK;
+}
+
+// Times every configuration of each apply class this factor uses (a zero input: the kernels are
+// data-independent) on its own stream position, keeps the fastest, and caches the choice for the
+// partition's shape.  Runs at factor time, outside any capture.
+int tune_apply(dd_factor_t *f, cudaStream_t s) {
+    for (int k = 0; k < 3; ++k) f->apply_cfg[k] = 1;  // variant 0, 64-row work items
+    if (!autotune_enabled() || !f->inverse || f->nblocks == 0) return IE_OK;
+    const ie_problem *p = f->prob;
+    const dd_partition_t *part = f->part;
+    const bool batch_fits = sizeof(float) * 8 * (size_t)f->max_pad <= (size_t)kApplySmemCeiling;
+    const std::string shape = "d" + std::to_string(p->dim) + "/n" + std::to_string(p->n) + "/blocks" +
+                              std::to_string(f->nblocks) + "/total" + std::to_string(part->total) + "/max" +
+                              std::to_string(f->max_pad);
+    struct Cls { int klass, nrhs; bool use; };
+    const Cls classes[3] = {{kApplyE1, 1, true}, {kApplyE4, 8, p->dim == 2 && batch_fits},
+                            {kApplyF8, 8, p->dim == 3 && batch_fits}};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    IE_TRY_CUDA(cudaEventCreate(&e0));
+    IE_TRY_CUDA(cudaEventCreate(&e1));
+    int st = IE_OK;
+    for (const Cls &c : classes) {
+        if (!c.use) continue;
+        const std::string key = "apply/" + std::to_string(c.klass) + "/" + shape;
+        int best = 1;
+        if (tune_get(key, &best)) { f->apply_cfg[c.klass] = best; continue; }
+        DevBuf r, z;
+        if ((st = r.alloc(sizeof(double) * (size_t)p->N * c.nrhs, s)) != IE_OK) break;
+        if ((st = z.alloc(sizeof(double) * (size_t)p->N * c.nrhs, s)) != IE_OK) break;
+        if (cudaMemsetAsync(r.ptr, 0, sizeof(double) * (size_t)p->N * c.nrhs, s) != cudaSuccess) { st = IE_ERR_CUDA; break; }
+        float best_ms = 0.f;
+        std::string detail;
+        for (int cand = 0; cand < 9 && st == IE_OK; ++cand) {
+            f->apply_cfg[c.klass] = cand;
+            if ((st = launch_apply(f, r.as<double>(), p->N, z.as<double>(), p->N, c.nrhs, s)) != IE_OK) break;
+            cudaEventRecord(e0, s);
+            for (int rep = 0; rep < 3 && st == IE_OK; ++rep)
+                st = launch_apply(f, r.as<double>(), p->N, z.as<double>(), p->N, c.nrhs, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { st = IE_ERR_CUDA; break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= 3.f;
+            detail += (cand ? " " : "") + std::to_string(cand) + ":" + std::to_string((int)(ms * 1000.f)) + "us";
+            if (cand == 0 || ms < best_ms) { best_ms = ms; best = cand; }
+        }
+        if (st != IE_OK) break;
+        f->apply_cfg[c.klass] = best;
+        tune_put(key, best, detail);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != IE_OK) for (int k = 0; k < 3; ++k) f->apply_cfg[k] = 1;
+    return st;
 }

@@ -196,14 +196,16 @@ __global__ void fft_chat(const double2 *__restrict__ Z, double inv, long long T,
     if (k < T) chat[k] = Z[k].x * inv;
 }
 
-int lines_per_cta(int lg, long long lines, int sms, bool strided) {
+// Launch shape cfg = 3 a + b: enough CTAs to fill the GPU (1 << a) times where the line count
+// allows, and strided passes keep at least (2 << b) adjacent lines per CTA (global accesses in
+// runs of 32 (2 << b) bytes).  The default is cfg 4; prepare_fft times all nine.
+int lines_per_cta(int lg, long long lines, int sms, bool strided, int cfg) {
     const size_t per_line = sizeof(double2) * (size_t)((1 << lg) + 1);
     const size_t tw = sizeof(double2) * (size_t)(1 << lg) / 2;
     const long long cap = std::min<long long>((long long)((kFftSmemCeiling - tw) / per_line), 64);
-    // enough CTAs to fill the GPU twice where the line count allows; strided passes keep at least
-    // 4 adjacent lines per CTA so that global accesses come in 64-byte runs
-    long long cb = std::min<long long>(cap, std::max<long long>(1, lines / (2LL * sms)));
-    if (strided) cb = std::max<long long>(cb, std::min<long long>(cap, 4));
+    const int a = cfg / 3, b = cfg % 3;
+    long long cb = std::min<long long>(cap, std::max<long long>(1, lines / ((long long)(1 << a) * sms)));
+    if (strided) cb = std::max<long long>(cb, std::min<long long>(cap, 2 << b));
     return (int)std::max<long long>(cb, 1);
 }
 
@@ -213,7 +215,7 @@ int fft_pass(const ie_problem *p, double2 *Z, long long zstride, int npairs, int
              int nout, cudaStream_t s) {
     const int lg = p->fft_lg, L = 1 << lg;
     const long long lines = (long long)ext1 * ext2;
-    const int cb = lines_per_cta(lg, lines, p->sm_count, axis != p->dim - 1);
+    const int cb = lines_per_cta(lg, lines, p->sm_count, axis != p->dim - 1, p->fft_cfg);
     const size_t smem = sizeof(double2) * ((size_t)cb * (L + 1) + (size_t)L / 2);
     const long long ctas = (lines + cb - 1) / cb;
     if (ctas > 0x7fffffffLL || npairs > 65535) {
@@ -235,6 +237,47 @@ int fft_supported(const ie_problem *p, std::string *why) {
         return 0;
     }
     return 1;
+}
+
+// Times the nine launch shapes on one matvec of a zero vector (the transforms are
+// data-independent) and keeps the fastest; cached per (dim, n).
+int tune_fft(ie_problem *p) {
+    p->fft_cfg = 4;
+    if (!autotune_enabled()) return IE_OK;
+    const std::string key = "fft/d" + std::to_string(p->dim) + "/n" + std::to_string(p->n);
+    int best = 4;
+    if (tune_get(key, &best)) { p->fft_cfg = best; return IE_OK; }
+    double *x = nullptr, *y = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int st = IE_OK;
+    if (cudaMalloc(&x, sizeof(double) * p->N) != cudaSuccess || cudaMalloc(&y, sizeof(double) * p->N) != cudaSuccess ||
+        cudaMemset(x, 0, sizeof(double) * p->N) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        st = IE_ERR_CUDA;
+    }
+    float best_ms = 0.f;
+    std::string detail;
+    for (int cand = 0; cand < 9 && st == IE_OK; ++cand) {
+        p->fft_cfg = cand;
+        st = launch_matvec_fft(p, x, p->N, y, p->N, 1, nullptr);
+        cudaEventRecord(e0, nullptr);
+        for (int rep = 0; rep < 3 && st == IE_OK; ++rep) st = launch_matvec_fft(p, x, p->N, y, p->N, 1, nullptr);
+        cudaEventRecord(e1, nullptr);
+        if (st == IE_OK && cudaEventSynchronize(e1) != cudaSuccess) st = IE_ERR_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 3.f;
+        detail += (cand ? " " : "") + std::to_string(cand) + ":" + std::to_string((int)(ms * 1000.f)) + "us";
+        if (cand == 0 || ms < best_ms) { best_ms = ms; best = cand; }
+    }
+    cudaFree(x);
+    cudaFree(y);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != IE_OK) { p->fft_cfg = 4; return st; }
+    p->fft_cfg = best;
+    tune_put(key, best, detail);
+    return IE_OK;
 }
 
 int prepare_fft(const ie_problem *cp) {
@@ -292,6 +335,7 @@ int prepare_fft(const ie_problem *cp) {
     }
     if (st == IE_OK && cudaDeviceSynchronize() != cudaSuccess) st = IE_ERR_CUDA;
     cudaFree(Z);
+    if (st == IE_OK) st = tune_fft(p);
     if (st != IE_OK) {
         ie_set_error("ie_matvec: building the FFT of the kernel failed");
         p->d_fft_tw = nullptr;

@@ -79,6 +79,7 @@ struct ie_problem {
     int fft_lg = 0;
     double2 *d_fft_tw = nullptr;
     double *d_fft_chat = nullptr;
+    int fft_cfg = 4;               // autotuned launch shape of the FFT passes (see fft.cu)
 };
 
 struct dd_partition_t {
@@ -115,17 +116,24 @@ struct dd_factor_t {
     int inverse = 0;               // FP32 explicit inverses in d_pool (IE_MIXED, max_pad <= kInvMaxPad)
     long long *d_xoff = nullptr;   // per block: offset of its padded slice of the apply's split x
     long long xtotal = 0;          // sum of the padded block sizes
-    int nchunks = 0;               // apply work items: (block, first row) per kApplyRows rows
-    int2 *d_chunks = nullptr;
+    // apply work items, one table per candidate row count kApplyRowOpts[k]: (block, first row)
+    int nchunks[3] = {0, 0, 0};
+    int2 *d_chunks[3] = {nullptr, nullptr, nullptr};
+    // autotuned apply configuration per class (kApplyE1, kApplyE4, kApplyF8): variant * 3 + row option
+    int apply_cfg[3] = {1, 1, 1};
 };
+
+// Classes of the explicit-inverse apply: double-float single column, double-float 4-column
+// batches (2D), FP32 8-column batches (3D); candidate row counts per work item.
+constexpr int kApplyE1 = 0, kApplyE4 = 1, kApplyF8 = 2;
+constexpr int kApplyRowOpts[3] = {32, 64, 128};
 
 // Largest padded block applied through its explicit inverse: the apply stages the block's split x
 // (8 bytes per point and right-hand side) in one CTA's shared memory.
 constexpr int kInvMaxPad = 25600;
 // Largest block of an FP64 factor (one CTA per block factors it on CUDA cores).
 constexpr int kFp64MaxBlock = 8192;
-// Rows of one subdomain handled by one CTA of the explicit-inverse apply.
-constexpr int kApplyRows = 64;
+
 
 // ---------------------------------------------------------------------------------------------
 // Device vector helpers: host / device pointer detection and staging
@@ -183,6 +191,14 @@ int launch_matvec_fft(const ie_problem *p, const double *x, long long ldx, doubl
                       cudaStream_t s);
 
 int launch_factor(dd_factor_t *f, cudaStream_t s);
+// apply.cu: time the candidate apply configurations of an explicit-inverse factor (outside any
+// capture; cached per partition shape) and record the fastest in f->apply_cfg.
+int tune_apply(dd_factor_t *f, cudaStream_t s);
+
+// Autotuning switch and process-wide cache of measured choices (api.cu).
+bool autotune_enabled();
+bool tune_get(const std::string &key, int *choice);
+void tune_put(const std::string &key, int choice, const std::string &detail);
 // tc_factor.cu: Cholesky and explicit inverse of the gathered FP32 blocks in f->d_pool (M_i
 // replaces the block), bulk on the tensor cores; synchronizes.  f->d_info must hold -1 per block.
 int launch_factor_tc(dd_factor_t *f, const std::vector<int> &npad, const std::vector<long long> &loff,

@@ -31,7 +31,7 @@ EXPORTS = ("ie_last_error", "ie_version", "ie_discretize", "ie_problem_info", "i
            "dd_factor_destroy", "dd_apply", "ie_kernel_launches", "pcg_default_opts", "pcg_solve",
            "ie_matvec_noalloc", "ws_create", "ws_destroy", "ws_num_params", "ws_get_params", "ws_set_params",
            "ws_forward_raw", "ws_backward_raw", "ws_train_step", "ws_predict", "ie_store_matrix",
-           "ie_release_matrix")
+           "ie_release_matrix", "ie_autotune", "ie_autotune_report")
 IE_NOALLOC_MAX_N = 4194304 - 1024
 
 
@@ -87,6 +87,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dd_factor_destroy": (None, [vp]),
         "dd_apply": (i, [vp, vp, vp, i, ll, vp]),
         "ie_kernel_launches": (ll, [i]),
+        "ie_autotune": (i, [i]),
+        "ie_autotune_report": (ctypes.c_char_p, []),
         "ie_store_matrix": (i, [vp, vp]),
         "ie_release_matrix": (i, [vp]),
         "ie_matvec_noalloc": (i, [i, i, d, i, vp, vp, vp]),
@@ -351,6 +353,15 @@ def ws_create(device: int = 0, seed: int = 0) -> WarmStartModel:
 
 def ie_kernel_launches(reset: bool = False) -> int:
     return load_library().ie_kernel_launches(1 if reset else 0)
+
+
+def ie_autotune(mode: int = -1) -> bool:
+    """Autotuner switch: -1 query, 0 off, 1 on, 2 forget cached choices; returns the previous state."""
+    return bool(load_library().ie_autotune(mode))
+
+
+def ie_autotune_report() -> str:
+    return load_library().ie_autotune_report().decode()
 
 
 def pcg_default_opts() -> PcgOpts:

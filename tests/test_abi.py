@@ -103,3 +103,16 @@ def test_product_path_never_imports_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "ie_oracle" not in text and "direct_sum" not in text, f
+
+
+def test_autotune_switch_without_gpu():
+    # the autotuner's switch and report touch no device: query, off, on, forget
+    from paper_2108_12574_gb300 import iedd
+    prev = iedd.ie_autotune(-1)
+    assert iedd.ie_autotune(0) == prev
+    assert iedd.ie_autotune(-1) is False
+    assert iedd.ie_autotune(1) is False
+    assert iedd.ie_autotune(-1) is True
+    iedd.ie_autotune(2)
+    assert iedd.ie_autotune_report() == ""
+    iedd.ie_autotune(1 if prev else 0)

@@ -366,6 +366,50 @@ def test_mixed_apply_is_a_fixed_symmetric_operator(dim, n, m, delta):
             assert float(torch.linalg.norm(z - Z8[k]) / torch.linalg.norm(z)) <= 1e-6, k
 
 
+@pytest.mark.parametrize("dim,n,m,delta,nrhs", [(2, 128, 8, 2, 1), (2, 128, 8, 2, 8), (3, 16, 2, 1, 8)])
+def test_autotuned_apply_is_bitwise_the_default(dim, n, m, delta, nrhs):
+    # every tuning candidate sums each row in the same order: tuned and untuned applies agree bit
+    # for bit, and the tuner records its choice
+    N = n ** dim
+    prob = iedd.ie_discretize(dim, n)
+    part = iedd.dd_partition(prob, m, delta, iedd.DD_SCHWARZ)
+    R = dev(I.uniform_rhs_batch(N, list(range(60, 60 + nrhs))).T.copy())
+    outs = []
+    prev = iedd.ie_autotune(-1)
+    try:
+        for mode in (0, 1):
+            iedd.ie_autotune(mode)
+            iedd.ie_autotune(2)
+            fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
+            Z = torch.zeros_like(R)
+            iedd.dd_apply(fac, R, Z)
+            outs.append(Z)
+            fac.close()
+        assert "apply/" in iedd.ie_autotune_report()
+    finally:
+        iedd.ie_autotune(1 if prev else 0)
+    assert torch.equal(outs[0], outs[1])
+
+
+def test_autotuned_fft_is_bitwise_the_default():
+    n = 96
+    x = dev(I.uniform_rhs(n * n, 5))
+    ys = []
+    prev = iedd.ie_autotune(-1)
+    try:
+        for mode in (0, 1):
+            iedd.ie_autotune(mode)
+            iedd.ie_autotune(2)
+            prob = iedd.ie_discretize(2, n)
+            y = torch.zeros_like(x)
+            iedd.ie_matvec(prob, x, y, iedd.IE_FFT)
+            ys.append(y)
+        assert "fft/" in iedd.ie_autotune_report()
+    finally:
+        iedd.ie_autotune(1 if prev else 0)
+    assert torch.equal(ys[0], ys[1])
+
+
 def test_apply_is_deterministic():
     n = 64
     prob = iedd.ie_discretize(2, n)
