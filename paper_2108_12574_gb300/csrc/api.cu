@@ -180,6 +180,7 @@ extern "C" void ie_destroy(ie_problem *p) {
     cudaFree(p->d_table64);
     cudaFree(p->d_stored);
     cudaFree(p->d_err);
+    cudaFree(p->d_table_tc);
     cudaFree(p->d_fft_tw);
     cudaFree(p->d_fft_chat);
     delete p;

@@ -73,6 +73,7 @@ struct ie_problem {
     double *d_table64 = nullptr;   // same table in FP64
     float *d_stored = nullptr;     // optional dense FP32 copy of A (zero diagonal), ie_store_matrix
     int *d_err = nullptr;          // device error word of the tensor-core matvec (bounded waits)
+    uint2 *d_table_tc = nullptr;   // per |offset|: the entry split into TF32 high / low words (0 at 0)
     int sm_count = 0;
     // FFT matvec (built on first use): periodic grid of L = 2^fft_lg points per axis, twiddles
     // exp(-2 pi i k / L) (k < L / 2) and the kernel's spectrum (FP64, L^d, forward-pass order)
@@ -176,6 +177,8 @@ int build_problem_tables(ie_problem *p);
 int launch_matvec_tc(const ie_problem *p, const double *x, long long ldx, int nrhs, double *partial, int S, int cps,
                      int nchunks, int *d_err, cudaStream_t s);
 int prepare_tc();
+int build_tc_table(ie_problem *p);
+bool tc_toeplitz(const ie_problem *p);  // the tensor-core matvec reads its tiles from d_table_tc
 int tc_chunk();
 int tc_rows();
 int tc_cols();

@@ -279,6 +279,18 @@ __global__ void combine_multi_kernel(const double *__restrict__ partial, int nsp
     y[(long long)r * ldy + i] = y0;
 }
 
+// Multi-RHS partials of exact off-diagonal entries (the Toeplitz-fed tensor-core matvec).
+__global__ void combine_exact_multi_kernel(const double *__restrict__ partial, int nsplit, int nrhs,
+                                           const double *__restrict__ x, long long ldx, double *__restrict__ y,
+                                           long long ldy, long long N, double diag) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (i >= N) return;
+    double s = 0.0;
+    for (int k = 0; k < nsplit; ++k) s += partial[((long long)k * nrhs + r) * N + i];
+    y[(long long)r * ldy + i] = fma(diag, x[(long long)r * ldx + i], s);
+}
+
 // y_i = diag x_i + off-diagonal part from the split partials (FP64 combine).
 template <typename TP>
 __global__ void combine_kernel(const TP *__restrict__ partial, int nsplit, const double *__restrict__ x,
@@ -631,6 +643,7 @@ int build_problem_tables(ie_problem *p) {
     table_kernel<<<(unsigned)((T + 255) / 256), 256>>>(p->d_table, p->d_table64, p->dim, p->n, T, p->diag,
                                                       p->c_const, p->c_ln, p->c_r);
     IE_LAUNCHED();
+    IE_TRY(build_tc_table(p));
     IE_TRY_CUDA(cudaDeviceSynchronize());
     return IE_OK;
 }
@@ -645,7 +658,7 @@ int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, doubl
     }
     const int ntiles = (int)((N + kThreads - 1) / kThreads);
     DevBuf xsum;
-    if (p->dim == 2 && (precision == IE_MIXED || precision == IE_FP64 || precision == IE_TENSOR)) {
+    if (p->dim == 2 && (precision == IE_MIXED || precision == IE_FP64 || (precision == IE_TENSOR && !tc_toeplitz(p)))) {
         DevBuf part;
         IE_TRY(part.alloc(sizeof(double) * iedd::kRedBlocks * nrhs, s));
         IE_TRY(xsum.alloc(sizeof(double) * nrhs, s));
@@ -666,9 +679,14 @@ int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, doubl
         DevBuf part;
         IE_TRY(part.alloc(sizeof(double) * N * nrhs * Se, s));
         IE_TRY(launch_matvec_tc(p, x, ldx, nrhs, part.as<double>(), Se, cps, nchunks, p->d_err, s));
-        combine_multi_kernel<<<dim3((unsigned)((N + 255) / 256), nrhs), 256, 0, s>>>(
-            part.as<double>(), Se, nrhs, x, ldx, y, ldy, N, p->dim, p->diag, p->c_const,
-            p->dim == 2 ? p->c_log2 : p->c_r, xsum.ptr ? xsum.as<double>() : nullptr);
+        if (tc_toeplitz(p)) {  // exact off-diagonal entries: y = diag x + the partial sums
+            combine_exact_multi_kernel<<<dim3((unsigned)((N + 255) / 256), nrhs), 256, 0, s>>>(
+                part.as<double>(), Se, nrhs, x, ldx, y, ldy, N, p->diag);
+        } else {
+            combine_multi_kernel<<<dim3((unsigned)((N + 255) / 256), nrhs), 256, 0, s>>>(
+                part.as<double>(), Se, nrhs, x, ldx, y, ldy, N, p->dim, p->diag, p->c_const,
+                p->dim == 2 ? p->c_log2 : p->c_r, xsum.ptr ? xsum.as<double>() : nullptr);
+        }
         IE_LAUNCHED();
         if (dot_out) IE_TRY(launch_dots(x, ldx, y, ldy, N, nrhs, dot_out, s));
         return IE_OK;

@@ -84,20 +84,22 @@ __device__ __forceinline__ void gmma(uint32_t d_tmem, uint64_t a, uint64_t b, ui
         "l"(a), "l"(b), "r"(kGIdesc), "r"(accumulate));
 }
 
-__device__ __forceinline__ bool gbar_test(uint32_t bar, uint32_t phase) {
+// one suspending probe (the thread may sleep up to ~1 us while the phase is pending)
+__device__ __forceinline__ bool gbar_try(uint32_t bar, uint32_t phase) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(phase)
+        : "r"(bar), "r"(phase), "r"(1000u)
         : "memory");
     return ok != 0;
 }
 
+// bounded wait (a few seconds at most); false if the limit ran out
 __device__ __forceinline__ bool gbar_wait(uint32_t bar, uint32_t phase) {
-    for (long long i = 0; i < kGSpin; ++i)
-        if (gbar_test(bar, phase)) return true;
+    for (long long i = 0; i < kGSpin / 8; ++i)
+        if (gbar_try(bar, phase)) return true;
     return false;
 }
 
@@ -163,8 +165,9 @@ tc_gemm_tasks(const GemmTask *__restrict__ tasks, int *__restrict__ err) {
     for (int ch = 0; ch < nch; ++ch) {
         const int st = ch & 1;
         uint32_t *Ahi = gsm + st * kGStage, *Alo = Ahi + kGOp, *Bhi = Alo + kGOp, *Blo = Bhi + kGOp;
-        if (pending[st]) {  // the stage's previous MMAs must be done before its operands change
-            if (!gbar_wait(gsmem_u32(&mbar[st]), ph[st])) abort_flag = 1;
+        if (pending[st]) {  // the stage's previous MMAs must be done before its operands change;
+                            // one thread waits, the barrier below releases the others
+            if (tid == 0 && !gbar_wait(gsmem_u32(&mbar[st]), ph[st])) abort_flag = 1;
             ph[st] ^= 1u;
             pending[st] = 0;
         }
@@ -194,9 +197,9 @@ tc_gemm_tasks(const GemmTask *__restrict__ tasks, int *__restrict__ err) {
         }
         pending[st] = 1;
     }
-    for (int st = 0; st < 2; ++st) {  // drain (bounded)
+    for (int st = 0; st < 2; ++st) {  // drain (bounded, one thread)
         if (pending[st]) {
-            if (!gbar_wait(gsmem_u32(&mbar[st]), ph[st])) abort_flag = 1;
+            if (tid == 0 && !gbar_wait(gsmem_u32(&mbar[st]), ph[st])) abort_flag = 1;
             pending[st] = 0;
         }
     }

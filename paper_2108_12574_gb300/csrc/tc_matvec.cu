@@ -17,6 +17,7 @@
 // LBO = 128 (next 4 K elements), SBO = 1024 (next 8 rows, K = 32 per chunk).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "iedd_internal.cuh"
@@ -58,26 +59,23 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t phase) {
+// one suspending probe: the thread may sleep up to ~1 us in hardware while the phase is pending
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t phase) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(phase)
+        : "r"(bar), "r"(phase), "r"(1000u)
         : "memory");
     return ok != 0;
 }
 
-// bounded wait for the given phase of the barrier; false if the limit ran out
+// bounded wait for the given phase of the barrier; false if the limit ran out (a few seconds)
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
-    for (long long i = 0; i < kSpinLimit; ++i)
-        if (mbar_test(bar, phase)) return true;
+    for (long long i = 0; i < kSpinLimit / 8; ++i)
+        if (mbar_try(bar, phase)) return true;
     return false;
-}
-
-__device__ __forceinline__ uint32_t op_off(int r, int k) {
-    return (uint32_t)((r >> 3) * kSBO + (k >> 2) * kLBO + (r & 7) * 16 + (k & 3) * 4);
 }
 
 // x pre-split for the tensor-core matvec: for right-hand-side group g (64 columns) and source
@@ -121,16 +119,34 @@ __device__ __forceinline__ void two_sum_acc(float v, float &hi, float &lo) {
 }
 
 constexpr int kStage = 2 * kTM * kTK + 2 * kTN * kTK;  // uint32 words per operand stage (48 KB)
-constexpr int kFlush = 8;                              // chunks accumulated in TMEM between flushes
+constexpr int kStages = 2;                             // operand stages (96 KB, two CTAs per SM)
+constexpr int kFlush = 256 / kTK;                      // chunks accumulated in TMEM between flushes
 
-template <int DIM>
-__global__ void __launch_bounds__(256)
+// TOEP: the grid size n is a multiple of 32 and a tile's 128 rows are whole lines of the fastest
+// axis or one part of a line (n = 32, 64 or a multiple of 128).  A chunk's 32 sources then lie on
+// one line, and the entry of (row r, source k) depends on r only through its line q = r / Lr and
+// on (r mod Lr) - k: per chunk the nl x (Lr + 31) distinct entries (at most 252) are read from the
+// exact per-offset table, already split into TF32 high / low words, and the 128 x 32 tile is
+// filled from them -- no SFU evaluation, and the entries are the FP64 ones (excluding i = j).
+//
+// Pipeline (one CTA = 128 rows x 64 right-hand sides x a range of chunks, two CTAs per SM): two
+// operand stages; chunk c's entries are built while chunk c - 1's MMAs run.  A stage is reused
+// only after the commit of its previous MMAs was waited for (by one thread, with a suspending
+// try_wait; the block barrier releases the others).  (Deeper pipelines -- four 16-wide or 32-wide
+// stages with the B operand requested two chunks ahead -- measured slower on GB300: 3.0-3.3 ms
+// against 2.0 ms per 64-column 32^3 product.)
+template <int DIM, bool TOEP>
+__global__ void __launch_bounds__(256, 2)
 k1t_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsplit, int nrhs, long long N,
-              int chunks_per_split, int nchunks, double *__restrict__ partial, int *__restrict__ err) {
-    extern __shared__ __align__(128) uint32_t opnd[];  // 2 stages of [A hi | A lo | B hi | B lo]
+              int chunks_per_split, int nchunks, double *__restrict__ partial, int *__restrict__ err,
+              const uint2 *__restrict__ ttab, int n, int Lr) {
+    extern __shared__ __align__(128) uint32_t opnd[];  // kStages x [A hi | A lo | B hi | B lo]
+    constexpr int kPer = kTM + kTK - 1;               // distinct entries per line and chunk (Lr = 128)
     __shared__ float4 rc[kTM];
-    __shared__ __align__(8) uint64_t mbar_mma[2];
-    __shared__ __align__(8) uint64_t mbar_ld[2];
+    __shared__ uint2 tval[2][kTM / 32 * kPer];        // TOEP: this chunk's and the next one's entries
+    __shared__ int4 rline[kTM / 32];                  // TOEP: slow, mid, first fast coordinate of line q
+    __shared__ __align__(8) uint64_t mbar_mma[kStages];
+    __shared__ __align__(8) uint64_t mbar_ld[kStages];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
 
@@ -145,7 +161,7 @@ k1t_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsp
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int st = 0; st < 2; ++st) {
+        for (int st = 0; st < kStages; ++st) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar_mma[st])), "r"(1u));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar_ld[st])), "r"(1u));
         }
@@ -155,6 +171,11 @@ k1t_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsp
     if (tid < kTM) {
         const long long i = row0 + tid;
         rc[tid] = i < N ? coord[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const int nl = kTM / Lr;  // TOEP: target lines per tile
+    if (TOEP && tid < nl) {
+        const float4 c = coord[row0 + (long long)tid * Lr];
+        rline[tid] = DIM == 2 ? make_int4((int)c.x, 0, (int)c.y, 0) : make_int4((int)c.x, (int)c.y, (int)c.z, 0);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -169,10 +190,30 @@ k1t_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsp
 
     const int k0 = blockIdx.y * chunks_per_split;
     const int k1 = min(k0 + chunks_per_split, nchunks);
-    uint32_t ph_mma[2] = {0u, 0u}, ph_ld[2] = {0u, 0u};
-    int pending[2] = {0, 0};   // stage has MMAs in flight
+    // per stage: phase parities, and whether a commit (MMAs) or a copy (B) is outstanding; the
+    // flags are uniform over the block, only thread 0 waits
+    uint32_t ph_mma[kStages], ph_ld[kStages];
+    int pend_mma[kStages], pend_ld[kStages];
+#pragma unroll
+    for (int st = 0; st < kStages; ++st) { ph_mma[st] = 0u; ph_ld[st] = 0u; pend_mma[st] = 0; pend_ld[st] = 0; }
     int since_flush = 0;
 
+    auto wait_mma = [&](int st) {  // the stage's last MMAs have completed (bounded, thread 0)
+        if (pend_mma[st]) {
+            if (tid == 0 && !mbar_wait(smem_u32(&mbar_mma[st]), ph_mma[st])) abort_flag = 1;
+            ph_mma[st] ^= 1u;
+            pend_mma[st] = 0;
+        }
+    };
+    auto issue_b = [&](int c) {  // B operand of chunk c (pre-split x) into its stage, thread 0
+        const int st = (c - k0) % kStages;
+        if (tid == 0) {
+            const uint32_t *src = xsplit + ((long long)grp * nchunks + c) * (2LL * kTN * kTK);
+            bulk_g2s(smem_u32(opnd + st * kStage + 2 * kTM * kTK), src, (uint32_t)(2 * kTN * kTK * sizeof(uint32_t)),
+                     smem_u32(&mbar_ld[st]));
+        }
+        pend_ld[st] = 1;
+    };
     auto flush = [&](void) {
         // all MMAs issued so far have completed (caller waited); read and add to (hi, lo)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -191,89 +232,115 @@ k1t_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsp
         for (int c = 0; c < 32; ++c) two_sum_acc(__uint_as_float(v[c]), ahi[c], alo[c]);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     };
+    // TOEP: thread tid holds entry tid of chunk c's nl x (Lr + 31) distinct entries (at most 252, so
+    // one per thread).  The chunk's line follows from its first index; the value is fetched two
+    // chunks ahead into a register and stored to tval one chunk ahead, so no chunk waits for it.
+    const int per = Lr + kTK - 1;
+    const bool tv_own = TOEP && tid < nl * per;
+    auto fetch_tval = [&](int c) -> uint2 {
+        if (!tv_own || c >= k1) return make_uint2(0u, 0u);
+        const long long j0c = (long long)c * kTK;
+        const int fj = (int)(j0c % n);
+        const long long tj = j0c / n;
+        const int mj = DIM == 2 ? 0 : (int)(tj % n), sj = DIM == 2 ? (int)tj : (int)(tj / n);
+        const int qq = tid / per, t = tid - qq * per;
+        const int4 L = rline[qq];
+        const int df = abs(L.z - fj - (kTK - 1) + t), dm = abs(L.y - mj), ds = abs(L.x - sj);
+        return ttab[DIM == 2 ? (long long)ds * n + df : ((long long)ds * n + dm) * n + df];
+    };
 
+    // prologue: the first chunk's entries stored, the second chunk's in a register
+    uint2 tv_next = make_uint2(0u, 0u);
+    if (TOEP) {
+        const uint2 first = fetch_tval(k0);
+        if (tv_own) tval[0][tid] = first;
+        tv_next = fetch_tval(k0 + 1);
+    }
+    // element e = tid + 256 it of a part in core-matrix order (RG = kTK / 4 core-matrix columns per
+    // row group) is row (64 / RG) it + 8 (warp / RG) + lane / 4 of source column 4 (warp % RG) + lane % 4
+    constexpr int RG = kTK / 4, kRowStep = 64 / RG, kIters = kTM * kTK / 256;
+    const int kk = 4 * (warp % RG) + (lane & 3);
+    const int rbase = 8 * (warp / RG) + (lane >> 2);
     for (int ch = k0; ch < k1; ++ch) {  // abort_flag is acted on only after a barrier (uniform exit)
-        const int st = (ch - k0) & 1;
+        const int ci = ch - k0, st = ci % kStages;
         uint32_t *Ahi = opnd + st * kStage, *Alo = Ahi + kTM * kTK, *Bv = Ahi + 2 * kTM * kTK;
-        // the stage's previous MMAs must be done before its operands are overwritten
-        if (pending[st]) {
-            const bool ok = mbar_wait(smem_u32(&mbar_mma[st]), ph_mma[st]);
-            if (!ok) abort_flag = 1;
-            ph_mma[st] ^= 1u;
-            pending[st] = 0;
-        }
+        wait_mma(st);  // the stage's previous MMAs (chunk ch - 2) are done before its operands change
         __syncthreads();
         if (abort_flag) break;
         if (since_flush == kFlush) {
-            // the other stage's MMAs (the newest) must also be done before reading TMEM
-            if (pending[st ^ 1]) {
-                const bool ok = mbar_wait(smem_u32(&mbar_mma[st ^ 1]), ph_mma[st ^ 1]);
-                if (!ok) abort_flag = 1;
-                ph_mma[st ^ 1] ^= 1u;
-                pending[st ^ 1] = 0;
-            }
+            for (int s2 = 0; s2 < kStages; ++s2) wait_mma(s2);
             __syncthreads();
             if (abort_flag) break;
             flush();
             __syncthreads();
             since_flush = 0;
         }
-        // B operand (pre-split x) by a bulk asynchronous copy
-        if (tid == 0) {
-            const uint32_t *src = xsplit + ((long long)grp * nchunks + ch) * (2LL * kTN * kTK);
-            bulk_g2s(smem_u32(Bv), src, (uint32_t)(2 * kTN * kTK * sizeof(uint32_t)), smem_u32(&mbar_ld[st]));
-        }
-        // A operand: entries of 128 rows x 32 sources; one warp writes one 8 x 4 core matrix
+        issue_b(ch);
+        // A operand of chunk ch
         const long long j0 = (long long)ch * kTK;
-        for (int e = tid; e < kTM * kTK; e += 256) {
-            const int cm = e >> 5, l = e & 31;
-            const int r = (cm / (kTK / 4)) * 8 + (l >> 2);
-            const int k = (cm % (kTK / 4)) * 4 + (l & 3);
-            const long long j = j0 + k;
-            const float4 a = rc[r];
-            const float4 b = j < N ? coord[j] : make_float4(1e6f, 1e6f, 1e6f, 0.f);
-            const float dx = a.x - b.x, dy = a.y - b.y;
-            float v;
-            if (DIM == 2) {
-                v = __log2f(fmaf(dx, dx, fmaf(dy, dy, 0x1p-30f)));
-            } else {
-                const float dz = a.z - b.z;
-                v = rsqrtf(fmaxf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), 1.0f));
+        if (TOEP) {
+            const int buf = ci & 1;
+            const int lgL = __ffs(Lr) - 1, tb = kTK - 1 - kk;
+            if (tv_own) tval[buf ^ 1][tid] = tv_next;  // chunk ch + 1, read after the next barriers
+            tv_next = fetch_tval(ch + 2);
+#pragma unroll
+            for (int it = 0; it < kIters; ++it) {
+                const int r = kRowStep * it + rbase;
+                const uint2 w = tval[buf][(r >> lgL) * per + (r & (Lr - 1)) + tb];
+                Ahi[tid + 256 * it] = w.x;
+                Alo[tid + 256 * it] = w.y;
             }
-            const uint32_t hi = to_tf32(v);
-            Ahi[e] = hi;
-            Alo[e] = to_tf32(v - __uint_as_float(hi));
+        } else {
+            const long long j = j0 + kk;
+            const float4 b = j < N ? coord[j] : make_float4(1e6f, 1e6f, 1e6f, 0.f);
+#pragma unroll 4
+            for (int it = 0; it < kIters; ++it) {
+                const float4 a = rc[kRowStep * it + rbase];
+                const float dx = a.x - b.x, dy = a.y - b.y;
+                float v;
+                if (DIM == 2) {
+                    v = __log2f(fmaf(dx, dx, fmaf(dy, dy, 0x1p-30f)));
+                } else {
+                    const float dz = a.z - b.z;
+                    v = rsqrtf(fmaxf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), 1.0f));
+                }
+                const uint32_t hi = to_tf32(v);
+                Ahi[tid + 256 * it] = hi;
+                Alo[tid + 256 * it] = to_tf32(v - __uint_as_float(hi));
+            }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
+        if (abort_flag) break;
         if (tid == 0) {
             const bool ok = mbar_wait(smem_u32(&mbar_ld[st]), ph_ld[st]);
-            ph_ld[st] ^= 1u;
             if (!ok) {
                 abort_flag = 1;
             } else {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo);
+                const uint32_t ahi_ = smem_u32(Ahi), alo_ = smem_u32(Alo);
                 const uint32_t bhi = smem_u32(Bv), blo = bhi + kTN * kTK * 4;
 #pragma unroll
                 for (int s = 0; s < kTK / 8; ++s) {
                     const uint32_t koff = (uint32_t)s * 2 * kLBO;
-                    mma_tf32(tmem, make_desc(ahi + koff), make_desc(bhi + koff), (since_flush > 0 || s > 0) ? 1u : 0u);
-                    mma_tf32(tmem, make_desc(ahi + koff), make_desc(blo + koff), 1u);
-                    mma_tf32(tmem, make_desc(alo + koff), make_desc(bhi + koff), 1u);
+                    mma_tf32(tmem, make_desc(ahi_ + koff), make_desc(bhi + koff), (since_flush > 0 || s > 0) ? 1u : 0u);
+                    mma_tf32(tmem, make_desc(ahi_ + koff), make_desc(blo + koff), 1u);
+                    mma_tf32(tmem, make_desc(alo_ + koff), make_desc(bhi + koff), 1u);
                 }
                 mma_commit(smem_u32(&mbar_mma[st]));
             }
         }
-        pending[st] = 1;
+        ph_ld[st] ^= 1u;
+        pend_ld[st] = 0;
+        pend_mma[st] = 1;
         ++since_flush;
     }
-    // drain both stages (bounded), then the final flush
-    for (int st = 0; st < 2; ++st) {
-        if (pending[st]) {
-            const bool ok = mbar_wait(smem_u32(&mbar_mma[st]), ph_mma[st]);
-            if (!ok) abort_flag = 1;
-            pending[st] = 0;
+    // drain (bounded): outstanding MMAs and any B copies still in flight after an early exit
+    for (int st = 0; st < kStages; ++st) {
+        wait_mma(st);
+        if (pend_ld[st]) {
+            if (tid == 0 && !mbar_wait(smem_u32(&mbar_ld[st]), ph_ld[st])) abort_flag = 1;
+            pend_ld[st] = 0;
         }
     }
     __syncthreads();
@@ -312,11 +379,47 @@ int launch_matvec_tc(const ie_problem *p, const double *x, long long ldx, int nr
     xsplit_kernel<<<(unsigned)((words / 2 + 255) / 256), 256, 0, s>>>(x, ldx, nrhs, p->N, nchunks, xs.as<uint32_t>());
     IE_LAUNCHED();
     const dim3 g(rt, S, groups);
-    const size_t dsm = sizeof(uint32_t) * 2 * kStage;
-    if (p->dim == 2)
-        k1t_matvec_tc<2><<<g, 256, dsm, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial, d_err);
+    const size_t dsm = sizeof(uint32_t) * kStages * kStage;
+    const bool toep = tc_toeplitz(p);
+    const int Lr = std::min(p->n, kTM);
+    if (toep && p->dim == 2)
+        k1t_matvec_tc<2, true><<<g, 256, dsm, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial, d_err,
+                                                   p->d_table_tc, p->n, Lr);
+    else if (toep)
+        k1t_matvec_tc<3, true><<<g, 256, dsm, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial, d_err,
+                                                   p->d_table_tc, p->n, Lr);
+    else if (p->dim == 2)
+        k1t_matvec_tc<2, false><<<g, 256, dsm, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial, d_err,
+                                                    nullptr, p->n, Lr);
     else
-        k1t_matvec_tc<3><<<g, 256, dsm, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial, d_err);
+        k1t_matvec_tc<3, false><<<g, 256, dsm, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial, d_err,
+                                                    nullptr, p->n, Lr);
+    IE_LAUNCHED();
+    return IE_OK;
+}
+
+// The Toeplitz-fed variant applies when n is a multiple of 32 and 128 rows are whole lines (n = 32,
+// 64) or part of one (n a multiple of 128), and the table is built.
+bool tc_toeplitz(const ie_problem *p) {
+    return p->d_table_tc && p->n % 32 == 0 && (p->n >= kTM ? p->n % kTM == 0 : kTM % p->n == 0);
+}
+
+// Per |offset| q: the exact entry (FP64 table; 0 at q = 0, the diagonal being added in FP64) split
+// into TF32 high and low words.
+__global__ void tc_table_kernel(const double *__restrict__ t64, long long T, uint2 *__restrict__ out) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= T) return;
+    const float v = q == 0 ? 0.f : (float)t64[q];
+    const float r = q == 0 ? 0.f : (float)(t64[q] - (double)v);
+    const uint32_t hi = to_tf32(v);
+    // low word: the rest of the FP64 value below the TF32 high part
+    out[q] = make_uint2(hi, to_tf32((v - __uint_as_float(hi)) + r));
+}
+
+int build_tc_table(ie_problem *p) {
+    const long long T = p->N;
+    IE_TRY_CUDA(cudaMalloc(&p->d_table_tc, sizeof(uint2) * T));
+    tc_table_kernel<<<(unsigned)((T + 255) / 256), 256>>>(p->d_table64, T, p->d_table_tc);
     IE_LAUNCHED();
     return IE_OK;
 }
@@ -326,8 +429,10 @@ int tc_rows() { return kTM; }
 int tc_cols() { return kTN; }
 
 int prepare_tc() {
-    const int dsm = (int)(sizeof(uint32_t) * 2 * kStage);
-    IE_TRY_CUDA(cudaFuncSetAttribute(k1t_matvec_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
-    IE_TRY_CUDA(cudaFuncSetAttribute(k1t_matvec_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
+    const int dsm = (int)(sizeof(uint32_t) * kStages * kStage);
+    IE_TRY_CUDA(cudaFuncSetAttribute(k1t_matvec_tc<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
+    IE_TRY_CUDA(cudaFuncSetAttribute(k1t_matvec_tc<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
+    IE_TRY_CUDA(cudaFuncSetAttribute(k1t_matvec_tc<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
+    IE_TRY_CUDA(cudaFuncSetAttribute(k1t_matvec_tc<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
     return IE_OK;
 }

@@ -77,16 +77,20 @@ def test_matvec_multi_rhs_and_shift(dim, n, nrhs):
         assert np.max(np.abs(host(Y) - ref)) <= tol * scale, prec
 
 
-@pytest.mark.parametrize("dim,n,nrhs", [(3, 16, 64), (3, 12, 70), (2, 40, 20), (3, 10, 1)])
-def test_tensor_core_matvec(dim, n, nrhs):
-    # tcgen05 3xTF32 contraction of SFU entries: FP32-class accuracy, like IE_MIXED
+@pytest.mark.parametrize("dim,n,nrhs,conv", [(3, 16, 64, O.GRID_TEXT), (3, 12, 70, O.GRID_TEXT),
+                                             (2, 40, 20, O.GRID_TEXT), (3, 10, 1, O.GRID_TEXT),
+                                             # tiles fed from the exact per-offset table (n = 32, 64, 128k)
+                                             (3, 32, 64, O.GRID_TEXT), (3, 32, 3, O.GRID_TABLE),
+                                             (2, 64, 16, O.GRID_TEXT), (2, 128, 9, O.GRID_TEXT)])
+def test_tensor_core_matvec(dim, n, nrhs, conv):
+    # tcgen05 3xTF32 contraction: FP32-class accuracy, like IE_MIXED
     N = n ** dim
     X = I.uniform_rhs_batch(N, list(range(nrhs))).T.copy()
-    prob = iedd.ie_discretize(dim, n)
+    prob = iedd.ie_discretize(dim, n, grid=conv)
     Y = torch.zeros((nrhs, N), dtype=torch.float64, device="cuda")
     iedd.ie_matvec(prob, dev(X), Y, iedd.IE_TENSOR)
-    ref = O.matvec_direct(dim, n, X.T).T
-    assert np.max(np.abs(host(Y) - ref)) <= 4e-6 * _scale(dim, n, X, O.GRID_TEXT)
+    ref = O.matvec_direct(dim, n, X.T, convention=conv).T
+    assert np.max(np.abs(host(Y) - ref)) <= 4e-6 * _scale(dim, n, X, conv)
 
 
 def test_matvec_strided_batch():
