@@ -54,6 +54,10 @@ FP32_LANES_PER_SM = 128
 # source it was measured on (k2_source_hash: the 2D exact kernel's source text); otherwise the
 # bench reports null.
 NCU_TRAFFIC = {"24904137a1834c92": 4624128}  # k2_accurate_2d<true,1>, n = 512, bytes per launch
+# the same for the exact tensor-core matvec, keyed by tc_exact_source_hash()
+NCU_TRAFFIC_KZ = {"c727ca201a22a3b7": 8757248}  # kz_matvec_tc, n = 512, bytes per launch
+# BF16 digit products per pair of the exact tensor-core matvec (six digits per factor, levels 0..5)
+KZ_PRODUCTS_PER_PAIR = 21
 
 
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates per GPU
@@ -76,6 +80,12 @@ def k2_source_hash() -> str:
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
+def tc_exact_source_hash() -> str:
+    """sha256 (16 hex digits) of the exact tensor-core matvec's source file."""
+    src = open(os.path.join(ROOT, "paper_2108_12574_gb300", "csrc", "tc_exact.cu")).read()
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -84,7 +94,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=WORKLOAD)
     ap.add_argument("--no-extras", action="store_true", help="skip FP64-plain and CPU-baseline legs")
-    ap.add_argument("--kernel", choices=["k1", "k2", "kd", "tc", "stored", "fft", "apply", "factor"], default=None,
+    ap.add_argument("--kernel", choices=["k1", "k2", "kd", "tc", "kz", "stored", "fft", "apply", "factor"], default=None,
                     help="profiling case: run one hot operation twice on a --dim/--n/--nrhs problem and exit")
     ap.add_argument("--dim", type=int, default=DIM)
     ap.add_argument("--n", type=int, default=NGRID)
@@ -107,9 +117,9 @@ def kernel_case(args):
     Y = torch.zeros_like(X)
     m = args.n // 16 if args.dim == 2 else args.n // 8
     for _ in range(2):
-        if args.kernel in ("k1", "k2", "kd", "tc", "stored", "fft"):
+        if args.kernel in ("k1", "k2", "kd", "tc", "kz", "stored", "fft"):
             prec = {"k1": iedd.IE_MIXED, "k2": iedd.IE_ACCURATE, "kd": iedd.IE_FP64, "tc": iedd.IE_TENSOR,
-                    "stored": iedd.IE_STORED, "fft": iedd.IE_FFT}[args.kernel]
+                    "kz": iedd.IE_TENSOR_EXACT, "stored": iedd.IE_STORED, "fft": iedd.IE_FFT}[args.kernel]
             if args.kernel == "stored":
                 iedd.ie_store_matrix(prob)
             iedd.ie_matvec(prob, X, Y, prec)
@@ -126,9 +136,10 @@ def kernel_case(args):
 def config_dict():
     return {"workload": WORKLOAD, "dim": DIM, "n": NGRID, "N": NGRID ** DIM, "m": MPART, "delta": DELTA,
             "rhs": f"GRF l={ELL} seed=rank", "tol": TOL, "decomposition": "schwarz",
-            "precision": "mixed (double-float table matvec on FP32 pipes, FP32 explicit subdomain inverses "
-                         "with double-float products, FP64 scalars and vectors; the FP64 true residual "
-                         "and replacements by the FP64 FFT matvec)",
+            "precision": "mixed (exact direct-sum matvec on the tcgen05 tensor cores: FP64 entries and x cut "
+                         "into six BF16 digits, 21 digit products summed exactly; FP32 explicit subdomain "
+                         "inverses with double-float products; FP64 scalars and vectors; the FP64 true "
+                         "residual and replacements by the FP64 FFT matvec)",
             "l2": "flushed between timed steps (512 MiB write)"}
 
 
@@ -358,7 +369,25 @@ def main():
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     f_mhz = clocks.get("sm_mhz") or 2070.0
     src_hash = k2_source_hash()
-    if prec == iedd.IE_MIXED and dim_w == 2:
+    kz_inner = prec == iedd.IE_MIXED and dim_w == 2 and W["n"] % 128 == 0 and W["n"] <= 4096
+    if kz_inner:
+        # 2D: the exact tensor-core matvec (Ozaki scheme), 21 BF16 digit products (2 flops each) per
+        # pair, against the measured sustained bf16 dense peak (the kernel runs inside a long step)
+        bf16 = measured_peak("bf16_tflops_sustained", 1700.0)
+        peak = bf16 * 1e12
+        achieved = pairs * nr * 2.0 * KZ_PRODUCTS_PER_PAIR / mv_launch_s
+        fp32_pair_peak = sms * FP32_LANES_PER_SM / FP32_OPS_PER_PAIR_K2 * f_mhz * 1e6
+        roofline = {"bound": "tensor", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                    "frac": achieved / peak,
+                    "traffic": NCU_TRAFFIC_KZ.get(tc_exact_source_hash()) if args.workload == WORKLOAD else None,
+                    "kernel": "kz_matvec_tc",
+                    "pairs_per_s": pairs * nr / mv_launch_s,
+                    "pairs_vs_fp32_pair_peak": pairs * nr / mv_launch_s / fp32_pair_peak,
+                    "peak_basis": (f"bf16 dense {bf16:.1f} TFLOP/s sustained (of measured); work = "
+                                   f"{KZ_PRODUCTS_PER_PAIR} BF16 digit products (2 flops each) per pair; "
+                                   f"pairs_vs_fp32_pair_peak against {fp32_pair_peak / 1e12:.2f} Tpairs/s, the "
+                                   "FP32-pipe peak of the double-float kernel")}
+    elif prec == iedd.IE_MIXED and dim_w == 2:
         per_clk = FP32_LANES_PER_SM / FP32_OPS_PER_PAIR_K2
         peak = sms * per_clk * f_mhz * 1e6
         achieved = pairs * nr / mv_launch_s
@@ -394,7 +423,9 @@ def main():
     cfg = config_dict() if args.workload == WORKLOAD else {"workload": args.workload, **W, "tol": TOL}
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 (double-float sums) + f64" if prec == iedd.IE_MIXED else "f64",
+            "vs_baseline": None,
+            "dtype": ("bf16 digit slices (Ozaki) + f32 windows + int64 sums + f64" if kz_inner else
+                      "f32 (double-float sums) + f64" if prec == iedd.IE_MIXED else "f64"),
             "data": "synthetic", "config": cfg, "iterations": last["iterations"],
             "iterations_max": max(its_all), "true_relres": max(r["true_relres"] for r in reps[-1]),
             "replacements": last["replacements"], "converged": ok,
@@ -477,7 +508,16 @@ def extras(torch, iedd, I, dev, stream, iterations):
     fp64_its = 44  # FP64 PCG iterations of this workload at 1e-8 (the FP64 path's own count)
     stored = stored_matvec_leg(torch, iedd, I, dev, stream)
     t_fft = t_mv(iedd.IE_FFT, 20)
+    t_kz = t_mv(iedd.IE_TENSOR_EXACT, 10)
+    bf16_peak = measured_peak("bf16_tflops", 1900.0)
     return {
+        "tensor_exact_matvec": {
+            "ms": t_kz * 1e3, "gpairs_s": pairs / t_kz / 1e9,
+            "tflops_bf16": 42.0 * pairs / t_kz / 1e12, "peak_bf16_tflops": bf16_peak,
+            "frac": 42.0 * pairs / t_kz / 1e12 / bf16_peak,
+            "basis": "21 BF16 digit products per pair (Ozaki scheme, 6 digits per factor) on tcgen05, "
+                     "2 flops each; peak = measured bf16 burst (of measured)"},
+        "k2_inner_solve": fft_solve_leg(torch, iedd, I, dev, stream, inner=iedd.IE_ACCURATE, variants=("mixed",)),
         "matvec_gpairs_s": {"k2_double_float_table": pairs / t_k2 / 1e9, "k1_fp32_sfu_compensated": pairs / t_k1 / 1e9,
                             "kd_fp64_regenerated": pairs / t_64 / 1e9},
         "fft_matvec": {"ms": t_fft * 1e3, "pairs_equivalent_gpairs_s": pairs / t_fft / 1e9,
@@ -492,20 +532,24 @@ def extras(torch, iedd, I, dev, stream, iterations):
     }
 
 
-def fft_solve_leg(torch, iedd, I, dev, stream, steps=3):
+def fft_solve_leg(torch, iedd, I, dev, stream, steps=3, inner=None, variants=("mixed", "fp64")):
     """The same workload and step (discretize + partition + factor + pcg_solve, L2 flushed, CUDA
-    events) with the paper's FFT matvec as the inner product and for the true residual: FP32
-    explicit inverses (IE_MIXED factors) and FP64 factors."""
+    events) with another inner matvec (default: the paper's FFT matvec, which also gives the true
+    residual): FP32 explicit inverses (IE_MIXED factors) and FP64 factors."""
+    inner = iedd.IE_FFT if inner is None else inner
     f = torch.from_numpy(I.grf(DIM, NGRID, ELL, 0)).to(dev)
     u = torch.zeros_like(f)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     out = {}
     for name, fprec, prec in (("mixed", iedd.IE_MIXED, iedd.IE_MIXED), ("fp64", iedd.IE_FP64, iedd.IE_FP64)):
+        if name not in variants:
+            continue
+
         def step():
             prob = iedd.ie_discretize(DIM, NGRID, device=dev.index)
             part = iedd.dd_partition(prob, MPART, DELTA, iedd.DD_SCHWARZ)
             fac = iedd.dd_factor(prob, part, fprec, stream=stream)
-            rep = iedd.pcg_solve(prob, fac, f, u, tol=TOL, precision=prec, inner=iedd.IE_FFT, stream=stream)[0]
+            rep = iedd.pcg_solve(prob, fac, f, u, tol=TOL, precision=prec, inner=inner, stream=stream)[0]
             fac.close(); part.close(); prob.close()
             return rep
         u.zero_()

@@ -129,6 +129,15 @@ IEDD_API int ie_matvec(const ie_problem *p, const double *x, double *y, int nrhs
                          spectrum (8 L^d bytes, kept until ie_destroy) and synchronizes; it must
                          not be inside a stream capture and must not run concurrently with another
                          call on the same problem.  Scratch: 16 L^d bytes per pair of columns. */
+#define IE_TENSOR_EXACT 10 /* the 2D direct sum on the tcgen05 tensor cores with an FP64-class
+                         result (Ozaki scheme): the per-offset FP64 entries and x are cut into six
+                         fixed-point BF16 digits each; the 21 leading digit products are summed
+                         exactly (FP32 windows of 128 terms, then 64-bit integers).  Relative
+                         error ~1e-16 of sum |A_ij x_j|.  2D with n a multiple of 128, n <= 4096
+                         (IE_ERR_ARG otherwise).  The first call on a problem builds the digit
+                         table (12 N bytes, kept until ie_destroy) and synchronizes; it must not
+                         be inside a stream capture.  Returns IE_ERR_TIMEOUT if a CTA gave up
+                         waiting for its MMAs (bounded waits). */
 
 /*
  * ie_store_matrix -- stored-matrix fallback: materialise the off-diagonal part of A densely in
@@ -204,14 +213,16 @@ typedef struct {
     int verify;          /* IE_FP64: 1 = compute the true residual at the end (one more matvec)    */
     int inner;           /* matvec inside the iteration (q = A p):
                               0            the library's choice: IE_FP64 precision -> the FP64
-                                           regenerated matvec; IE_MIXED -> IE_ACCURATE in 2D,
-                                           IE_TENSOR for 3D batches of >= 16 columns,
-                                           IE_MIXED for fewer
+                                           regenerated matvec; IE_MIXED -> IE_TENSOR_EXACT in
+                                           2D where supported (n a multiple of 128, n <= 4096),
+                                           else IE_ACCURATE; IE_TENSOR for 3D batches of >= 16
+                                           columns, IE_MIXED for fewer
                               IE_MIXED     FP32 SFU entries with compensated FP32 sums
                               IE_ACCURATE  double-float table sums on the FP32 pipes
                               4            as IE_ACCURATE with the search directions rounded to
                                            FP32 (one FFMA less per pair, more iterations)
                               IE_TENSOR    the tcgen05 batched kernel (many right-hand sides)
+                              IE_TENSOR_EXACT  the exact 2D tensor-core sum (see ie_matvec)
                               IE_FFT       the FP64 FFT matvec (Sec. 6), also used for the
                                            accurate residual; the first use builds its plan
                               16           the FP64 regenerated matvec in either precision */

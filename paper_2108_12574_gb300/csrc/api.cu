@@ -183,6 +183,8 @@ extern "C" void ie_destroy(ie_problem *p) {
     cudaFree(p->d_table_tc);
     cudaFree(p->d_fft_tw);
     cudaFree(p->d_fft_chat);
+    cudaFree(p->d_zt_dig);
+    cudaFree(p->d_zt_max);
     delete p;
 }
 
@@ -234,8 +236,12 @@ extern "C" int ie_matvec(const ie_problem *p, const double *x, double *y, int nr
                          int precision, void *stream) {
     IE_TRY(check_vec_args("ie_matvec", p, x, y, nrhs, ld));
     if (precision != IE_FP64 && precision != IE_MIXED && precision != IE_ACCURATE && precision != IE_STORED &&
-        precision != IE_TENSOR && precision != IE_FFT) {
+        precision != IE_TENSOR && precision != IE_FFT && precision != IE_TENSOR_EXACT) {
         ie_set_error("ie_matvec: unknown precision"); return IE_ERR_ARG;
+    }
+    if (precision == IE_TENSOR_EXACT && !tc_exact_supported(p)) {
+        ie_set_error("ie_matvec: IE_TENSOR_EXACT needs a 2D grid with n a multiple of 128 and n <= 4096");
+        return IE_ERR_ARG;
     }
     if (precision == IE_STORED && !p->d_stored) {
         ie_set_error("ie_matvec: IE_STORED needs ie_store_matrix first"); return IE_ERR_ARG;
@@ -251,6 +257,18 @@ extern "C" int ie_matvec(const ie_problem *p, const double *x, double *y, int nr
         }
         IE_TRY(prepare_fft(p));
     }
+    if (precision == IE_TENSOR_EXACT && !p->d_zt_dig) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        IE_TRY_CUDA(cudaStreamIsCapturing(s, &cs));
+        if (cs != cudaStreamCaptureStatusNone) {
+            ie_set_error("ie_matvec: the first IE_TENSOR_EXACT call on a problem builds its digit table and must not "
+                         "be captured");
+            return IE_ERR_ARG;
+        }
+        IE_TRY(prepare_tc_exact(p));
+    }
+    if (precision == IE_TENSOR || precision == IE_TENSOR_EXACT)
+        IE_TRY_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int), s));
     Staged sx, sy;
     IE_TRY(stage_in(x, p->N, nrhs, ld, true, s, sx));
     IE_TRY(stage_in(y, p->N, nrhs, ld, false, s, sy));
@@ -259,8 +277,8 @@ extern "C" int ie_matvec(const ie_problem *p, const double *x, double *y, int nr
     else
         IE_TRY(launch_matvec(p, sx.dev, sx.ld, const_cast<double *>(sy.dev), sy.ld, nrhs, precision, s));
     IE_TRY(stage_out(y, sy, p->N, nrhs, ld, s));
-    if (precision == IE_TENSOR) {
-        // the tensor-core kernel reports a CTA that gave up waiting for its MMAs
+    if (precision == IE_TENSOR || precision == IE_TENSOR_EXACT) {
+        // the tensor-core kernels report a CTA that gave up waiting for its MMAs
         int err = 0;
         IE_TRY_CUDA(cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
         IE_TRY_CUDA(cudaStreamSynchronize(s));

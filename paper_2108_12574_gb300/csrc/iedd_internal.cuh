@@ -81,6 +81,10 @@ struct ie_problem {
     double2 *d_fft_tw = nullptr;
     double *d_fft_chat = nullptr;
     int fft_cfg = 4;               // autotuned launch shape of the FFT passes (see fft.cu)
+    // exact tensor-core matvec (built on first use): six BF16 digit planes of the per-offset table
+    // and the bits of max |t| (its power-of-two scale)
+    uint16_t *d_zt_dig = nullptr;
+    unsigned long long *d_zt_max = nullptr;
 };
 
 struct dd_partition_t {
@@ -192,6 +196,12 @@ int prepare_fft(const ie_problem *p);
 int fft_supported(const ie_problem *p, std::string *why);
 int launch_matvec_fft(const ie_problem *p, const double *x, long long ldx, double *y, long long ldy, int nrhs,
                       cudaStream_t s);
+// Exact tensor-core 2D matvec (tc_exact.cu): prepare_tc_exact builds the digit table once per
+// problem (synchronizes; not inside a stream capture).
+bool tc_exact_supported(const ie_problem *p);
+int prepare_tc_exact(const ie_problem *p);
+int launch_matvec_tc_exact(const ie_problem *p, const double *x, long long ldx, double *y, long long ldy, int nrhs,
+                           cudaStream_t s);
 
 int launch_factor(dd_factor_t *f, cudaStream_t s);
 // apply.cu: time the candidate apply configurations of an explicit-inverse factor (outside any

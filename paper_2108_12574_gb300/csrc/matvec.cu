@@ -656,6 +656,11 @@ int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, doubl
         if (dot_out) IE_TRY(launch_dots(x, ldx, y, ldy, N, nrhs, dot_out, s));
         return IE_OK;
     }
+    if (precision == IE_TENSOR_EXACT) {
+        IE_TRY(launch_matvec_tc_exact(p, x, ldx, y, ldy, nrhs, s));
+        if (dot_out) IE_TRY(launch_dots(x, ldx, y, ldy, N, nrhs, dot_out, s));
+        return IE_OK;
+    }
     const int ntiles = (int)((N + kThreads - 1) / kThreads);
     DevBuf xsum;
     if (p->dim == 2 && (precision == IE_MIXED || precision == IE_FP64 || (precision == IE_TENSOR && !tc_toeplitz(p)))) {

@@ -261,10 +261,10 @@ struct Solver {
     int mv_precision() const {
         if (o.inner == IE_FP64 + 16) return IE_FP64;
         if (o.inner == IE_MIXED || o.inner == IE_ACCURATE || o.inner == IE_ACCURATE_X32 || o.inner == IE_TENSOR ||
-            o.inner == IE_ACCURATE_R4 || o.inner == IE_ACCURATE_R16 || o.inner == IE_FFT)
+            o.inner == IE_ACCURATE_R4 || o.inner == IE_ACCURATE_R16 || o.inner == IE_FFT || o.inner == IE_TENSOR_EXACT)
             return o.inner;
         if (o.precision == IE_FP64) return IE_FP64;
-        if (p->dim == 2) return IE_ACCURATE;
+        if (p->dim == 2) return tc_exact_supported(p) ? IE_TENSOR_EXACT : IE_ACCURATE;
         return nrhs >= 16 ? IE_TENSOR : IE_MIXED;  // 3D batches: the tcgen05 kernel
     }
     bool exact_inner() const { return mv_precision() != IE_MIXED && mv_precision() != IE_TENSOR; }
@@ -367,7 +367,7 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
         o.replace_every < 0 || o.check_every < 0 || o.use_x0 < 0 || o.use_x0 > 2 ||
         (o.inner != 0 && o.inner != IE_MIXED && o.inner != IE_ACCURATE && o.inner != IE_ACCURATE_X32 &&
          o.inner != IE_TENSOR && o.inner != IE_ACCURATE_R4 && o.inner != IE_ACCURATE_R16 &&
-         o.inner != IE_FP64 + 16 && o.inner != IE_FFT) ||
+         o.inner != IE_FP64 + 16 && o.inner != IE_FFT && o.inner != IE_TENSOR_EXACT) ||
         (o.residual != 0 && o.residual != IE_ACCURATE && o.residual != IE_FP64 && o.residual != IE_FFT)) {
         ie_set_error("pcg_solve: invalid options"); return IE_ERR_ARG;
     }
@@ -378,7 +378,15 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
     IE_TRY(ps.init(static_cast<cudaStream_t>(stream)));
     Solver S{p, fac, nrhs, p->N, o, ps.s};
     if (S.mv_precision() == IE_FFT || S.acc_precision() == IE_FFT) IE_TRY(prepare_fft(p));  // before any capture
-    if (S.mv_precision() == IE_TENSOR) IE_TRY_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
+    if (S.mv_precision() == IE_TENSOR_EXACT) {
+        if (!tc_exact_supported(p)) {
+            ie_set_error("pcg_solve: IE_TENSOR_EXACT needs a 2D grid with n a multiple of 128 and n <= 4096");
+            return IE_ERR_ARG;
+        }
+        IE_TRY(prepare_tc_exact(p));  // before any capture
+    }
+    if (S.mv_precision() == IE_TENSOR || S.mv_precision() == IE_TENSOR_EXACT)
+        IE_TRY_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
     IE_TRY(S.alloc());
     IE_TRY(S.make_events(std::max(o.check_every, 1)));
     const long long N = p->N;
@@ -526,7 +534,7 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
                                   u_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     IE_TRY_CUDA(cudaMemcpyAsync(x0_used.data(), used.ptr, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
     int tc_err = 0;
-    if (S.mv_precision() == IE_TENSOR)  // a tensor-core CTA that gave up waiting for its MMAs
+    if (S.mv_precision() == IE_TENSOR || S.mv_precision() == IE_TENSOR_EXACT)  // a CTA gave up waiting for its MMAs
         IE_TRY_CUDA(cudaMemcpyAsync(&tc_err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     IE_TRY_CUDA(cudaStreamSynchronize(s));
     int ret = IE_OK;

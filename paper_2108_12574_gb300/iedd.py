@@ -16,7 +16,7 @@ import numpy as np
 
 IE_OK, IE_ERR_ARG, IE_ERR_CUDA, IE_ERR_OOM, IE_ERR_NOT_SPD = 0, -1, -2, -3, -4
 IE_ERR_BREAKDOWN, IE_ERR_MAXIT, IE_ERR_STAGNATION, IE_ERR_TIMEOUT = -5, -6, -7, -8
-IE_FP64, IE_MIXED, IE_ACCURATE, IE_STORED, IE_TENSOR, IE_FFT = 0, 1, 3, 5, 6, 9
+IE_FP64, IE_MIXED, IE_ACCURATE, IE_STORED, IE_TENSOR, IE_FFT, IE_TENSOR_EXACT = 0, 1, 3, 5, 6, 9, 10
 DD_JACOBI, DD_SCHWARZ, DD_CBD = 0, 1, 2
 IE_GRID_TEXT, IE_GRID_TABLE = 0, 1
 
