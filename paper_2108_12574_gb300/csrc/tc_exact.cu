@@ -30,14 +30,17 @@
 //   * builds the A operand: the six digit planes of the 240 distinct rows of the Toeplitz strip
 //     (rows r hold t(|d1|, |r - k|), k < 16); the 128-row tile of K-step s is the strip seen from
 //     row 112 - 16 s, so one strip serves all 8 K-steps through shifted shared-memory descriptors;
-//   * copies the B operand (the six digit planes of the 32 source rows i1 - d1 over the 128
-//     columns, pre-split once per matvec) with bulk asynchronous copies;
+//   * loads the B operand (the six digit planes of the 32 source rows i1 - d1 over the 128
+//     columns, pre-split once per matvec) with one TMA tensor copy (4D map: 8 values x rows x
+//     planes x column groups, which lands directly in the canonical K-major layout);
 //   * issues, per K-step, one MMA per A digit a with the B digit planes 0..5-a side by side
 //     (N = 32 (6 - a)) into TMEM columns from level a on: digit pair (a, b) lands in level a + b.
 // Strip and B operand are double-buffered, and so are the TMEM accumulators (2 x 192 columns):
 // window w + 1's operands are built and window w - 1's accumulators read while window w's MMAs run.
 // Waits are bounded: a CTA that waits too long records an error code, drains, frees its TMEM and
 // returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -163,8 +166,8 @@ __global__ void table_digits_kernel(const double *__restrict__ t64, int n, const
     for (int a = 0; a < kZD; ++a) out[(long long)a * T + e] = bf16_bits(d[a]);
 }
 
-// x digits in the B-operand source layout: [plane][8-column group][row + 32][8 values], rows -32..n+31
-// (rows outside the grid are zero).  One thread per (row, group): six 16-byte chunks.
+// x digits in the B-operand source layout: [8-column group][plane][row + 32][8 values], rows
+// -32..n+31 (rows outside the grid are zero).  One thread per (row, group): six 16-byte chunks.
 __global__ void x_digits_kernel(const double *__restrict__ x, int n, const unsigned long long *__restrict__ maxbits,
                                 uint4 *__restrict__ out) {
     const int groups = n >> 3, rows = n + 64;
@@ -183,7 +186,7 @@ __global__ void x_digits_kernel(const double *__restrict__ x, int n, const unsig
         for (int a = 0; a < kZD; ++a) w[a][k >> 1] = (uint32_t)bf16_bits(d0[a]) | ((uint32_t)bf16_bits(d1[a]) << 16);
     }
 #pragma unroll
-    for (int a = 0; a < kZD; ++a) out[((long long)a * groups + g) * rows + rr] = make_uint4(w[a][0], w[a][1], w[a][2], w[a][3]);
+    for (int a = 0; a < kZD; ++a) out[((long long)g * kZD + a) * rows + rr] = make_uint4(w[a][0], w[a][1], w[a][2], w[a][3]);
 }
 
 // One CTA: target points i2 in [128 bx, +128) of lines i1 in [32 by, +32), source columns
@@ -193,7 +196,7 @@ __global__ void x_digits_kernel(const double *__restrict__ x, int n, const unsig
 // Warp roles, handing over through mbarriers (no block-wide barrier inside the window loop):
 //   warp 0      one lane issues a window's 48 MMAs once its strip and B operand are in place and
 //               its accumulator set has been read, and commits them to mdone[stage];
-//   warp 1      bulk copies of the B operand into a free stage (expect_tx on bfull[stage]);
+//   warp 1      one lane: the TMA copy of the B operand into a free stage (expect_tx on bfull);
 //   warps 2-3   the strip: table digits fetched a window ahead into registers, staged as pair
 //               words, expanded into the 240-row strip (one lane per warp arrives on sfull);
 //   warps 4-7   read a finished window's accumulator set (their TMEM lane quarter, all 32 lines),
@@ -203,7 +206,7 @@ __global__ void x_digits_kernel(const double *__restrict__ x, int n, const unsig
 // waiter (each role's next use waits for the consumer of the previous one).  Every wait is
 // bounded: a role that gives up sets the shared abort flag, which ends the other roles' waits.
 __global__ void __launch_bounds__(256, 1)
-kz_matvec_tc(const uint16_t *__restrict__ tdig, const uint4 *__restrict__ xdig, int n, int dsplit, int F,
+kz_matvec_tc(const uint16_t *__restrict__ tdig, const __grid_constant__ CUtensorMap xmap, int n, int dsplit, int F,
              long long *__restrict__ part, int *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char zsm[];  // 2 x [strip | B]
     __shared__ __align__(16) uint32_t pw[kZD][kZSeg + 1];   // strip source: word j = (E_j, E_j+1)
@@ -298,27 +301,24 @@ kz_matvec_tc(const uint16_t *__restrict__ tdig, const uint4 *__restrict__ xdig, 
         __syncwarp();
     } else if (warp == 1) {
         // ---- B operand: six digit planes of the 32 source lines over the 128 columns ----
-        const int groups = n >> 3, rows = n + 64;
         int issued = 0;
         for (int w = 0; w < T; ++w) {
             const int sb = w & 1;
             const uint32_t par = (uint32_t)(w >> 1) & 1u;
             if (w >= 2 && !warp_wait(&mdone[sb], par ^ 1u)) break;  // the stage's last MMAs are done
-            const uint32_t bar = smem_u32(&bfull[sb]);
-            if (lane == 0)
+            if (lane == 0) {
+                const uint32_t bar = smem_u32(&bfull[sb]);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBBytes) : "memory");
-            __syncwarp();
-            const int r0 = i1_0 - (d_begin + w);  // first source line, in [-31, n - 1]
-            const uint32_t bdst = smem0 + sb * kStageBytes + kStripBytes;
-            for (int k = lane; k < (kZK / 8) * kZD; k += 32) {
-                const int G = k / kZD, b = k - G * kZD;
-                const uint4 *src = xdig + ((long long)b * groups + (kb >> 3) + G) * rows + (r0 + 32);
-                const uint32_t dst = bdst + G * kBGroup + b * (kZC * 16);
+                // box (8 values, 32 rows, 6 planes, 16 groups) at (0, first source row + 32, 0, kb / 8):
+                // the padded rows keep every coordinate inside the tensor, x = 0 is 16-byte aligned
+                const int r0 = i1_0 - (d_begin + w);  // first source line, in [-31, n - 1]
                 asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                    "l"(src), "r"((uint32_t)(kZC * 16)), "r"(bar)
+                    "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                    ::"r"(smem0 + sb * kStageBytes + kStripBytes), "l"(reinterpret_cast<uint64_t>(&xmap)), "r"(0),
+                    "r"(r0 + 32), "r"(0), "r"(kb >> 3), "r"(bar)
                     : "memory");
             }
+            __syncwarp();
             issued = w + 1;
         }
         // no copy may still be landing when the CTA ends (waits that ignore the abort flag, bounded)
@@ -498,6 +498,21 @@ int prepare_tc_exact(const ie_problem *p_) {
     return IE_OK;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no libcuda link)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
+}
+
 int launch_matvec_tc_exact(const ie_problem *p, const double *x, long long ldx, double *y, long long ldy, int nrhs,
                            cudaStream_t s) {
     if (!tc_exact_supported(p)) {
@@ -519,6 +534,25 @@ int launch_matvec_tc_exact(const ie_problem *p, const double *x, long long ldx, 
     IE_TRY(xd.alloc(sizeof(uint4) * (size_t)kZD * (n / 8) * (n + 64), s));
     IE_TRY(part.alloc(sizeof(long long) * (size_t)nparts * N, s));
     IE_TRY(mx.alloc(sizeof(unsigned long long), s));
+    // the x digits as a packed 4D tensor of 16-bit words: (8 values, n + 64 rows, 6 planes, n / 8
+    // groups); one box is a CTA's B operand for one d1
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) {
+        ie_set_error("ie_matvec: cuTensorMapEncodeTiled is not available from the driver");
+        return IE_ERR_CUDA;
+    }
+    CUtensorMap xmap;
+    const cuuint64_t gdim[4] = {8, (cuuint64_t)(n + 64), (cuuint64_t)kZD, (cuuint64_t)(n / 8)};
+    const cuuint64_t gstride[3] = {16, (cuuint64_t)(n + 64) * 16, (cuuint64_t)(n + 64) * 16 * kZD};
+    const cuuint32_t box[4] = {8, (cuuint32_t)kZC, (cuuint32_t)kZD, (cuuint32_t)(kZK / 8)};
+    const cuuint32_t estride[4] = {1, 1, 1, 1};
+    const CUresult cr = encode(&xmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, xd.ptr, gdim, gstride, box, estride,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) {
+        ie_set_error("ie_matvec: cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")");
+        return IE_ERR_CUDA;
+    }
     const dim3 g(n / kZM, n / kZC, nparts);
     for (int k = 0; k < nrhs; ++k) {
         const double *xk = x + (long long)k * ldx;
@@ -529,7 +563,7 @@ int launch_matvec_tc_exact(const ie_problem *p, const double *x, long long ldx, 
         const long long chunks = (long long)(n / 8) * (n + 64);
         x_digits_kernel<<<(unsigned)((chunks + 255) / 256), 256, 0, s>>>(xk, n, mx.as<unsigned long long>(), xd.as<uint4>());
         IE_LAUNCHED();
-        kz_matvec_tc<<<g, 256, kZSmem, s>>>(p->d_zt_dig, xd.as<uint4>(), n, ds, F, part.as<long long>(), p->d_err);
+        kz_matvec_tc<<<g, 256, kZSmem, s>>>(p->d_zt_dig, xmap, n, ds, F, part.as<long long>(), p->d_err);
         IE_LAUNCHED();
         kz_combine_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(part.as<long long>(), nparts, N, xk, yk, p->diag,
                                                                      p->d_zt_max, mx.as<unsigned long long>(), F);
