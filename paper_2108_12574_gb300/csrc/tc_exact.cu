@@ -31,8 +31,8 @@
 //     (rows r hold t(|d1|, |r - k|), k < 16); the 128-row tile of K-step s is the strip seen from
 //     row 112 - 16 s, so one strip serves all 8 K-steps through shifted shared-memory descriptors;
 //   * loads the B operand (the six digit planes of the 32 source rows i1 - d1 over the 128
-//     columns, pre-split once per matvec) with one TMA tensor copy (4D map: 8 values x rows x
-//     planes x column groups, which lands directly in the canonical K-major layout);
+//     columns, pre-split once per matvec) with one TMA tensor copy (3D map: runs of 32 rows x 8
+//     values x planes x column groups, which lands directly in the canonical K-major layout);
 //   * issues, per K-step, one MMA per A digit a with the B digit planes 0..5-a side by side
 //     (N = 32 (6 - a)) into TMEM columns from level a on: digit pair (a, b) lands in level a + b.
 // Strip and B operand are double-buffered, and so are the TMEM accumulators (2 x 192 columns):
@@ -309,13 +309,14 @@ kz_matvec_tc(const uint16_t *__restrict__ tdig, const __grid_constant__ CUtensor
             if (lane == 0) {
                 const uint32_t bar = smem_u32(&bfull[sb]);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBBytes) : "memory");
-                // box (8 values, 32 rows, 6 planes, 16 groups) at (0, first source row + 32, 0, kb / 8):
-                // the padded rows keep every coordinate inside the tensor, x = 0 is 16-byte aligned
+                // box (32 rows x 8 values, 6 planes, 16 groups) at ((first source row + 32) x 8, 0,
+                // kb / 8): the padded rows keep every coordinate inside the tensor, and x is a whole
+                // number of 16-byte rows
                 const int r0 = i1_0 - (d_begin + w);  // first source line, in [-31, n - 1]
                 asm volatile(
-                    "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
-                    ::"r"(smem0 + sb * kStageBytes + kStripBytes), "l"(reinterpret_cast<uint64_t>(&xmap)), "r"(0),
-                    "r"(r0 + 32), "r"(0), "r"(kb >> 3), "r"(bar)
+                    "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                    ::"r"(smem0 + sb * kStageBytes + kStripBytes), "l"(reinterpret_cast<uint64_t>(&xmap)),
+                    "r"((r0 + 32) * 8), "r"(0), "r"(kb >> 3), "r"(bar)
                     : "memory");
             }
             __syncwarp();
@@ -534,19 +535,19 @@ int launch_matvec_tc_exact(const ie_problem *p, const double *x, long long ldx, 
     IE_TRY(xd.alloc(sizeof(uint4) * (size_t)kZD * (n / 8) * (n + 64), s));
     IE_TRY(part.alloc(sizeof(long long) * (size_t)nparts * N, s));
     IE_TRY(mx.alloc(sizeof(unsigned long long), s));
-    // the x digits as a packed 4D tensor of 16-bit words: (8 values, n + 64 rows, 6 planes, n / 8
-    // groups); one box is a CTA's B operand for one d1
+    // the x digits as a packed 3D tensor of 16-bit words: ((n + 64) rows x 8 values, 6 planes, n / 8
+    // groups); one box (32 rows, all planes, 16 groups) is a CTA's B operand for one d1
     PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
     if (!encode) {
         ie_set_error("ie_matvec: cuTensorMapEncodeTiled is not available from the driver");
         return IE_ERR_CUDA;
     }
     CUtensorMap xmap;
-    const cuuint64_t gdim[4] = {8, (cuuint64_t)(n + 64), (cuuint64_t)kZD, (cuuint64_t)(n / 8)};
-    const cuuint64_t gstride[3] = {16, (cuuint64_t)(n + 64) * 16, (cuuint64_t)(n + 64) * 16 * kZD};
-    const cuuint32_t box[4] = {8, (cuuint32_t)kZC, (cuuint32_t)kZD, (cuuint32_t)(kZK / 8)};
-    const cuuint32_t estride[4] = {1, 1, 1, 1};
-    const CUresult cr = encode(&xmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, xd.ptr, gdim, gstride, box, estride,
+    const cuuint64_t gdim[3] = {(cuuint64_t)(n + 64) * 8, (cuuint64_t)kZD, (cuuint64_t)(n / 8)};
+    const cuuint64_t gstride[2] = {(cuuint64_t)(n + 64) * 16, (cuuint64_t)(n + 64) * 16 * kZD};
+    const cuuint32_t box[3] = {(cuuint32_t)kZC * 8, (cuuint32_t)kZD, (cuuint32_t)(kZK / 8)};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    const CUresult cr = encode(&xmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, xd.ptr, gdim, gstride, box, estride,
                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) {
