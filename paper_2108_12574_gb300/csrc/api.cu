@@ -483,6 +483,19 @@ extern "C" int dd_factor(const ie_problem *p, const dd_partition_t *s, int preci
                                                    cudaMemcpyHostToDevice)) != cudaSuccess)
                 return fail(e);
         }
+        if (f->max_pad > kApplyColFrom) {  // large blocks: column-chunked single-column work items
+            std::vector<int4> items;
+            for (int i : order)
+                for (int r0 = 0; r0 < nb[(size_t)i]; r0 += kApplyColRows)
+                    for (int c0 = 0; c0 < npad[(size_t)i]; c0 += kApplyColChunk)
+                        items.push_back(make_int4(i, r0, c0, c0 / kApplyColChunk));
+            f->ncitems = (int)items.size();
+            f->maxcol = (f->max_pad + kApplyColChunk - 1) / kApplyColChunk;
+            if ((e = cudaMalloc(&f->d_citems, sizeof(int4) * items.size())) != cudaSuccess) return fail(e);
+            if ((e = cudaMemcpy(f->d_citems, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice)) !=
+                cudaSuccess)
+                return fail(e);
+        }
     }
     if ((e = cudaMemcpy(f->d_loff, loff.data(), sizeof(long long) * loff.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpy(f->d_npad, npad.data(), sizeof(int) * npad.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
@@ -529,6 +542,7 @@ extern "C" void dd_factor_destroy(dd_factor_t *f) {
     cudaFree(f->d_pool);
     cudaFree(f->d_xoff);
     for (int k = 0; k < 3; ++k) cudaFree(f->d_chunks[k]);
+    cudaFree(f->d_citems);
     delete f;
 }
 

@@ -401,6 +401,85 @@ apply_inverse(const float *__restrict__ pool, const long long *__restrict__ loff
     }
 }
 
+// K6c: the exact single-column apply for blocks padded above kApplyColFrom points (the paper's CBD
+// colour blocks).  Staging a whole block's split x would leave one CTA per SM to stream the
+// inverse; here a work item is (block, kApplyColRows rows, kApplyColChunk columns) and stages only
+// that slice (32 KB), so several CTAs share an SM.  Each item leaves its rows' partial double-float
+// sums for its column chunk; apply_col_combine adds a row's chunk partials in FP64, in chunk
+// order, and applies the block's scale.  The same rows and lanes as K6i otherwise (8 lanes per row,
+// RW rows per lane group, U float4 loads in flight).
+template <int RW, int U>
+__global__ void __launch_bounds__(256)
+apply_inverse_cols(const float *__restrict__ pool, const long long *__restrict__ loff, const int *__restrict__ npad,
+                   const int *__restrict__ nb, const long long *__restrict__ offs, const int4 *__restrict__ items,
+                   const long long *__restrict__ xoff, const float *__restrict__ xh_g, const float *__restrict__ xl_g,
+                   long long xtotal, long long total, int maxcol, float2 *__restrict__ zpart) {
+    constexpr int SUB = 32 / kLPR;
+    constexpr int K = (RW + kLPR - 1) / kLPR;
+    __shared__ __align__(16) float4 xs4[2 * kApplyColChunk / 4];  // hi words, then lo words
+    const int4 it = items[blockIdx.x];
+    const int b = it.x, row0 = it.y, col0 = it.z, chunk = it.w;
+    const int k = blockIdx.y;  // right-hand side
+    const int np = npad[b], n = nb[b];
+    const int cw4 = min(kApplyColChunk, np - col0) >> 2;  // np and col0 are multiples of 32
+    const int rend = min(row0 + kApplyColRows, n);
+    const float *M = pool + loff[b] + col0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int sub = lane / kLPR, cl = lane % kLPR;
+    const int cnt = cw4 / kLPR;
+    float4 *xh4 = xs4, *xl4 = xs4 + kApplyColChunk / 4;
+    const long long src0 = ((long long)k * xtotal + xoff[b] + col0) / 4;
+    for (int e = tid; e < cw4; e += 256) {
+        xh4[e] = reinterpret_cast<const float4 *>(xh_g)[src0 + e];
+        xl4[e] = reinterpret_cast<const float4 *>(xl_g)[src0 + e];
+    }
+    __syncthreads();
+    for (int a0 = row0 + warp * SUB * RW; a0 < rend; a0 += 8 * SUB * RW) {
+        const int ab = a0 + sub * RW;
+        const float4 *mrow[RW];
+#pragma unroll
+        for (int q = 0; q < RW; ++q)
+            mrow[q] = reinterpret_cast<const float4 *>(M + (long long)min(ab + q, n - 1) * np) + cl;
+        float s[RW][1], c[RW][1];
+#pragma unroll
+        for (int q = 0; q < RW; ++q) { s[q][0] = 0.f; c[q][0] = 0.f; }
+        int u = 0;
+        for (; u + U <= cnt; u += U) inverse_chunk<1, RW, U, true>(s, c, mrow, u, cl, cw4, xh4, xl4);
+        for (; u < cnt; ++u) inverse_chunk<1, RW, 1, true>(s, c, mrow, u, cl, cw4, xh4, xl4);
+        float oh[K], ol[K];
+#pragma unroll
+        for (int t = 0; t < K; ++t) { oh[t] = 0.f; ol[t] = 0.f; }
+#pragma unroll
+        for (int q = 0; q < RW; ++q) {
+            float hi = s[q][0], lo = c[q][0];
+            df_group_sum(hi, lo);
+            if (cl == q % kLPR) { oh[q / kLPR] = hi; ol[q / kLPR] = lo; }
+        }
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            const int q = t * kLPR + cl;
+            if (q < RW && ab + q < rend)
+                zpart[((long long)k * total + offs[b] + ab + q) * maxcol + chunk] = make_float2(oh[t], ol[t]);
+        }
+    }
+}
+
+// a row's chunk partials summed in FP64 in chunk order, scaled back by the block's 2^e
+__global__ void apply_col_combine(const float2 *__restrict__ zpart, const int *__restrict__ npad,
+                                  const int *__restrict__ nb, const long long *__restrict__ offs,
+                                  const int *__restrict__ xexp, int nblocks, long long total, int maxcol,
+                                  double *__restrict__ zbuf) {
+    const int b = blockIdx.x, k = blockIdx.z;
+    const int a = blockIdx.y * blockDim.x + threadIdx.x;
+    if (a >= nb[b]) return;
+    const int nch = (npad[b] + kApplyColChunk - 1) / kApplyColChunk;
+    const long long row = (long long)k * total + offs[b] + a;
+    const float2 *p = zpart + row * maxcol;
+    double z = 0.0;
+    for (int c = 0; c < nch; ++c) z += (double)p[c].x + (double)p[c].y;
+    zbuf[row] = scale2(z, xexp[(long long)k * nblocks + b]);
+}
+
 __global__ void overlap_sum(const double *__restrict__ zbuf, long long total, const long long *__restrict__ inv_ptr,
                             const long long *__restrict__ inv_pos, double *__restrict__ z, long long ldz, long long N) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -490,8 +569,20 @@ int launch_apply(const dd_factor_t *f, const double *r, long long ldr, double *z
                                                   f->xtotal, f->nblocks, xh, xl, xe.as<int>());
         }
         IE_LAUNCHED();
-        if (f->nchunks[0] > 0) {
-            const int klass = !exact ? kApplyF8 : (nrhs >= 4 && batch_fits) ? kApplyE4 : kApplyE1;
+        const int klass = !exact ? kApplyF8 : (nrhs >= 4 && batch_fits) ? kApplyE4 : kApplyE1;
+        if (klass == kApplyE1 && f->ncitems > 0) {
+            // large blocks: column-chunked work items, then the FP64 chunk sums
+            DevBuf zp;
+            IE_TRY(zp.alloc(sizeof(float2) * (size_t)part->total * nrhs * f->maxcol, s));
+            apply_inverse_cols<2, 4><<<dim3((unsigned)f->ncitems, nrhs), 256, 0, s>>>(
+                (const float *)f->d_pool, f->d_loff, f->d_npad, f->d_n, part->d_offs, f->d_citems, f->d_xoff, xh, xl,
+                f->xtotal, part->total, f->maxcol, zp.as<float2>());
+            IE_LAUNCHED();
+            apply_col_combine<<<dim3(f->nblocks, (part->max_block + 255) / 256, nrhs), 256, 0, s>>>(
+                zp.as<float2>(), f->d_npad, f->d_n, part->d_offs, xe.as<int>(), f->nblocks, part->total, f->maxcol,
+                zbuf.as<double>());
+            IE_LAUNCHED();
+        } else if (f->nchunks[0] > 0) {
             IE_TRY(launch_apply_inverse(f, klass, f->apply_cfg[klass], xh, xl, xe.as<int>(), nrhs, zbuf.as<double>(), s));
         }
     } else if (f->nblocks > 0 && nrhs >= 4 && smm <= (size_t)kApplySmemCeiling) {
@@ -544,7 +635,7 @@ int tune_apply(dd_factor_t *f, cudaStream_t s) {
                               std::to_string(f->nblocks) + "/total" + std::to_string(part->total) + "/max" +
                               std::to_string(f->max_pad);
     struct Cls { int klass, nrhs; bool use; };
-    const Cls classes[3] = {{kApplyE1, 1, true}, {kApplyE4, 8, p->dim == 2 && batch_fits},
+    const Cls classes[3] = {{kApplyE1, 1, f->ncitems == 0}, {kApplyE4, 8, p->dim == 2 && batch_fits},
                             {kApplyF8, 8, p->dim == 3 && batch_fits}};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     IE_TRY_CUDA(cudaEventCreate(&e0));

@@ -124,6 +124,11 @@ struct dd_factor_t {
     // apply work items, one table per candidate row count kApplyRowOpts[k]: (block, first row)
     int nchunks[3] = {0, 0, 0};
     int2 *d_chunks[3] = {nullptr, nullptr, nullptr};
+    // blocks padded above kApplyColFrom: single-column work items (block, first row, first
+    // column, column chunk) of kApplyColRows rows x kApplyColChunk columns; maxcol = chunks of the
+    // largest block
+    int ncitems = 0, maxcol = 0;
+    int4 *d_citems = nullptr;
     // autotuned apply configuration per class (kApplyE1, kApplyE4, kApplyF8): variant * 3 + row option
     int apply_cfg[3] = {1, 1, 1};
 };
@@ -132,6 +137,8 @@ struct dd_factor_t {
 // batches (2D), FP32 8-column batches (3D); candidate row counts per work item.
 constexpr int kApplyE1 = 0, kApplyE4 = 1, kApplyF8 = 2;
 constexpr int kApplyRowOpts[3] = {32, 64, 128};
+// The column-chunked apply for large blocks (CBD colour blocks): x staged per 4096 columns
+constexpr int kApplyColFrom = 8192, kApplyColChunk = 4096, kApplyColRows = 64;
 
 // Largest padded block applied through its explicit inverse: the apply stages the block's split x
 // (8 bytes per point and right-hand side) in one CTA's shared memory.

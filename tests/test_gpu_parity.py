@@ -216,6 +216,34 @@ def test_cbd_mixed_matches_oracle_64():
     assert it_ref - 1 <= rep["iterations"] <= it_ref + 3, (rep, it_ref)
 
 
+def test_cbd_large_blocks_column_chunked_apply():
+    # 160^2 CBD: colour blocks of ~10^4 points, padded above 8192, take the column-chunked apply
+    # (x staged per 4096 columns, FP64 sums of the chunk partials).  Against the definition
+    # T^{-1} r = sum_i R_i^T A_i^{-1} R_i r (Eq. e:ad) with FP64 dense solves of the oracle's
+    # blocks: the FP32-inverse tolerance; bitwise repeatable; symmetric to 1e-10
+    n, m, delta = 160, 10, 2
+    prob = iedd.ie_discretize(2, n)
+    part = iedd.dd_partition(prob, m, delta, iedd.DD_CBD)
+    assert part.nblocks == 4 and part.max_block > 8192
+    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
+    N = n * n
+    R = I.uniform_rhs_batch(N, [3, 4]).T.copy()
+    Z = torch.zeros((2, N), dtype=torch.float64, device="cuda")
+    iedd.dd_apply(fac, dev(R), Z)
+    Z = host(Z)
+    Z2 = torch.zeros((2, N), dtype=torch.float64, device="cuda")
+    iedd.dd_apply(fac, dev(R), Z2)
+    assert np.array_equal(host(Z2), Z)
+    blocks = O.partition(2, n, m, delta, O.CBD)
+    ref = np.zeros_like(R)
+    for b, A in zip(blocks, O.block_matrices(2, n, blocks)):
+        ref[:, b] += np.linalg.solve(A, R[:, b].T).T
+    for k in range(2):
+        assert np.linalg.norm(Z[k] - ref[k]) / np.linalg.norm(ref[k]) <= 2e-3
+    a, b = R[0] @ Z[1], R[1] @ Z[0]
+    assert abs(a - b) <= 1e-10 * max(abs(a), abs(b))
+
+
 def test_cbd_mixed_256_converges_in_fewer_iterations_than_schwarz():
     # 256^2: colour blocks of 24964 points (four dense FP32 inverses of 2.5 GB each); the true
     # residual is checked by the oracle's FFT matvec
