@@ -640,6 +640,27 @@ def test_pcg_full_size_512_mixed():
     assert np.linalg.norm(host(u) - u_ref) / np.linalg.norm(u_ref) <= 1e-6
 
 
+def test_pcg_3d_tensor_batch_iterations():
+    # 16 right-hand sides take the tensor-core inner matvec (>= 16 columns); its FP32-class error
+    # must leave the oracle's iteration count (+5: where the oscillating residual first dips below
+    # tol) and the true residual at tol -- a matvec error of ~1e-6 of max |y| would not
+    n, m, delta = 32, 4, 1
+    N = n ** 3
+    F = I.uniform_rhs_batch(N, range(16)).T.copy()
+    prob = iedd.ie_discretize(3, n)
+    part = iedd.dd_partition(prob, m, delta, iedd.DD_SCHWARZ)
+    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
+    U = torch.zeros((16, N), dtype=torch.float64, device="cuda")
+    reps = iedd.pcg_solve(prob, fac, dev(F), U, tol=1e-8)
+    Uh = host(U)
+    rel = O.true_relative_residual(3, n, F[:2].T, Uh[:2].T)
+    assert np.all(rel <= 1e-8 * 1.01), rel
+    P = O.Problem(3, n, m, delta, O.SCHWARZ, matvec="fft")
+    _, its, _ = P.solve(F[:2].T, 1e-8)
+    for k in range(2):
+        assert its[k] - 1 <= reps[k]["iterations"] <= its[k] + 5, (reps[k], its[k])
+
+
 def test_pcg_full_size_3d_batched_mixed():
     # 32^3, Schwarz 4 x 4 x 4 partitions (blocks of 729-1000 points), 1-cell overlap, 8 of the
     # 64 uniform right-hand sides (seeds 0..7), FP32 factors, FP64 scalars
