@@ -4,9 +4,11 @@
 Workload (synthetic stand-in for the paper's uniform-grid problems): 2D Laplace first-kind
 IE, 512 x 512 cell-centred grid (N = 262144), f a Gaussian random field (squared-exponential
 covariance, length scale 0.1, seed = rank), Schwarz preconditioner with 32 x 32 partitions of
-16 x 16 cells extended by 2 cells, FP32 factors (FP64 solves), exact double-float matvec on the
-FP32 pipes (per-offset FP64 entry table split hi/lo), FP64 CG scalars, residual replacement every
-50 iterations and at convergence; tolerance 1e-8 on the true residual.
+16 x 16 cells extended by 2 cells; subdomain Cholesky and explicit FP32 inverses on the tensor
+cores, applied with double-float products; the exact direct-sum matvec on the tensor cores (the
+FP64 per-offset entries and x cut into six BF16 digits, 21 digit products summed exactly); FP64
+CG vectors and scalars; the FP64 FFT matvec for the true residual, which replaces the recursive
+one every 50 iterations and at convergence; tolerance 1e-8 on the true residual.
 
 One step = the whole hot path for one right-hand side: ie_discretize, dd_partition, dd_factor,
 pcg_solve (inputs already in HBM).  N > 1 GPUs run independent replicas (weak scaling).
