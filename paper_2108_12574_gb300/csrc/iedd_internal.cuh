@@ -190,6 +190,7 @@ int launch_matvec_tc(const ie_problem *p, const double *x, long long ldx, int nr
 int prepare_tc();
 int build_tc_table(ie_problem *p);
 bool tc_toeplitz(const ie_problem *p);  // the tensor-core matvec reads its tiles from d_table_tc
+int tc_splits_toeplitz(long long tiles, int nchunks, int sms);  // source splits of that kernel
 int tc_chunk();
 int tc_rows();
 int tc_cols();

@@ -45,14 +45,16 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
     return d;
 }
 
-// kind::tf32 instruction descriptor: D FP32, A and B TF32, both K-major, N = 64, M = 128
+// kind::tf32 instruction descriptor: D FP32, A and B TF32, both K-major, N = 64 (or 128), M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTN >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+constexpr uint32_t kIdesc128 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)((2 * kTN) >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate,
+                                         uint32_t idesc = kIdesc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -365,6 +367,299 @@ k1t_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsp
     }
 }
 
+// K1w: the table-fed (TOEP) batched matvec with warp roles.  The products are K1t's (A tiles of
+// exact table entries split into TF32 high / low words, the same pre-split B operand: hi hi,
+// hi lo and lo hi), but the B record's low rows follow its high rows at the same stride, so per
+// K-step one N = 128 MMA gives hi hi (level 0, columns 0-63) and hi lo (level 1, columns 64-127)
+// and a second adds lo hi to level 1: 8 MMAs per 32-source chunk instead of 12.  No block-wide
+// barrier couples the roles: one lane issues the MMAs (warp 0), one the bulk copy of each chunk's
+// B operand (warp 1), six warps write the A tiles (warps 2-7), and four warps fold finished
+// accumulator sets (levels 0 + 1, FP32 over 8 chunks) into running (high, low) sums kept in
+// tensor memory (warps 8-11, one TMEM lane quarter each).  Four operand stages, two accumulator
+// sets of 128 columns; mbarriers hand over; every wait is bounded.
+constexpr int kWStages = 4, kWThreads = 384, kWWin = 8, kWFillWarps = 6;
+constexpr int kWSmem = kWStages * kStage * (int)sizeof(uint32_t);  // 192 KB
+constexpr int kWSlots = 2;  // staged entries per fill thread (nl (Lr + 31) <= 252 <= 2 x 192)
+
+__device__ __forceinline__ void tmem_ld16w(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st16w(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kWThreads, 1)
+k1w_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsplit, int nrhs, long long N,
+              int chunks_per_split, int nchunks, double *__restrict__ partial, int *__restrict__ err,
+              const uint2 *__restrict__ ttab, int n, int Lr) {
+    extern __shared__ __align__(128) uint32_t opnd[];  // kWStages x [A hi | A lo | B hi | B lo]
+    constexpr int kPer = kTM + kTK - 1;
+    __shared__ uint2 tval[2][kTM / 32 * kPer];          // a chunk's distinct entries, double-buffered
+    __shared__ int4 rline[kTM / 32];                    // slow, mid, fast coordinate of target line q
+    __shared__ __align__(8) uint64_t sfull[kWStages], bfull[kWStages], mdone[kWStages], afull[2], aempty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long row0 = (long long)blockIdx.x * kTM;
+    const int grp = blockIdx.z;
+    const int k0 = blockIdx.y * chunks_per_split;
+    const int T = max(0, min(chunks_per_split, nchunks - k0));
+    const int nl = kTM / Lr, per = Lr + kTK - 1;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(512u));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int st = 0; st < kWStages; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sfull[st])), "r"((uint32_t)kWFillWarps));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bfull[st])), "r"(1u));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mdone[st])), "r"(1u));
+        }
+        for (int st = 0; st < 2; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&afull[st])), "r"(1u));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&aempty[st])), "r"(4u));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    if (tid < nl) {
+        const float4 c = coord[row0 + (long long)tid * Lr];
+        rline[tid] = DIM == 2 ? make_int4((int)c.x, 0, (int)c.y, 0) : make_int4((int)c.x, (int)c.y, (int)c.z, 0);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    auto wait_bar = [&](uint64_t *bar, uint32_t parity) -> bool {
+        for (long long i = 0; i < kSpinLimit / 8; ++i) {
+            if (mbar_try(smem_u32(bar), parity)) return true;
+            if (abort_flag) return false;
+        }
+        abort_flag = 1;
+        return false;
+    };
+    auto warp_wait = [&](uint64_t *bar, uint32_t parity) -> bool {
+        int ok = 1;
+        if (lane == 0) ok = wait_bar(bar, parity) ? 1 : 0;
+        return __shfl_sync(0xffffffffu, ok, 0) != 0;
+    };
+
+    if (warp == 0) {
+        // ---- MMA issue (one lane): per chunk 4 K-steps x (hi hi, hi lo, lo hi) ----
+        if (lane == 0) {
+            int issued = 0;
+            for (int c = 0; c < T; ++c) {
+                const int st = c % kWStages, f = c / kWWin, set = f & 1;
+                const uint32_t spar = (uint32_t)(c / kWStages) & 1u, fpar = (uint32_t)(f >> 1) & 1u;
+                if (!wait_bar(&sfull[st], spar) || !wait_bar(&bfull[st], spar)) break;
+                if (c % kWWin == 0 && f >= 2 && !wait_bar(&aempty[set], fpar ^ 1u)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t ahi = smem_u32(opnd + st * kStage), alo = ahi + kTM * kTK * 4;
+                const uint32_t bhi = ahi + 2 * kTM * kTK * 4, blo = bhi + kTN * kTK * 4;
+                const uint32_t dt = tmem + (uint32_t)set * (2 * kTN);
+                (void)blo;
+#pragma unroll
+                for (int s = 0; s < kTK / 8; ++s) {
+                    const uint32_t koff = (uint32_t)s * 2 * kLBO;
+                    // [hi hi | hi lo] over the high then low rows of B, then lo hi into level 1
+                    mma_tf32(dt, make_desc(ahi + koff), make_desc(bhi + koff), (c % kWWin == 0 && s == 0) ? 0u : 1u,
+                             kIdesc128);
+                    mma_tf32(dt + kTN, make_desc(alo + koff), make_desc(bhi + koff), 1u);
+                }
+                mma_commit(smem_u32(&mdone[st]));
+                if (c % kWWin == kWWin - 1 || c == T - 1) mma_commit(smem_u32(&afull[set]));
+                issued = c + 1;
+            }
+            if (issued > 0 && !mbar_wait(smem_u32(&mdone[(issued - 1) % kWStages]), (uint32_t)((issued - 1) / kWStages) & 1u))
+                abort_flag = 1;  // (a wait that ignores the abort flag: the TMEM must be idle)
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---- B operand: one bulk copy of the pre-split x per chunk ----
+        int issued = 0;
+        for (int c = 0; c < T; ++c) {
+            const int st = c % kWStages;
+            const uint32_t spar = (uint32_t)(c / kWStages) & 1u;
+            if (c >= kWStages && !warp_wait(&mdone[st], spar ^ 1u)) break;
+            if (lane == 0) {
+                const uint32_t *src = xsplit + ((long long)grp * nchunks + k0 + c) * (2LL * kTN * kTK);
+                bulk_g2s(smem_u32(opnd + st * kStage + 2 * kTM * kTK), src, (uint32_t)(2 * kTN * kTK * sizeof(uint32_t)),
+                         smem_u32(&bfull[st]));
+            }
+            __syncwarp();
+            issued = c + 1;
+        }
+        if (lane == 0)  // no copy may still be landing when the CTA ends
+            for (int c = max(0, issued - kWStages); c < issued; ++c)
+                if (!mbar_wait(smem_u32(&bfull[c % kWStages]), (uint32_t)(c / kWStages) & 1u)) abort_flag = 1;
+        __syncwarp();
+    } else if (warp < 2 + kWFillWarps) {
+        // ---- A tiles (192 threads); every fill warp runs every chunk and every named barrier ----
+        const int ft = tid - 64;
+        int sq[kWSlots], stt[kWSlots];  // staged entry e = ft + 192 i: line and position
+#pragma unroll
+        for (int i = 0; i < kWSlots; ++i) {
+            const int e = ft + 32 * kWFillWarps * i;
+            sq[i] = e < nl * per ? e / per : -1;
+            stt[i] = e < nl * per ? e - sq[i] * per : 0;
+        }
+        uint2 tv[kWSlots];
+        // coordinates of the next chunk to fetch (chunks are fetched in order, 32 sources each)
+        int fj, mj, sj;
+        {
+            const int j0 = k0 * kTK, tj = j0 / n;
+            fj = j0 % n;
+            mj = DIM == 2 ? 0 : tj % n;
+            sj = DIM == 2 ? tj : tj / n;
+        }
+        auto fetch = [&](int c) {
+#pragma unroll
+            for (int i = 0; i < kWSlots; ++i) {
+                tv[i] = make_uint2(0u, 0u);
+                if (c < T && sq[i] >= 0) {
+                    const int4 L = rline[sq[i]];
+                    const int df = abs(L.z - fj - (kTK - 1) + stt[i]), dm = abs(L.y - mj), ds = abs(L.x - sj);
+                    tv[i] = __ldg(ttab + (DIM == 2 ? (long long)ds * n + df : ((long long)ds * n + dm) * n + df));
+                }
+            }
+            fj += kTK;  // the next chunk
+            if (fj >= n) {
+                fj = 0;
+                if (DIM == 2) {
+                    ++sj;
+                } else if (++mj >= n) {
+                    mj = 0;
+                    ++sj;
+                }
+            }
+        };
+        auto stage_tv = [&](int buf) {
+#pragma unroll
+            for (int i = 0; i < kWSlots; ++i)
+                if (sq[i] >= 0) tval[buf][sq[i] * per + stt[i]] = tv[i];
+        };
+        fetch(0);
+        stage_tv(0);
+        fetch(1);
+        const int lgL = __ffs(Lr) - 1;
+        for (int c = 0; c < T; ++c) {
+            const int st = c % kWStages;
+            const uint32_t spar = (uint32_t)(c / kWStages) & 1u;
+            bool ok = !abort_flag;
+            if (ok && c >= kWStages) ok = warp_wait(&mdone[st], spar ^ 1u);
+            asm volatile("bar.sync 1, 192;" ::: "memory");  // tval[c & 1] is complete
+            if (ok) {
+                uint32_t *Ahi = opnd + st * kStage, *Alo = Ahi + kTM * kTK;
+                const uint2 *tb = tval[c & 1];
+                // unit u = (column group g, row r): the 4 sources 4g..4g+3 of row r, one 16-byte
+                // core-matrix row in each of the hi and lo planes
+                for (int u = ft; u < kTM * (kTK / 4); u += 32 * kWFillWarps) {
+                    const int g = u >> 7, r = u & (kTM - 1);
+                    const int base = (r >> lgL) * per + (r & (Lr - 1)) + (kTK - 1) - 4 * g;
+                    const uint2 w0 = tb[base], w1 = tb[base - 1], w2 = tb[base - 2], w3 = tb[base - 3];
+                    const int off = (r >> 3) * (kSBO / 4) + g * (kLBO / 4) + (r & 7) * 4;
+                    *reinterpret_cast<uint4 *>(Ahi + off) = make_uint4(w0.x, w1.x, w2.x, w3.x);
+                    *reinterpret_cast<uint4 *>(Alo + off) = make_uint4(w0.y, w1.y, w2.y, w3.y);
+                }
+            }
+            stage_tv((c + 1) & 1);  // the buffer was last read in chunk c - 1, before this barrier
+            fetch(c + 2);
+            if (ok) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&sfull[st])) : "memory");
+            }
+        }
+    } else {
+        // ---- accumulator sets into running (high, low) sums in TMEM columns 128.. and 192.. ----
+        const int q4 = warp & 3;
+        const uint32_t lanes = (uint32_t)(32 * q4) << 16;
+        {
+            uint32_t z[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) z[k] = 0u;
+#pragma unroll
+            for (int b = 0; b < kTN / 16; ++b) {
+                tmem_st16w(tmem + lanes + 256u + 16u * b, z);
+                tmem_st16w(tmem + lanes + 320u + 16u * b, z);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
+        const int nwin = (T + kWWin - 1) / kWWin;
+        for (int f = 0; f < nwin; ++f) {
+            const int set = f & 1;
+            if (!warp_wait(&afull[set], (uint32_t)(f >> 1) & 1u)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int b = 0; b < kTN / 16; ++b) {
+                uint32_t a[16], a1[16], h[16], l[16];
+                tmem_ld16w(tmem + lanes + (uint32_t)set * (2 * kTN) + 16u * b, a);
+                tmem_ld16w(tmem + lanes + (uint32_t)set * (2 * kTN) + kTN + 16u * b, a1);
+                tmem_ld16w(tmem + lanes + 256u + 16u * b, h);
+                tmem_ld16w(tmem + lanes + 320u + 16u * b, l);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (b == kTN / 16 - 1) {  // every read of this set is complete: release it
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0)
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&aempty[set])) : "memory");
+                }
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    float hi = __uint_as_float(h[k]), lo = __uint_as_float(l[k]);
+                    two_sum_acc(__uint_as_float(a[k]) + __uint_as_float(a1[k]), hi, lo);
+                    h[k] = __float_as_uint(hi);
+                    l[k] = __float_as_uint(lo);
+                }
+                tmem_st16w(tmem + lanes + 256u + 16u * b, h);
+                tmem_st16w(tmem + lanes + 320u + 16u * b, l);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
+        const long long i = row0 + 32 * q4 + lane;
+        if (!abort_flag) {
+#pragma unroll
+            for (int b = 0; b < kTN / 16; ++b) {
+                uint32_t h[16], l[16];
+                tmem_ld16w(tmem + lanes + 256u + 16u * b, h);
+                tmem_ld16w(tmem + lanes + 320u + 16u * b, l);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (i < N) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const int r = grp * kTN + 16 * b + k;
+                        if (r < nrhs)
+                            partial[((long long)blockIdx.y * nrhs + r) * N + i] =
+                                (double)__uint_as_float(h[k]) + (double)__uint_as_float(l[k]);
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (abort_flag && tid == 0) atomicExch(err, 1);
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
+    }
+}
+
 }  // namespace
 
 // y partials for nrhs >= 1 right-hand sides through the tensor cores; returns IE_ERR_TIMEOUT
@@ -383,11 +678,11 @@ int launch_matvec_tc(const ie_problem *p, const double *x, long long ldx, int nr
     const bool toep = tc_toeplitz(p);
     const int Lr = std::min(p->n, kTM);
     if (toep && p->dim == 2)
-        k1t_matvec_tc<2, true><<<g, 256, dsm, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial, d_err,
-                                                   p->d_table_tc, p->n, Lr);
+        k1w_matvec_tc<2><<<g, kWThreads, kWSmem, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial,
+                                                      d_err, p->d_table_tc, p->n, Lr);
     else if (toep)
-        k1t_matvec_tc<3, true><<<g, 256, dsm, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial, d_err,
-                                                   p->d_table_tc, p->n, Lr);
+        k1w_matvec_tc<3><<<g, kWThreads, kWSmem, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial,
+                                                      d_err, p->d_table_tc, p->n, Lr);
     else if (p->dim == 2)
         k1t_matvec_tc<2, false><<<g, 256, dsm, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial, d_err,
                                                     nullptr, p->n, Lr);
@@ -424,6 +719,19 @@ int build_tc_table(ie_problem *p) {
     return IE_OK;
 }
 
+// source splits of the warp-specialized kernel (one CTA per SM): the smallest modelled time
+// ceil(CTAs / SMs) x (chunks per CTA + 8 for a CTA's setup and final write)
+int tc_splits_toeplitz(long long tiles, int nchunks, int sms) {
+    int best = 1;
+    long long best_cost = -1;
+    for (int s = 1; s <= 64 && s <= nchunks; ++s) {
+        const long long cps = (nchunks + s - 1) / s;
+        const long long cost = (tiles * s + sms - 1) / sms * (cps + 8);
+        if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = s; }
+    }
+    return best;
+}
+
 int tc_chunk() { return kTK; }
 int tc_rows() { return kTM; }
 int tc_cols() { return kTN; }
@@ -434,5 +742,7 @@ int prepare_tc() {
     IE_TRY_CUDA(cudaFuncSetAttribute(k1t_matvec_tc<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
     IE_TRY_CUDA(cudaFuncSetAttribute(k1t_matvec_tc<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
     IE_TRY_CUDA(cudaFuncSetAttribute(k1t_matvec_tc<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
+    IE_TRY_CUDA(cudaFuncSetAttribute(k1w_matvec_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWSmem));
+    IE_TRY_CUDA(cudaFuncSetAttribute(k1w_matvec_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWSmem));
     return IE_OK;
 }
