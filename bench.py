@@ -405,10 +405,10 @@ def main():
         peak = bf16 * TF32_PER_BF16 * 1e12
         achieved = pairs * nr * 6.0 / mv_launch_s
         roofline = {"bound": "tensor", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": "k1t_matvec_tc<3>",
+                    "frac": achieved / peak, "traffic": None, "kernel": "k1w_matvec_tc<3>",
                     "pair_rhs_per_s": pairs * nr / mv_launch_s,
                     "peak_basis": (f"TF32 dense = {bf16:.1f} TFLOP/s bf16 sustained (of measured) x {TF32_PER_BF16:.3f} "
-                                   "(nominal 1.1 / 2.25 PFLOP/s); work = 3 TF32 MMAs (2 flops each) per pair per RHS")}
+                                   "(nominal 1.1 / 2.25 PFLOP/s); work = 3 TF32 products (hi hi, hi lo, lo hi; 2 flops each) per pair per RHS")}
     elif prec == iedd.IE_MIXED:
         # batched FP32 kernel: one FFMA per pair and right-hand side dominates (entries amortised)
         peak = sms * FP32_LANES_PER_SM * f_mhz * 1e6
