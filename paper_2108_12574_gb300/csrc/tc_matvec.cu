@@ -1,6 +1,8 @@
-// K1t: the batched-RHS matvec on the 5th-generation tensor cores (tcgen05, sm_103a).
+// The batched-RHS matvecs on the 5th-generation tensor cores (tcgen05, sm_103a): K1w (below)
+// for grids of n = 32, 64 or a multiple of 128, whose tiles come from the exact per-offset table,
+// and K1t for the other sizes.
 //
-// For a batch of right-hand sides the matvec is a dense contraction: a CTA owns 128 target rows
+// K1t.  For a batch of right-hand sides the matvec is a dense contraction: a CTA owns 128 target rows
 // and 64 right-hand sides; for each chunk of 32 source points it evaluates the 128 x 32 entry
 // tile E (SFU rsqrt / log2, as K1), split into TF32 high and low parts, while a bulk
 // asynchronous copy (cp.async.bulk, mbarrier complete_tx) brings the matching 64 x 32 slice of
@@ -124,29 +126,17 @@ constexpr int kStage = 2 * kTM * kTK + 2 * kTN * kTK;  // uint32 words per opera
 constexpr int kStages = 2;                             // operand stages (96 KB, two CTAs per SM)
 constexpr int kFlush = 256 / kTK;                      // chunks accumulated in TMEM between flushes
 
-// TOEP: the grid size n is a multiple of 32 and a tile's 128 rows are whole lines of the fastest
-// axis or one part of a line (n = 32, 64 or a multiple of 128).  A chunk's 32 sources then lie on
-// one line, and the entry of (row r, source k) depends on r only through its line q = r / Lr and
-// on (r mod Lr) - k: per chunk the nl x (Lr + 31) distinct entries (at most 252) are read from the
-// exact per-offset table, already split into TF32 high / low words, and the 128 x 32 tile is
-// filled from them -- no SFU evaluation, and the entries are the FP64 ones (excluding i = j).
-//
-// Pipeline (one CTA = 128 rows x 64 right-hand sides x a range of chunks, two CTAs per SM): two
-// operand stages; chunk c's entries are built while chunk c - 1's MMAs run.  A stage is reused
-// only after the commit of its previous MMAs was waited for (by one thread, with a suspending
-// try_wait; the block barrier releases the others).  (Deeper pipelines -- four 16-wide or 32-wide
-// stages with the B operand requested two chunks ahead -- measured slower on GB300: 3.0-3.3 ms
-// against 2.0 ms per 64-column 32^3 product.)
-template <int DIM, bool TOEP>
+// K1t serves the grids K1w does not take (n not 32, 64 or a multiple of 128): its entries come
+// from the SFU as in K1.  Pipeline (one CTA = 128 rows x 64 right-hand sides x a range of chunks,
+// two CTAs per SM): two operand stages; chunk c's entries are built while chunk c - 1's MMAs run.
+// A stage is reused only after the commit of its previous MMAs was waited for (by one thread, with
+// a suspending try_wait; the block barrier releases the others).
+template <int DIM>
 __global__ void __launch_bounds__(256, 2)
 k1t_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsplit, int nrhs, long long N,
-              int chunks_per_split, int nchunks, double *__restrict__ partial, int *__restrict__ err,
-              const uint2 *__restrict__ ttab, int n, int Lr) {
+              int chunks_per_split, int nchunks, double *__restrict__ partial, int *__restrict__ err) {
     extern __shared__ __align__(128) uint32_t opnd[];  // kStages x [A hi | A lo | B hi | B lo]
-    constexpr int kPer = kTM + kTK - 1;               // distinct entries per line and chunk (Lr = 128)
     __shared__ float4 rc[kTM];
-    __shared__ uint2 tval[2][kTM / 32 * kPer];        // TOEP: this chunk's and the next one's entries
-    __shared__ int4 rline[kTM / 32];                  // TOEP: slow, mid, first fast coordinate of line q
     __shared__ __align__(8) uint64_t mbar_mma[kStages];
     __shared__ __align__(8) uint64_t mbar_ld[kStages];
     __shared__ uint32_t tmem_base;
@@ -173,11 +163,6 @@ k1t_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsp
     if (tid < kTM) {
         const long long i = row0 + tid;
         rc[tid] = i < N ? coord[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    const int nl = kTM / Lr;  // TOEP: target lines per tile
-    if (TOEP && tid < nl) {
-        const float4 c = coord[row0 + (long long)tid * Lr];
-        rline[tid] = DIM == 2 ? make_int4((int)c.x, 0, (int)c.y, 0) : make_int4((int)c.x, (int)c.y, (int)c.z, 0);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -234,30 +219,6 @@ k1t_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsp
         for (int c = 0; c < 32; ++c) two_sum_acc(__uint_as_float(v[c]), ahi[c], alo[c]);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     };
-    // TOEP: thread tid holds entry tid of chunk c's nl x (Lr + 31) distinct entries (at most 252, so
-    // one per thread).  The chunk's line follows from its first index; the value is fetched two
-    // chunks ahead into a register and stored to tval one chunk ahead, so no chunk waits for it.
-    const int per = Lr + kTK - 1;
-    const bool tv_own = TOEP && tid < nl * per;
-    auto fetch_tval = [&](int c) -> uint2 {
-        if (!tv_own || c >= k1) return make_uint2(0u, 0u);
-        const long long j0c = (long long)c * kTK;
-        const int fj = (int)(j0c % n);
-        const long long tj = j0c / n;
-        const int mj = DIM == 2 ? 0 : (int)(tj % n), sj = DIM == 2 ? (int)tj : (int)(tj / n);
-        const int qq = tid / per, t = tid - qq * per;
-        const int4 L = rline[qq];
-        const int df = abs(L.z - fj - (kTK - 1) + t), dm = abs(L.y - mj), ds = abs(L.x - sj);
-        return ttab[DIM == 2 ? (long long)ds * n + df : ((long long)ds * n + dm) * n + df];
-    };
-
-    // prologue: the first chunk's entries stored, the second chunk's in a register
-    uint2 tv_next = make_uint2(0u, 0u);
-    if (TOEP) {
-        const uint2 first = fetch_tval(k0);
-        if (tv_own) tval[0][tid] = first;
-        tv_next = fetch_tval(k0 + 1);
-    }
     // element e = tid + 256 it of a part in core-matrix order (RG = kTK / 4 core-matrix columns per
     // row group) is row (64 / RG) it + 8 (warp / RG) + lane / 4 of source column 4 (warp % RG) + lane % 4
     constexpr int RG = kTK / 4, kRowStep = 64 / RG, kIters = kTM * kTK / 256;
@@ -279,21 +240,8 @@ k1t_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsp
         }
         issue_b(ch);
         // A operand of chunk ch
-        const long long j0 = (long long)ch * kTK;
-        if (TOEP) {
-            const int buf = ci & 1;
-            const int lgL = __ffs(Lr) - 1, tb = kTK - 1 - kk;
-            if (tv_own) tval[buf ^ 1][tid] = tv_next;  // chunk ch + 1, read after the next barriers
-            tv_next = fetch_tval(ch + 2);
-#pragma unroll
-            for (int it = 0; it < kIters; ++it) {
-                const int r = kRowStep * it + rbase;
-                const uint2 w = tval[buf][(r >> lgL) * per + (r & (Lr - 1)) + tb];
-                Ahi[tid + 256 * it] = w.x;
-                Alo[tid + 256 * it] = w.y;
-            }
-        } else {
-            const long long j = j0 + kk;
+        const long long j = (long long)ch * kTK + kk;
+        {
             const float4 b = j < N ? coord[j] : make_float4(1e6f, 1e6f, 1e6f, 0.f);
 #pragma unroll 4
             for (int it = 0; it < kIters; ++it) {
@@ -367,7 +315,7 @@ k1t_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsp
     }
 }
 
-// K1w: the table-fed (TOEP) batched matvec with warp roles.  The products are K1t's (A tiles of
+// K1w: the table-fed batched matvec with warp roles (n = 32, 64 or a multiple of 128).  The products are K1t's (A tiles of
 // exact table entries split into TF32 high / low words, the same pre-split B operand: hi hi,
 // hi lo and lo hi), but the B record's low rows follow its high rows at the same stride, so per
 // K-step one N = 128 MMA gives hi hi (level 0, columns 0-63) and hi lo (level 1, columns 64-127)
@@ -684,11 +632,9 @@ int launch_matvec_tc(const ie_problem *p, const double *x, long long ldx, int nr
         k1w_matvec_tc<3><<<g, kWThreads, kWSmem, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial,
                                                       d_err, p->d_table_tc, p->n, Lr);
     else if (p->dim == 2)
-        k1t_matvec_tc<2, false><<<g, 256, dsm, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial, d_err,
-                                                    nullptr, p->n, Lr);
+        k1t_matvec_tc<2><<<g, 256, dsm, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial, d_err);
     else
-        k1t_matvec_tc<3, false><<<g, 256, dsm, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial, d_err,
-                                                    nullptr, p->n, Lr);
+        k1t_matvec_tc<3><<<g, 256, dsm, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial, d_err);
     IE_LAUNCHED();
     return IE_OK;
 }
@@ -738,10 +684,8 @@ int tc_cols() { return kTN; }
 
 int prepare_tc() {
     const int dsm = (int)(sizeof(uint32_t) * kStages * kStage);
-    IE_TRY_CUDA(cudaFuncSetAttribute(k1t_matvec_tc<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
-    IE_TRY_CUDA(cudaFuncSetAttribute(k1t_matvec_tc<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
-    IE_TRY_CUDA(cudaFuncSetAttribute(k1t_matvec_tc<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
-    IE_TRY_CUDA(cudaFuncSetAttribute(k1t_matvec_tc<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
+    IE_TRY_CUDA(cudaFuncSetAttribute(k1t_matvec_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
+    IE_TRY_CUDA(cudaFuncSetAttribute(k1t_matvec_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
     IE_TRY_CUDA(cudaFuncSetAttribute(k1w_matvec_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWSmem));
     IE_TRY_CUDA(cudaFuncSetAttribute(k1w_matvec_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWSmem));
     return IE_OK;
