@@ -44,6 +44,24 @@ bool ie_is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The library's scratch and factor pools come from the device's default memory pool
+// (cudaMallocAsync).  A pool returns freed memory to the driver at every synchronization unless
+// its release threshold says otherwise, and the solver frees and re-allocates the same large
+// buffers every step; so the first problem on a device raises this process's threshold to keep
+// up to 16 GB cached (a larger threshold set by the caller is left as it is).
+void keep_pool_cached(int device) {
+    static std::mutex mu;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(done.begin(), done.end(), device) != done.end()) return;
+    done.push_back(device);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) != cudaSuccess) return;
+    uint64_t cur = 0, want = 16ULL << 30;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur) == cudaSuccess && cur < want)
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &want);
+}
+
 int DevBuf::alloc(size_t b, cudaStream_t st) {
     s = st;
     bytes = b;
@@ -140,6 +158,7 @@ extern "C" int ie_discretize(int dim, int n, double a_shift, int grid, int devic
     if (device < 0 || device >= ndev) { ie_set_error("ie_discretize: bad device ordinal"); return IE_ERR_ARG; }
     DeviceGuard g(device);
 
+    keep_pool_cached(device);
     ie_problem *p = new (std::nothrow) ie_problem();
     if (!p) { ie_set_error("ie_discretize: out of host memory"); return IE_ERR_OOM; }
     const double pi = 3.14159265358979323846;
@@ -465,7 +484,8 @@ extern "C" int dd_factor(const ie_problem *p, const dd_partition_t *s, int preci
     if ((e = cudaMalloc(&f->d_n, sizeof(int) * nb.size())) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&f->d_order, sizeof(int) * order.size())) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&f->d_info, sizeof(int) * nb.size())) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&f->d_pool, esz * (size_t)f->pool_elems)) != cudaSuccess) return fail(e);
+    // the pool of blocks comes from the cached memory pool (freed after a device synchronize)
+    if ((e = cudaMallocAsync(&f->d_pool, esz * (size_t)f->pool_elems, st)) != cudaSuccess) return fail(e);
     f->inverse = precision == IE_MIXED && f->max_pad <= kInvMaxPad;
     if (f->inverse) {
         std::vector<long long> xoff((size_t)s->nblocks + 1, 0);
@@ -539,7 +559,10 @@ extern "C" void dd_factor_destroy(dd_factor_t *f) {
     cudaFree(f->d_n);
     cudaFree(f->d_order);
     cudaFree(f->d_info);
-    cudaFree(f->d_pool);
+    if (f->d_pool) {  // from cudaMallocAsync: every use on any stream has finished after the synchronize
+        cudaDeviceSynchronize();
+        cudaFreeAsync(f->d_pool, nullptr);
+    }
     cudaFree(f->d_xoff);
     for (int k = 0; k < 3; ++k) cudaFree(f->d_chunks[k]);
     cudaFree(f->d_citems);
