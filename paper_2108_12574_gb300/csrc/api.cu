@@ -202,7 +202,7 @@ extern "C" void ie_destroy(ie_problem *p) {
     cudaFree(p->d_table_tc);
     cudaFree(p->d_fft_tw);
     cudaFree(p->d_fft_chat);
-    cudaFree(p->d_zt_dig);
+    cudaFree(p->d_zt_win);
     cudaFree(p->d_zt_max);
     delete p;
 }
@@ -276,11 +276,11 @@ extern "C" int ie_matvec(const ie_problem *p, const double *x, double *y, int nr
         }
         IE_TRY(prepare_fft(p));
     }
-    if (precision == IE_TENSOR_EXACT && !p->d_zt_dig) {
+    if (precision == IE_TENSOR_EXACT && !p->d_zt_win) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         IE_TRY_CUDA(cudaStreamIsCapturing(s, &cs));
         if (cs != cudaStreamCaptureStatusNone) {
-            ie_set_error("ie_matvec: the first IE_TENSOR_EXACT call on a problem builds its digit table and must not "
+            ie_set_error("ie_matvec: the first IE_TENSOR_EXACT call on a problem builds its digit window table and must not "
                          "be captured");
             return IE_ERR_ARG;
         }

@@ -81,9 +81,9 @@ struct ie_problem {
     double2 *d_fft_tw = nullptr;
     double *d_fft_chat = nullptr;
     int fft_cfg = 4;               // autotuned launch shape of the FFT passes (see fft.cu)
-    // exact tensor-core matvec (built on first use): six BF16 digit planes of the per-offset table
-    // and the bits of max |t| (its power-of-two scale)
-    uint16_t *d_zt_dig = nullptr;
+    // exact tensor-core matvec (built on first use): the window table of the six BF16 digit planes
+    // of the per-offset table (192 n^2 bytes) and the bits of max |t| (its power-of-two scale)
+    void *d_zt_win = nullptr;
     unsigned long long *d_zt_max = nullptr;
 };
 

@@ -27,16 +27,17 @@
 // Tile.  A CTA owns 128 target points of one grid line segment (M = 128 values of i2) for 32
 // consecutive lines (i1), one block of 128 source columns j2, and a range of d1.  Per d1 (one
 // window) it
-//   * builds the A operand: the six digit planes of the 240 distinct rows of the Toeplitz strip
-//     (rows r hold t(|d1|, |r - k|), k < 16); the 128-row tile of K-step s is the strip seen from
-//     row 112 - 16 s, so one strip serves all 8 K-steps through shifted shared-memory descriptors;
+//   * loads the A operand with one TMA tensor copy: the six digit planes of a 248-row strip of the
+//     window table (built once per problem; row p holds 8 consecutive table values along the
+//     Toeplitz diagonal), which the MMAs of all 8 K-steps read through shifted shared-memory
+//     descriptors (MMA row m is target i2_0 + 127 - m, so the tile entry depends on m + k);
 //   * loads the B operand (the six digit planes of the 32 source rows i1 - d1 over the 128
 //     columns, pre-split once per matvec) with one TMA tensor copy (3D map: runs of 32 rows x 8
 //     values x planes x column groups, which lands directly in the canonical K-major layout);
 //   * issues, per K-step, one MMA per A digit a with the B digit planes 0..5-a side by side
 //     (N = 32 (6 - a)) into TMEM columns from level a on: digit pair (a, b) lands in level a + b.
-// Strip and B operand are double-buffered, and so are the TMEM accumulators (2 x 192 columns):
-// window w + 1's operands are built and window w - 1's accumulators read while window w's MMAs run.
+// Operands are triple-buffered and the TMEM accumulators double-buffered (2 x 192 columns):
+// later windows' operands land and window w - 1's accumulators are read while window w's MMAs run.
 // Waits are bounded: a CTA that waits too long records an error code, drains, frees its TMEM and
 // returns.
 #include <cuda.h>
@@ -56,16 +57,16 @@ constexpr int kZM = 128;                     // i2 per tile (MMA M)
 constexpr int kZC = 32;                      // grid lines i1 per tile (N per digit plane)
 constexpr int kZK = 128;                     // source columns j2 per window (8 K-steps of 16)
 constexpr int kZD = 6;                       // digits per factor
-constexpr int kZRows = kZK + kZM - 16;       // strip rows: 240
-constexpr int kZSeg = kZK + kZM - 1;         // distinct offsets q per window: 255
+constexpr int kZWin = kZK + kZM - 8;        // strip rows (window-table rows per window): 248
+constexpr int kZStages = 3;                  // operand stages
 constexpr int kTopBits = 7, kDigBits = 9;
-constexpr uint32_t kStripPlane = 2u * kZRows * 16u;            // bytes per digit plane (7680)
-constexpr uint32_t kStripBytes = kZD * kStripPlane;            // 46080
+constexpr uint32_t kStripPlane = kZWin * 16u;                  // bytes per digit plane (3968)
+constexpr uint32_t kStripBytes = kZD * kStripPlane;            // 23808
 constexpr uint32_t kBRows = kZD * kZC;                         // B rows: 6 planes x 32 lines
 constexpr uint32_t kBGroup = kBRows * 16u;                     // bytes per 8-column group (3072)
 constexpr uint32_t kBBytes = (kZK / 8) * kBGroup;              // 49152
-constexpr uint32_t kStageBytes = kStripBytes + kBBytes;
-constexpr int kZSmem = 2 * (int)kStageBytes;                   // 190464
+constexpr uint32_t kStageBytes = kStripBytes + kBBytes;        // 72960 (a multiple of 128)
+constexpr int kZSmem = kZStages * (int)kStageBytes;            // 218880
 constexpr long long kSpinLimit = 1LL << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -102,6 +103,19 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t phase) {
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
         : "r"(bar), "r"(phase), "r"(1000u)
+        : "memory");
+    return ok != 0;
+}
+
+// non-blocking probe: one shared-memory round trip, cheaper than try_wait on a phase that has
+// already completed
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
         : "memory");
     return ok != 0;
 }
@@ -153,17 +167,31 @@ __global__ void absmax_kernel(const double *__restrict__ v, long long count, uns
     if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
-// Table digits: out[a][d][q] = digit a of t(d, q) / sigma_t, q = the fast offset; t(0, 0) -> 0.
-__global__ void table_digits_kernel(const double *__restrict__ t64, int n, const unsigned long long *__restrict__ maxbits,
-                                    uint16_t *__restrict__ out) {
+// Window table of the A operand.  With v_d(p) = t(d, |n - 1 - p|) (0 outside the table and at
+// t(0, 0), the diagonal), row p of plane a for offset d holds digit a of v_d(p), ..., v_d(p + 7):
+// out[(d D + a) 2n + p] (16 bytes), p < 2n.  A run of 248 consecutive rows is the Toeplitz strip of
+// one window (see kz_matvec_tc), so a window's A operand is one TMA copy.  One thread per (d, p).
+__global__ void window_table_kernel(const double *__restrict__ t64, int n, const unsigned long long *__restrict__ maxbits,
+                                    uint4 *__restrict__ out) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long T = (long long)n * n;
-    if (e >= T) return;
+    const int rows = 2 * n;
+    if (e >= (long long)n * rows) return;
+    const int d = (int)(e / rows), p = (int)(e % rows);
     const double sig = scale_of(*maxbits);
-    float d[kZD];
-    digits6(e == 0 ? 0.0 : t64[e] / sig, d);
+    uint32_t w[kZD][4];
 #pragma unroll
-    for (int a = 0; a < kZD; ++a) out[(long long)a * T + e] = bf16_bits(d[a]);
+    for (int k = 0; k < 8; k += 2) {
+        float d0[kZD], d1[kZD];
+        const int q0 = abs(n - 1 - (p + k)), q1 = abs(n - 1 - (p + k + 1));
+        const long long e0 = (long long)d * n + q0, e1 = (long long)d * n + q1;
+        digits6(q0 < n && e0 != 0 ? t64[e0] / sig : 0.0, d0);
+        digits6(q1 < n && e1 != 0 ? t64[e1] / sig : 0.0, d1);
+#pragma unroll
+        for (int a = 0; a < kZD; ++a) w[a][k >> 1] = (uint32_t)bf16_bits(d0[a]) | ((uint32_t)bf16_bits(d1[a]) << 16);
+    }
+#pragma unroll
+    for (int a = 0; a < kZD; ++a)
+        out[((long long)d * kZD + a) * rows + p] = make_uint4(w[a][0], w[a][1], w[a][2], w[a][3]);
 }
 
 // x digits in the B-operand source layout: [8-column group][plane][row + 32][8 values], rows
@@ -193,24 +221,29 @@ __global__ void x_digits_kernel(const double *__restrict__ x, int n, const unsig
 // j2 in [128 kb, +128), d1 in its share of [i1_0 - n + 1, i1_0 + 31].  Writes the CTA's integer
 // partial sums (units 2^-F of a level-0 product) to part[z][i].
 //
+// MMA row m is target i2_0 + 127 - m, so that the A tile entry (m, k) of a window, t(|d1|,
+// |i2_0 + 127 - kb - (m + k)|), depends on m + k alone and rises with both: the tile of K-step s
+// is the window-table strip seen from row 16 s, and its second 8-column half is the same strip
+// 8 rows further on (core-matrix strides of 128 bytes in both directions).
+//
 // Warp roles, handing over through mbarriers (no block-wide barrier inside the window loop):
-//   warp 0      one lane issues a window's 48 MMAs once its strip and B operand are in place and
-//               its accumulator set has been read, and commits them to mdone[stage];
-//   warp 1      one lane: the TMA copy of the B operand into a free stage (expect_tx on bfull);
-//   warps 2-3   the strip: table digits fetched a window ahead into registers, staged as pair
-//               words, expanded into the 240-row strip (one lane per warp arrives on sfull);
-//   warps 4-7   read a finished window's accumulator set (their TMEM lane quarter, all 32 lines),
-//               release it (aempty[stage]) and add it into the 64-bit sums.
-// Window w uses stage and accumulator set w & 1; the k-th phase of a stage's barrier belongs to
-// window 2k + stage, so waits use parity (w >> 1) & 1.  No barrier can run two phases ahead of a
-// waiter (each role's next use waits for the consumer of the previous one).  Every wait is
-// bounded: a role that gives up sets the shared abort flag, which ends the other roles' waits.
-__global__ void __launch_bounds__(256, 1)
-kz_matvec_tc(const uint16_t *__restrict__ tdig, const __grid_constant__ CUtensorMap xmap, int n, int dsplit, int F,
-             long long *__restrict__ part, int *__restrict__ err) {
-    extern __shared__ __align__(1024) unsigned char zsm[];  // 2 x [strip | B]
-    __shared__ __align__(16) uint32_t pw[kZD][kZSeg + 1];   // strip source: word j = (E_j, E_j+1)
-    __shared__ __align__(8) uint64_t sfull[2], bfull[2], mdone[2], aempty[2];
+//   warp 0      one lane issues a window's 48 MMAs once full[stage] has completed; commits them
+//               to sfree[stage] and afull[set];
+//   warp 1      one lane: once the stage is free (sfree) and the window's accumulator set has been
+//               read (aempty), the two TMA copies of the window (strip, B operand), completing
+//               full[stage] (expect_tx);
+//   warps 2-5   read a finished window's accumulator set (TMEM lane quarter warp & 3, all 32
+//               lines), release it (aempty[set]) and add it into the 64-bit sums.
+// Window w uses operand stage w % kZStages (its (w / kZStages)-th use, so waits take parity
+// (w / kZStages) & 1) and accumulator set w & 1 (parity (w >> 1) & 1).  No barrier can run two
+// phases ahead of a waiter (each role's next use waits for the consumer of the previous one).
+// Every wait is bounded: a role that gives up sets the shared abort flag, which ends the other
+// roles' waits.
+__global__ void __launch_bounds__(192, 1)
+kz_matvec_tc(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ CUtensorMap xmap, int n, int dsplit,
+             int F, long long *__restrict__ part, int *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char zsm[];  // kZStages x [strip | B]
+    __shared__ __align__(8) uint64_t full[kZStages], sfree[kZStages], afull[2], aempty[2];
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
 
@@ -221,7 +254,7 @@ kz_matvec_tc(const uint16_t *__restrict__ tdig, const __grid_constant__ CUtensor
     const int dn = n + kZC - 1, per = (dn + dsplit - 1) / dsplit;
     const int d_begin = i1_0 - n + 1 + ds * per;
     const int T = max(0, min(per, dn - ds * per));
-    const int q_lo = kb - i2_0 - (kZM - 1);  // first strip offset: strip word j holds q_lo + j
+    const int R0 = n - kZM - i2_0 + kb;  // first window-table row of the strip, in [0, 2n - 256]
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -229,10 +262,12 @@ kz_matvec_tc(const uint16_t *__restrict__ tdig, const __grid_constant__ CUtensor
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
+        for (int st = 0; st < kZStages; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[st])), "r"(1u));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sfree[st])), "r"(1u));
+        }
         for (int st = 0; st < 2; ++st) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sfull[st])), "r"(2u));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bfull[st])), "r"(1u));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mdone[st])), "r"(1u));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&afull[st])), "r"(1u));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&aempty[st])), "r"(4u));
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -247,6 +282,7 @@ kz_matvec_tc(const uint16_t *__restrict__ tdig, const __grid_constant__ CUtensor
     // bounded wait for a phase of a barrier; false (and the abort flag set) if it ran out or if
     // another role gave up
     auto wait_bar = [&](uint64_t *bar, uint32_t parity) -> bool {
+        if (mbar_test(smem_u32(bar), parity)) return true;
         for (long long i = 0; i < kSpinLimit / 8; ++i) {
             if (mbar_try(smem_u32(bar), parity)) return true;
             if (abort_flag) return false;
@@ -261,7 +297,7 @@ kz_matvec_tc(const uint16_t *__restrict__ tdig, const __grid_constant__ CUtensor
         return __shfl_sync(0xffffffffu, ok, 0) != 0;
     };
 
-    long long acc[32];  // warps 4-7: lines i1_0 + c (c < 32) at target i2_0 + 32 (warp & 3) + lane
+    long long acc[32];  // warps 2-5: lines i1_0 + c (c < 32) at MMA row 32 (warp & 3) + lane
 #pragma unroll
     for (int c = 0; c < 32; ++c) acc[c] = 0;
 
@@ -273,114 +309,72 @@ kz_matvec_tc(const uint16_t *__restrict__ tdig, const __grid_constant__ CUtensor
             for (int a = 0; a < kZD; ++a) idesc[a] = idesc_bf16((kZD - a) * kZC);
             int issued = 0;
             for (int w = 0; w < T; ++w) {
-                const int sb = w & 1;
-                const uint32_t par = (uint32_t)(w >> 1) & 1u;
-                if (!wait_bar(&sfull[sb], par) || !wait_bar(&bfull[sb], par)) break;
-                if (w >= 2 && !wait_bar(&aempty[sb], par ^ 1u)) break;
+                const int sb = w % kZStages, set = w & 1;
+                // operands in place; the accumulator set is free too (the copies were issued after
+                // its release)
+                if (!wait_bar(&full[sb], (uint32_t)(w / kZStages) & 1u)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t strip = smem0 + sb * kStageBytes, bop = strip + kStripBytes;
-                const uint64_t a0 = make_desc(strip, kZRows * 16u, 128u), b0 = make_desc(bop, kBGroup, 128u);
-                const uint32_t dt = tmem + sb * 256u;
+                const uint64_t a0 = make_desc(strip, 128u, 128u), b0 = make_desc(bop, kBGroup, 128u);
+                const uint32_t dt = tmem + set * 256u;
 #pragma unroll 1
                 for (int s = 0; s < kZK / 16; ++s) {
                     const uint64_t bd = b0 + (uint64_t)((2u * s * kBGroup) >> 4);
 #pragma unroll
                     for (int a = 0; a < kZD; ++a) {
-                        const uint64_t ad = a0 + (uint64_t)((a * kStripPlane + (uint32_t)(kZRows - kZM - 16 * s) * 16u) >> 4);
+                        const uint64_t ad = a0 + (uint64_t)((a * kStripPlane + (uint32_t)s * 256u) >> 4);
                         mma_bf16(dt + (uint32_t)(a * kZC), ad, bd, idesc[a], (s > 0 || a > 0) ? 1u : 0u);
                     }
                 }
-                mma_commit(smem_u32(&mdone[sb]));
+                mma_commit(smem_u32(&sfree[sb]));
+                mma_commit(smem_u32(&afull[set]));
                 issued = w + 1;
             }
             // every MMA issued has completed before the accumulators are freed (commit tracks
             // all earlier MMAs of this thread); this wait ignores the abort flag (still bounded)
-            if (issued > 0 && !mbar_wait(smem_u32(&mdone[(issued - 1) & 1]), (uint32_t)((issued - 1) >> 1) & 1u))
+            if (issued > 0 && !mbar_wait(smem_u32(&afull[(issued - 1) & 1]), (uint32_t)((issued - 1) >> 1) & 1u))
                 abort_flag = 1;
         }
         __syncwarp();
     } else if (warp == 1) {
-        // ---- B operand: six digit planes of the 32 source lines over the 128 columns ----
+        // ---- operands of a window: the strip (six planes of 248 window-table rows) and the B
+        // operand (six digit planes of the 32 source lines over the 128 columns) ----
         int issued = 0;
         for (int w = 0; w < T; ++w) {
-            const int sb = w & 1;
-            const uint32_t par = (uint32_t)(w >> 1) & 1u;
-            if (w >= 2 && !warp_wait(&mdone[sb], par ^ 1u)) break;  // the stage's last MMAs are done
+            const int sb = w % kZStages;
+            if (w >= kZStages && !warp_wait(&sfree[sb], ((uint32_t)(w / kZStages) & 1u) ^ 1u)) break;
+            // the window's accumulator set must have been read (window w - 2): full[sb] then tells
+            // the MMA lane both things
+            if (w >= 2 && !warp_wait(&aempty[w & 1], ((uint32_t)(w >> 1) & 1u) ^ 1u)) break;
             if (lane == 0) {
-                const uint32_t bar = smem_u32(&bfull[sb]);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBBytes) : "memory");
-                // box (32 rows x 8 values, 6 planes, 16 groups) at ((first source row + 32) x 8, 0,
-                // kb / 8): the padded rows keep every coordinate inside the tensor, and x is a whole
-                // number of 16-byte rows
+                const uint32_t bar = smem_u32(&full[sb]), dst = smem0 + sb * kStageBytes;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kStageBytes)
+                             : "memory");
+                // strip: box (8 values, 248 rows, 6 planes) at (0, R0, |d1| x 6)
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                    ::"r"(dst), "l"(reinterpret_cast<uint64_t>(&wmap)), "r"(0), "r"(R0), "r"(abs(d_begin + w) * kZD),
+                    "r"(bar)
+                    : "memory");
+                // B: box (32 rows x 8 values, 6 planes, 16 groups) at ((first source row + 32) x 8,
+                // 0, kb / 8): the padded rows keep every coordinate inside the tensor, and x is a
+                // whole number of 16-byte rows
                 const int r0 = i1_0 - (d_begin + w);  // first source line, in [-31, n - 1]
                 asm volatile(
                     "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                    ::"r"(smem0 + sb * kStageBytes + kStripBytes), "l"(reinterpret_cast<uint64_t>(&xmap)),
-                    "r"((r0 + 32) * 8), "r"(0), "r"(kb >> 3), "r"(bar)
+                    ::"r"(dst + kStripBytes), "l"(reinterpret_cast<uint64_t>(&xmap)), "r"((r0 + 32) * 8), "r"(0),
+                    "r"(kb >> 3), "r"(bar)
                     : "memory");
             }
             __syncwarp();
             issued = w + 1;
         }
-        // no copy may still be landing when the CTA ends (waits that ignore the abort flag, bounded)
+        // no copy may still be landing when the CTA ends (waits that ignore the abort flag, bounded;
+        // an earlier window's copies completed before its stage was reused)
         if (lane == 0)
-            for (int w = max(0, issued - 2); w < issued; ++w)
-                if (!mbar_wait(smem_u32(&bfull[w & 1]), (uint32_t)(w >> 1) & 1u)) abort_flag = 1;
+            for (int w = max(0, issued - kZStages); w < issued; ++w)
+                if (!mbar_wait(smem_u32(&full[w % kZStages]), (uint32_t)(w / kZStages) & 1u)) abort_flag = 1;
         __syncwarp();
-    } else if (warp < 4) {
-        // ---- strip (64 threads); both warps run every window and both named barriers, so an
-        // abort never leaves one of them waiting at a barrier.  Thread st owns pair words
-        // 4 st .. 4 st + 3 of every plane (five table values, fetched a window ahead) and strip
-        // rows st, st + 64, ... ----
-        const int st = tid - 64, j0 = 4 * st;
-        uint32_t ew[kZD][4];
-        auto fetch_w = [&](int w) {
-            const int ad1 = abs(d_begin + w);
-            uint32_t e[kZD][5];
-#pragma unroll
-            for (int k = 0; k < 5; ++k) {
-                const int j = j0 + k, aq = abs(q_lo + j);
-                const bool in = w < T && j < kZSeg && aq < n;
-                const uint16_t *src = tdig + (long long)ad1 * n + aq;
-#pragma unroll
-                for (int a = 0; a < kZD; ++a) e[a][k] = in ? (uint32_t)__ldg(src + (long long)a * N) : 0u;
-            }
-#pragma unroll
-            for (int a = 0; a < kZD; ++a)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) ew[a][k] = e[a][k] | (e[a][k + 1] << 16);
-        };
-        fetch_w(0);
-        for (int w = 0; w < T; ++w) {
-            const int sb = w & 1;
-            const uint32_t par = (uint32_t)(w >> 1) & 1u;
-            bool ok = !abort_flag;
-            if (ok && w >= 2) ok = warp_wait(&mdone[sb], par ^ 1u);  // the stage's last MMAs are done
-            if (ok) {
-#pragma unroll
-                for (int a = 0; a < kZD; ++a)
-                    *reinterpret_cast<uint4 *>(&pw[a][j0]) = make_uint4(ew[a][0], ew[a][1], ew[a][2], ew[a][3]);
-            }
-            asm volatile("bar.sync 1, 64;" ::: "memory");
-            if (ok) {
-                fetch_w(w + 1);
-                unsigned char *strip = zsm + sb * kStageBytes;
-                for (int u = st; u < kZRows; u += 64) {
-                    const int js = kZRows - 1 - u;  // row u, column group g: words js + 8 g + 2 k
-#pragma unroll
-                    for (int a = 0; a < kZD; ++a) {
-                        const uint32_t *src = &pw[a][js];
-                        unsigned char *dst = strip + a * kStripPlane + u * 16;
-                        *reinterpret_cast<uint4 *>(dst) = make_uint4(src[0], src[2], src[4], src[6]);
-                        *reinterpret_cast<uint4 *>(dst + kZRows * 16) = make_uint4(src[8], src[10], src[12], src[14]);
-                    }
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&sfull[sb])) : "memory");
-            }
-            asm volatile("bar.sync 1, 64;" ::: "memory");  // pw is read by both warps before it changes
-        }
     } else {
         // ---- accumulator reads and exact sums (TMEM lane quarter warp & 3, all 32 lines) ----
         const int q4 = warp & 3;
@@ -388,11 +382,10 @@ kz_matvec_tc(const uint16_t *__restrict__ tdig, const __grid_constant__ CUtensor
         const int w2 = 1 << (F - 2 * kDigBits);
         const float w3 = __int_as_float((127 + F - 3 * kDigBits) << 23);  // 2^(F - 27)
         for (int w = 0; w < T; ++w) {
-            const int sb = w & 1;
-            const uint32_t par = (uint32_t)(w >> 1) & 1u;
-            if (!warp_wait(&mdone[sb], par)) break;
+            const int set = w & 1;
+            if (!warp_wait(&afull[set], (uint32_t)(w >> 1) & 1u)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t base = tmem + ((uint32_t)(32 * q4) << 16) + sb * 256u;
+            const uint32_t base = tmem + ((uint32_t)(32 * q4) << 16) + set * 256u;
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) {
                 const uint32_t cb = base + 16u * hh;
@@ -418,7 +411,7 @@ kz_matvec_tc(const uint16_t *__restrict__ tdig, const __grid_constant__ CUtensor
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
                     if (lane == 0)
-                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&aempty[sb])) : "memory");
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&aempty[set])) : "memory");
                 }
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
@@ -434,9 +427,9 @@ kz_matvec_tc(const uint16_t *__restrict__ tdig, const __grid_constant__ CUtensor
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (!abort_flag) {
-        if (warp >= 4) {
+        if (warp >= 2) {
             long long *outp = part + (long long)blockIdx.z * N;
-            const int i2 = i2_0 + 32 * (warp & 3) + lane;
+            const int i2 = i2_0 + (kZM - 1) - (32 * (warp & 3) + lane);
 #pragma unroll
             for (int c = 0; c < 32; ++c) outp[(long long)(i1_0 + c) * n + i2] = acc[c];
         }
@@ -483,7 +476,7 @@ static int kz_dsplit(int n, int sms) {
 
 int prepare_tc_exact(const ie_problem *p_) {
     ie_problem *p = const_cast<ie_problem *>(p_);
-    if (p->d_zt_dig) return IE_OK;
+    if (p->d_zt_win) return IE_OK;
     IE_TRY_CUDA(cudaFuncSetAttribute(kz_matvec_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kZSmem));
     const long long T = (long long)p->n * p->n;
     IE_TRY_CUDA(cudaMalloc(&p->d_zt_max, sizeof(unsigned long long)));
@@ -492,8 +485,11 @@ int prepare_tc_exact(const ie_problem *p_) {
     absmax_kernel<<<std::max(1, (int)std::min<long long>(1024, (T - 1 + 255) / 256)), 256>>>(p->d_table64 + 1, T - 1,
                                                                                           p->d_zt_max);
     IE_LAUNCHED();
-    IE_TRY_CUDA(cudaMalloc(&p->d_zt_dig, sizeof(uint16_t) * kZD * T));
-    table_digits_kernel<<<(unsigned)((T + 255) / 256), 256>>>(p->d_table64, p->n, p->d_zt_max, p->d_zt_dig);
+    // window table: n offsets x 6 planes x 2n rows of 16 bytes (192 n^2 bytes)
+    const long long rows = 2 * T;
+    IE_TRY_CUDA(cudaMalloc(&p->d_zt_win, sizeof(uint4) * kZD * rows));
+    window_table_kernel<<<(unsigned)((rows + 255) / 256), 256>>>(p->d_table64, p->n, p->d_zt_max,
+                                                                 static_cast<uint4 *>(p->d_zt_win));
     IE_LAUNCHED();
     IE_TRY_CUDA(cudaDeviceSynchronize());
     return IE_OK;
@@ -520,7 +516,7 @@ int launch_matvec_tc_exact(const ie_problem *p, const double *x, long long ldx, 
         ie_set_error("ie_matvec: the exact tensor-core matvec needs a 2D grid with n a multiple of 128, n <= 4096");
         return IE_ERR_ARG;
     }
-    if (!p->d_zt_dig) {
+    if (!p->d_zt_win) {
         ie_set_error("ie_matvec: the exact tensor-core matvec was not prepared for this problem");
         return IE_ERR_ARG;
     }
@@ -550,8 +546,18 @@ int launch_matvec_tc_exact(const ie_problem *p, const double *x, long long ldx, 
     const CUresult cr = encode(&xmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, xd.ptr, gdim, gstride, box, estride,
                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) {
-        ie_set_error("ie_matvec: cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")");
+    // the window table as a 3D tensor of 16-bit words: (8 values, 2n rows, n offsets x 6 planes);
+    // one box (8 values, 248 rows, 6 planes) is a CTA's strip for one d1
+    CUtensorMap wmap;
+    const cuuint64_t wdim[3] = {8, (cuuint64_t)2 * n, (cuuint64_t)n * kZD};
+    const cuuint64_t wstride[2] = {16, (cuuint64_t)2 * n * 16};
+    const cuuint32_t wbox[3] = {8, (cuuint32_t)kZWin, (cuuint32_t)kZD};
+    const CUresult cw = cr != CUDA_SUCCESS ? cr
+                                           : encode(&wmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, p->d_zt_win, wdim, wstride, wbox,
+                                                    estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cw != CUDA_SUCCESS) {
+        ie_set_error("ie_matvec: cuTensorMapEncodeTiled failed (" + std::to_string((int)cw) + ")");
         return IE_ERR_CUDA;
     }
     const dim3 g(n / kZM, n / kZC, nparts);
@@ -564,7 +570,7 @@ int launch_matvec_tc_exact(const ie_problem *p, const double *x, long long ldx, 
         const long long chunks = (long long)(n / 8) * (n + 64);
         x_digits_kernel<<<(unsigned)((chunks + 255) / 256), 256, 0, s>>>(xk, n, mx.as<unsigned long long>(), xd.as<uint4>());
         IE_LAUNCHED();
-        kz_matvec_tc<<<g, 256, kZSmem, s>>>(p->d_zt_dig, xmap, n, ds, F, part.as<long long>(), p->d_err);
+        kz_matvec_tc<<<g, 192, kZSmem, s>>>(wmap, xmap, n, ds, F, part.as<long long>(), p->d_err);
         IE_LAUNCHED();
         kz_combine_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(part.as<long long>(), nparts, N, xk, yk, p->diag,
                                                                      p->d_zt_max, mx.as<unsigned long long>(), F);
