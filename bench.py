@@ -57,7 +57,7 @@ FP32_LANES_PER_SM = 128
 # bench reports null.
 NCU_TRAFFIC = {"24904137a1834c92": 4624128}  # k2_accurate_2d<true,1>, n = 512, bytes per launch
 # the same for the exact tensor-core matvec, keyed by tc_exact_source_hash()
-NCU_TRAFFIC_KZ = {"436f86b1f61fb2d0": 8422144}  # kz_matvec_tc, n = 512, bytes per launch
+NCU_TRAFFIC_KZ = {"91affb0f46974cb4": 85065472}  # kz_matvec_tc, n = 512, bytes per launch
 # BF16 digit products per pair of the exact tensor-core matvec (six digits per factor, levels 0..5)
 KZ_PRODUCTS_PER_PAIR = 21
 

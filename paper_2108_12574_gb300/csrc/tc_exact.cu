@@ -227,11 +227,12 @@ __global__ void x_digits_kernel(const double *__restrict__ x, int n, const unsig
 // 8 rows further on (core-matrix strides of 128 bytes in both directions).
 //
 // Warp roles, handing over through mbarriers (no block-wide barrier inside the window loop):
-//   warp 0      one lane issues a window's 48 MMAs once full[stage] has completed; commits them
-//               to sfree[stage] and afull[set];
-//   warp 1      one lane: once the stage is free (sfree) and the window's accumulator set has been
-//               read (aempty), the two TMA copies of the window (strip, B operand), completing
-//               full[stage] (expect_tx);
+//   warp 0      one lane issues a window's 48 MMAs once its operands are in place (full[stage])
+//               and its accumulator set has been read (aempty[set]); commits them to
+//               sfree[stage] and afull[set];
+//   warp 1      one lane: once the stage is free (sfree), the two TMA copies of the window
+//               (strip, B operand), completing full[stage] (expect_tx); copies run up to two
+//               windows ahead;
 //   warps 2-5   read a finished window's accumulator set (TMEM lane quarter warp & 3, all 32
 //               lines), release it (aempty[set]) and add it into the 64-bit sums.
 // Window w uses operand stage w % kZStages (its (w / kZStages)-th use, so waits take parity
@@ -310,9 +311,8 @@ kz_matvec_tc(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ C
             int issued = 0;
             for (int w = 0; w < T; ++w) {
                 const int sb = w % kZStages, set = w & 1;
-                // operands in place; the accumulator set is free too (the copies were issued after
-                // its release)
                 if (!wait_bar(&full[sb], (uint32_t)(w / kZStages) & 1u)) break;
+                if (w >= 2 && !wait_bar(&aempty[set], ((uint32_t)(w >> 1) & 1u) ^ 1u)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t strip = smem0 + sb * kStageBytes, bop = strip + kStripBytes;
                 const uint64_t a0 = make_desc(strip, 128u, 128u), b0 = make_desc(bop, kBGroup, 128u);
@@ -343,9 +343,6 @@ kz_matvec_tc(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ C
         for (int w = 0; w < T; ++w) {
             const int sb = w % kZStages;
             if (w >= kZStages && !warp_wait(&sfree[sb], ((uint32_t)(w / kZStages) & 1u) ^ 1u)) break;
-            // the window's accumulator set must have been read (window w - 2): full[sb] then tells
-            // the MMA lane both things
-            if (w >= 2 && !warp_wait(&aempty[w & 1], ((uint32_t)(w >> 1) & 1u) ^ 1u)) break;
             if (lane == 0) {
                 const uint32_t bar = smem_u32(&full[sb]), dst = smem0 + sb * kStageBytes;
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kStageBytes)
