@@ -117,3 +117,50 @@ def test_autotune_switch_without_gpu():
     iedd.ie_autotune(2)
     assert iedd.ie_autotune_report() == ""
     iedd.ie_autotune(1 if prev else 0)
+
+
+C_CALLER = r"""
+#include <stdio.h>
+#include <string.h>
+#include "iedd.h"
+
+int main(void) {
+    pcg_opts o;
+    pcg_report rep;
+    ie_problem *p = NULL;
+    memset(&rep, 0, sizeof rep);
+    pcg_default_opts(&o);
+    if (o.max_it != 1000 || o.replace_every != 50 || o.precision != IE_MIXED) return 2;
+    if (strstr(ie_version(), "sm_103a") == NULL) return 3;
+    /* host-side argument checks return before any device work */
+    if (ie_discretize(5, 8, 0.0, IE_GRID_TEXT, 0, &p) != IE_ERR_ARG || p != NULL) return 4;
+    if (pcg_solve(NULL, NULL, NULL, NULL, 1, 1, &o, &rep, NULL) != IE_ERR_ARG) return 5;
+    if (dd_apply(NULL, NULL, NULL, 1, 1, NULL) != IE_ERR_ARG) return 6;
+    if (ie_last_error()[0] == '\0') return 7;
+    ie_destroy(NULL);
+    dd_partition_destroy(NULL);
+    dd_factor_destroy(NULL);
+    ws_destroy(NULL);
+    printf("ok %s\n", ie_version());
+    return 0;
+}
+"""
+
+
+def test_plain_c_caller_builds_links_and_runs(lib, tmp_path):
+    # the header is plain C (C99, no C++ or CUDA types) and a C program links the library and
+    # calls its host-side entry points; nothing here touches a GPU
+    src = tmp_path / "caller.c"
+    src.write_text(C_CALLER)
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(lib._name)
+    cuda_lib = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64")
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", str(src),
+                        "-I", os.path.join(ROOT, "include"), "-L", libdir, "-liedd",
+                        f"-Wl,-rpath,{libdir}", f"-Wl,-rpath-link,{cuda_lib}", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    env = dict(os.environ, LD_LIBRARY_PATH=cuda_lib + os.pathsep + os.environ.get("LD_LIBRARY_PATH", ""))
+    r = subprocess.run([str(exe)], capture_output=True, text=True, env=env, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert r.stdout.startswith("ok ")
