@@ -43,3 +43,14 @@ def test_max_over_ranks_single_process():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.max_over_ranks(2.5) == 2.5
+
+
+def test_reference_arm_runs_on_rank_0_only():
+    # under torchrun the reference arm (the CPU oracle) runs on rank 0 alone; the other ranks
+    # exit 0 at once, print nothing and touch no device
+    import subprocess
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "3"], capture_output=True, text=True, env=env, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
