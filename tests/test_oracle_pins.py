@@ -237,6 +237,30 @@ def test_projection_identities_and_lemma():
         assert np.allclose(P @ x, x, atol=1e-10)
 
 
+def test_apply_independent_of_order_inside_blocks():
+    # the order of the indices inside a subdomain is a reading (ascending); R_i^T A_i^{-1} R_i
+    # is the same operator for any order, so permuted index sets give the same z
+    n = 16
+    blocks = O.partition(2, n, 4, 1, O.SCHWARZ)
+    rng = np.random.default_rng(3)
+    shuffled = [b[rng.permutation(len(b))] for b in blocks]
+    r = I.uniform_rhs(n * n, 4)
+    z1 = O.apply(O.factor(2, n, blocks), blocks, r)
+    z2 = O.apply(O.factor(2, n, shuffled), shuffled, r)
+    assert np.linalg.norm(z1 - z2) <= 1e-12 * np.linalg.norm(z1)
+
+
+def test_second_kind_shift_moves_the_spectrum():
+    # the a u term of the second-kind equation adds a to the diagonal only: every eigenvalue of
+    # A moves by exactly a, and the shifted blocks are the shifted sub-matrices
+    n, a = 8, 0.3
+    A0, Aa = O.dense_matrix(2, n), O.dense_matrix(2, n, a_shift=a)
+    assert np.array_equal(Aa - np.diag(np.diag(Aa)), A0 - np.diag(np.diag(A0)))
+    assert np.allclose(scipy.linalg.eigvalsh(Aa), scipy.linalg.eigvalsh(A0) + a, atol=1e-13)
+    b = O.partition(2, n, 2, 1, O.SCHWARZ)[0]
+    assert np.allclose(O.block_matrices(2, n, [b], a_shift=a)[0], Aa[np.ix_(b, b)], atol=0, rtol=0)
+
+
 @pytest.mark.parametrize("dim,n,m", [(2, 8, 2), (2, 16, 2), (3, 4, 2), (2, 16, 4)])
 def test_lambda_max_bounds(dim, n, m):
     # Thm th:max: lambda_max(T^{-1} A) <= D; Thm th:max48: = 2^d when D = 2^d (Schwarz)
