@@ -81,3 +81,61 @@ def test_features_scale_invariant():
     b, rl2 = U.features(7.0 * f, 16)
     assert np.allclose(a, b) and np.isclose(rl2, 7.0 * rl)
     assert np.isclose(np.sqrt(np.mean(a[..., 0] ** 2)), 1.0)
+
+
+# --- Planted slips in the U-Net oracle, each caught by one of the pins above -----------------
+
+def _fails(pin):
+    try:
+        pin()
+    except AssertionError:
+        return True
+    return False
+
+
+def test_slip_flipped_forward_kernel_is_caught(monkeypatch):
+    # convolution (kernel flipped) instead of the cross-correlation the layout defines
+    orig = U.conv3x3
+    monkeypatch.setattr(U, "conv3x3", lambda x, W, b: orig(x, W[:, ::-1, ::-1, :], b))
+    assert _fails(test_conv3x3_orientation_by_shifts)
+    assert _fails(test_gradient_matches_central_differences)
+
+
+def test_slip_unflipped_data_gradient_is_caught(monkeypatch):
+    # the data gradient must run the kernel the other way round; reading it as the forward
+    # direction (offsets not mirrored) is a classic slip
+    def bad(x, W, dout):
+        B, H, Wd, C = x.shape
+        xp = np.zeros((B, H + 2, Wd + 2, C))
+        xp[:, 1:-1, 1:-1, :] = x
+        dW = np.zeros_like(W)
+        dxp = np.zeros_like(xp)
+        for dy in range(3):
+            for dx in range(3):
+                dW[:, dy, dx, :] = np.einsum("bhwo,bhwi->oi", dout, xp[:, dy:dy + H, dx:dx + Wd, :])
+                dxp[:, 2 - dy:2 - dy + H, 2 - dx:2 - dx + Wd, :] += dout @ W[:, dy, dx, :]
+        return dxp[:, 1:-1, 1:-1, :], dW, dout.sum(axis=(0, 1, 2))
+    monkeypatch.setattr(U, "conv3x3_backward", bad)
+    assert _fails(test_gradient_matches_central_differences)
+
+
+def test_slip_pooling_gradient_scale_is_caught(monkeypatch):
+    # the 1/4 of the 2x2 average dropped from its gradient
+    monkeypatch.setattr(U, "avgpool2_backward", lambda d: np.repeat(np.repeat(d, 2, axis=1), 2, axis=2))
+    assert _fails(test_gradient_matches_central_differences)
+
+
+def test_slip_upsampling_gradient_averaged_is_caught(monkeypatch):
+    # nearest upsampling copies each value four times, so its gradient sums the four (not averages)
+    orig = U.upsample2_backward
+    monkeypatch.setattr(U, "upsample2_backward", lambda d: 0.25 * orig(d))
+    assert _fails(test_gradient_matches_central_differences)
+
+
+def test_slip_bf16_truncation_is_caught(monkeypatch):
+    # chopping the low 16 bits instead of rounding to nearest even
+    def chop(a):
+        x = np.asarray(a, dtype=np.float32)
+        return (x.view(np.uint32) & np.uint32(0xFFFF0000)).view(np.float32).astype(np.float64)
+    monkeypatch.setattr(U, "bf16_round", chop)
+    assert _fails(test_bf16_rounding)
