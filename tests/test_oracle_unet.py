@@ -1,5 +1,6 @@
 """Pins of the FP64 U-Net oracle (no GPU): the convolution's orientation against shifted
-inputs, pooling/upsampling identities, and every gradient against central finite differences."""
+inputs, pooling/upsampling identities, and every gradient against central finite differences.
+The second half plants slips in the oracle and checks that one of these pins catches each."""
 import numpy as np
 import pytest
 
