@@ -205,6 +205,19 @@ def gpu_id_of(torch, dev):
 # ------------------------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of the workload, scaled
 # ------------------------------------------------------------------------------------------
+def cpu_model() -> str:
+    """The host CPU's model name and architecture (for the CPU-baseline record)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return f"{line.split(':', 1)[1].strip()} ({platform.machine()})"
+    except Exception:
+        pass
+    return platform.machine() or "unknown"
+
+
 def cpu_baseline(iterations: int, seed: int = 0):
     import numpy as np
 
@@ -229,7 +242,7 @@ def cpu_baseline(iterations: int, seed: int = 0):
     t_ap = (time.perf_counter() - t0) * len(blocks) / len(sb)
     total = t_fac + iterations * (t_mv + t_ap)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": total, "unit": "s", "cores": cores, "kind": "oracle",
+    return {"value": total, "unit": "s", "cores": cores, "cpu": cpu_model(), "kind": "oracle",
             "sample": (f"FP64 direct-sum matvec over {rows.size} of {N} rows (C, OpenMP), own Cholesky and "
                        f"triangular-solve apply on {len(sb)} of {len(blocks)} subdomains, each scaled to the "
                        f"full workload; total = factor + {iterations} iterations x (matvec + apply); "
