@@ -117,9 +117,10 @@ IEDD_API int ie_matvec(const ie_problem *p, const double *x, double *y, int nrhs
               int precision, void *stream);
 #define IE_ACCURATE 3
 #define IE_STORED 5   /* ie_matvec from the stored FP32 matrix (ie_store_matrix); HBM-bound */
-#define IE_TENSOR 6   /* FP32 SFU entries contracted with x on the tcgen05 tensor cores (3xTF32
-                         split, FP32 accumulation in tensor memory), 64 right-hand sides per CTA;
-                         same accuracy class as IE_MIXED.  Returns IE_ERR_TIMEOUT if a CTA gave
+#define IE_TENSOR 6   /* entries contracted with x on the tcgen05 tensor cores (3xTF32 split,
+                         FP32 accumulation in tensor memory), 64 right-hand sides per CTA; the
+                         entries come from the exact per-offset table for n = 32, 64 or a multiple
+                         of 128, else from the FP32 SFU; same accuracy class as IE_MIXED.  Returns IE_ERR_TIMEOUT if a CTA gave
                          up waiting for its MMAs (bounded waits; the call then synchronizes). */
 #define IE_FFT 9      /* the paper's FFT matvec (Sec. 6): A is Toeplitz in every coordinate on the
                          uniform grid, so A x is a convolution, computed in FP64 on the periodic
