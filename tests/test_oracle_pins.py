@@ -54,7 +54,24 @@ def test_2d_self_cell_scaling_law():
     d1, d2 = O.self_cell_integral(2, 1 / 64), O.self_cell_integral(2, 1 / 128)
     c0 = d1 / (1 / 64) ** 2 + math.log(1 / 64) / (2 * math.pi)
     assert abs(d2 - (1 / 128) ** 2 * (-math.log(1 / 128) / (2 * math.pi) + c0)) < 1e-18
-    assert abs(O.self_cell_integral(2, 1 / 64) - 2.0283157107762713e-04) < 1e-16
+
+
+def test_closed_forms_by_30_digit_quadrature():
+    # the same integrals by tanh-sinh quadrature at 30 digits (mpmath), which copes with the
+    # singular corner: the closed forms must hold to the last bit of FP64
+    mp = pytest.importorskip("mpmath")
+    with mp.workdps(30):
+        # int_{[0,1]^2} ln(s^2 + t^2)
+        L = mp.quad(lambda s, t: mp.log(s * s + t * t), [0, 1], [0, 1])
+        # int_{[0,1]^3} 1/|x|, innermost integral in closed form:
+        # int_0^1 dx / sqrt(x^2 + c^2) = asinh(1/c)
+        J = mp.quad(lambda y, z: mp.asinh(1 / mp.sqrt(y * y + z * z)), [0, 1], [0, 1])
+        # the 2D self-cell integral itself at h = 1/64, straight from its definition
+        h = mp.mpf(1) / 64
+        q = 4 * mp.quad(lambda x, y: -mp.log(mp.sqrt(x * x + y * y)) / (2 * mp.pi), [0, h / 2], [0, h / 2])
+    assert abs(float(L) - O.log_integral_unit_square()) <= 2e-16
+    assert abs(float(J) - O.inverse_distance_integral_unit_cube()) <= 4e-16
+    assert abs(float(q) - O.self_cell_integral(2, 1 / 64)) <= 1e-19
 
 
 def test_3d_self_cell_equals_direct_cell_quadrature():
