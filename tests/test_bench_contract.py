@@ -1,0 +1,59 @@
+"""The benchmark's command-line defaults and the reference arm's JSON line (no GPU).
+
+The reference arm is the FP64 oracle on the host cores; its timing is replaced here by a fast
+stand-in so that only the line's structure is checked.
+"""
+import json
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _args(monkeypatch, *argv):
+    monkeypatch.setattr(sys, "argv", ["bench.py", *argv])
+    return bench.parse()
+
+
+def test_defaults_are_one_gpu_with_three_warmup_steps(monkeypatch):
+    a = _args(monkeypatch)
+    assert a.gpus == 1 and a.impl == "ours" and a.kernel is None
+    assert a.warmup >= 3 and 1 <= a.steps <= 10
+    assert a.workload == bench.WORKLOAD
+
+
+def test_headline_config_names_the_workload():
+    c = bench.config_dict()
+    assert c["workload"] == bench.WORKLOAD
+    assert c["N"] == c["n"] ** c["dim"] and c["tol"] == 1e-8
+    assert "flushed" in c["l2"]
+
+
+def test_reference_line_structure(monkeypatch, capsys):
+    calls = []
+
+    def fake_baseline(iterations, seed=0):
+        calls.append(iterations)
+        return {"value": 10.0 + len(calls), "unit": "s", "cores": 4, "cpu": "test", "kind": "oracle",
+                "sample": "stand-in", "parts_s": {"matvec": 0.1, "apply": 0.01, "factor": 1.0}}
+    monkeypatch.setattr(bench, "cpu_baseline", fake_baseline)
+    monkeypatch.delenv("RANK", raising=False)
+    a = _args(monkeypatch, "--impl", "reference", "--steps", "2", "--warmup", "3")
+    assert bench.run_reference(a) == 0
+    assert len(calls) == 5  # three warm-up runs, two timed
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["metric"] == bench.METRIC and line["unit"] == "s" and line["higher_is_better"] is False
+    assert (line["n_gpus"], line["steps"], line["warmup"]) == (1, 2, 3)
+    assert line["value"] == pytest.approx((14.0 + 15.0) / 2)
+    assert line["ms_per_step"] == pytest.approx(line["value"] * 1e3)
+    assert line["config"]["workload"] == bench.WORKLOAD
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert line["vs_baseline"] is None and line["data"] == "synthetic"
