@@ -57,3 +57,34 @@ def test_reference_line_structure(monkeypatch, capsys):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert line["vs_baseline"] is None and line["data"] == "synthetic"
+
+
+def test_clock_sampler_parses_samples_and_throttle_reasons(tmp_path, monkeypatch):
+    # a stand-in nvidia-smi on PATH prints three samples; the sampler reports the median SM clock,
+    # the maximum clock and every throttle reason seen Active
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo '0, 1900, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo '0, 2070, 2070, 1200.5, 0x4, Not Active, Not Active, Not Active, Active'\n"
+                    "echo '0, 1500, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active'\n"
+                    "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ['PATH']}")
+    s = bench.ClockSampler(None)
+    s.start()
+    import time
+    for _ in range(100):  # wait until the stand-in has written its samples
+        time.sleep(0.05)
+        if open(s.path).read().count("\n") >= 3:
+            break
+    out = s.stop()
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 1900.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    s = bench.ClockSampler(None)
+    s.start()
+    assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
