@@ -438,6 +438,28 @@ def test_uniform_rhs_range_and_moments():
     assert abs(x.mean()) < 0.01 and abs(x.var() - 1 / 3) < 0.01
 
 
+def test_gaussian_noise_moments_and_independence():
+    # Box-Muller over two SplitMix64 streams: standard normal moments, and the streams of
+    # different seeds are uncorrelated
+    z = I.gaussian_noise(400000, 0)
+    assert abs(z.mean()) < 0.01 and abs(z.var() - 1.0) < 0.01
+    assert abs(np.mean(z ** 4) - 3.0) < 0.05  # normal kurtosis
+    assert abs(np.mean(np.abs(z) > 1.959964) - 0.05) < 0.003  # two-sided 5 % tail
+    w = I.gaussian_noise(400000, 1)
+    assert abs(np.mean(z * w)) < 0.01
+
+
+def test_workloads_are_well_formed():
+    # every named workload partitions uniformly (n a multiple of m) and the CBD condition
+    # 2 delta <= w holds, so the oracle and the library accept it
+    for name, w in I.WORKLOADS.items():
+        assert w["n"] % w["m"] == 0, name
+        assert 2 * w["delta"] <= w["n"] // w["m"], name
+        f = I.workload_rhs(name) if w["n"] ** w["dim"] <= 70000 else None
+        if f is not None:
+            assert f.shape[0] == w["n"] ** w["dim"] and np.all(np.isfinite(f))
+
+
 def test_grf_covariance():
     n, ell = 64, 0.1
     h = 1 / n
