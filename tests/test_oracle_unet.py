@@ -140,3 +140,17 @@ def test_slip_bf16_truncation_is_caught(monkeypatch):
         return (x.view(np.uint32) & np.uint32(0xFFFF0000)).view(np.float32).astype(np.float64)
     monkeypatch.setattr(U, "bf16_round", chop)
     assert _fails(test_bf16_rounding)
+
+
+def test_features_laplacian_stencil():
+    # the second input channel is the 5-point stencil 4 f - (four neighbours): on the quadratic
+    # f(i, j) = i^2 + j^2 every interior value is -4 (each axis' second difference is 2), and the
+    # replicated edge makes the outward second difference along a boundary row i = 0 equal to 1
+    # (f(1) - f(0) = 1 on that axis) instead of 2
+    n = 12
+    i, j = np.meshgrid(np.arange(n, dtype=np.float64), np.arange(n, dtype=np.float64), indexing="ij")
+    f = (i * i + j * j).reshape(-1)
+    a, rl = U.features(f, n)
+    lap = a[0, :, :, 1] * rl
+    assert np.allclose(lap[1:-1, 1:-1], -4.0, rtol=0, atol=1e-12)
+    assert np.allclose(lap[0, 1:-1], -3.0, rtol=0, atol=1e-12)
