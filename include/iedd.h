@@ -136,7 +136,7 @@ IEDD_API int ie_matvec(const ie_problem *p, const double *x, double *y, int nrhs
                          exactly (FP32 windows of 128 terms, then 64-bit integers).  Relative
                          error ~1e-16 of sum |A_ij x_j|.  2D with n a multiple of 128, n <= 4096
                          (IE_ERR_ARG otherwise).  The first call on a problem builds the digit
-                         table (12 N bytes, kept until ie_destroy) and synchronizes; it must not
+                         window table (192 N bytes, kept until ie_destroy) and synchronizes; it must not
                          be inside a stream capture.  Returns IE_ERR_TIMEOUT if a CTA gave up
                          waiting for its MMAs (bounded waits). */
 
