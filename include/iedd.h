@@ -259,15 +259,24 @@ typedef struct {
  *   dim, n, a_shift, grid   as ie_discretize (no problem handle is needed: the point
  *                           coordinates are derived from the grid index); N = n^dim must be
  *                           <= IE_NOALLOC_MAX_N, else IE_ERR_ARG with a message
- *   x, y                    device FP64 vectors of length N (one right-hand side); host pointers
- *                           are rejected with IE_ERR_ARG (staging them would allocate)
- *   stream                  cudaStream_t (NULL: legacy default stream); the call is asynchronous
+ *   x, y                    FP64 vectors of length N (one right-hand side) in the memory of the
+ *                           current device (device or managed memory); host pointers and
+ *                           another device's memory are rejected with IE_ERR_ARG (staging or
+ *                           peer access would allocate or fault), as are overlapping x and y
+ *   stream                  cudaStream_t of the current device (NULL: legacy default stream),
+ *                           else IE_ERR_ARG; the call is asynchronous
  * It allocates nothing: no cudaMalloc, cudaFree or allocating library routine.  Its scratch is one
- * file-scope device array of IE_NOALLOC_SCRATCH_BYTES, present on every GPU that loads the
- * library until the process exits.  The first call on a device looks up the array's address
- * (cudaGetSymbolAddress, with that device current); make that first call before any stream
- * capture.  All calls share the array: calls whose GPU work overlaps (other streams, other
- * threads) race and must be ordered by the caller.
+ * file-scope device array of IE_NOALLOC_SCRATCH_BYTES.  The array is reserved on a device when
+ * the library's device code for this call is loaded there -- lazily by default in CUDA (the
+ * first call on that device), eagerly at context creation under CUDA_MODULE_LOADING=EAGER --
+ * and it stays until the process exits.  A caller that reserves all free memory up front must
+ * therefore make one call on each device first (or load eagerly).  The first call on a device
+ * also looks up the array's address (cudaGetSymbolAddress, with that device current) and
+ * caches it for the process; make that first call before any stream capture.  The cached
+ * address does not survive cudaDeviceReset: do not use this call on a device after resetting
+ * it.  All calls share the array and each overwrites what it reads, so nothing carries over
+ * from one call to the next; calls whose GPU work overlaps (other streams, other threads)
+ * race on the array and must be ordered by the caller.
  */
 #define IE_NOALLOC_SCRATCH_BYTES (32LL << 20)
 #define IE_NOALLOC_MAX_N (4194304LL - 1024LL)

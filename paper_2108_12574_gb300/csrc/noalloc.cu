@@ -4,11 +4,13 @@
 // are all made up front.  The paper has no counterpart; this is a deployment variant.
 //
 // Everything the call needs besides the caller's x and y lives in one file-scope device array,
-// g_noalloc_scratch (IE_NOALLOC_SCRATCH_BYTES = 32 MiB, 256-byte aligned).  The array exists on
-// every GPU that loads the library until the process exits.  Host code never uses its name as
-// an address: the first call on each device looks the address up with cudaGetSymbolAddress
-// (with that device current) and caches it.  Point coordinates are derived from the grid index
-// inside the kernel, so no problem handle (and no allocation) is needed either.
+// g_noalloc_scratch (IE_NOALLOC_SCRATCH_BYTES = 32 MiB, 256-byte aligned).  The array is part of
+// this file's device code: it is reserved on a device when that code is loaded there, which
+// CUDA does lazily by default (at the first launch or symbol lookup), and it stays until the
+// process exits.  Host code never uses the array's name as an address: the first call on each
+// device looks the address up with cudaGetSymbolAddress (with that device current) and caches
+// it for the life of the process.  Point coordinates are derived from the grid index inside the
+// kernel, so no problem handle (and no allocation) is needed either.
 //
 // Calls share the array: a call overwrites every word it later reads (each split's partial sum
 // for every row, every reduction slot), so nothing has to start at zero, and calls whose GPU
@@ -20,6 +22,7 @@
 #include <string>
 
 #include "iedd_internal.cuh"
+#include "noalloc_args.h"
 
 namespace {
 
@@ -47,6 +50,18 @@ int scratch_for_current_device(double **out) {
     }
     *out = g_scratch_ptr[dev];
     return IE_OK;
+}
+
+// The device that owns p's memory: its ordinal for device memory, the current device for
+// managed memory (reachable from it), -1 for host or unregistered memory.
+int owning_device(const void *p, int current) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // clear: an unknown pointer is host memory
+        return -1;
+    }
+    if (a.type == cudaMemoryTypeManaged) return current;
+    return a.type == cudaMemoryTypeDevice ? a.device : -1;
 }
 
 __device__ __forceinline__ float4 lattice_point(long long i, int dim, int n) {
@@ -160,27 +175,27 @@ __global__ void combine_na(const double *__restrict__ partial, int nsplit, const
 
 extern "C" int ie_matvec_noalloc(int dim, int n, double a_shift, int grid, const double *x, double *y,
                                  void *stream) {
-    if (dim != 2 && dim != 3) { ie_set_error("ie_matvec_noalloc: dim must be 2 or 3"); return IE_ERR_ARG; }
-    if (n < 2) { ie_set_error("ie_matvec_noalloc: n must be >= 2"); return IE_ERR_ARG; }
-    if (grid != IE_GRID_TEXT && grid != IE_GRID_TABLE) { ie_set_error("ie_matvec_noalloc: unknown grid"); return IE_ERR_ARG; }
-    if (!std::isfinite(a_shift)) { ie_set_error("ie_matvec_noalloc: a_shift must be finite"); return IE_ERR_ARG; }
-    long long N = 1;
-    for (int d = 0; d < dim; ++d) N *= n;
-    if (N > IE_NOALLOC_MAX_N) {
-        ie_set_error("ie_matvec_noalloc: N = n^dim = " + std::to_string(N) + " exceeds the limit " +
-                     std::to_string((long long)IE_NOALLOC_MAX_N) + " of the static scratch array");
+    int dev = 0;
+    IE_TRY_CUDA(cudaGetDevice(&dev));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    NoallocArgs args;
+    args.dim = dim; args.n = n; args.grid = grid; args.a_shift = a_shift; args.x = x; args.y = y;
+    args.dev_current = dev;
+    args.x_device = x ? owning_device(x, dev) : -1;
+    args.y_device = y ? owning_device(y, dev) : -1;
+    args.stream_device = dev;
+    if (s != nullptr) IE_TRY_CUDA(cudaStreamGetDevice(s, &args.stream_device));
+    long long N = 0;
+    const char *why = "";
+    if (noalloc_check_args(args, IE_NOALLOC_MAX_N, &N, &why) != 0) {
+        std::string msg = std::string("ie_matvec_noalloc: ") + why;
+        if (dim >= 2 && dim <= 3 && n >= 2 && std::string(why).find("exceeds") != std::string::npos)
+            msg += " (" + std::to_string((long long)IE_NOALLOC_MAX_N) + " points)";
+        ie_set_error(msg);
         return IE_ERR_ARG;
     }
-    if (!x || !y) { ie_set_error("ie_matvec_noalloc: NULL vector"); return IE_ERR_ARG; }
-    if (!ie_is_device_ptr(x) || !ie_is_device_ptr(y)) {
-        ie_set_error("ie_matvec_noalloc: x and y must be device memory (host data would need staging)");
-        return IE_ERR_ARG;
-    }
-    const char *px = reinterpret_cast<const char *>(x), *py = reinterpret_cast<const char *>(y);
-    if (px < py + 8 * N && py < px + 8 * N) { ie_set_error("ie_matvec_noalloc: x and y overlap"); return IE_ERR_ARG; }
     double *scratch = nullptr;
     IE_TRY(scratch_for_current_device(&scratch));
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
 
     // constants of the collocation matrix (Sec. 2.1), as ie_discretize computes them
     const double pi = 3.14159265358979323846;
@@ -199,8 +214,6 @@ extern "C" int ie_matvec_noalloc(int dim, int n, double a_shift, int grid, const
     double *partial = scratch + kReserve;   // [split][N]
     const int ntiles = (int)((N + kThreadsNA - 1) / kThreadsNA);
     const int rt = (int)((N + kThreadsNA * kRowsNA - 1) / (kThreadsNA * kRowsNA));
-    int dev = 0;
-    IE_TRY_CUDA(cudaGetDevice(&dev));
     int sms = 0;
     IE_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     long long want = ((long long)sms * 6 * 8 + rt - 1) / rt;
