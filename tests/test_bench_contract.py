@@ -38,15 +38,20 @@ def test_headline_config_names_the_workload():
 def test_reference_line_structure(monkeypatch, capsys):
     calls = []
 
-    def fake_baseline(iterations, seed=0):
-        calls.append(iterations)
+    def fake_baseline(name, iterations):
+        calls.append((name, iterations))
         return {"value": 10.0 + len(calls), "unit": "s", "cores": 4, "cpu": "test", "kind": "oracle",
                 "sample": "stand-in", "parts_s": {"matvec": 0.1, "apply": 0.01, "factor": 1.0}}
+
+    def fake_full(name, matvec):
+        return {"value": 0.5, "unit": "s", "workload": name, "extrapolated": False}
     monkeypatch.setattr(bench, "cpu_baseline", fake_baseline)
+    monkeypatch.setattr(bench, "oracle_full_solve", fake_full)
     monkeypatch.delenv("RANK", raising=False)
     a = _args(monkeypatch, "--impl", "reference", "--steps", "2", "--warmup", "3")
     assert bench.run_reference(a) == 0
     assert len(calls) == 5  # three warm-up runs, two timed
+    assert all(c[0] == bench.WORKLOAD for c in calls)
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference"
     assert line["metric"] == bench.METRIC and line["unit"] == "s" and line["higher_is_better"] is False
@@ -57,6 +62,31 @@ def test_reference_line_structure(monkeypatch, capsys):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert line["vs_baseline"] is None and line["data"] == "synthetic"
+    # measured (not extrapolated) end-to-end oracle solves ride along: the 64^2 workload every
+    # step, the 3D 64-column workload once
+    meas = line["cpu_baseline"]["measured_end_to_end"]
+    assert set(meas) == {"ie2d_n64_schwarz_m4_d1", "ie3d_n32_schwarz_m4_d1_rhs64"}
+    assert all(v["extrapolated"] is False for v in meas.values())
+
+
+def test_headline_is_the_largest_workload():
+    # kernel pairs per matvec: N^2 per right-hand side
+    sizes = {k: (w["n"] ** w["dim"]) ** 2 * w["seeds"] for k, w in bench.WORKLOADS.items()}
+    assert bench.WORKLOAD == max(sizes, key=sizes.get) == "ie2d_n1024_schwarz_m64_d2"
+
+
+@pytest.mark.parametrize("clocks,kind", [({"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}, "burst"),
+                                         ({"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": []}, "burst"),
+                                         ({"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"]},
+                                          "sustained"),
+                                         ({"sm_mhz": 1440.0, "sm_max_mhz": 2070.0, "reasons": []}, "sustained"),
+                                         ({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]},
+                                          "sustained")])
+def test_tensor_peak_follows_the_clock_record(clocks, kind):
+    peak, got = bench.tensor_peak(clocks)
+    assert got == kind
+    key = "bf16_tflops" if kind == "burst" else "bf16_tflops_sustained"
+    assert peak == bench.measured_peak(key, -1.0) or bench.measured_peak(key, -1.0) == -1.0
 
 
 def test_clock_sampler_parses_samples_and_throttle_reasons(tmp_path, monkeypatch):
