@@ -2,33 +2,46 @@
 // inverse M_i = A_i^{-1} = W_i^T W_i (W_i = L_i^{-1}) for every block at once, FP32 storage, the
 // bulk of the flops as 3xTF32 tcgen05 MMAs (the exact subdomain solver of Sec. 4.3, Eq. e:ai).
 //
-// Blocks are cut into tiles of P = 128 rows (the last one ragged, a multiple of 32).  Per panel
-// k0 (all blocks in the same launches):
-//   KD diag_factor   one CTA per block: Cholesky of the diagonal tile in shared memory (32-wide
-//                    blocked, 32 x 32 diagonal sub-tiles in one warp's registers), its triangular
-//                    inverse Tinv in place (kept per tile), and the diagonal tile of W^T (= Tinv^T,
-//                    zero below its diagonal).
-//   panel            L_21 = A_21 Tinv^T                         (GEMM tasks, in place)
-//   trailing         A_22 -= L_21 L_21^T over the lower tiles    (GEMM tasks)
-// Then W by tile rows i = 1, 2, ...: G_ij = sum_{k=j}^{i-1} L_ik W_kj (stored transposed) and
-// W_ij = -Tinv_i G_ij (stored transposed, in W^T), and finally M_ab = sum_k W_ka W_kb for the lower
-// tiles a >= b, written to (a, b) and mirrored to (b, a) from the same values, so M_i is exactly
-// symmetric; M_i replaces L_i in the pool.
+// Blocks are cut into tiles of P = 128 rows (the last one ragged, a multiple of 32).  Per block,
+// in phases (a phase's tasks are independent of each other; phase p needs phases < p done):
+//   for each panel k0:
+//     DIAG       Cholesky of the diagonal tile in shared memory (32-wide blocked, 32 x 32
+//                diagonal sub-tiles in one warp's registers), its triangular inverse Tinv in place
+//                (kept per tile), and the diagonal tile of W^T (= Tinv^T, zero below its diagonal)
+//     PANEL      L_21 = A_21 Tinv^T                                 (GEMM tasks, in place)
+//     TRAILING   A_22 -= L_21 L_21^T over the lower tiles            (GEMM tasks)
+//   then W by tile rows i = 1, 2, ...: G_ij = sum_{k=j}^{i-1} L_ik W_kj (stored transposed), then
+//   W_ij = -Tinv_i G_ij (stored transposed, in W^T); finally M_ab = sum_k W_ka W_kb for the lower
+//   tiles a >= b, written to (a, b) and mirrored to (b, a) from the same values, so M_i is exactly
+//   symmetric; M_i replaces L_i in the pool.
 //
-// KG tc_gemm_tasks  one CTA per task C (<= 128 x 128) = s_old C + s_acc A B^T, A: m x k and B: n x k
-//                   row-major FP32 with k contiguous (k a multiple of 32).  Per 32-wide chunk the
-//                   threads load A and B with 16-byte loads, split each value into TF32 high and low
-//                   parts and store them in the canonical K-major no-swizzle layout (8-row x 16-byte
-//                   core matrices); one thread issues 12 tcgen05.mma.kind::tf32 (M = N = 128, K = 8;
-//                   A_hi B_hi + A_hi B_lo + A_lo B_hi) into an FP32 accumulator in tensor memory; two
-//                   operand stages, tcgen05.commit to per-stage mbarriers, bounded waits (a CTA that
-//                   waits too long records an error, frees its tensor memory and returns).  The
-//                   epilogue stages the accumulator in shared memory (tcgen05.ld 32x32b) and writes C
-//                   row-wise and / or the transposed CT column-wise, both coalesced.
+// KF factor_persistent  ONE launch for all blocks: a grid of CTAs resident on every SM takes tasks
+//                       (DIAG or GEMM) from one list in order (an atomic counter) and, before each,
+//                       waits until every task of the earlier phases of its block is done (a
+//                       per-block counter of finished tasks, release/acquire ordering; bounded
+//                       wait).  The list is ordered by (phase + skew, block), largest blocks first,
+//                       so every task's dependencies come earlier in it: a CTA only ever waits for
+//                       tasks that running CTAs have taken, and nothing deadlocks whatever the
+//                       number of resident CTAs.  The skew staggers the blocks' phases, so the
+//                       CUDA-core DIAG tasks of some blocks run beside the GEMM tasks of others.
+//                       CTAs per SM and the skew are chosen by the autotuner (every choice runs
+//                       the same arithmetic per task: results are bitwise the same).
+// GEMM task             C (<= 128 x 128) = s_old C + s_acc A B^T, A: m x k and B: n x k row-major
+//                       FP32 with k contiguous (k a multiple of 32).  Per 16-wide chunk the threads
+//                       load A and B with 16-byte L2 loads (the next chunk in flight), split each
+//                       value into TF32 high and low parts and store them in the canonical K-major
+//                       no-swizzle layout (8-row x 16-byte core matrices); one thread issues
+//                       tcgen05.mma.kind::tf32 (M = 128, N = n rounded up to 16, K = 8; A_hi B_hi
+//                       + A_hi B_lo + A_lo B_hi) into an FP32 accumulator in tensor memory; two
+//                       operand stages, tcgen05.commit to per-stage mbarriers, bounded waits.  The
+//                       epilogue stages the accumulator in shared memory (tcgen05.ld 32x32b) and
+//                       writes C row-wise and / or the transposed CT column-wise, both coalesced.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -48,7 +61,9 @@ constexpr int kTS = kP + 1;             // diagonal-kernel tile row stride (floa
 constexpr int kES = kP / 2 + 1;         // epilogue half-tile row stride (floats)
 constexpr long long kGSpin = 1LL << 24; // non-blocking mbarrier polls before giving up
 // kind::tf32: D FP32 (bit 4), A and B TF32 (bits 7, 10), K-major both, N >> 3 at bit 17, M >> 4 at bit 24
-constexpr uint32_t kGIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kP >> 3) << 17) | ((uint32_t)(kP >> 4) << 24);
+__host__ __device__ constexpr uint32_t gidesc(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kP >> 4) << 24);
+}
 
 struct GemmTask {
     const float *A, *B;  // operand origins: A rows 0..m-1, B rows 0..n-1, k contiguous
@@ -77,11 +92,11 @@ __device__ __forceinline__ uint64_t gdesc(uint32_t saddr) {
     return d;
 }
 
-__device__ __forceinline__ void gmma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void gmma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kGIdesc), "r"(accumulate));
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
 // one suspending probe (the thread may sleep up to ~1 us while the phase is pending)
@@ -105,14 +120,15 @@ __device__ __forceinline__ bool gbar_wait(uint32_t bar, uint32_t phase) {
 
 // One operand part of a chunk: 128 rows x 16 columns as 512 float4; element e of thread tid is
 // e = tid + 256 u: row (e / 32) * 8 + e % 8, float4 column (e / 8) % 4.  Eight consecutive threads
-// take the 8 rows of one core matrix (conflict-free 16-byte stores, 64-byte row segments).
+// take the 8 rows of one core matrix (conflict-free 16-byte stores, 64-byte row segments).  The
+// loads bypass L1 (other CTAs of the persistent factor write these tiles between tasks).
 __device__ __forceinline__ void chunk_fetch(const float *src, int ld, int rows_valid, int c0, int tid,
                                             float4 (&v)[kGF4]) {
 #pragma unroll
     for (int u = 0; u < kGF4; ++u) {
         const int e = tid + 256 * u;
         const int r = (e >> 5) * 8 + (e & 7), k4 = (e >> 3) & 3;
-        v[u] = r < rows_valid ? *reinterpret_cast<const float4 *>(src + (long long)r * ld + c0 + 4 * k4)
+        v[u] = r < rows_valid ? __ldcg(reinterpret_cast<const float4 *>(src + (long long)r * ld + c0 + 4 * k4))
                               : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
@@ -131,31 +147,19 @@ __device__ __forceinline__ void chunk_store(const float4 (&v)[kGF4], uint32_t *h
     }
 }
 
-__global__ void __launch_bounds__(256)
-tc_gemm_tasks(const GemmTask *__restrict__ tasks, int *__restrict__ err) {
-    extern __shared__ __align__(1024) uint32_t gsm[];
-    __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ uint32_t tmem_base;
-    __shared__ int abort_flag;
-    const GemmTask t = tasks[blockIdx.x];
+// Per-CTA state of the GEMM tasks kept across the tasks of the persistent kernel
+struct GemmCta {
+    uint32_t tmem;     // 128 TMEM columns (the accumulator)
+    uint64_t *mbar;    // two stage barriers
+    uint32_t ph[2];    // their next parities
+    int *abort_flag;   // shared: a bounded wait ran out
+};
+
+// One GEMM task (all 256 threads).  Returns with every MMA it issued complete.
+__device__ void gemm_task(const GemmTask &t, uint32_t *gsm, GemmCta &c) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(gsmem_u32(&tmem_base)),
-                     "r"((uint32_t)kP));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    if (tid == 0) {
-        for (int st = 0; st < 2; ++st)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(gsmem_u32(&mbar[st])), "r"(1u));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        abort_flag = 0;
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_base;
     const int nch = t.k / kGK;
-    uint32_t ph[2] = {0u, 0u};
+    const uint32_t idesc = gidesc((t.n + 15) & ~15);
     int pending[2] = {0, 0};
     float4 va[kGF4], vb[kGF4];  // the next chunk, in flight while the current one is stored and multiplied
     if (nch > 0) {
@@ -167,12 +171,12 @@ tc_gemm_tasks(const GemmTask *__restrict__ tasks, int *__restrict__ err) {
         uint32_t *Ahi = gsm + st * kGStage, *Alo = Ahi + kGOp, *Bhi = Alo + kGOp, *Blo = Bhi + kGOp;
         if (pending[st]) {  // the stage's previous MMAs must be done before its operands change;
                             // one thread waits, the barrier below releases the others
-            if (tid == 0 && !gbar_wait(gsmem_u32(&mbar[st]), ph[st])) abort_flag = 1;
-            ph[st] ^= 1u;
+            if (tid == 0 && !gbar_wait(gsmem_u32(&c.mbar[st]), c.ph[st])) *c.abort_flag = 1;
+            c.ph[st] ^= 1u;
             pending[st] = 0;
         }
         __syncthreads();
-        if (abort_flag) break;
+        if (*c.abort_flag) break;
         chunk_store(va, Ahi, Alo, tid);
         chunk_store(vb, Bhi, Blo, tid);
         if (ch + 1 < nch) {
@@ -187,96 +191,87 @@ tc_gemm_tasks(const GemmTask *__restrict__ tasks, int *__restrict__ err) {
 #pragma unroll
             for (int s = 0; s < kGK / 8; ++s) {
                 const uint32_t ko = (uint32_t)s * 2 * kGLBO;
-                gmma(tmem, gdesc(ah + ko), gdesc(bh + ko), (ch > 0 || s > 0) ? 1u : 0u);
-                gmma(tmem, gdesc(ah + ko), gdesc(bl + ko), 1u);
-                gmma(tmem, gdesc(al + ko), gdesc(bh + ko), 1u);
+                gmma(c.tmem, gdesc(ah + ko), gdesc(bh + ko), idesc, (ch > 0 || s > 0) ? 1u : 0u);
+                gmma(c.tmem, gdesc(ah + ko), gdesc(bl + ko), idesc, 1u);
+                gmma(c.tmem, gdesc(al + ko), gdesc(bh + ko), idesc, 1u);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             gsmem_u32(&mbar[st]))
+                             gsmem_u32(&c.mbar[st]))
                          : "memory");
         }
         pending[st] = 1;
     }
-    for (int st = 0; st < 2; ++st) {  // drain (bounded, one thread)
+    for (int st = 0; st < 2; ++st) {  // drain (bounded, one thread; waits even after an abort so
+                                      // that no MMA is in flight when the CTA moves on)
         if (pending[st]) {
-            if (tid == 0 && !gbar_wait(gsmem_u32(&mbar[st]), ph[st])) abort_flag = 1;
+            if (tid == 0 && !gbar_wait(gsmem_u32(&c.mbar[st]), c.ph[st])) *c.abort_flag = 1;
+            c.ph[st] ^= 1u;
             pending[st] = 0;
         }
     }
     __syncthreads();
-    if (!abort_flag && nch > 0) {
-        // accumulator -> shared half tile T[r][c] (64 columns per pass, stride kES): warp w reads
-        // TMEM lanes 32 (w % 4) .., columns 64 pass + 32 (w / 4) ..; then C row-wise, CT column-wise
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        float *T = reinterpret_cast<float *>(gsm);
-        const int q = warp & 3, h = warp >> 2;
-        for (int pass = 0; pass < 2; ++pass) {
-            const int cbase = 64 * pass;
-            {
-                uint32_t v[32];
-                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(cbase + 32 * h);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                float *row = T + (32 * q + lane) * kES + 32 * h;
+    if (*c.abort_flag || nch == 0) return;
+    // accumulator -> shared half tile T[r][cl] (64 columns per pass, stride kES): warp w reads TMEM
+    // lanes 32 (w % 4) .., columns 64 pass + 32 (w / 4) ..; then C row-wise, CT column-wise
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float *T = reinterpret_cast<float *>(gsm);
+    const int q = warp & 3, h = warp >> 2;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int cbase = 64 * pass;
+        if (cbase >= t.n) break;  // uniform
+        {
+            uint32_t v[32];
+            const uint32_t taddr = c.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(cbase + 32 * h);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float *row = T + (32 * q + lane) * kES + 32 * h;
 #pragma unroll
-                for (int c = 0; c < 32; ++c) row[c] = __uint_as_float(v[c]);
-            }
-            __syncthreads();
-            if (t.C) {
-                for (int e = tid; e < kP * 64; e += 256) {
-                    const int r = e >> 6, cl = e & 63, c = cbase + cl;
-                    if (r < t.m && c < t.n && (!t.diag || r >= c)) {
-                        float *dst = t.C + (long long)r * t.ldc + c;
-                        const float a = T[r * kES + cl];
-                        *dst = t.s_old != 0.f ? fmaf(t.s_acc, a, t.s_old * *dst) : t.s_acc * a;
-                    }
-                }
-            }
-            if (t.CT) {
-                for (int e = tid; e < kP * 64; e += 256) {
-                    const int cl = e >> 7, r = e & (kP - 1), c = cbase + cl;
-                    if (r < t.m && c < t.n && (!t.diag || c < r))
-                        t.CT[(long long)c * t.ldct + r] = t.s_acc * T[r * kES + cl];
-                }
-            }
-            __syncthreads();
+            for (int cc = 0; cc < 32; ++cc) row[cc] = __uint_as_float(v[cc]);
         }
-    } else if (abort_flag && tid == 0) {
-        atomicExch(err, 1);
+        __syncthreads();
+        if (t.C) {
+            for (int e = tid; e < kP * 64; e += 256) {
+                const int r = e >> 6, cl = e & 63, cc = cbase + cl;
+                if (r < t.m && cc < t.n && (!t.diag || r >= cc)) {
+                    float *dst = t.C + (long long)r * t.ldc + cc;
+                    const float a = T[r * kES + cl];
+                    *dst = t.s_old != 0.f ? fmaf(t.s_acc, a, t.s_old * __ldcg(dst)) : t.s_acc * a;
+                }
+            }
+        }
+        if (t.CT) {
+            for (int e = tid; e < kP * 64; e += 256) {
+                const int cl = e >> 7, r = e & (kP - 1), cc = cbase + cl;
+                if (r < t.m && cc < t.n && (!t.diag || cc < r))
+                    t.CT[(long long)cc * t.ldct + r] = t.s_acc * T[r * kES + cl];
+            }
+        }
+        __syncthreads();
     }
+    // the next task's MMAs overwrite the accumulator only after every thread has read it
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kP));
-    }
 }
 
-// KD: the diagonal tile of panel k0 of each listed block, in one 128 x 129 shared tile D: the
-// block's entries, then L_kk (written back), then Tinv = L_kk^{-1} in place (three CTAs per SM).
-__global__ void __launch_bounds__(256)
-diag_factor(float *__restrict__ pool, float *__restrict__ wt, float *__restrict__ tinv,
-            const long long *__restrict__ loff, const long long *__restrict__ toff, const int *__restrict__ npad,
-            const int *__restrict__ list, int k0, int *__restrict__ info) {
-    extern __shared__ float dsm[];
-    float *D = dsm;
-    __shared__ int bad;
-    const int b = list[blockIdx.x];
+// The diagonal tile of panel k0 of block b, in one 128 x 129 shared tile D: the block's entries,
+// then L_kk (written back), then Tinv = L_kk^{-1} in place.
+__device__ void diag_task(float *__restrict__ pool, float *__restrict__ wt, float *__restrict__ tinv,
+                          const long long *__restrict__ loff, const long long *__restrict__ toff,
+                          const int *__restrict__ npad, int b, int k0, int *__restrict__ info, float *D, int *bad) {
     const int np = npad[b], pk = min(kP, np - k0), nt = pk / 32;
     float *A = pool + loff[b] + (long long)k0 * np + k0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) bad = -1;
+    if (tid == 0) *bad = -1;
     for (int e = tid; e < kP * kP; e += 256) {
         const int r = e >> 7, c = e & (kP - 1);
-        D[r * kTS + c] = (r < pk && c <= r) ? A[(long long)r * np + c] : 0.f;
+        D[r * kTS + c] = (r < pk && c <= r) ? __ldcg(A + (long long)r * np + c) : 0.f;
     }
     __syncthreads();
     // blocked Cholesky of D (32-wide): diagonal sub-tile column by column, panel, trailing update
@@ -292,7 +287,7 @@ diag_factor(float *__restrict__ pool, float *__restrict__ wt, float *__restrict_
             for (int j = 0; j < 32; ++j) {
                 float piv = __shfl_sync(0xffffffffu, row[j], j);
                 if (!(piv > 0.f)) {  // uniform: every lane holds the same pivot
-                    if (lane == 0 && bad < 0) bad = c0 + j;
+                    if (lane == 0 && *bad < 0) *bad = c0 + j;
                     piv = 1.f;
                 }
                 const float djj = sqrtf(piv);
@@ -420,20 +415,217 @@ diag_factor(float *__restrict__ pool, float *__restrict__ wt, float *__restrict_
         Tb[e] = (r < pk && c <= r) ? D[r * kTS + c] : 0.f;
         if (r < pk && c < pk) Wb[(long long)r * np + c] = c >= r ? D[c * kTS + r] : 0.f;
     }
-    if (tid == 0 && bad >= 0 && info[b] < 0) info[b] = k0 + bad;
+    __syncthreads();
+    if (tid == 0 && *bad >= 0 && info[b] < 0) info[b] = k0 + *bad;
+}
+
+// One entry of the persistent factor's task list
+struct FTask {
+    GemmTask g;    // kind 0
+    int kind;      // 0 GEMM, 1 DIAG
+    int block;
+    int need;      // finished tasks of this block required first (all of its earlier phases)
+    int k0;        // DIAG: first row of the diagonal tile
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+constexpr long long kDepSpin = 1LL << 26;  // polls (~1 us each at most) of a block's counter
+
+__global__ void __launch_bounds__(256, 3)
+factor_persistent(const FTask *__restrict__ tasks, int ntasks, int *__restrict__ next, int *__restrict__ done,
+                  float *__restrict__ pool, float *__restrict__ wt, float *__restrict__ tinv,
+                  const long long *__restrict__ loff, const long long *__restrict__ toff,
+                  const int *__restrict__ npad, int *__restrict__ info, int *__restrict__ err) {
+    extern __shared__ __align__(1024) uint32_t gsm[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag, cur, bad;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(gsmem_u32(&tmem_base)),
+                     "r"((uint32_t)kP));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int st = 0; st < 2; ++st)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(gsmem_u32(&mbar[st])), "r"(1u));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    GemmCta c;
+    c.tmem = tmem_base;
+    c.mbar = mbar;
+    c.ph[0] = c.ph[1] = 0u;
+    c.abort_flag = &abort_flag;
+    for (;;) {
+        if (tid == 0) {
+            int t = atomicAdd(next, 1);
+            if (t < ntasks) {
+                // wait (bounded) until the block's earlier phases are done; give up if another
+                // CTA has recorded an error
+                const FTask &ft = tasks[t];
+                long long i = 0;
+                while (ld_acquire(done + ft.block) < ft.need) {
+                    if (ld_acquire(err) != 0) { t = ntasks; break; }
+                    if (++i > kDepSpin) { atomicExch(err, 2); t = ntasks; break; }
+                    __nanosleep(256);
+                }
+            }
+            cur = t;
+        }
+        __syncthreads();
+        const int t = cur;
+        if (t >= ntasks) break;
+        const FTask &ft = tasks[t];
+        if (ft.kind == 1) {
+            diag_task(pool, wt, tinv, loff, toff, npad, ft.block, ft.k0, info, reinterpret_cast<float *>(gsm), &bad);
+        } else {
+            gemm_task(ft.g, gsm, c);
+        }
+        __syncthreads();
+        if (abort_flag) {
+            if (tid == 0) atomicExch(err, 1);
+            break;
+        }
+        if (tid == 0) {
+            __threadfence();  // this task's writes before the count that releases its dependants
+            atomicAdd(done + ft.block, 1);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(c.tmem), "r"((uint32_t)kP));
+    }
 }
 
 }  // namespace
 
 constexpr int kDiagSmem = kP * kTS * (int)sizeof(float);
+constexpr int kFSmem = kDiagSmem > kGSmem ? kDiagSmem : kGSmem;
 
 int prepare_tc_factor() {
-    IE_TRY_CUDA(cudaFuncSetAttribute(tc_gemm_tasks, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem));
-    IE_TRY_CUDA(cudaFuncSetAttribute(diag_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, kDiagSmem));
+    IE_TRY_CUDA(cudaFuncSetAttribute(factor_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, kFSmem));
     return IE_OK;
 }
 
-// L and then M in f->d_pool (FP32, already holding the gathered lower blocks); synchronizes.
+namespace {
+
+// The task list of the persistent factor for a given skew: each block's phases (DIAG, PANEL and
+// TRAILING per panel; then G and W per tile row of W; then M), ordered by (phase + rank % skew,
+// rank), rank = the block's place in decreasing size order.  A task's `need` is the number of
+// tasks of its block in the phases before its own.
+void build_plan(const std::vector<int> &npad, const std::vector<long long> &loff, const std::vector<int> &order,
+                float *pool, float *W, float *T, float *G, const std::vector<long long> &toff,
+                const std::vector<long long> &goff, int skew, std::vector<FTask> &out) {
+    const int nb = (int)npad.size();
+    // per block: its tasks in phase order and the first task of every phase
+    std::vector<std::vector<FTask>> bt((size_t)nb);
+    std::vector<std::vector<int>> first((size_t)nb);
+    size_t total = 0;
+    int max_levels = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int np = npad[(size_t)b];
+        std::vector<FTask> &tl = bt[(size_t)b];
+        std::vector<int> &ph = first[(size_t)b];
+        float *P_ = pool + loff[(size_t)b], *W_ = W + loff[(size_t)b], *G_ = G + goff[(size_t)b];
+        auto T_ = [&](int i) { return T + toff[(size_t)b] + (long long)i * kP * kP; };
+        int open = 0;  // tasks since the phase began
+        auto begin = [&]() { open = 0; ph.push_back((int)tl.size()); };
+        auto close_phase = [&]() {
+            if (open == 0) ph.pop_back();  // an empty phase
+        };
+        auto need = [&]() { return ph.back(); };  // every task of the earlier phases
+        auto gemm = [&](const float *A, int lda, const float *B, int ldb, int m, int n, int k, float *C, int ldc,
+                        float *CT, int ldct, float s_old, float s_acc, int diag) {
+            FTask t{};
+            t.kind = 0; t.block = b; t.need = need(); t.k0 = 0;
+            t.g.A = A; t.g.B = B; t.g.C = C; t.g.CT = CT;
+            t.g.lda = lda; t.g.ldb = ldb; t.g.ldc = ldc; t.g.ldct = ldct;
+            t.g.m = m; t.g.n = n; t.g.k = k; t.g.s_old = s_old; t.g.s_acc = s_acc; t.g.diag = diag; t.g.pad_ = 0;
+            tl.push_back(t);
+            ++open;
+        };
+        for (int k0 = 0; k0 < np; k0 += kP) {
+            const int pk = std::min(kP, np - k0);
+            begin();
+            FTask d{};
+            d.kind = 1; d.block = b; d.need = need(); d.k0 = k0;
+            tl.push_back(d);
+            ++open;
+            close_phase();
+            begin();
+            for (int r0 = k0 + pk; r0 < np; r0 += kP) {  // panel: L_21 = A_21 Tinv^T, in place
+                float *a = P_ + (long long)r0 * np + k0;
+                gemm(a, np, T_(k0 / kP), kP, std::min(kP, np - r0), pk, pk, a, np, nullptr, 0, 0.f, 1.f, 0);
+            }
+            close_phase();
+            begin();
+            for (int ra = k0 + pk; ra < np; ra += kP)  // trailing: A_22 -= L_21 L_21^T, lower tiles
+                for (int rb = k0 + pk; rb <= ra; rb += kP)
+                    gemm(P_ + (long long)ra * np + k0, np, P_ + (long long)rb * np + k0, np, std::min(kP, np - ra),
+                         std::min(kP, np - rb), pk, P_ + (long long)ra * np + rb, np, nullptr, 0, 1.f, -1.f, 0);
+            close_phase();
+        }
+        const int nt = (np + kP - 1) / kP;
+        for (int i = 1; i < nt; ++i) {  // W = L^{-1} by tile rows (W^T stored)
+            const int ri = i * kP, mi = std::min(kP, np - ri);
+            begin();
+            for (int j = 0; j < i; ++j) {
+                const int rj = j * kP;
+                gemm(P_ + (long long)ri * np + rj, np, W_ + (long long)rj * np + rj, np, mi, kP, ri - rj, nullptr, 0,
+                     G_ + (long long)rj * kP, kP, 0.f, 1.f, 0);
+            }
+            close_phase();
+            begin();
+            for (int j = 0; j < i; ++j) {
+                const int rj = j * kP;
+                gemm(T_(i), kP, G_ + (long long)rj * kP, kP, mi, kP, mi, nullptr, 0, W_ + (long long)rj * np + ri, np,
+                     0.f, -1.f, 0);
+            }
+            close_phase();
+        }
+        begin();
+        for (int ra = 0; ra < np; ra += kP)  // M = W^T W into the pool: lower tiles a >= b, mirrored
+            for (int rb = 0; rb <= ra; rb += kP)
+                gemm(W_ + (long long)ra * np + ra, np, W_ + (long long)rb * np + ra, np, std::min(kP, np - ra),
+                     std::min(kP, np - rb), np - ra, P_ + (long long)ra * np + rb, np, P_ + (long long)rb * np + ra, np,
+                     0.f, 1.f, ra == rb ? 1 : 0);
+        close_phase();
+        ph.push_back((int)tl.size());  // sentinel: the end of the last phase
+        total += tl.size();
+        max_levels = std::max(max_levels, (int)ph.size() - 1);
+    }
+    // emit by (phase + rank % skew, rank): every task's dependencies come before it
+    out.clear();
+    out.reserve(total);
+    for (int key = 0; key < max_levels + skew; ++key)
+        for (int r = 0; r < nb; ++r) {
+            const int b = order[(size_t)r], l = key - r % skew;
+            const std::vector<int> &ph = first[(size_t)b];
+            if (l < 0 || l + 1 >= (int)ph.size()) continue;
+            for (int i = ph[(size_t)l]; i < ph[(size_t)l + 1]; ++i) out.push_back(bt[(size_t)b][(size_t)i]);
+        }
+}
+
+// candidates of the factor's autotuner: CTAs per SM x skew
+constexpr int kFactorCand[][2] = {{3, 1}, {3, 2}, {3, 4}, {2, 2}};
+constexpr int kFactorNCand = (int)(sizeof(kFactorCand) / sizeof(kFactorCand[0]));
+
+}  // namespace
+
+// L and then M in f->d_pool (FP32, already holding the gathered lower blocks); synchronizes.  One
+// launch of the persistent kernel; with the autotuner on, the first factor of a shape times every
+// candidate (CTAs per SM, skew) on a copy of the gathered blocks and keeps the fastest.
 int launch_factor_tc(dd_factor_t *f, const std::vector<int> &npad, const std::vector<long long> &loff,
                      cudaStream_t s) {
     const int nb = f->nblocks;
@@ -441,128 +633,108 @@ int launch_factor_tc(dd_factor_t *f, const std::vector<int> &npad, const std::ve
     IE_TRY(prepare_tc_factor());
     float *pool = (float *)f->d_pool;
     std::vector<long long> toff((size_t)nb + 1, 0), goff((size_t)nb + 1, 0);
-    int max_np = 0;
+    long long sum_np = 0;
     for (int b = 0; b < nb; ++b) {
         const int nt = (npad[(size_t)b] + kP - 1) / kP;
         toff[(size_t)b + 1] = toff[(size_t)b] + (long long)nt * kP * kP;
         goff[(size_t)b + 1] = goff[(size_t)b] + (long long)npad[(size_t)b] * kP;
-        max_np = std::max(max_np, npad[(size_t)b]);
+        sum_np += npad[(size_t)b];
     }
-    DevBuf wt, tinv, gbuf, dtoff, derr;
+    std::vector<int> order((size_t)nb);
+    for (int b = 0; b < nb; ++b) order[(size_t)b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return npad[(size_t)a] > npad[(size_t)b]; });
+    DevBuf wt, tinv, gbuf, dtoff, derr, dnext, ddone;
     IE_TRY(wt.alloc(sizeof(float) * (size_t)f->pool_elems, s));
     IE_TRY(tinv.alloc(sizeof(float) * (size_t)toff.back(), s));
     IE_TRY(gbuf.alloc(sizeof(float) * (size_t)goff.back(), s));
     IE_TRY(dtoff.alloc(sizeof(long long) * toff.size(), s));
     IE_TRY(derr.alloc(sizeof(int), s));
+    IE_TRY(dnext.alloc(sizeof(int), s));
+    IE_TRY(ddone.alloc(sizeof(int) * (size_t)nb, s));
     IE_TRY_CUDA(cudaMemcpyAsync(dtoff.ptr, toff.data(), sizeof(long long) * toff.size(), cudaMemcpyHostToDevice, s));
     IE_TRY_CUDA(cudaMemsetAsync(derr.ptr, 0, sizeof(int), s));
     float *W = wt.as<float>(), *T = tinv.as<float>(), *G = gbuf.as<float>();
-    auto P_ = [&](int b) { return pool + loff[(size_t)b]; };
-    auto W_ = [&](int b) { return W + loff[(size_t)b]; };
-    auto T_ = [&](int b, int i) { return T + toff[(size_t)b] + (long long)i * kP * kP; };
-    auto G_ = [&](int b) { return G + goff[(size_t)b]; };
-    // the whole schedule is built first (GEMM task lists and diagonal-kernel block lists), copied
-    // once, and launched back to back with no host synchronization in between
-    std::vector<GemmTask> tasks;
-    std::vector<int> lists;
-    struct Op { int diag; int k0; size_t off, cnt; };
-    std::vector<Op> ops;
-    size_t mark = 0;
-    auto close_gemm = [&]() {
-        if (tasks.size() > mark) ops.push_back({0, 0, mark, tasks.size() - mark});
-        mark = tasks.size();
-    };
-    auto task = [&](const float *A, int lda, const float *B, int ldb, int m, int n, int k, float *C, int ldc,
-                    float *CT, int ldct, float s_old, float s_acc, int diag) {
-        GemmTask g;
-        g.A = A; g.B = B; g.C = C; g.CT = CT;
-        g.lda = lda; g.ldb = ldb; g.ldc = ldc; g.ldct = ldct;
-        g.m = m; g.n = n; g.k = k; g.s_old = s_old; g.s_acc = s_acc; g.diag = diag; g.pad_ = 0;
-        tasks.push_back(g);
-    };
-    // Cholesky, panel by panel
-    for (int k0 = 0; k0 < max_np; k0 += kP) {
-        const size_t l0 = lists.size();
-        for (int b = 0; b < nb; ++b)
-            if (npad[(size_t)b] > k0) lists.push_back(b);
-        ops.push_back({1, k0, l0, lists.size() - l0});
-        for (int b = 0; b < nb; ++b) {  // panel: L_21 = A_21 Tinv^T, in place
-            const int np = npad[(size_t)b];
-            if (np <= k0) continue;
-            const int pk = std::min(kP, np - k0);
-            for (int r0 = k0 + pk; r0 < np; r0 += kP) {
-                float *a = P_(b) + (long long)r0 * np + k0;
-                task(a, np, T_(b, k0 / kP), kP, std::min(kP, np - r0), pk, pk, a, np, nullptr, 0, 0.f, 1.f, 0);
-            }
-        }
-        close_gemm();
-        for (int b = 0; b < nb; ++b) {  // trailing: A_22 -= L_21 L_21^T, lower tiles
-            const int np = npad[(size_t)b];
-            if (np <= k0) continue;
-            const int pk = std::min(kP, np - k0);
-            for (int ra = k0 + pk; ra < np; ra += kP)
-                for (int rb = k0 + pk; rb <= ra; rb += kP)
-                    task(P_(b) + (long long)ra * np + k0, np, P_(b) + (long long)rb * np + k0, np, std::min(kP, np - ra),
-                         std::min(kP, np - rb), pk, P_(b) + (long long)ra * np + rb, np, nullptr, 0, 1.f, -1.f, 0);
-        }
-        close_gemm();
+    const int sms = f->prob->sm_count;
+
+    // IEDD_FACTOR_SCHEDULE="c,s" fixes the schedule (c CTAs per SM, skew s) instead of the tuner's
+    int force_ctas = 0, force_skew = 0;
+    if (const char *env = std::getenv("IEDD_FACTOR_SCHEDULE")) {
+        if (std::sscanf(env, "%d,%d", &force_ctas, &force_skew) != 2 || force_ctas < 1 || force_ctas > 3 ||
+            force_skew < 1 || force_skew > 64)
+            force_ctas = force_skew = 0;
     }
-    // W = L^{-1} by tile rows (W^T stored): G_ij^T, then W_ij^T = -(Tinv_i G_ij)^T
-    const int max_nt = (max_np + kP - 1) / kP;
-    for (int i = 1; i < max_nt; ++i) {
-        for (int b = 0; b < nb; ++b) {
-            const int np = npad[(size_t)b], ri = i * kP;
-            if (ri >= np) continue;
-            const int mi = std::min(kP, np - ri);
-            for (int j = 0; j < i; ++j) {
-                const int rj = j * kP;
-                task(P_(b) + (long long)ri * np + rj, np, W_(b) + (long long)rj * np + rj, np, mi, kP, ri - rj, nullptr, 0,
-                     G_(b) + (long long)rj * kP, kP, 0.f, 1.f, 0);
-            }
-        }
-        close_gemm();
-        for (int b = 0; b < nb; ++b) {
-            const int np = npad[(size_t)b], ri = i * kP;
-            if (ri >= np) continue;
-            const int mi = std::min(kP, np - ri);
-            for (int j = 0; j < i; ++j) {
-                const int rj = j * kP;
-                task(T_(b, i), kP, G_(b) + (long long)rj * kP, kP, mi, kP, mi, nullptr, 0, W_(b) + (long long)rj * np + ri,
-                     np, 0.f, -1.f, 0);
-            }
-        }
-        close_gemm();
-    }
-    // M = W^T W into the pool: lower tiles a >= b, mirrored
-    for (int b = 0; b < nb; ++b) {
-        const int np = npad[(size_t)b];
-        for (int ra = 0; ra < np; ra += kP)
-            for (int rb = 0; rb <= ra; rb += kP)
-                task(W_(b) + (long long)ra * np + ra, np, W_(b) + (long long)rb * np + ra, np, std::min(kP, np - ra),
-                     std::min(kP, np - rb), np - ra, P_(b) + (long long)ra * np + rb, np, P_(b) + (long long)rb * np + ra,
-                     np, 0.f, 1.f, ra == rb ? 1 : 0);
-    }
-    close_gemm();
-    DevBuf dtasks, dlists;
-    IE_TRY(dtasks.alloc(sizeof(GemmTask) * std::max<size_t>(tasks.size(), 1), s));
-    IE_TRY(dlists.alloc(sizeof(int) * std::max<size_t>(lists.size(), 1), s));
-    IE_TRY_CUDA(cudaMemcpyAsync(dtasks.ptr, tasks.data(), sizeof(GemmTask) * tasks.size(), cudaMemcpyHostToDevice, s));
-    IE_TRY_CUDA(cudaMemcpyAsync(dlists.ptr, lists.data(), sizeof(int) * lists.size(), cudaMemcpyHostToDevice, s));
-    for (const Op &op : ops) {
-        if (op.cnt == 0) continue;
-        if (op.diag) {
-            diag_factor<<<(unsigned)op.cnt, 256, kDiagSmem, s>>>(pool, W, T, f->d_loff, dtoff.as<long long>(), f->d_npad,
-                                                                 dlists.as<int>() + op.off, op.k0, f->d_info);
-        } else {
-            tc_gemm_tasks<<<(unsigned)op.cnt, 256, kGSmem, s>>>(dtasks.as<GemmTask>() + op.off, derr.as<int>());
-        }
+    auto run = [&](int ctas, const std::vector<FTask> &tasks, DevBuf &dtasks) -> int {
+        IE_TRY_CUDA(cudaMemsetAsync(dnext.ptr, 0, sizeof(int), s));
+        IE_TRY_CUDA(cudaMemsetAsync(ddone.ptr, 0, sizeof(int) * (size_t)nb, s));
+        const int grid = std::max(1, std::min((int)tasks.size(), sms * ctas));
+        factor_persistent<<<grid, 256, kFSmem, s>>>(dtasks.as<FTask>(), (int)tasks.size(), dnext.as<int>(),
+                                                    ddone.as<int>(), pool, W, T, f->d_loff, dtoff.as<long long>(),
+                                                    f->d_npad, f->d_info, derr.as<int>());
         IE_LAUNCHED();
+        return IE_OK;
+    };
+    auto upload = [&](const std::vector<FTask> &tasks, DevBuf &dtasks) -> int {
+        IE_TRY(dtasks.alloc(sizeof(FTask) * std::max<size_t>(tasks.size(), 1), s));
+        IE_TRY_CUDA(cudaMemcpyAsync(dtasks.ptr, tasks.data(), sizeof(FTask) * tasks.size(), cudaMemcpyHostToDevice, s));
+        return IE_OK;
+    };
+
+    const std::string key = "factor/nb" + std::to_string(nb) + "/max" + std::to_string(f->max_pad) + "/sum" +
+                            std::to_string(sum_np);
+    int cand = 1;  // default: three CTAs per SM, skew 2
+    int tuned = -1;
+    // tuning runs every candidate once: only where a factor is cheap (not the dense CBD colour
+    // blocks, whose factor takes seconds)
+    double work = 0.0;
+    for (int b = 0; b < nb; ++b) work += (double)npad[(size_t)b] * npad[(size_t)b] * npad[(size_t)b];
+    const bool tune = force_ctas == 0 && autotune_enabled() && !ie_capturing() && work < 2e12 && !tune_get(key, &tuned);
+    if (tuned >= 0) cand = tuned;
+    if (tune) {
+        // time every candidate on a copy of the gathered blocks (the factor works in place)
+        DevBuf saved;
+        IE_TRY(saved.alloc(sizeof(float) * (size_t)f->pool_elems, s));
+        IE_TRY_CUDA(cudaMemcpyAsync(saved.ptr, pool, sizeof(float) * (size_t)f->pool_elems, cudaMemcpyDeviceToDevice, s));
+        cudaEvent_t e0, e1;
+        IE_TRY_CUDA(cudaEventCreate(&e0));
+        IE_TRY_CUDA(cudaEventCreate(&e1));
+        float best = -1.f;
+        std::string detail;
+        for (int c = 0; c < kFactorNCand; ++c) {
+            std::vector<FTask> tasks;
+            build_plan(npad, loff, order, pool, W, T, G, toff, goff, kFactorCand[c][1], tasks);
+            DevBuf dtasks;
+            IE_TRY(upload(tasks, dtasks));
+            IE_TRY_CUDA(cudaMemcpyAsync(pool, saved.ptr, sizeof(float) * (size_t)f->pool_elems, cudaMemcpyDeviceToDevice, s));
+            IE_TRY_CUDA(cudaEventRecord(e0, s));
+            IE_TRY(run(kFactorCand[c][0], tasks, dtasks));
+            IE_TRY_CUDA(cudaEventRecord(e1, s));
+            IE_TRY_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            IE_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            detail += (c ? ", " : "") + std::to_string(kFactorCand[c][0]) + "x" + std::to_string(kFactorCand[c][1]) + ":" +
+                      std::to_string(ms).substr(0, 6) + "ms";
+            if (best < 0.f || ms < best) { best = ms; cand = c; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        tune_put(key, cand, "CTAs/SM x skew: " + detail);
+        IE_TRY_CUDA(cudaMemcpyAsync(pool, saved.ptr, sizeof(float) * (size_t)f->pool_elems, cudaMemcpyDeviceToDevice, s));
+        IE_TRY_CUDA(cudaMemsetAsync(f->d_info, 0xFF, sizeof(int) * (size_t)nb, s));
+        IE_TRY_CUDA(cudaMemsetAsync(derr.ptr, 0, sizeof(int), s));
     }
+    const int ctas = force_ctas ? force_ctas : kFactorCand[cand][0];
+    const int skew = force_ctas ? force_skew : kFactorCand[cand][1];
+    std::vector<FTask> tasks;
+    build_plan(npad, loff, order, pool, W, T, G, toff, goff, skew, tasks);
+    DevBuf dtasks;
+    IE_TRY(upload(tasks, dtasks));
+    IE_TRY(run(ctas, tasks, dtasks));
     int herr = 0;
     IE_TRY_CUDA(cudaMemcpyAsync(&herr, derr.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
     IE_TRY_CUDA(cudaStreamSynchronize(s));
     if (herr) {
-        ie_set_error("dd_factor: a tensor-core GEMM timed out waiting for its MMAs");
+        ie_set_error(herr == 2 ? "dd_factor: a task of the persistent factor timed out waiting for its block"
+                               : "dd_factor: a tensor-core GEMM timed out waiting for its MMAs");
         return IE_ERR_TIMEOUT;
     }
     return IE_OK;

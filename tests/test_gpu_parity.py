@@ -8,13 +8,19 @@ Tolerances (derived in the design notes):
   * PCG FP64: iterations within +-1 of the oracle; solution within 1e-10 (relative L2) of the
     oracle run for the same number of iterations
   * PCG mixed: true relative residual <= tol checked by the oracle, solution within 1e-6 of
-    the oracle's solution at the same tolerance, iterations within +-2
+    the oracle's solution at the same tolerance; iterations within +-1 of the oracle's FP64 count
+    at a tolerance where that count is well conditioned (tests/golden/pcg_counts.json, written by
+    a script that calls only the oracle), and at 1e-8 within the counts that the oracle and its
+    FP32-perturbed versions reach there, +-1 (the design notes' reading: at 1e-8 single residual
+    norms are hypersensitive and the count itself is not a property of the method)
 """
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle_cache  # noqa: E402
+import pcg_golden as G  # noqa: E402
 from oracle import ie_oracle as O  # noqa: E402
 from paper_2108_12574_gb300 import iedd  # noqa: E402
 from paper_2108_12574_gb300 import inputs as I  # noqa: E402
@@ -199,21 +205,69 @@ def test_pcg_accurate_residual_modes(residual):
     assert O.true_relative_residual(2, n, f, host(u)) <= 1e-9 * 1.01
 
 
+def _kind_of(c):
+    return {"jacobi": iedd.DD_JACOBI, "schwarz": iedd.DD_SCHWARZ, "cbd": iedd.DD_CBD}[c["kind"]]
+
+
+def _mixed_solves(c, tol, inner=0):
+    """GPU mixed-precision solve of a stored case at ``tol``: (reports, U as (N, ncol))."""
+    F = G.rhs(c)
+    N = F.shape[0]
+    prob = iedd.ie_discretize(c["dim"], c["n"])
+    part = iedd.dd_partition(prob, c["m"], c["delta"], _kind_of(c))
+    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
+    U = torch.zeros((F.shape[1], N), dtype=torch.float64, device="cuda")
+    Fd = dev(F.T.copy())
+    if F.shape[1] == 1:
+        U, Fd = U[0], Fd[0]
+    reps = iedd.pcg_solve(prob, fac, Fd, U, tol=tol, precision=iedd.IE_MIXED, replace_every=50, inner=inner)
+    Uh = host(U).reshape(F.shape[1], N).T
+    fac.close(); part.close(); prob.close()
+    return reps, Uh
+
+
+def _check_mixed_case(name, inner=0, check_oracle_count=True):
+    """The mixed path on a stored case: at 1e-8 the true residual (oracle FFT matvec), the solution
+    against the oracle's (<= 1e-6) and the count within the oracle ensemble's band; at the case's
+    stable tolerance +-1 of the oracle's FP64 count.  The stored counts are re-derived from the
+    oracle here (``check_oracle_count``) so that the golden file cannot drift from the oracle."""
+    c = G.case(name)
+    F = G.rhs(c)
+    dim, n = c["dim"], c["n"]
+    reps, U = _mixed_solves(c, 1e-8, inner)
+    assert all(r["status"] == 0 and r["true_relres"] <= 1e-8 for r in reps), reps
+    rel = np.atleast_1d(O.true_relative_residual(dim, n, F, U))
+    assert np.all(rel <= 1e-8 * 1.01), rel
+    for k, r in enumerate(reps):
+        lo, hi = G.band_at_1e8(c, k)
+        assert lo <= r["iterations"] <= hi, (k, r["iterations"], (lo, hi))
+    kind = {"jacobi": O.JACOBI, "schwarz": O.SCHWARZ, "cbd": O.CBD}[c["kind"]]
+    P = O.Problem(dim, n, c["m"], c["delta"], kind, matvec="fft")
+    cols = list(range(F.shape[1])) if F.shape[1] <= 2 else [0, F.shape[1] - 1]
+    u_ref, its_ref, _ = P.solve(F[:, cols], 1e-8)
+    u_ref = u_ref.reshape(F.shape[0], -1)
+    its_ref = np.atleast_1d(its_ref)
+    for j, k in enumerate(cols):
+        assert its_ref[j] == c["it_fp64_at_1e-8"][k]
+        err = np.linalg.norm(U[:, k] - u_ref[:, j]) / np.linalg.norm(u_ref[:, j])
+        assert err <= 1e-6, (k, err)
+    if check_oracle_count:
+        _, its_s, _ = P.solve(F[:, [0]], c["tol"])
+        assert int(np.atleast_1d(its_s)[0]) == c["columns"][0]["it_fp64"]
+    reps_s, U_s = _mixed_solves(c, c["tol"], inner)
+    assert all(r["status"] == 0 for r in reps_s), reps_s
+    G.check_counts_at_stable_tol(c, [r["iterations"] for r in reps_s])
+    return reps, reps_s
+
+
 def test_cbd_mixed_matches_oracle_64():
     # the paper's CBD preconditioner (4 colour blocks of 1444 points) with the tensor-core factor
-    # and explicit inverses: true residual <= tol and the oracle's iteration count (FP64 blocks)
+    # and explicit inverses: true residual <= tol, the oracle's solution, and its iteration count
     n, m, delta = 64, 4, 2
-    f = I.grf(2, n, 0.1, 0)
     prob = iedd.ie_discretize(2, n)
     part = iedd.dd_partition(prob, m, delta, iedd.DD_CBD)
     assert part.nblocks == 4 and part.max_block == 1444
-    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
-    u = torch.zeros(n * n, dtype=torch.float64, device="cuda")
-    rep = iedd.pcg_solve(prob, fac, dev(f), u, tol=1e-8, inner=iedd.IE_FFT)[0]
-    assert rep["status"] == 0
-    assert O.true_relative_residual(2, n, f, host(u)) <= 1e-8 * 1.01
-    _, it_ref, _ = O.Problem(2, n, m, delta, O.CBD, matvec="fft").solve(f, 1e-8)
-    assert it_ref - 1 <= rep["iterations"] <= it_ref + 3, (rep, it_ref)
+    _check_mixed_case("ie2d_n64_m4_d2_cbd_grf", inner=iedd.IE_FFT)
 
 
 def test_cbd_large_blocks_column_chunked_apply():
@@ -265,18 +319,8 @@ def test_cbd_mixed_256_converges_in_fewer_iterations_than_schwarz():
 
 
 def test_pcg_fft_inner_mixed_512():
-    # the 512^2 workload with the FFT inner matvec and FP32 inverses: the true residual meets tol
-    n, m, delta = 512, 32, 2
-    f = I.grf(2, n, 0.1, 0)
-    prob = iedd.ie_discretize(2, n)
-    part = iedd.dd_partition(prob, m, delta, iedd.DD_SCHWARZ)
-    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
-    u = torch.zeros(n * n, dtype=torch.float64, device="cuda")
-    rep = iedd.pcg_solve(prob, fac, dev(f), u, tol=1e-8, precision=iedd.IE_MIXED, inner=iedd.IE_FFT)[0]
-    assert rep["status"] == 0 and rep["true_relres"] <= 1e-8
-    assert O.true_relative_residual(2, n, f, host(u)) <= 1e-8 * 1.01
-    _, it_ref, _ = O.Problem(2, n, m, delta, O.SCHWARZ, matvec="fft").solve(f, 1e-8)
-    assert it_ref - 1 <= rep["iterations"] <= it_ref + 5, (rep, it_ref)
+    # the 512^2 workload with the FFT inner matvec and FP32 inverses
+    _check_mixed_case("ie2d_n512_m32_d2_grf", inner=iedd.IE_FFT, check_oracle_count=False)
 
 
 def test_accurate_matvec_3d_full_size_sampled_rows():
@@ -423,6 +467,45 @@ def test_autotuned_apply_is_bitwise_the_default(dim, n, m, delta, nrhs):
     assert torch.equal(outs[0], outs[1])
 
 
+@pytest.mark.parametrize("dim,n,m,delta,kind", [(2, 128, 8, 2, iedd.DD_SCHWARZ), (3, 16, 2, 1, iedd.DD_SCHWARZ),
+                                                 (2, 64, 4, 2, iedd.DD_CBD)])
+def test_persistent_factor_is_bitwise_independent_of_its_schedule(monkeypatch, dim, n, m, delta, kind):
+    # the one-launch factor runs the same arithmetic per task whatever the number of resident CTAs
+    # and the phase skew of its task list: the inverses, and so the apply, agree bit for bit (the
+    # CBD case has 1472-point colour blocks: 12 tile rows, a deep chain of dependent phases)
+    N = n ** dim
+    prob = iedd.ie_discretize(dim, n)
+    part = iedd.dd_partition(prob, m, delta, kind)
+    R = dev(I.uniform_rhs_batch(N, [70, 71]).T.copy())
+    outs = []
+    for sched in ("3,1", "3,4", "2,2", "1,3", "3,64"):
+        monkeypatch.setenv("IEDD_FACTOR_SCHEDULE", sched)
+        fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
+        Z = torch.zeros_like(R)
+        iedd.dd_apply(fac, R, Z)
+        outs.append(Z)
+        fac.close()
+    for Z in outs[1:]:
+        assert torch.equal(Z, outs[0])
+    # and it is the operator of Eq. e:ad with the oracle's blocks (FP32-inverse tolerance)
+    blocks = O.partition(dim, n, m, delta, {iedd.DD_SCHWARZ: O.SCHWARZ, iedd.DD_CBD: O.CBD}[kind])
+    ref = O.apply(O.factor(dim, n, blocks), blocks, host(R).T).T
+    assert np.linalg.norm(host(outs[0]) - ref) / np.linalg.norm(ref) <= 2e-3
+
+
+def test_factor_autotuner_records_its_choice():
+    prev = iedd.ie_autotune(-1)
+    try:
+        iedd.ie_autotune(1)
+        iedd.ie_autotune(2)
+        prob = iedd.ie_discretize(2, 96)
+        part = iedd.dd_partition(prob, 6, 2, iedd.DD_SCHWARZ)
+        iedd.dd_factor(prob, part, iedd.IE_MIXED).close()
+        assert "factor/" in iedd.ie_autotune_report()
+    finally:
+        iedd.ie_autotune(1 if prev else 0)
+
+
 def test_autotuned_fft_is_bitwise_the_default():
     n = 96
     x = dev(I.uniform_rhs(n * n, 5))
@@ -486,24 +569,10 @@ def test_pcg_fp64_parity(dim, n, m, delta):
     assert rep["true_relres"] <= 1e-8 * 1.05
 
 
-@pytest.mark.parametrize("dim,n,m,delta", [(2, 64, 4, 1), (3, 16, 2, 1), (2, 96, 6, 2)])
-def test_pcg_mixed_parity(dim, n, m, delta):
-    N = n ** dim
-    f = I.uniform_rhs(N, 0) if dim == 3 else I.grf(2, n, 0.1, 0)
-    prob = iedd.ie_discretize(dim, n)
-    part = iedd.dd_partition(prob, m, delta, iedd.DD_SCHWARZ)
-    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
-    u = torch.zeros(N, dtype=torch.float64, device="cuda")
-    rep = iedd.pcg_solve(prob, fac, dev(f), u, tol=1e-8, precision=iedd.IE_MIXED, replace_every=50)[0]
-    assert rep["status"] == 0 and rep["true_relres"] <= 1e-8
-    P = _oracle_problem(dim, n, m, delta, matvec="fft")
-    true_rel = O.true_relative_residual(dim, n, f, host(u))
-    assert true_rel <= 1e-8 * 1.01, true_rel
-    u_ref, it_ref, _ = P.solve(f, 1e-8)
-    # FP32-class inner matvec (3D) and FP32 inverses move where the oscillating residual first
-    # dips below tol by a few iterations
-    assert it_ref - 1 <= rep["iterations"] <= it_ref + 5, (rep, it_ref)
-    assert np.linalg.norm(host(u) - u_ref) / np.linalg.norm(u_ref) <= 1e-6
+@pytest.mark.parametrize("case", ["ie2d_n64_m4_d1_grf", "ie3d_n16_m2_d1_uniform", "ie2d_n96_m6_d2_grf",
+                                  "ie2d_n128_m8_d2_grf"])
+def test_pcg_mixed_parity(case):
+    _check_mixed_case(case)
 
 
 def test_pcg_multi_rhs_columns_match_single_solves():
@@ -618,89 +687,43 @@ def test_pcg_cbd_and_jacobi_iteration_counts():
 
 
 def test_pcg_full_size_512_mixed():
-    # 512^2, GRF l = 0.1, Schwarz 32 x 32 partitions, 2-cell overlap, FP32 matvec and factors,
-    # FP64 residual replacement every 50 iterations, tol 1e-8 on the true residual
-    n, m, delta = 512, 32, 2
-    N = n * n
-    f = I.grf(2, n, 0.1, 0)
-    prob = iedd.ie_discretize(2, n)
-    part = iedd.dd_partition(prob, m, delta, iedd.DD_SCHWARZ)
-    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
-    u = torch.zeros(N, dtype=torch.float64, device="cuda")
-    rep = iedd.pcg_solve(prob, fac, dev(f), u, tol=1e-8, precision=iedd.IE_MIXED, replace_every=50)[0]
-    assert rep["status"] == 0
-    assert O.true_relative_residual(2, n, f, host(u)) <= 1e-8 * 1.01
-    P = O.Problem(2, n, m, delta, O.SCHWARZ, matvec="fft")
-    u_ref, it_ref, _ = P.solve(f, 1e-8)
-    # mixed mode: an FP32-stored preconditioner is a slightly different SPD operator (its
-    # smallest eigenvalues move by ~eps_fp32 cond(A_i)): with an exact matvec and exact products,
-    # every FP32 rounding of A_i^{-1} or L_i takes 46 to 48 iterations where FP64 takes 44, and
-    # the double-float matvec and the residual replacement move the count by one or two more
-    assert it_ref - 1 <= rep["iterations"] <= it_ref + 5, (rep, it_ref)
-    assert np.linalg.norm(host(u) - u_ref) / np.linalg.norm(u_ref) <= 1e-6
+    # 512^2, GRF l = 0.1, Schwarz 32 x 32 partitions, 2-cell overlap, the exact tensor-core matvec,
+    # FP32 inverses, FP64 residual replacement every 50 iterations; tol 1e-8 on the true residual,
+    # then +-1 of the oracle's FP64 count at the stable tolerance (1e-9 here)
+    _check_mixed_case("ie2d_n512_m32_d2_grf", check_oracle_count=False)
 
 
 def test_pcg_full_size_1024_mixed():
-    # 1024^2, GRF l = 0.05, Schwarz 64 x 64 partitions, 2-cell overlap, the launch configuration
-    # of the large 2D workload.  The oracle's full solve is too slow here, so the check is the
-    # property that holds at any size: the oracle's own FP64 FFT matvec, applied to the returned
-    # u, gives a true relative residual <= tol, and the library reports the same value.
-    n, m, delta = 1024, 64, 2
-    N = n * n
-    f = I.grf(2, n, 0.05, 0)
-    prob = iedd.ie_discretize(2, n)
-    part = iedd.dd_partition(prob, m, delta, iedd.DD_SCHWARZ)
-    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
-    u = torch.zeros(N, dtype=torch.float64, device="cuda")
-    rep = iedd.pcg_solve(prob, fac, dev(f), u, tol=1e-8, precision=iedd.IE_MIXED, replace_every=50)[0]
-    assert rep["status"] == 0, rep
-    rel = O.true_relative_residual(2, n, f, host(u))
+    # 1024^2, GRF l = 0.05, Schwarz 64 x 64 partitions, 2-cell overlap: the launch configuration of
+    # the large 2D workload.  The oracle's solve (its own Cholesky of the 4096 blocks and FFT-matvec
+    # PCG, minutes on the host) runs in a background process started at the beginning of the
+    # session.  Checked: the true residual by the oracle's FFT matvec, the library's reported true
+    # residual, the solution against the oracle's (<= 1e-6), the count at 1e-8 within the oracle
+    # ensemble's band and +-1 of the oracle's FP64 count at the stable tolerance.
+    c = G.case("ie2d_n1024_m64_d2_grf")
+    n = c["n"]
+    f = G.rhs(c)[:, 0]
+    reps, U = _mixed_solves(c, 1e-8)
+    rep = reps[0]
+    rel = O.true_relative_residual(2, n, f, U[:, 0])
     assert rel <= 1e-8 * 1.01, rel
     assert abs(rep["true_relres"] - rel) <= 1e-11, (rep["true_relres"], rel)
-    # Schwarz iteration counts grow like n^(1/2) at fixed subdomain size (76-83 measured here
-    # against 44-48 at 512^2); a count far outside means a broken preconditioner or matvec
-    assert 60 <= rep["iterations"] <= 110, rep
-
-
-def test_pcg_3d_tensor_batch_iterations():
-    # 16 right-hand sides take the tensor-core inner matvec (>= 16 columns); its FP32-class error
-    # must leave the oracle's iteration count (+5: where the oscillating residual first dips below
-    # tol) and the true residual at tol -- a matvec error of ~1e-6 of max |y| would not
-    n, m, delta = 32, 4, 1
-    N = n ** 3
-    F = I.uniform_rhs_batch(N, range(16)).T.copy()
-    prob = iedd.ie_discretize(3, n)
-    part = iedd.dd_partition(prob, m, delta, iedd.DD_SCHWARZ)
-    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
-    U = torch.zeros((16, N), dtype=torch.float64, device="cuda")
-    reps = iedd.pcg_solve(prob, fac, dev(F), U, tol=1e-8)
-    Uh = host(U)
-    rel = O.true_relative_residual(3, n, F[:2].T, Uh[:2].T)
-    assert np.all(rel <= 1e-8 * 1.01), rel
-    P = O.Problem(3, n, m, delta, O.SCHWARZ, matvec="fft")
-    _, its, _ = P.solve(F[:2].T, 1e-8)
-    for k in range(2):
-        assert its[k] - 1 <= reps[k]["iterations"] <= its[k] + 5, (reps[k], its[k])
+    u_ref, it_ref, _, _ = oracle_cache.result("ie2d_n1024_m64_d2_grf")
+    assert it_ref == c["it_fp64_at_1e-8"][0]
+    err = np.linalg.norm(U[:, 0] - u_ref) / np.linalg.norm(u_ref)
+    assert err <= 1e-6, err
+    lo, hi = G.band_at_1e8(c)
+    assert lo <= rep["iterations"] <= hi, (rep["iterations"], (lo, hi))
+    reps_s, _ = _mixed_solves(c, c["tol"])
+    assert reps_s[0]["status"] == 0, reps_s
+    G.check_counts_at_stable_tol(c, [r["iterations"] for r in reps_s])
 
 
 def test_pcg_full_size_3d_batched_mixed():
-    # 32^3, Schwarz 4 x 4 x 4 partitions (blocks of 729-1000 points), 1-cell overlap, 8 of the
-    # 64 uniform right-hand sides (seeds 0..7), FP32 factors, FP64 scalars
-    n, m, delta = 32, 4, 1
-    N = n ** 3
-    F = I.uniform_rhs_batch(N, range(8)).T.copy()
-    prob = iedd.ie_discretize(3, n)
-    part = iedd.dd_partition(prob, m, delta, iedd.DD_SCHWARZ)
-    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
-    U = torch.zeros((8, N), dtype=torch.float64, device="cuda")
-    reps = iedd.pcg_solve(prob, fac, dev(F), U, tol=1e-8)
-    Uh = host(U)
-    rel = O.true_relative_residual(3, n, F.T, Uh.T)
-    assert np.all(rel <= 1e-8 * 1.01), rel
-    P = O.Problem(3, n, m, delta, O.SCHWARZ, matvec="fft")
-    U_ref, its, _ = P.solve(F[:2].T, 1e-8)
-    for k in range(2):
-        # the 3D batch runs the tcgen05 inner matvec (3xTF32 products, FP32 accumulation): FP32
-        # class rounding moves where the oscillating residual first dips below tol
-        assert its[k] - 1 <= reps[k]["iterations"] <= its[k] + 5, (reps[k], its[k])
-        assert np.linalg.norm(Uh[k] - U_ref[:, k]) / np.linalg.norm(U_ref[:, k]) <= 1e-6
+    # 32^3, Schwarz 4 x 4 x 4 partitions (blocks of 729-1000 points), 1-cell overlap, the 64 uniform
+    # right-hand sides (seeds 0..63) in one solve: the launch configuration of the 3D workload
+    # (tcgen05 3xTF32 inner matvec, FP32 inverses, FP64 scalars).  Every column: the true residual
+    # by the oracle's FFT matvec and the count within the oracle ensemble's band at 1e-8 (+-1); two
+    # columns: the oracle's solution; at the stable tolerance every column +-1 of the oracle's FP64
+    # count where the ensemble agrees on it
+    _check_mixed_case("ie3d_n32_m4_d1_uniform64", check_oracle_count=False)
