@@ -4,9 +4,10 @@
 // Storage: block i is padded to npad_i = 32 * ceil(n_i / 32) with an identity in the padding
 // (so its factor is diag(L_i, I) and every tile is full), row-major, at d_loff[i] in one pool.
 //
-// K4 gather_blocks   one thread per entry (a, c), c <= a: the entry is recomputed from the
-//                    integer lattice offset of points idx[a], idx[c] (FP32 SFU-free log2f /
-//                    rsqrtf in IE_MIXED, FP64 log / rsqrt in IE_FP64); the upper part is zeroed.
+// K4 gather_blocks   one thread per entry (a, c), c <= a: the entry of the problem's per-offset FP64
+//                    table at the integer lattice offset of points idx[a], idx[c] (the same FP64
+//                    values as every matvec's), rounded once to the factor's type; the upper part
+//                    is zeroed.
 // K5 chol_blocked    one CTA of 256 threads per block (largest blocks first), right-looking
 //                    blocked Cholesky with 32 x 32 tiles: factor the diagonal tile in shared
 //                    memory, solve the panel below it (one warp per row, lanes = columns), then
@@ -27,10 +28,9 @@ template <typename T>
 __global__ void gather_blocks(T *__restrict__ pool, const long long *__restrict__ loff,
                               const int *__restrict__ npad, const int *__restrict__ nb,
                               const long long *__restrict__ offs, const int *__restrict__ idx,
-                              const float4 *__restrict__ coord, int dim, double diag, double c_const,
-                              double c_ln, double c_log2, double c_r) {
+                              const float4 *__restrict__ coord, const double *__restrict__ t64, int n) {
     const int b = blockIdx.x;
-    const int np = npad[b], n = nb[b];
+    const int np = npad[b], nbk = nb[b];
     T *A = pool + loff[b];
     const int *id = idx + offs[b];
     const long long total = (long long)np * np;
@@ -40,19 +40,15 @@ __global__ void gather_blocks(T *__restrict__ pool, const long long *__restrict_
         T v = 0;
         if (c > a) {
             v = 0;
-        } else if (a >= n || c >= n) {
+        } else if (a >= nbk || c >= nbk) {
             v = (a == c) ? T(1) : T(0);
-        } else if (a == c) {
-            v = (T)diag;
         } else {
+            // the entry of the per-offset FP64 table at the integer lattice offset (exact small
+            // integers in the coordinates; entry 0 is the diagonal), rounded once to T
             const float4 pa = coord[id[a]], pc = coord[id[c]];
-            const float dx = pa.x - pc.x, dy = pa.y - pc.y, dz = pa.z - pc.z;
-            const float r2 = dx * dx + dy * dy + dz * dz;  // exact: small integers
-            if (sizeof(T) == 4) {
-                v = dim == 2 ? (T)((float)c_const + (float)c_log2 * log2f(r2)) : (T)((float)c_r * rsqrtf(r2));
-            } else {
-                v = dim == 2 ? (T)(c_const + c_ln * log((double)r2)) : (T)(c_r * rsqrt((double)r2));
-            }
+            const long long dx = (long long)fabsf(pa.x - pc.x), dy = (long long)fabsf(pa.y - pc.y),
+                            dz = (long long)fabsf(pa.z - pc.z);
+            v = (T)t64[dx + n * (dy + (long long)n * dz)];
         }
         A[e] = v;
     }
@@ -158,16 +154,14 @@ int launch_factor(dd_factor_t *f, cudaStream_t s) {
     dim3 g(f->nblocks, (unsigned)std::min<long long>(65535, std::max<long long>(64, ent / (256LL * 1024))));
     if (f->precision == IE_FP64) {
         gather_blocks<double><<<g, 256, 0, s>>>((double *)f->d_pool, f->d_loff, f->d_npad, f->d_n, part->d_offs,
-                                                part->d_idx, p->d_coord, p->dim, p->diag, p->c_const, p->c_ln,
-                                                p->c_log2, p->c_r);
+                                                part->d_idx, p->d_coord, p->d_table64, p->n);
         IE_LAUNCHED();
         chol_blocked<double><<<f->nblocks, 256, 0, s>>>((double *)f->d_pool, f->d_loff, f->d_npad, f->d_order,
                                                        f->d_info);
         IE_LAUNCHED();
     } else {
         gather_blocks<float><<<g, 256, 0, s>>>((float *)f->d_pool, f->d_loff, f->d_npad, f->d_n, part->d_offs,
-                                               part->d_idx, p->d_coord, p->dim, p->diag, p->c_const, p->c_ln,
-                                               p->c_log2, p->c_r);
+                                               part->d_idx, p->d_coord, p->d_table64, p->n);
         IE_LAUNCHED();
         if (f->inverse) return IE_OK;  // Cholesky and inverse on the tensor cores (launch_factor_tc)
         chol_blocked<float><<<f->nblocks, 256, 0, s>>>((float *)f->d_pool, f->d_loff, f->d_npad, f->d_order,

@@ -1,6 +1,7 @@
 // Mixed-precision subdomain factor on the tensor cores: A_i = L_i L_i^T and the explicit symmetric
 // inverse M_i = A_i^{-1} = W_i^T W_i (W_i = L_i^{-1}) for every block at once, FP32 storage, the
-// bulk of the flops as 3xTF32 tcgen05 MMAs (the exact subdomain solver of Sec. 4.3, Eq. e:ai).
+// bulk of the flops as tcgen05 BF16 MMAs on exact three-part splits of the FP32 operands (the
+// exact subdomain solver of Sec. 4.3, Eq. e:ai).
 //
 // Blocks are cut into tiles of P = 128 rows (the last one ragged, a multiple of 32).  Per block,
 // in phases (a phase's tasks are independent of each other; phase p needs phases < p done):
@@ -28,14 +29,22 @@
 //                       the same arithmetic per task: results are bitwise the same).
 // GEMM task             C (<= 128 x 128) = s_old C + s_acc A B^T, A: m x k and B: n x k row-major
 //                       FP32 with k contiguous (k a multiple of 32).  Per 16-wide chunk the threads
-//                       load A and B with 16-byte L2 loads (the next chunk in flight), split each
-//                       value into TF32 high and low parts and store them in the canonical K-major
-//                       no-swizzle layout (8-row x 16-byte core matrices); one thread issues
-//                       tcgen05.mma.kind::tf32 (M = 128, N = n rounded up to 16, K = 8; A_hi B_hi
-//                       + A_hi B_lo + A_lo B_hi) into an FP32 accumulator in tensor memory; two
-//                       operand stages, tcgen05.commit to per-stage mbarriers, bounded waits.  The
-//                       epilogue stages the accumulator in shared memory (tcgen05.ld 32x32b) and
-//                       writes C row-wise and / or the transposed CT column-wise, both coalesced.
+//                       copy A and B into a ring of three raw shared-memory slots with cp.async (L2
+//                       only; two chunks ahead; each thread later reads back exactly the 16-byte
+//                       pieces it copied, so the ring needs no block barrier), split each FP32
+//                       value v exactly into three BF16 parts v = v0 + v1 + v2 and store the
+//                       parts as three planes in the canonical K-major no-swizzle layout (8-row x
+//                       16-byte core matrices); one thread issues six tcgen05.mma.kind::f16 (M =
+//                       128, N = n rounded up to 16, K = 16) for the part products a_p b_q with
+//                       p + q <= 2 (weights down to 2^-18; every BF16 product is exact in FP32, the
+//                       dropped ones weigh <= 2^-26, so each product is FP32-accurate: three TF32
+//                       products would give only ~2^-21) into an FP32 accumulator in tensor memory;
+//                       same MMA time as three TF32 products, since BF16 runs at twice the TF32
+//                       rate; two operand stages, tcgen05.commit to per-stage mbarriers, bounded
+//                       waits.  The epilogue stages the accumulator in shared memory (tcgen05.ld
+//                       32x32b) and writes C row-wise and / or the transposed CT column-wise, both
+//                       coalesced.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,18 +60,23 @@ namespace {
 
 constexpr int kP = 128;                 // tile rows
 constexpr int kGK = 16;                 // K per operand chunk
-constexpr uint32_t kGLBO = 128;         // bytes between core matrices along K
-constexpr uint32_t kGSBO = (kGK / 4) * 128;  // bytes between 8-row groups
-constexpr int kGOp = kP * kGK;          // 32-bit words of one operand part (128 x 16)
-constexpr int kGStage = 4 * kGOp;       // A hi, A lo, B hi, B lo
-constexpr int kGSmem = 2 * kGStage * 4; // two stages, bytes (64 KB: three CTAs per SM)
+constexpr uint32_t kGLBO = 128;         // bytes between core matrices along K (8 BF16 values each)
+constexpr uint32_t kGSBO = (kGK / 8) * 128;  // bytes between 8-row groups
+constexpr int kGOp = kP * kGK / 2;      // 32-bit words of one BF16 operand plane (128 x 16)
+constexpr int kGStage = 6 * kGOp;       // A planes 0..2, B planes 0..2 (24 KB)
+constexpr int kGPlaneBytes = 2 * kGStage * 4;  // two plane stages (48 KB)
 constexpr int kGF4 = kP * kGK / 4 / 256;  // float4 per thread per operand and chunk (2)
+constexpr int kGRawRow = kGK * 4 + 16;  // raw FP32 row stride in shared memory (80 bytes: the
+                                        // 16-byte reads of eight consecutive rows hit distinct banks)
+constexpr int kGRawOp = kP * kGRawRow;  // one raw operand chunk (10 KB)
+constexpr int kGRawStages = 3;          // raw chunks in flight (cp.async, L2 -> shared memory)
+constexpr int kGSmem = kGPlaneBytes + kGRawStages * 2 * kGRawOp;  // 108 KB: two CTAs per SM
 constexpr int kTS = kP + 1;             // diagonal-kernel tile row stride (floats)
 constexpr int kES = kP / 2 + 1;         // epilogue half-tile row stride (floats)
 constexpr long long kGSpin = 1LL << 24; // non-blocking mbarrier polls before giving up
-// kind::tf32: D FP32 (bit 4), A and B TF32 (bits 7, 10), K-major both, N >> 3 at bit 17, M >> 4 at bit 24
+// kind::f16: D FP32 (bit 4), A and B BF16 (bits 7, 10), K-major both, N >> 3 at bit 17, M >> 4 at bit 24
 __host__ __device__ constexpr uint32_t gidesc(int n) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kP >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kP >> 4) << 24);
 }
 
 struct GemmTask {
@@ -77,10 +91,17 @@ struct GemmTask {
 
 __device__ __forceinline__ uint32_t gsmem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ uint32_t tf32_of(float v) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-    return r;
+// v = b0 + b1 + b2 exactly (three BF16 numbers of 8 significant bits each cover FP32's 24): each
+// part is the round-to-nearest BF16 of what the earlier parts leave, and every remainder is exact
+// in FP32.  Two values at a time (packed conversions): p_q holds part q of x (low half) and of y
+// (high half).
+__device__ __forceinline__ void bf16x3_pair(float x, float y, uint32_t &p0, uint32_t &p1, uint32_t &p2) {
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p0) : "f"(y), "f"(x));
+    float rx = x - __uint_as_float(p0 << 16), ry = y - __uint_as_float(p0 & 0xFFFF0000u);
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p1) : "f"(ry), "f"(rx));
+    rx -= __uint_as_float(p1 << 16);
+    ry -= __uint_as_float(p1 & 0xFFFF0000u);
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p2) : "f"(ry), "f"(rx));
 }
 
 __device__ __forceinline__ uint64_t gdesc(uint32_t saddr) {
@@ -95,7 +116,7 @@ __device__ __forceinline__ uint64_t gdesc(uint32_t saddr) {
 __device__ __forceinline__ void gmma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
@@ -118,32 +139,49 @@ __device__ __forceinline__ bool gbar_wait(uint32_t bar, uint32_t phase) {
     return false;
 }
 
-// One operand part of a chunk: 128 rows x 16 columns as 512 float4; element e of thread tid is
-// e = tid + 256 u: row (e / 32) * 8 + e % 8, float4 column (e / 8) % 4.  Eight consecutive threads
-// take the 8 rows of one core matrix (conflict-free 16-byte stores, 64-byte row segments).  The
-// loads bypass L1 (other CTAs of the persistent factor write these tiles between tasks).
-__device__ __forceinline__ void chunk_fetch(const float *src, int ld, int rows_valid, int c0, int tid,
-                                            float4 (&v)[kGF4]) {
+// One operand chunk (128 rows x 16 columns, 512 float4) copied from global memory into a raw
+// shared-memory slot with cp.async (L2 only: other CTAs of the persistent factor write these tiles
+// between tasks); element e = tid + 256 u: row (e / 32) * 8 + e % 8, float4 column (e / 8) % 4.
+// Rows past rows_valid are zero-filled (source size 0).
+__device__ __forceinline__ void chunk_issue(const float *src, int ld, int rows_valid, int c0, int tid,
+                                            uint32_t raw) {
 #pragma unroll
     for (int u = 0; u < kGF4; ++u) {
         const int e = tid + 256 * u;
         const int r = (e >> 5) * 8 + (e & 7), k4 = (e >> 3) & 3;
-        v[u] = r < rows_valid ? __ldcg(reinterpret_cast<const float4 *>(src + (long long)r * ld + c0 + 4 * k4))
-                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool ok = r < rows_valid;
+        const float *g = src + (ok ? (long long)r * ld + c0 + 4 * k4 : 0);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(raw + (uint32_t)(r * kGRawRow + 16 * k4)),
+                     "l"(g), "r"(ok ? 16 : 0)
+                     : "memory");
     }
 }
 
-__device__ __forceinline__ void chunk_store(const float4 (&v)[kGF4], uint32_t *hi, uint32_t *lo, int tid) {
+// The same elements back from the raw slot (the thread reads the float4s it copied itself)
+__device__ __forceinline__ void chunk_read(const unsigned char *raw, int tid, float4 (&v)[kGF4]) {
 #pragma unroll
     for (int u = 0; u < kGF4; ++u) {
         const int e = tid + 256 * u;
         const int r = (e >> 5) * 8 + (e & 7), k4 = (e >> 3) & 3;
-        const uint32_t off = (uint32_t)(((r >> 3) * kGSBO + k4 * kGLBO + (r & 7) * 16) >> 2);
-        const uint32_t h0 = tf32_of(v[u].x), h1 = tf32_of(v[u].y), h2 = tf32_of(v[u].z), h3 = tf32_of(v[u].w);
-        *reinterpret_cast<uint4 *>(hi + off) = make_uint4(h0, h1, h2, h3);
-        *reinterpret_cast<uint4 *>(lo + off) =
-            make_uint4(tf32_of(v[u].x - __uint_as_float(h0)), tf32_of(v[u].y - __uint_as_float(h1)),
-                       tf32_of(v[u].z - __uint_as_float(h2)), tf32_of(v[u].w - __uint_as_float(h3)));
+        v[u] = *reinterpret_cast<const float4 *>(raw + r * kGRawRow + 16 * k4);
+    }
+}
+
+// The three BF16 planes of one operand chunk in the canonical K-major layout: plane q holds part
+// q of every value; row r's 16 values are two core-matrix rows of 8 (16 bytes each), a float4 of
+// thread data is half of one (8 bytes).
+__device__ __forceinline__ void chunk_store(const float4 (&v)[kGF4], uint32_t *planes, int tid) {
+#pragma unroll
+    for (int u = 0; u < kGF4; ++u) {
+        const int e = tid + 256 * u;
+        const int r = (e >> 5) * 8 + (e & 7), k4 = (e >> 3) & 3;
+        const uint32_t off = (uint32_t)(((r >> 3) * kGSBO + (k4 >> 1) * kGLBO + (r & 7) * 16 + (k4 & 1) * 8) >> 2);
+        uint32_t p0, p1, p2, q0, q1, q2;
+        bf16x3_pair(v[u].x, v[u].y, p0, p1, p2);
+        bf16x3_pair(v[u].z, v[u].w, q0, q1, q2);
+        *reinterpret_cast<uint2 *>(planes + off) = make_uint2(p0, q0);
+        *reinterpret_cast<uint2 *>(planes + kGOp + off) = make_uint2(p1, q1);
+        *reinterpret_cast<uint2 *>(planes + 2 * kGOp + off) = make_uint2(p2, q2);
     }
 }
 
@@ -161,46 +199,60 @@ __device__ void gemm_task(const GemmTask &t, uint32_t *gsm, GemmCta &c) {
     const int nch = t.k / kGK;
     const uint32_t idesc = gidesc((t.n + 15) & ~15);
     int pending[2] = {0, 0};
-    float4 va[kGF4], vb[kGF4];  // the next chunk, in flight while the current one is stored and multiplied
-    if (nch > 0) {
-        chunk_fetch(t.A, t.lda, t.m, 0, tid, va);
-        chunk_fetch(t.B, t.ldb, t.n, 0, tid, vb);
+    unsigned char *raw0 = reinterpret_cast<unsigned char *>(gsm) + kGPlaneBytes;
+    const uint32_t raw0_s = gsmem_u32(raw0);
+    auto raw_of = [&](int ch) { return (uint32_t)((ch % kGRawStages) * 2 * kGRawOp); };
+    // prologue: chunks 0 and 1 in flight; every chunk index gets one commit group (empty past the
+    // end), so that "all but the newest group" is always the chunk about to be converted
+    for (int ch = 0; ch < 2; ++ch) {
+        if (ch < nch) {
+            chunk_issue(t.A, t.lda, t.m, ch * kGK, tid, raw0_s + raw_of(ch));
+            chunk_issue(t.B, t.ldb, t.n, ch * kGK, tid, raw0_s + raw_of(ch) + kGRawOp);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
     for (int ch = 0; ch < nch; ++ch) {
         const int st = ch & 1;
-        uint32_t *Ahi = gsm + st * kGStage, *Alo = Ahi + kGOp, *Bhi = Alo + kGOp, *Blo = Bhi + kGOp;
-        if (pending[st]) {  // the stage's previous MMAs must be done before its operands change;
+        uint32_t *Ap = gsm + st * kGStage, *Bp = Ap + 3 * kGOp;
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // this thread's copies of chunk ch
+        if (pending[st]) {  // the plane stage's previous MMAs must be done before it changes;
                             // one thread waits, the barrier below releases the others
             if (tid == 0 && !gbar_wait(gsmem_u32(&c.mbar[st]), c.ph[st])) *c.abort_flag = 1;
             c.ph[st] ^= 1u;
             pending[st] = 0;
         }
-        __syncthreads();
+        __syncthreads();  // every copy of chunk ch landed; every read of raw slot (ch + 2) % 3 done
         if (*c.abort_flag) break;
-        chunk_store(va, Ahi, Alo, tid);
-        chunk_store(vb, Bhi, Blo, tid);
-        if (ch + 1 < nch) {
-            chunk_fetch(t.A, t.lda, t.m, (ch + 1) * kGK, tid, va);
-            chunk_fetch(t.B, t.ldb, t.n, (ch + 1) * kGK, tid, vb);
+        float4 va[kGF4], vb[kGF4];
+        chunk_read(raw0 + raw_of(ch), tid, va);
+        chunk_read(raw0 + raw_of(ch) + kGRawOp, tid, vb);
+        if (ch + 2 < nch) {
+            chunk_issue(t.A, t.lda, t.m, (ch + 2) * kGK, tid, raw0_s + raw_of(ch + 2));
+            chunk_issue(t.B, t.ldb, t.n, (ch + 2) * kGK, tid, raw0_s + raw_of(ch + 2) + kGRawOp);
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        chunk_store(va, Ap, tid);
+        chunk_store(vb, Bp, tid);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ah = gsmem_u32(Ahi), al = gsmem_u32(Alo), bh = gsmem_u32(Bhi), bl = gsmem_u32(Blo);
-#pragma unroll
-            for (int s = 0; s < kGK / 8; ++s) {
-                const uint32_t ko = (uint32_t)s * 2 * kGLBO;
-                gmma(c.tmem, gdesc(ah + ko), gdesc(bh + ko), idesc, (ch > 0 || s > 0) ? 1u : 0u);
-                gmma(c.tmem, gdesc(ah + ko), gdesc(bl + ko), idesc, 1u);
-                gmma(c.tmem, gdesc(al + ko), gdesc(bh + ko), idesc, 1u);
-            }
+            // the six BF16 part products of weight >= 2^-16 relative (a_p b_q with p + q <= 2), one
+            // K = 16 MMA each: every product is exact in the FP32 accumulator
+            const uint32_t a0 = gsmem_u32(Ap), b0 = gsmem_u32(Bp), pl = (uint32_t)kGOp * 4u;
+            gmma(c.tmem, gdesc(a0), gdesc(b0), idesc, ch > 0 ? 1u : 0u);
+            gmma(c.tmem, gdesc(a0), gdesc(b0 + pl), idesc, 1u);
+            gmma(c.tmem, gdesc(a0 + pl), gdesc(b0), idesc, 1u);
+            gmma(c.tmem, gdesc(a0), gdesc(b0 + 2 * pl), idesc, 1u);
+            gmma(c.tmem, gdesc(a0 + pl), gdesc(b0 + pl), idesc, 1u);
+            gmma(c.tmem, gdesc(a0 + 2 * pl), gdesc(b0), idesc, 1u);
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              gsmem_u32(&c.mbar[st]))
                          : "memory");
         }
         pending[st] = 1;
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy in flight past the task
     for (int st = 0; st < 2; ++st) {  // drain (bounded, one thread; waits even after an abort so
                                       // that no MMA is in flight when the CTA moves on)
         if (pending[st]) {
@@ -238,12 +290,21 @@ __device__ void gemm_task(const GemmTask &t, uint32_t *gsm, GemmCta &c) {
         }
         __syncthreads();
         if (t.C) {
-            for (int e = tid; e < kP * 64; e += 256) {
-                const int r = e >> 6, cl = e & 63, cc = cbase + cl;
-                if (r < t.m && cc < t.n && (!t.diag || r >= cc)) {
-                    float *dst = t.C + (long long)r * t.ldc + cc;
-                    const float a = T[r * kES + cl];
-                    *dst = t.s_old != 0.f ? fmaf(t.s_acc, a, t.s_old * __ldcg(dst)) : t.s_acc * a;
+            // 16 elements per batch: their old values are loaded together before any store (the
+            // compiler cannot overlap a load with an earlier store through the same pointer)
+            for (int e0 = 0; e0 < kP * 64; e0 += 256 * 16) {
+                float old[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int e = e0 + tid + 256 * i, r = e >> 6, cc = cbase + (e & 63);
+                    const bool in = r < t.m && cc < t.n && (!t.diag || r >= cc);
+                    old[i] = (in && t.s_old != 0.f) ? __ldcg(t.C + (long long)r * t.ldc + cc) : 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int e = e0 + tid + 256 * i, r = e >> 6, cl = e & 63, cc = cbase + cl;
+                    if (r < t.m && cc < t.n && (!t.diag || r >= cc))
+                        t.C[(long long)r * t.ldc + cc] = fmaf(t.s_acc, T[r * kES + cl], t.s_old * old[i]);
                 }
             }
         }
@@ -260,25 +321,71 @@ __device__ void gemm_task(const GemmTask &t, uint32_t *gsm, GemmCta &c) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 
+// X = L^{-1} of the lower-triangular 32 x 32 tile L (row stride ld) into X (row stride 33, zero
+// above the diagonal), all 256 threads: warp w takes columns 4w .. 4w + 3 and runs their chains
+// down the column together (lane = row, entries shuffled down).
+__device__ __forceinline__ void tile_inverse32(const float *L, int ld, float *X) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float lrow[32];
+    float dii = 1.f;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        lrow[c] = c <= lane ? L[lane * ld + c] : 0.f;
+        if (c == lane) dii = lrow[c];
+    }
+    const float rdii = 1.f / dii;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) X[lane * 33 + 4 * warp + q] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = 4 * warp + q;
+            if (k >= j) {
+                const float mine = lane == k ? (k == j ? rdii : -acc[q] * rdii) : 0.f;
+                const float xk = __shfl_sync(0xffffffffu, mine, k);
+                if (lane == k) X[k * 33 + j] = xk;
+                if (lane > k) acc[q] = fmaf(lrow[k], xk, acc[q]);
+            }
+        }
+    }
+}
+
 // The diagonal tile of panel k0 of block b, in one 128 x 129 shared tile D: the block's entries,
-// then L_kk (written back), then Tinv = L_kk^{-1} in place.
+// then L_kk (written back), then Tinv = L_kk^{-1} in place.  Per 32-column step: one warp factors
+// the 32 x 32 diagonal sub-tile in registers, all warps invert it (X11, kept in Xd for the final
+// inverse), the rows below become L21 = A21 X11^T (a product, no divisions or dependency chains),
+// and the trailing lower part is updated.  Xd: 4 x 32 x 33 floats after D.
 __device__ void diag_task(float *__restrict__ pool, float *__restrict__ wt, float *__restrict__ tinv,
                           const long long *__restrict__ loff, const long long *__restrict__ toff,
                           const int *__restrict__ npad, int b, int k0, int *__restrict__ info, float *D, int *bad) {
     const int np = npad[b], pk = min(kP, np - k0), nt = pk / 32;
     float *A = pool + loff[b] + (long long)k0 * np + k0;
+    float *Xd = D + kP * kTS;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kRows = (kP - 32) * 32 / 256;  // outputs per thread below a 32-column block (12)
     if (tid == 0) *bad = -1;
-    for (int e = tid; e < kP * kP; e += 256) {
-        const int r = e >> 7, c = e & (kP - 1);
-        D[r * kTS + c] = (r < pk && c <= r) ? __ldcg(A + (long long)r * np + c) : 0.f;
+    // the tile's lower part into D, 16 loads in flight per thread (the compiler cannot overlap
+    // loads with stores through pointers that may alias)
+    for (int e0 = 0; e0 < kP * kP; e0 += 256 * 16) {
+        float v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int e = e0 + tid + 256 * i, r = e >> 7, c = e & (kP - 1);
+            v[i] = (r < pk && c <= r) ? __ldcg(A + (long long)r * np + c) : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int e = e0 + tid + 256 * i;
+            D[(e >> 7) * kTS + (e & (kP - 1))] = v[i];
+        }
     }
     __syncthreads();
-    // blocked Cholesky of D (32-wide): diagonal sub-tile column by column, panel, trailing update
     for (int kk = 0; kk < nt; ++kk) {
-        const int c0 = kk * 32;
+        const int c0 = kk * 32, r0 = c0 + 32, rest = pk - r0;
         // the 32 x 32 diagonal sub-tile in one warp's registers (lane = row): right-looking,
-        // column j's entries shuffled to the lanes that update with them; no block barrier
+        // column j's entries shuffled to the lanes that update with them
         if (warp == 0) {
             float row[32];
 #pragma unroll
@@ -306,29 +413,41 @@ __device__ void diag_task(float *__restrict__ pool, float *__restrict__ wt, floa
                 if (c <= lane) D[(c0 + lane) * kTS + c0 + c] = row[c];
         }
         __syncthreads();
-        // rows below the sub-tile: X L^T = D (one warp per row, lanes = columns)
-        for (int row = c0 + 32 + warp; row < pk; row += 8) {
-            float v = D[row * kTS + c0 + lane];
-            for (int c = 0; c < 32; ++c) {
-                const float xc = __shfl_sync(0xffffffffu, v, c) / D[(c0 + c) * kTS + c0 + c];
-                if (lane == c) v = xc;
-                if (lane > c) v = fmaf(-xc, D[(c0 + lane) * kTS + c0 + c], v);
-            }
-            D[row * kTS + c0 + lane] = v;
-        }
+        float *X11 = Xd + kk * 32 * 33;
+        tile_inverse32(D + c0 * kTS + c0, kTS, X11);
         __syncthreads();
-        // trailing lower part: D[i][c] -= sum_t D[i][c0 + t] D[c][c0 + t], c0 + 32 <= c <= i < pk
-        const int r0 = c0 + 32, rest = pk - r0;
-        for (int e = tid; e < rest * rest; e += 256) {
-            const int i = r0 + e / rest, c = r0 + e % rest;
-            if (c <= i) {
-                float s = 0.f;
+        if (rest > 0) {
+            // L21 = A21 X11^T: thread column c = lane, rows r0 + warp + 8 i
+            float u[kRows];
+#pragma unroll
+            for (int i = 0; i < kRows; ++i) {
+                const int r = r0 + warp + 8 * i;
+                float acc = 0.f;
+                if (r < pk) {
 #pragma unroll 8
-                for (int t2 = 0; t2 < 32; ++t2) s = fmaf(D[i * kTS + c0 + t2], D[c * kTS + c0 + t2], s);
-                D[i * kTS + c] -= s;
+                    for (int t2 = 0; t2 < 32; ++t2) acc = fmaf(D[r * kTS + c0 + t2], X11[lane * 33 + t2], acc);
+                }
+                u[i] = acc;
             }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < kRows; ++i) {
+                const int r = r0 + warp + 8 * i;
+                if (r < pk) D[r * kTS + c0 + lane] = u[i];
+            }
+            __syncthreads();
+            // trailing lower part: D[i][c] -= sum_t D[i][c0 + t] D[c][c0 + t], r0 <= c <= i < pk
+            // (warp: rows i = r0 + warp + 8 s; lane: columns c = r0 + lane + 32 q)
+            for (int i = r0 + warp; i < pk; i += 8) {
+                for (int c = r0 + lane; c <= i; c += 32) {
+                    float sum = 0.f;
+#pragma unroll 8
+                    for (int t2 = 0; t2 < 32; ++t2) sum = fmaf(D[i * kTS + c0 + t2], D[c * kTS + c0 + t2], sum);
+                    D[i * kTS + c] -= sum;
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
     // L_kk back to the pool (lower part)
     for (int e = tid; e < pk * pk; e += 256) {
@@ -337,38 +456,11 @@ __device__ void diag_task(float *__restrict__ pool, float *__restrict__ wt, floa
     }
     __syncthreads();
     // D := L_kk^{-1} in place, 32-column blocks from the last one back: with L = [L11 0; L21 L22]
-    // and X22 = L22^{-1} already in place, X11 = L11^{-1} (one warp, registers) and
-    // X21 = -X22 (L21 X11), each product formed in registers before it overwrites its operand
-    constexpr int kRows = (kP - 32) * 32 / 256;  // outputs per thread below a 32-column block (12)
+    // and X22 = L22^{-1} already in place, X21 = -X22 (L21 X11) with X11 from Xd, each product
+    // formed in registers before it overwrites its operand
     for (int jb = nt - 1; jb >= 0; --jb) {
         const int c0 = jb * 32, r0 = c0 + 32, rest = pk - r0;
-        {
-            // X11 = L11^{-1}: the columns are independent; warp w takes columns 4w .. 4w + 3 and
-            // runs their chains down the column together (lane = row, entries shuffled down)
-            float lrow[32];
-            float dii = 1.f;
-#pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                lrow[c] = c <= lane ? D[(c0 + lane) * kTS + c0 + c] : 0.f;
-                if (c == lane) dii = lrow[c];
-            }
-            __syncthreads();  // every warp holds its rows of L11 before X11 overwrites them
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int k = 0; k < 32; ++k) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int j = 4 * warp + q;
-                    if (k >= j) {
-                        const float mine = lane == k ? (k == j ? 1.f / dii : -acc[q] / dii) : 0.f;
-                        const float xk = __shfl_sync(0xffffffffu, mine, k);
-                        if (lane == k) D[(c0 + k) * kTS + c0 + j] = xk;
-                        if (lane > k) acc[q] = fmaf(lrow[k], xk, acc[q]);
-                    }
-                }
-            }
-        }
-        __syncthreads();
+        const float *X11 = Xd + jb * 32 * 33;
         if (rest > 0) {
             // thread: column c = lane, rows r0 + warp + 8 i
             float u[kRows];
@@ -377,8 +469,7 @@ __device__ void diag_task(float *__restrict__ pool, float *__restrict__ wt, floa
                 const int r = r0 + warp + 8 * i;
                 float acc = 0.f;
                 if (r < pk) {
-                    for (int t2 = lane; t2 < 32; ++t2)
-                        acc = fmaf(D[r * kTS + c0 + t2], D[(c0 + t2) * kTS + c0 + lane], acc);
+                    for (int t2 = lane; t2 < 32; ++t2) acc = fmaf(D[r * kTS + c0 + t2], X11[t2 * 33 + lane], acc);
                 }
                 u[i] = acc;  // (L21 X11)[r][c]
             }
@@ -404,8 +495,13 @@ __device__ void diag_task(float *__restrict__ pool, float *__restrict__ wt, floa
                 const int r = r0 + warp + 8 * i;
                 if (r < pk) D[r * kTS + c0 + lane] = u[i];
             }
-            __syncthreads();
         }
+        // X11 into the diagonal block (L11 is no longer needed)
+        for (int e = tid; e < 32 * 32; e += 256) {
+            const int r = e >> 5, c = e & 31;
+            D[(c0 + r) * kTS + c0 + c] = X11[r * 33 + c];
+        }
+        __syncthreads();
     }
     // Tinv (128 x 128, zero outside pk x pk) and the diagonal tile of W^T (Tinv^T, zero below)
     float *Tb = tinv + toff[b] + (long long)(k0 / kP) * kP * kP;
@@ -436,7 +532,7 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
 
 constexpr long long kDepSpin = 1LL << 26;  // polls (~1 us each at most) of a block's counter
 
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 2)
 factor_persistent(const FTask *__restrict__ tasks, int ntasks, int *__restrict__ next, int *__restrict__ done,
                   float *__restrict__ pool, float *__restrict__ wt, float *__restrict__ tinv,
                   const long long *__restrict__ loff, const long long *__restrict__ toff,
@@ -510,7 +606,7 @@ factor_persistent(const FTask *__restrict__ tasks, int ntasks, int *__restrict__
 
 }  // namespace
 
-constexpr int kDiagSmem = kP * kTS * (int)sizeof(float);
+constexpr int kDiagSmem = (kP * kTS + 4 * 32 * 33) * (int)sizeof(float);
 constexpr int kFSmem = kDiagSmem > kGSmem ? kDiagSmem : kGSmem;
 
 int prepare_tc_factor() {
@@ -618,7 +714,7 @@ void build_plan(const std::vector<int> &npad, const std::vector<long long> &loff
 }
 
 // candidates of the factor's autotuner: CTAs per SM x skew
-constexpr int kFactorCand[][2] = {{3, 1}, {3, 2}, {3, 4}, {2, 2}};
+constexpr int kFactorCand[][2] = {{2, 1}, {2, 2}, {2, 4}, {1, 2}};
 constexpr int kFactorNCand = (int)(sizeof(kFactorCand) / sizeof(kFactorCand[0]));
 
 }  // namespace
@@ -659,7 +755,7 @@ int launch_factor_tc(dd_factor_t *f, const std::vector<int> &npad, const std::ve
     // IEDD_FACTOR_SCHEDULE="c,s" fixes the schedule (c CTAs per SM, skew s) instead of the tuner's
     int force_ctas = 0, force_skew = 0;
     if (const char *env = std::getenv("IEDD_FACTOR_SCHEDULE")) {
-        if (std::sscanf(env, "%d,%d", &force_ctas, &force_skew) != 2 || force_ctas < 1 || force_ctas > 3 ||
+        if (std::sscanf(env, "%d,%d", &force_ctas, &force_skew) != 2 || force_ctas < 1 || force_ctas > 2 ||
             force_skew < 1 || force_skew > 64)
             force_ctas = force_skew = 0;
     }
@@ -681,7 +777,7 @@ int launch_factor_tc(dd_factor_t *f, const std::vector<int> &npad, const std::ve
 
     const std::string key = "factor/nb" + std::to_string(nb) + "/max" + std::to_string(f->max_pad) + "/sum" +
                             std::to_string(sum_np);
-    int cand = 1;  // default: three CTAs per SM, skew 2
+    int cand = 1;  // default: two CTAs per SM, skew 2
     int tuned = -1;
     // tuning runs every candidate once: only where a factor is cheap (not the dense CBD colour
     // blocks, whose factor takes seconds)
