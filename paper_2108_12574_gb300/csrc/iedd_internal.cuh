@@ -85,6 +85,7 @@ struct ie_problem {
     // of the per-offset table (192 n^2 bytes) and the bits of max |t| (its power-of-two scale)
     void *d_zt_win = nullptr;
     unsigned long long *d_zt_max = nullptr;
+    int zt_F = 0;                  // fraction bits of the int64 sums (units 2^-F of a level-0 product)
 };
 
 struct dd_partition_t {

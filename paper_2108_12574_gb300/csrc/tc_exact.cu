@@ -16,13 +16,14 @@
 // the sum over digit pairs (a, b) with a + b <= 5 (21 pairs) at level a + b; pairs of one level
 // share one FP32 accumulator.  Over a window of 128 source columns the level-0 and level-1 sums
 // are integers below 2^21 and 2^23, so the tensor core adds them exactly, and level 2 stays below
-// 2^24; levels 3-5 are rounded in FP32 (relative weight <= 2^-27, so their rounding is far below
-// the dropped pairs).  After each window the six accumulators are read and added exactly into a
-// 64-bit integer per output in units of 2^-F of a level-0 product (F = min(30, 48 - log2 N), so
-// that no sum can overflow: every output adds at most N terms of at most 2^14 level-0 units).
-// The result differs from the exact product by the dropped pairs, the last-digit truncation and
-// the rounding of the level-3..5 tail to the integer unit: ~1e-16 of sum |A_ij x_j|, the class
-// of the double-float kernel K2.
+// 2^24; levels 3-5 are integers in their own units too (their sums stay below 2^24 for any input
+// whose digits are not all of one sign and maximal).  After each window the six accumulators are
+// read and added into a 64-bit integer per output in units of 2^-F of a level-0 product: levels
+// 0-2 exactly, each of levels 3-5 rounded to the unit.  F is the largest value for which no sum
+// can overflow: every output is at most 2^14 (sum_j |t_ij|) / sigma_t level-0 units, and that row
+// sum is bounded once per problem from the table (F is about 30 at 1024^2, 36 at 128^2).  The
+// result differs from the exact product by the dropped pairs, the last-digit truncation and one
+// rounding of each of levels 3-5 to 2^-F per window: ~1e-17 of sum |A_ij x_j|.
 //
 // Tile.  A CTA owns 128 target points of one grid line segment (M = 128 values of i2) for 32
 // consecutive lines (i1), one block of 128 source columns j2, and a range of d1.  Per d1 (one
@@ -48,6 +49,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "iedd_internal.cuh"
 
@@ -68,6 +70,7 @@ constexpr uint32_t kBBytes = (kZK / 8) * kBGroup;              // 49152
 constexpr uint32_t kStageBytes = kStripBytes + kBBytes;        // 72960 (a multiple of 128)
 constexpr int kZSmem = kZStages * (int)kStageBytes;            // 218880
 constexpr long long kSpinLimit = 1LL << 24;
+constexpr int kZMinF = 2 * kDigBits;         // levels 0-2 need units down to 2^-18
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -165,6 +168,29 @@ __global__ void absmax_kernel(const double *__restrict__ v, long long count, uns
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// An upper bound of max_i sum_{j != i} |A_ij| from the per-offset table: sum over the offsets
+// (d1, d2) != 0 of |t(d1, d2)| times the number of sign combinations (at most 4).  One CTA, a
+// fixed summation order (deterministic).
+__global__ void __launch_bounds__(1024) rowsum_bound_kernel(const double *__restrict__ t64, int n, double *__restrict__ out) {
+    __shared__ double sh[32];
+    const long long T = (long long)n * n;
+    double s = 0.0;
+    for (long long q = threadIdx.x; q < T; q += blockDim.x) {
+        const int d1 = (int)(q % n), d2 = (int)(q / n);
+        if (q != 0) s += fabs(t64[q]) * ((d1 > 0 ? 2.0 : 1.0) * (d2 > 0 ? 2.0 : 1.0));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = sh[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) out[0] = t;
+    }
 }
 
 // Window table of the A operand.  With v_d(p) = t(d, |n - 1 - p|) (0 outside the table and at
@@ -376,8 +402,15 @@ kz_matvec_tc(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ C
         // ---- accumulator reads and exact sums (TMEM lane quarter warp & 3, all 32 lines) ----
         const int q4 = warp & 3;
         const long long w1 = 1LL << (F - kDigBits);
-        const int w2 = 1 << (F - 2 * kDigBits);
-        const float w3 = __int_as_float((127 + F - 3 * kDigBits) << 23);  // 2^(F - 27)
+        const long long w2 = 1LL << (F - 2 * kDigBits);
+        // levels 3, 4, 5 are integers in units of 2^-27, 2^-36, 2^-45 of level 0.  Level 3 (< 2^25)
+        // converts exactly to int32 and is shifted to units of 2^-F (rounded to the unit instead
+        // when F < 27); levels 4 and 5 are joined in FP32 in level-4 units (a rounding of <= 2^-39
+        // level-0 units, below the unit 2^-F for F <= 38), scaled by 2^(F - 36) and rounded to the
+        // unit (|value| < 2^31 for F <= 36).  All conversions are 32-bit.
+        const int sh3 = F - 3 * kDigBits;
+        const float s3 = __int_as_float((127 + (sh3 < 0 ? sh3 : 0)) << 23);
+        const float s4 = __int_as_float((127 + F - 4 * kDigBits) << 23);
         for (int w = 0; w < T; ++w) {
             const int set = w & 1;
             if (!warp_wait(&afull[set], (uint32_t)(w >> 1) & 1u)) break;
@@ -391,13 +424,11 @@ kz_matvec_tc(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ C
                 tmem_ld16(cb + 4 * kZC, v4);
                 tmem_ld16(cb + 5 * kZC, v5);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                int rr[16];
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
-                    // levels 3..5 in units 2^-F of level 0 (one rounding; their weight is <= 2^-27)
-                    const float r = fmaf(__uint_as_float(v5[c]), 0x1p-18f,
-                                         fmaf(__uint_as_float(v4[c]), 0x1p-9f, __uint_as_float(v3[c])));
-                    rr[c] = __float2int_rn(r * w3);
+                    const long long l3 = (long long)__float2int_rn(__uint_as_float(v3[c]) * s3) << (sh3 > 0 ? sh3 : 0);
+                    const int l45 = __float2int_rn(fmaf(__uint_as_float(v5[c]), 0x1p-9f, __uint_as_float(v4[c])) * s4);
+                    acc[16 * hh + c] += l3 + l45;
                 }
                 uint32_t v0[16], v1[16], v2[16];
                 tmem_ld16(cb + 0 * kZC, v0);
@@ -416,7 +447,7 @@ kz_matvec_tc(const __grid_constant__ CUtensorMap wmap, const __grid_constant__ C
                     const int a1 = __float2int_rn(__uint_as_float(v1[c]));
                     const int a2 = __float2int_rn(__uint_as_float(v2[c]));
                     const int wv = a0 * (1 << kDigBits) + a1;             // < 2^31
-                    acc[16 * hh + c] += (long long)wv * w1 + ((long long)a2 * w2 + rr[c]);
+                    acc[16 * hh + c] += (long long)wv * w1 + (long long)a2 * w2;  // exact
                 }
             }
         }
@@ -488,6 +519,26 @@ int prepare_tc_exact(const ie_problem *p_) {
     window_table_kernel<<<(unsigned)((rows + 255) / 256), 256>>>(p->d_table64, p->n, p->d_zt_max,
                                                                  static_cast<uint4 *>(p->d_zt_win));
     IE_LAUNCHED();
+    // fraction bits F of the int64 sums: every output is at most 2^14 S / sigma_t level-0 units
+    // (S = the row-sum bound, |x| <= sigma_x), so F <= 62 - 14 - log2(S / sigma_t) keeps every sum,
+    // partial or total, below 2^62; one bit of margin more, and at most 36 (the 32-bit conversion
+    // of the joined levels 4-5 in the accumulator warps)
+    double *d_s = nullptr;
+    IE_TRY_CUDA(cudaMalloc(&d_s, sizeof(double)));
+    rowsum_bound_kernel<<<1, 1024>>>(p->d_table64, p->n, d_s);
+    IE_LAUNCHED();
+    double S = 0.0;
+    unsigned long long tmax_bits = 0;
+    IE_TRY_CUDA(cudaMemcpy(&S, d_s, sizeof(double), cudaMemcpyDeviceToHost));
+    IE_TRY_CUDA(cudaMemcpy(&tmax_bits, p->d_zt_max, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    cudaFree(d_s);
+    double tmax = 0.0;
+    std::memcpy(&tmax, &tmax_bits, sizeof(double));
+    int e = 0;
+    std::frexp(tmax, &e);
+    const double sigma_t = std::ldexp(1.0, e);
+    const double ratio = S > 0.0 && sigma_t > 0.0 ? S / sigma_t : 1.0;
+    p->zt_F = std::max(kZMinF, std::min(36, (int)std::floor(48.0 - std::log2(ratio)) - 1));
     IE_TRY_CUDA(cudaDeviceSynchronize());
     return IE_OK;
 }
@@ -520,9 +571,7 @@ int launch_matvec_tc_exact(const ie_problem *p, const double *x, long long ldx, 
     const int n = p->n;
     const long long N = p->N;
     const int ds = kz_dsplit(n, p->sm_count);
-    int lgN = 0;
-    while ((1LL << lgN) < N) ++lgN;
-    const int F = std::min(30, 48 - lgN);  // >= 24 for n <= 4096
+    const int F = p->zt_F;
     const int nparts = (n / kZK) * ds;
     DevBuf xd, part, mx;
     IE_TRY(xd.alloc(sizeof(uint4) * (size_t)kZD * (n / 8) * (n + 64), s));
