@@ -231,7 +231,9 @@ typedef struct {
                             final verification, r0 from a given x0):
                               0            the library's choice: IE_FFT where supported
                                            (n <= 4096), else IE_FP64 / IE_ACCURATE by precision
-                              IE_FFT, IE_FP64, IE_ACCURATE   that matvec */
+                              IE_FFT, IE_ACCURATE   that matvec
+                              16           the FP64 regenerated matvec (IE_FP64 is 0, the
+                                           library's choice, so it is selected as 16) */
 } pcg_opts;
 
 typedef struct {
@@ -302,6 +304,10 @@ IEDD_API int ie_matvec_noalloc(int dim, int n, double a_shift, int grid, const d
  *                 the scaled target u, for `batch` <= 16 device columns of f and u (ld >= N) of a
  *                 2D problem; *loss (host, may be NULL) receives the loss before the step.
  * ws_predict      u0 for nrhs device columns of f (ld >= N).  Asynchronous.
+ * The forward 3x3 convolutions run on the tensor cores (BF16 operands, FP32 accumulation); a
+ * convolution whose bounded wait for its MMAs ran out leaves a device flag that the next
+ * synchronising call (ws_forward_raw, ws_backward_raw, ws_train_step with loss != NULL) reports
+ * as IE_ERR_TIMEOUT, clearing it; outputs are then unspecified.
  */
 typedef struct ws_model ws_model;
 IEDD_API int ws_create(int device, unsigned long long seed, ws_model **out);

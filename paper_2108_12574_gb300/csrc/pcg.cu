@@ -272,6 +272,7 @@ struct Solver {
     // matvec where it is supported (the paper's matvec, FP64-class and far cheaper than an FP64
     // or double-float regenerated sum); else the regenerated FP64 / double-float sum
     int acc_precision() const {
+        if (o.residual == IE_FP64 + 16) return IE_FP64;
         if (o.residual) return o.residual;
         if (o.inner == IE_FFT || fft_supported(p, nullptr)) return IE_FFT;
         return o.precision == IE_FP64 ? IE_FP64 : IE_ACCURATE;
@@ -368,7 +369,7 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
         (o.inner != 0 && o.inner != IE_MIXED && o.inner != IE_ACCURATE && o.inner != IE_ACCURATE_X32 &&
          o.inner != IE_TENSOR && o.inner != IE_ACCURATE_R4 && o.inner != IE_ACCURATE_R16 &&
          o.inner != IE_FP64 + 16 && o.inner != IE_FFT && o.inner != IE_TENSOR_EXACT) ||
-        (o.residual != 0 && o.residual != IE_ACCURATE && o.residual != IE_FP64 && o.residual != IE_FFT)) {
+        (o.residual != 0 && o.residual != IE_ACCURATE && o.residual != IE_FP64 + 16 && o.residual != IE_FFT)) {
         ie_set_error("pcg_solve: invalid options"); return IE_ERR_ARG;
     }
     if (o.check_every < 1) o.check_every = 1;
