@@ -493,6 +493,12 @@ extern "C" int dd_factor(const ie_problem *p, const dd_partition_t *s, int preci
         f->xtotal = xoff.back();
         if ((e = cudaMalloc(&f->d_xoff, sizeof(long long) * xoff.size())) != cudaSuccess) return fail(e);
         if ((e = cudaMemcpy(f->d_xoff, xoff.data(), sizeof(long long) * xoff.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+        // the tensor-core batched apply: per block the first of its 128-row tiles
+        std::vector<long long> toff((size_t)s->nblocks + 1, 0);
+        for (int i = 0; i < s->nblocks; ++i) toff[(size_t)i + 1] = toff[(size_t)i] + (nb[(size_t)i] + 127) / 128;
+        f->ntiles = (int)toff.back();
+        if ((e = cudaMalloc(&f->d_tile_off, sizeof(long long) * toff.size())) != cudaSuccess) return fail(e);
+        if ((e = cudaMemcpy(f->d_tile_off, toff.data(), sizeof(long long) * toff.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
         for (int k = 0; k < 3; ++k) {  // work items of kApplyRowOpts[k] rows, largest blocks first
             std::vector<int2> chunks;
             for (int i : order)
@@ -556,6 +562,7 @@ extern "C" void dd_factor_destroy(dd_factor_t *f) {
     DeviceGuard g(f->device);
     cudaFree(f->d_loff);
     cudaFree(f->d_npad);
+    cudaFree(f->d_tile_off);
     cudaFree(f->d_n);
     cudaFree(f->d_order);
     cudaFree(f->d_info);

@@ -570,7 +570,12 @@ int launch_apply(const dd_factor_t *f, const double *r, long long ldr, double *z
         }
         IE_LAUNCHED();
         const int klass = !exact ? kApplyF8 : (nrhs >= 4 && batch_fits) ? kApplyE4 : kApplyE1;
-        if (klass == kApplyE1 && f->ncitems > 0) {
+        if (klass == kApplyF8 && nrhs >= kApplyTensorFrom) {
+            // 3D batches of 32 or more columns: GEMM tasks on the tensor cores (measured on GB300,
+            // 32^3 blocks: 0.27 ms for 64 columns against 0.40 ms with FP32 FMAs; at 16 columns the
+            // FMA kernel is faster)
+            IE_TRY(launch_apply_tc(f, xh, xe.as<int>(), nrhs, zbuf.as<double>(), s));
+        } else if (klass == kApplyE1 && f->ncitems > 0) {
             // large blocks: column-chunked work items, then the FP64 chunk sums
             DevBuf zp;
             IE_TRY(zp.alloc(sizeof(float2) * (size_t)part->total * nrhs * f->maxcol, s));

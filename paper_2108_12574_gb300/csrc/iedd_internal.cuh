@@ -132,6 +132,9 @@ struct dd_factor_t {
     int4 *d_citems = nullptr;
     // autotuned apply configuration per class (kApplyE1, kApplyE4, kApplyF8): variant * 3 + row option
     int apply_cfg[3] = {1, 1, 1};
+    // tensor-core batched apply: per block the first of its 128-row tiles (prefix sums)
+    long long *d_tile_off = nullptr;
+    int ntiles = 0;
 };
 
 // Classes of the explicit-inverse apply: double-float single column, double-float 4-column
@@ -140,6 +143,8 @@ constexpr int kApplyE1 = 0, kApplyE4 = 1, kApplyF8 = 2;
 constexpr int kApplyRowOpts[3] = {32, 64, 128};
 // The column-chunked apply for large blocks (CBD colour blocks): x staged per 4096 columns
 constexpr int kApplyColFrom = 8192, kApplyColChunk = 4096, kApplyColRows = 64;
+// 3D batches of at least this many right-hand sides take the tensor-core apply (launch_apply_tc)
+constexpr int kApplyTensorFrom = 32;
 
 // Largest padded block applied through its explicit inverse: the apply stages the block's split x
 // (8 bytes per point and right-hand side) in one CTA's shared memory.
@@ -225,6 +230,10 @@ void tune_put(const std::string &key, int choice, const std::string &detail);
 // replaces the block), bulk on the tensor cores; synchronizes.  f->d_info must hold -1 per block.
 int launch_factor_tc(dd_factor_t *f, const std::vector<int> &npad, const std::vector<long long> &loff,
                      cudaStream_t s);
+// tc_factor.cu: z_i = M_i (R_i r) for a batch of right-hand sides as GEMM tasks of the persistent
+// kernel on the tensor cores (FP32-accurate products, FP32 sums); xh, xe as apply_split<false>
+// writes them; results into zbuf [rhs][sum n_i]
+int launch_apply_tc(const dd_factor_t *f, const float *xh, const int *xe, int nrhs, double *zbuf, cudaStream_t s);
 int prepare_apply(const dd_factor_t *f);
 // z = T^{-1} r for device FP64 r (ldr) and z (ldz).
 int launch_apply(const dd_factor_t *f, const double *r, long long ldr, double *z, long long ldz,

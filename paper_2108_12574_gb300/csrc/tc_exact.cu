@@ -21,7 +21,7 @@
 // read and added into a 64-bit integer per output in units of 2^-F of a level-0 product: levels
 // 0-2 exactly, each of levels 3-5 rounded to the unit.  F is the largest value for which no sum
 // can overflow: every output is at most 2^14 (sum_j |t_ij|) / sigma_t level-0 units, and that row
-// sum is bounded once per problem from the table (F is about 30 at 1024^2, 36 at 128^2).  The
+// sum is bounded once per problem from the table (F is 34 at 128^2, 30 at 512^2, 29 at 1024^2).  The
 // result differs from the exact product by the dropped pairs, the last-digit truncation and one
 // rounding of each of levels 3-5 to 2^-F per window: ~1e-17 of sum |A_ij x_j|.
 //

@@ -16,7 +16,7 @@
 //   tiles a >= b, written to (a, b) and mirrored to (b, a) from the same values, so M_i is exactly
 //   symmetric; M_i replaces L_i in the pool.
 //
-// KF factor_persistent  ONE launch for all blocks: a grid of CTAs resident on every SM takes tasks
+// KP factor_persistent  ONE launch for all blocks: a grid of CTAs resident on every SM takes tasks
 //                       (DIAG or GEMM) from one list in order (an atomic counter) and, before each,
 //                       waits until every task of the earlier phases of its block is done (a
 //                       per-block counter of finished tasks, release/acquire ordering; bounded
@@ -833,5 +833,92 @@ int launch_factor_tc(dd_factor_t *f, const std::vector<int> &npad, const std::ve
                                : "dd_factor: a tensor-core GEMM timed out waiting for its MMAs");
         return IE_ERR_TIMEOUT;
     }
+    return IE_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// The batched apply on the tensor cores: per block, per 128-row tile of M_i, per group of up to
+// 128 right-hand sides one GEMM task C^T = M_i[rows, :] X_i^T (X_i: the block's scaled FP32 right-
+// hand sides, K = the padded block size), run by the persistent kernel with no dependencies.  The
+// task list is written on the device (the call may be captured in a CUDA graph).
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+__global__ void apply_tasks_kernel(const int *__restrict__ npad, const int *__restrict__ nb,
+                                   const long long *__restrict__ loff, const long long *__restrict__ xoff,
+                                   const long long *__restrict__ tile_off, const float *pool, const float *xh, float *tmp,
+                                   long long xtotal, int nrhs, int ngroups, FTask *__restrict__ tasks) {
+    const int b = blockIdx.x;
+    const int np = npad[b], n = nb[b];
+    const int tiles = (n + kP - 1) / kP;
+    for (int e = threadIdx.x; e < tiles * ngroups; e += blockDim.x) {
+        const int i = e / ngroups, g = e % ngroups;
+        const int r0 = i * kP, c0 = g * kP;
+        FTask t{};
+        t.kind = 0; t.block = 0; t.need = 0; t.k0 = 0;
+        t.g.A = pool + loff[b] + (long long)r0 * np;
+        t.g.lda = np;
+        t.g.B = xh + (long long)c0 * xtotal + xoff[b];
+        t.g.ldb = (int)xtotal;
+        t.g.C = nullptr;
+        t.g.ldc = 0;
+        t.g.CT = tmp + (long long)c0 * xtotal + xoff[b] + r0;
+        t.g.ldct = (int)xtotal;
+        t.g.m = min(kP, n - r0);
+        t.g.n = min(kP, nrhs - c0);
+        t.g.k = np;
+        t.g.s_old = 0.f;
+        t.g.s_acc = 1.f;
+        t.g.diag = 0;
+        t.g.pad_ = 0;
+        tasks[(tile_off[b] + i) * ngroups + g] = t;
+    }
+}
+
+__device__ __forceinline__ double pow2_exp(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+
+// zbuf[k][offs[b] + j] = tmp[k][xoff[b] + j] 2^e(b, k) (exact: two power-of-two factors)
+__global__ void apply_widen_kernel(const float *__restrict__ tmp, const int *__restrict__ nb,
+                                   const long long *__restrict__ offs, const long long *__restrict__ xoff,
+                                   const int *__restrict__ xexp, long long xtotal, long long total, int nblocks,
+                                   double *__restrict__ zbuf) {
+    const int b = blockIdx.x, k = blockIdx.y;
+    const int n = nb[b], e = xexp[(long long)k * nblocks + b], e1 = e / 2;
+    const double s1 = pow2_exp(e1), s2 = pow2_exp(e - e1);
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+        zbuf[(long long)k * total + offs[b] + j] = ((double)tmp[(long long)k * xtotal + xoff[b] + j] * s1) * s2;
+}
+
+}  // namespace
+
+int launch_apply_tc(const dd_factor_t *f, const float *xh, const int *xe, int nrhs, double *zbuf, cudaStream_t s) {
+    const int nb = f->nblocks;
+    if (nb == 0 || nrhs < 1) return IE_OK;
+    if (!f->d_tile_off) {
+        ie_set_error("dd_apply: the tensor-core apply tables are missing");
+        return IE_ERR_ARG;
+    }
+    IE_TRY(prepare_tc_factor());
+    const int ngroups = (nrhs + kP - 1) / kP;
+    const long long ntasks = (long long)f->ntiles * ngroups;
+    DevBuf tmp, tasks, ctr;
+    IE_TRY(tmp.alloc(sizeof(float) * (size_t)f->xtotal * nrhs, s));
+    IE_TRY(tasks.alloc(sizeof(FTask) * (size_t)std::max<long long>(ntasks, 1), s));
+    IE_TRY(ctr.alloc(sizeof(int) * 2, s));  // next, done (one counter: no dependencies)
+    IE_TRY_CUDA(cudaMemsetAsync(ctr.ptr, 0, sizeof(int) * 2, s));
+    apply_tasks_kernel<<<nb, 128, 0, s>>>(f->d_npad, f->d_n, f->d_loff, f->d_xoff, f->d_tile_off,
+                                          (const float *)f->d_pool, xh, tmp.as<float>(), f->xtotal, nrhs, ngroups,
+                                          tasks.as<FTask>());
+    IE_LAUNCHED();
+    int *c = ctr.as<int>();
+    const int grid = (int)std::max<long long>(1, std::min<long long>(ntasks, (long long)f->prob->sm_count * 2));
+    // a GEMM that gives up waiting for its MMAs records it in the problem's error word, which
+    // pcg_solve reports (the tensor-core matvec uses the same word)
+    factor_persistent<<<grid, 256, kFSmem, s>>>(tasks.as<FTask>(), (int)ntasks, c, c + 1, nullptr, nullptr, nullptr,
+                                                f->d_loff, nullptr, f->d_npad, f->d_info, f->prob->d_err);
+    IE_LAUNCHED();
+    apply_widen_kernel<<<dim3(nb, nrhs), 256, 0, s>>>(tmp.as<float>(), f->d_n, f->part->d_offs, f->d_xoff, xe, f->xtotal,
+                                                      f->part->total, nb, zbuf);
+    IE_LAUNCHED();
     return IE_OK;
 }

@@ -747,3 +747,36 @@ def test_pcg_full_size_3d_batched_mixed():
     # columns: the oracle's solution; at the stable tolerance every column +-1 of the oracle's FP64
     # count where the ensemble agrees on it
     _check_mixed_case("ie3d_n32_m4_d1_uniform64", fp64_inner=iedd.IE_FFT, check_oracle_count=False)
+
+
+def test_3d_n64_batched_matvec_and_solve():
+    # 64^3 (N = 262144) with 64 uniform right-hand sides (seeds 0..63): the tcgen05 batched matvec
+    # (K1w, 3xTF32 products, FP32 accumulation) against the oracle's direct sum on sampled rows, and
+    # the 64-column mixed solve (Schwarz 8 x 8 x 8 boxes of 8^3 cells, 1-cell overlap, blocks of up
+    # to 1000 points): every column's reported true residual, the oracle's FFT true residual and
+    # solution for two columns, and the iteration count of column 0 between the FP64 oracle's and
+    # the count of the oracle with an FP32-class matvec (the product's FP32 rounding, amplified by
+    # cond(A) ~ N^(2/3), costs iterations)
+    n, m, delta = 64, 8, 1
+    N = n ** 3
+    F = I.uniform_rhs_batch(N, range(64)).T.copy()  # (64, N)
+    prob = iedd.ie_discretize(3, n)
+    Y = torch.zeros((64, N), dtype=torch.float64, device="cuda")
+    iedd.ie_matvec(prob, dev(F), Y, iedd.IE_TENSOR)
+    rows = np.unique(np.concatenate([[0, N - 1, N // 2 + n * n // 2 + n // 2], np.random.default_rng(64).integers(0, N, 13)]))
+    ref = O.matvec_direct(3, n, F.T, rows=rows)
+    assert np.max(np.abs(host(Y)[:, rows].T - ref)) <= 4e-6 * _scale(3, n, F, O.GRID_TEXT)
+    part = iedd.dd_partition(prob, m, delta, iedd.DD_SCHWARZ)
+    fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
+    U = torch.zeros((64, N), dtype=torch.float64, device="cuda")
+    reps = iedd.pcg_solve(prob, fac, dev(F), U, tol=1e-8)
+    assert all(r["status"] == 0 and r["true_relres"] <= 1e-8 for r in reps)
+    Uh = host(U)
+    u_ref, its_ref, _, _, its32 = oracle_cache.result("ie3d_n64_m8_d1_uniform")
+    rel = O.true_relative_residual(3, n, F[:2].T, Uh[:2].T)
+    assert np.all(rel <= 1e-8 * 1.01), rel
+    for k in range(2):
+        err = np.linalg.norm(Uh[k] - u_ref[:, k]) / np.linalg.norm(u_ref[:, k])
+        assert err <= 1e-6, (k, err)
+    lo, hi = int(min(its_ref[0], its32[0])), int(max(its_ref[0], its32[0]))
+    assert lo - 1 <= reps[0]["iterations"] <= hi + 3, (reps[0]["iterations"], its_ref[0], its32[0])
