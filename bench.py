@@ -62,7 +62,9 @@ FP32_LANES_PER_SM = 128
 NCU_TRAFFIC = {"24904137a1834c92": 4624128}  # k2_accurate_2d<true,1>, n = 512, bytes per launch
 # ncu figures of the exact tensor-core matvec per (tc_exact_source_hash(), grid side n): DRAM
 # bytes per launch and the tensor pipe's active fraction (sm__pipe_tensor_cycles_active)
-NCU_KZ = {("91affb0f46974cb4", 512): {"traffic": 85065472, "tensor_pipe": 0.617}}
+NCU_KZ = {("e2d6b85e8691647a", 1024): {"traffic": 1782236976, "tensor_pipe": 0.620}}
+# the same for the batched tensor-core matvec per (tc_matvec_source_hash(), grid side n), 3D
+NCU_K1W = {("c8970434ed8bad33", 32): {"traffic": 83382784, "tensor_pipe": 0.430}}
 # BF16 digit products per pair of the exact tensor-core matvec (six digits per factor, levels 0..5)
 KZ_PRODUCTS_PER_PAIR = 21
 
@@ -85,6 +87,12 @@ def k2_source_hash() -> str:
     src = open(os.path.join(ROOT, "paper_2108_12574_gb300", "csrc", "matvec.cu")).read()
     a, b = src.index("constexpr int kP1"), src.index("// 3D: 4 x 8 x 8 patches")
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+
+
+def tc_matvec_source_hash() -> str:
+    """sha256 (16 hex digits) of the batched tensor-core matvec's source file."""
+    src = open(os.path.join(ROOT, "paper_2108_12574_gb300", "csrc", "tc_matvec.cu")).read()
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
 def tc_exact_source_hash() -> str:
@@ -569,8 +577,10 @@ def roofline_of(iedd, name, rep, clocks, sms):
         bf16, kind = tensor_peak(clocks)
         peak = bf16 * TF32_PER_BF16 * 1e12
         achieved = pairs * nr * 6.0 / mv_launch_s
+        ncu = NCU_K1W.get((tc_matvec_source_hash(), n_w), {})
         roofline = {"bound": "tensor", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": "k1w_matvec_tc<3>", "peak_kind": kind,
+                    "frac": achieved / peak, "traffic": ncu.get("traffic"), "kernel": "k1w_matvec_tc<3>",
+                    "tensor_pipe_ncu": ncu.get("tensor_pipe"), "peak_kind": kind,
                     "pair_rhs_per_s": pairs * nr / mv_launch_s,
                     "peak_basis": (f"TF32 dense = {bf16:.1f} TFLOP/s bf16 {kind} (of measured) x {TF32_PER_BF16:.3f} "
                                    "(nominal 1.1 / 2.25 PFLOP/s); work = 3 TF32 products (hi hi, hi lo, lo hi; 2 flops "

@@ -200,6 +200,7 @@ extern "C" void ie_destroy(ie_problem *p) {
     cudaFree(p->d_stored);
     cudaFree(p->d_err);
     cudaFree(p->d_table_tc);
+    cudaFree(p->d_tc_strip);
     cudaFree(p->d_fft_tw);
     cudaFree(p->d_fft_chat);
     cudaFree(p->d_zt_win);

@@ -74,6 +74,7 @@ struct ie_problem {
     float *d_stored = nullptr;     // optional dense FP32 copy of A (zero diagonal), ie_store_matrix
     int *d_err = nullptr;          // device error word of the tensor-core matvec (bounded waits)
     uint2 *d_table_tc = nullptr;   // per |offset|: the entry split into TF32 high / low words (0 at 0)
+    void *d_tc_strip = nullptr;    // the batched tensor-core matvec's strip table (built on first use)
     int sm_count = 0;
     // FFT matvec (built on first use): periodic grid of L = 2^fft_lg points per axis, twiddles
     // exp(-2 pi i k / L) (k < L / 2) and the kernel's spectrum (FP64, L^d, forward-pass order)
@@ -195,10 +196,14 @@ int launch_matvec_tc(const ie_problem *p, const double *x, long long ldx, int nr
                      int nchunks, int *d_err, cudaStream_t s);
 int prepare_tc();
 int build_tc_table(ie_problem *p);
-bool tc_toeplitz(const ie_problem *p);  // the tensor-core matvec reads its tiles from d_table_tc
+bool tc_toeplitz(const ie_problem *p);  // the tensor-core matvec reads its tiles from the strip table
+int prepare_tc_strip(const ie_problem *p);  // builds the strip table (synchronizes; not under capture)
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (nullptr if absent)
+void *tensor_map_encode_fn();
 int tc_splits_toeplitz(long long tiles, int nchunks, int sms);  // source splits of that kernel
 int tc_chunk();
 int tc_rows();
+int tc_block_rows();  // target rows per CTA of the strip-fed kernel (tc_toeplitz)
 int tc_cols();
 int launch_matvec_stored(const ie_problem *p, const double *x, long long ldx, double *y, long long ldy, int nrhs,
                          cudaStream_t s);

@@ -677,7 +677,7 @@ int launch_matvec_dot(const ie_problem *p, const double *x, long long ldx, doubl
         const int rt = (int)((N + tc_rows() - 1) / tc_rows());
         const int nchunks = (int)((N + tc_chunk() - 1) / tc_chunk());
         const int groups = (nrhs + tc_cols() - 1) / tc_cols();
-        int S = tc_toeplitz(p) ? tc_splits_toeplitz((long long)rt * groups, nchunks, p->sm_count)
+        int S = tc_toeplitz(p) ? tc_splits_toeplitz((N + tc_block_rows() - 1) / tc_block_rows() * groups, nchunks, p->sm_count)
                                : std::min(splits_for((long long)rt * groups, nchunks, p->sm_count, 3), 16);
         const int cps = (nchunks + S - 1) / S;
         const int Se = (nchunks + cps - 1) / cps;

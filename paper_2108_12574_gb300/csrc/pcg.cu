@@ -386,6 +386,7 @@ extern "C" int pcg_solve(const ie_problem *p, const dd_factor_t *fac, const doub
         }
         IE_TRY(prepare_tc_exact(p));  // before any capture
     }
+    if (S.mv_precision() == IE_TENSOR) IE_TRY(prepare_tc_strip(p));  // before any capture
     if (S.mv_precision() == IE_TENSOR || S.mv_precision() == IE_TENSOR_EXACT)
         IE_TRY_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
     IE_TRY(S.alloc());

@@ -544,8 +544,8 @@ int prepare_tc_exact(const ie_problem *p_) {
 }
 
 // cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no libcuda link)
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+void *tensor_map_encode_fn() {
+    static void *fn = nullptr;
     static bool tried = false;
     if (!tried) {
         tried = true;
@@ -553,9 +553,12 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
         cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+            fn = f;
     }
     return fn;
+}
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encode_fn());
 }
 
 int launch_matvec_tc_exact(const ie_problem *p, const double *x, long long ldx, double *y, long long ldy, int nrhs,

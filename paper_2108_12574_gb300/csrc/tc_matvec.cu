@@ -17,10 +17,14 @@
 // Shared-memory operands use the canonical no-swizzle K-major layout: 8-row x 16-byte core
 // matrices, element (r, k) at (r / 8) * SBO + (k / 4) * LBO + (r % 8) * 16 + (k % 4) * 4 bytes,
 // LBO = 128 (next 4 K elements), SBO = 1024 (next 8 rows, K = 32 per chunk).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
+#include <string>
 
 #include "iedd_internal.cuh"
 
@@ -315,19 +319,50 @@ k1t_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsp
     }
 }
 
-// K1w: the table-fed batched matvec with warp roles (n = 32, 64 or a multiple of 128).  The products are K1t's (A tiles of
-// exact table entries split into TF32 high / low words, the same pre-split B operand: hi hi,
-// hi lo and lo hi), but the B record's low rows follow its high rows at the same stride, so per
-// K-step one N = 128 MMA gives hi hi (level 0, columns 0-63) and hi lo (level 1, columns 64-127)
-// and a second adds lo hi to level 1: 8 MMAs per 32-source chunk instead of 12.  No block-wide
-// barrier couples the roles: one lane issues the MMAs (warp 0), one the bulk copy of each chunk's
-// B operand (warp 1), six warps write the A tiles (warps 2-7), and four warps fold finished
-// accumulator sets (levels 0 + 1, FP32 over 8 chunks) into running (high, low) sums kept in
-// tensor memory (warps 8-11, one TMEM lane quarter each).  Four operand stages, two accumulator
-// sets of 128 columns; mbarriers hand over; every wait is bounded.
-constexpr int kWStages = 4, kWThreads = 384, kWWin = 8, kWFillWarps = 6;
-constexpr int kWSmem = kWStages * kStage * (int)sizeof(uint32_t);  // 192 KB
-constexpr int kWSlots = 2;  // staged entries per fill thread (nl (Lr + 31) <= 252 <= 2 x 192)
+// K1w: the batched matvec for grids whose lines tile the 256-row blocks (n = 32, 64 or a multiple
+// of 128), with exact table entries split into TF32 high / low words and 3xTF32 products (hi hi,
+// hi lo, lo hi).  The B record's low rows follow its high rows at the same stride, so per K-step
+// one N = 128 MMA gives hi hi (level 0, columns 0-63) and hi lo (level 1, columns 64-127) and a
+// second adds lo hi to level 1.
+//
+// A CTA owns a block of 256 targets (two M = 128 tiles sharing every B record: the copies, not the
+// MMAs, bound this kernel, and the B record is two thirds of them) and 64 right-hand sides.
+//
+// A operand from a Toeplitz strip.  The block holds nb = 256 / Lb grid lines of Lb = min(n, 256)
+// targets; block row mb (tile mb / 128, MMA row mb % 128) is line q = mb % nb, target f0 + Lb - 1
+// - mb / nb along it (reversed), so against the chunk's 32 sources j = fj + k of one source line
+// the entry depends on (mb / nb) + k only: t(.., |f0 + Lb - 1 - fj - (mb / nb + k)|).  The strip
+// table (built once per problem) holds, per plane, per slow-axis offset and per row rho, the 4
+// consecutive entries t(.., |n - 1 - rho - k'|), k' < 4, of every signed offset along the
+// interleaved axis (the mid axis in 3D, the slow axis in 2D, on which the block's nb lines are
+// consecutive).  One 4D TMA copy brings rows rho0 .. rho0 + Lb + 27 of the nb consecutive offsets
+// into shared memory as [row][line][4 entries] (one line, n >= 256: a bulk copy per plane of its
+// contiguous rows), so block row mb of K-group g sits at 16 ((mb / nb + 4 g) nb + mb % nb) = 16 mb
+// + 64 nb g bytes: K-major descriptors with SBO = 128 and LBO = 64 nb read each tile's 128 x 8
+// operand of a K-step straight from the strip (core matrices overlap).  A chunk's strip is
+// 2 x 16 nb (Lb + 28) bytes (<= 15 KB) for 256 targets.
+//
+// Roles: warp 0 issues the MMAs (one lane), warp 1 the copies (one lane: the strip, the pre-split
+// B record by a bulk copy, all completing one mbarrier), warps 2-9 fold finished accumulator sets
+// (levels 0 + 1, FP32 over 8 chunks) into running (high, low) sums kept in tensor memory (one tile
+// and TMEM lane quarter each).  Seven operand stages; one accumulator set per tile (TMEM: tile t
+// at columns 256 t: the set, then the high and the low running sums), so the MMAs of a window
+// wait for the fold of the previous one; mbarriers hand over; every wait is bounded.
+constexpr int kWStages = 7, kWThreads = 320, kWWin = 8, kWBM = 256, kWFold = 8;
+constexpr int kWStripMax = 2 * 8 * (32 + 28) * 16;             // strip bytes, both planes, at most (nb = 8)
+constexpr int kWBBytes = 2 * kTN * kTK * (int)sizeof(uint32_t); // B record: 16 KB
+constexpr int kWStage = kWStripMax + kWBBytes;                  // 31,744 bytes (248 x 128)
+constexpr int kWSmem = kWStages * kWStage;                      // 222,208 bytes
+constexpr long long kStripCap = 1LL << 30;                      // largest strip table (bytes)
+
+__device__ __forceinline__ uint64_t make_desc2(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
 
 __device__ __forceinline__ void tmem_ld16w(uint32_t taddr, uint32_t (&v)[16]) {
     asm volatile(
@@ -345,25 +380,50 @@ __device__ __forceinline__ void tmem_st16w(uint32_t taddr, const uint32_t (&v)[1
         : "memory");
 }
 
+// Strip table entries: plane pl (0: TF32 high, 1: low) of the entry at lattice offset (fast
+// |n - 1 - rho - k'|, interleaved axis |qq - (n - 1)|, slow o in 3D), 0 outside the grid; Q = R =
+// 2n values of qq and rho (the last one padding).  Layout [pl][o][rho][qq][k'] when a block holds
+// several lines (the TMA box interleaves them), [pl][o][qq][rho][k'] when it holds one (each plane
+// of a chunk's strip is then one contiguous run, fetched by a bulk copy).
+__global__ void tc_strip_kernel(const uint2 *__restrict__ tab, int dim, int n, int interleaved, uint4 *__restrict__ strip) {
+    const long long Q = 2LL * n, R = 2LL * n, O = dim == 3 ? n : 1;
+    const long long rows = 2 * O * R * Q;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= rows) return;
+    const int qq = interleaved ? (int)(e % Q) : (int)((e / R) % Q);
+    const int rho = interleaved ? (int)((e / Q) % R) : (int)(e % R);
+    const int o = (int)((e / (Q * R)) % O), pl = (int)(e / (Q * R * O));
+    const int di = abs(qq - (n - 1));
+    uint32_t v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int df = abs(n - 1 - rho - k);
+        v[k] = 0u;
+        if (df < n && di < n) {
+            const uint2 t = tab[dim == 3 ? ((long long)o * n + di) * n + df : (long long)di * n + df];
+            v[k] = pl ? t.y : t.x;
+        }
+    }
+    strip[e] = make_uint4(v[0], v[1], v[2], v[3]);
+}
+
 template <int DIM>
 __global__ void __launch_bounds__(kWThreads, 1)
-k1w_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsplit, int nrhs, long long N,
-              int chunks_per_split, int nchunks, double *__restrict__ partial, int *__restrict__ err,
-              const uint2 *__restrict__ ttab, int n, int Lr) {
-    extern __shared__ __align__(128) uint32_t opnd[];  // kWStages x [A hi | A lo | B hi | B lo]
-    constexpr int kPer = kTM + kTK - 1;
-    __shared__ uint2 tval[2][kTM / 32 * kPer];          // a chunk's distinct entries, double-buffered
-    __shared__ int4 rline[kTM / 32];                    // slow, mid, fast coordinate of target line q
-    __shared__ __align__(8) uint64_t sfull[kWStages], bfull[kWStages], mdone[kWStages], afull[2], aempty[2];
+k1w_matvec_tc(const __grid_constant__ CUtensorMap smap, const unsigned char *__restrict__ strip,
+              const uint32_t *__restrict__ xsplit, int nrhs, long long N, int chunks_per_split, int nchunks,
+              double *__restrict__ partial, int *__restrict__ err, int n, int Lb) {
+    extern __shared__ __align__(128) unsigned char wsm[];  // kWStages x [strip hi | strip lo | pad | B hi | B lo]
+    __shared__ __align__(8) uint64_t full[kWStages], mdone[kWStages], afull, aempty;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const long long row0 = (long long)blockIdx.x * kTM;
+    const long long blk0 = (long long)blockIdx.x * kWBM;
     const int grp = blockIdx.z;
     const int k0 = blockIdx.y * chunks_per_split;
     const int T = max(0, min(chunks_per_split, nchunks - k0));
-    const int nl = kTM / Lr, per = Lr + kTK - 1;
+    const int nb = kWBM / Lb;
+    const uint32_t plane_bytes = (uint32_t)(16 * nb * (Lb + 28));
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -372,20 +432,13 @@ k1w_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsp
     }
     if (tid == 0) {
         for (int st = 0; st < kWStages; ++st) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sfull[st])), "r"((uint32_t)kWFillWarps));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bfull[st])), "r"(1u));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[st])), "r"(1u));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mdone[st])), "r"(1u));
         }
-        for (int st = 0; st < 2; ++st) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&afull[st])), "r"(1u));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&aempty[st])), "r"(4u));
-        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&afull)), "r"(1u));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&aempty)), "r"((uint32_t)kWFold));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
-    }
-    if (tid < nl) {
-        const float4 c = coord[row0 + (long long)tid * Lr];
-        rline[tid] = DIM == 2 ? make_int4((int)c.x, 0, (int)c.y, 0) : make_int4((int)c.x, (int)c.y, (int)c.z, 0);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -407,29 +460,33 @@ k1w_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsp
     };
 
     if (warp == 0) {
-        // ---- MMA issue (one lane): per chunk 4 K-steps x (hi hi, hi lo, lo hi) ----
+        // ---- MMA issue (one lane): per chunk 4 K-steps x 2 tiles x (hi [hi | lo], lo hi) ----
         if (lane == 0) {
+            const uint32_t lbo_a = 64u * (uint32_t)nb;
             int issued = 0;
             for (int c = 0; c < T; ++c) {
-                const int st = c % kWStages, f = c / kWWin, set = f & 1;
-                const uint32_t spar = (uint32_t)(c / kWStages) & 1u, fpar = (uint32_t)(f >> 1) & 1u;
-                if (!wait_bar(&sfull[st], spar) || !wait_bar(&bfull[st], spar)) break;
-                if (c % kWWin == 0 && f >= 2 && !wait_bar(&aempty[set], fpar ^ 1u)) break;
+                const int st = c % kWStages, f = c / kWWin;
+                const uint32_t spar = (uint32_t)(c / kWStages) & 1u;
+                if (!wait_bar(&full[st], spar)) break;
+                // a window's first MMAs overwrite the accumulators: the previous fold must be done
+                if (c % kWWin == 0 && f >= 1 && !wait_bar(&aempty, (uint32_t)(f - 1) & 1u)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t ahi = smem_u32(opnd + st * kStage), alo = ahi + kTM * kTK * 4;
-                const uint32_t bhi = ahi + 2 * kTM * kTK * 4, blo = bhi + kTN * kTK * 4;
-                const uint32_t dt = tmem + (uint32_t)set * (2 * kTN);
-                (void)blo;
+                const uint32_t ahi = smem_u32(wsm + st * kWStage), alo = ahi + plane_bytes;
+                const uint32_t bhi = ahi + kWStripMax;
 #pragma unroll
                 for (int s = 0; s < kTK / 8; ++s) {
-                    const uint32_t koff = (uint32_t)s * 2 * kLBO;
-                    // [hi hi | hi lo] over the high then low rows of B, then lo hi into level 1
-                    mma_tf32(dt, make_desc(ahi + koff), make_desc(bhi + koff), (c % kWWin == 0 && s == 0) ? 0u : 1u,
-                             kIdesc128);
-                    mma_tf32(dt + kTN, make_desc(alo + koff), make_desc(bhi + koff), 1u);
+                    const uint64_t db = make_desc(bhi + (uint32_t)s * 2 * kLBO);
+                    const uint32_t acc = (c % kWWin == 0 && s == 0) ? 0u : 1u;
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        const uint32_t toff = (uint32_t)t * (16u * kTM) + 2u * s * lbo_a;  // tile t's rows
+                        const uint32_t dt = tmem + (uint32_t)t * 256u;
+                        mma_tf32(dt, make_desc2(ahi + toff, lbo_a, 128u), db, acc, kIdesc128);
+                        mma_tf32(dt + kTN, make_desc2(alo + toff, lbo_a, 128u), db, 1u);
+                    }
                 }
                 mma_commit(smem_u32(&mdone[st]));
-                if (c % kWWin == kWWin - 1 || c == T - 1) mma_commit(smem_u32(&afull[set]));
+                if (c % kWWin == kWWin - 1 || c == T - 1) mma_commit(smem_u32(&afull));
                 issued = c + 1;
             }
             if (issued > 0 && !mbar_wait(smem_u32(&mdone[(issued - 1) % kWStages]), (uint32_t)((issued - 1) / kWStages) & 1u))
@@ -437,134 +494,88 @@ k1w_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsp
         }
         __syncwarp();
     } else if (warp == 1) {
-        // ---- B operand: one bulk copy of the pre-split x per chunk ----
-        int issued = 0;
-        for (int c = 0; c < T; ++c) {
-            const int st = c % kWStages;
-            const uint32_t spar = (uint32_t)(c / kWStages) & 1u;
-            if (c >= kWStages && !warp_wait(&mdone[st], spar ^ 1u)) break;
-            if (lane == 0) {
+        // ---- operands of a chunk: the strip (several lines: one TMA copy of the 4D box (4 nb,
+        // Lb + 28, 1, 2); one line: a bulk copy per plane) and the B record ----
+        if (lane == 0) {
+            // the block's first target: slow, mid (3D) and fast coordinates
+            const int f0 = (int)(blk0 % n);
+            const int i_mid = DIM == 3 ? (int)((blk0 / n) % n) : 0;
+            const int i_slow = DIM == 3 ? (int)(blk0 / ((long long)n * n)) : (int)(blk0 / n);
+            const uint32_t bytes = 2u * plane_bytes + (uint32_t)kWBBytes;
+            int issued = 0;
+            for (int c = 0; c < T; ++c) {
+                const int st = c % kWStages;
+                const uint32_t spar = (uint32_t)(c / kWStages) & 1u;
+                if (c >= kWStages && !wait_bar(&mdone[st], spar ^ 1u)) break;
+                const long long j0 = (long long)(k0 + c) * kTK;  // the chunk's first source
+                const int fj = (int)(j0 % n);
+                const long long tj = j0 / n;
+                const int mj = DIM == 3 ? (int)(tj % n) : 0;
+                const int sj = DIM == 3 ? (int)(tj / n) : (int)tj;
+                const int o = DIM == 3 ? abs(i_slow - sj) : 0;
+                const int q0 = (DIM == 3 ? i_mid - mj : i_slow - sj) + (n - 1);
+                const int rho0 = n - f0 - Lb + fj;
+                const uint32_t bar = smem_u32(&full[st]), dst = smem_u32(wsm + st * kWStage);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+                if (nb > 1) {
+                    asm volatile(
+                        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(&smap)), "r"(4 * q0), "r"(rho0), "r"(o), "r"(0), "r"(bar)
+                        : "memory");
+                } else {
+                    const long long O = DIM == 3 ? n : 1;
+                    for (int pl = 0; pl < 2; ++pl) {
+                        const unsigned char *src = strip + ((((long long)pl * O + o) * (2 * n) + q0) * (2 * n) + rho0) * 16;
+                        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                         dst + (uint32_t)pl * plane_bytes),
+                                     "l"(src), "r"(plane_bytes), "r"(bar)
+                                     : "memory");
+                    }
+                }
                 const uint32_t *src = xsplit + ((long long)grp * nchunks + k0 + c) * (2LL * kTN * kTK);
-                bulk_g2s(smem_u32(opnd + st * kStage + 2 * kTM * kTK), src, (uint32_t)(2 * kTN * kTK * sizeof(uint32_t)),
-                         smem_u32(&bfull[st]));
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                 dst + (uint32_t)kWStripMax),
+                             "l"(src), "r"((uint32_t)kWBBytes), "r"(bar)
+                             : "memory");
+                issued = c + 1;
             }
-            __syncwarp();
-            issued = c + 1;
-        }
-        if (lane == 0)  // no copy may still be landing when the CTA ends
+            // no copy may still be landing when the CTA ends (waits that ignore the abort flag)
             for (int c = max(0, issued - kWStages); c < issued; ++c)
-                if (!mbar_wait(smem_u32(&bfull[c % kWStages]), (uint32_t)(c / kWStages) & 1u)) abort_flag = 1;
+                if (!mbar_wait(smem_u32(&full[c % kWStages]), (uint32_t)(c / kWStages) & 1u)) abort_flag = 1;
+        }
         __syncwarp();
-    } else if (warp < 2 + kWFillWarps) {
-        // ---- A tiles (192 threads); every fill warp runs every chunk and every named barrier ----
-        const int ft = tid - 64;
-        int sq[kWSlots], stt[kWSlots];  // staged entry e = ft + 192 i: line and position
-#pragma unroll
-        for (int i = 0; i < kWSlots; ++i) {
-            const int e = ft + 32 * kWFillWarps * i;
-            sq[i] = e < nl * per ? e / per : -1;
-            stt[i] = e < nl * per ? e - sq[i] * per : 0;
-        }
-        uint2 tv[kWSlots];
-        // coordinates of the next chunk to fetch (chunks are fetched in order, 32 sources each)
-        int fj, mj, sj;
-        {
-            const int j0 = k0 * kTK, tj = j0 / n;
-            fj = j0 % n;
-            mj = DIM == 2 ? 0 : tj % n;
-            sj = DIM == 2 ? tj : tj / n;
-        }
-        auto fetch = [&](int c) {
-#pragma unroll
-            for (int i = 0; i < kWSlots; ++i) {
-                tv[i] = make_uint2(0u, 0u);
-                if (c < T && sq[i] >= 0) {
-                    const int4 L = rline[sq[i]];
-                    const int df = abs(L.z - fj - (kTK - 1) + stt[i]), dm = abs(L.y - mj), ds = abs(L.x - sj);
-                    tv[i] = __ldg(ttab + (DIM == 2 ? (long long)ds * n + df : ((long long)ds * n + dm) * n + df));
-                }
-            }
-            fj += kTK;  // the next chunk
-            if (fj >= n) {
-                fj = 0;
-                if (DIM == 2) {
-                    ++sj;
-                } else if (++mj >= n) {
-                    mj = 0;
-                    ++sj;
-                }
-            }
-        };
-        auto stage_tv = [&](int buf) {
-#pragma unroll
-            for (int i = 0; i < kWSlots; ++i)
-                if (sq[i] >= 0) tval[buf][sq[i] * per + stt[i]] = tv[i];
-        };
-        fetch(0);
-        stage_tv(0);
-        fetch(1);
-        const int lgL = __ffs(Lr) - 1;
-        for (int c = 0; c < T; ++c) {
-            const int st = c % kWStages;
-            const uint32_t spar = (uint32_t)(c / kWStages) & 1u;
-            bool ok = !abort_flag;
-            if (ok && c >= kWStages) ok = warp_wait(&mdone[st], spar ^ 1u);
-            asm volatile("bar.sync 1, 192;" ::: "memory");  // tval[c & 1] is complete
-            if (ok) {
-                uint32_t *Ahi = opnd + st * kStage, *Alo = Ahi + kTM * kTK;
-                const uint2 *tb = tval[c & 1];
-                // unit u = (column group g, row r): the 4 sources 4g..4g+3 of row r, one 16-byte
-                // core-matrix row in each of the hi and lo planes
-                for (int u = ft; u < kTM * (kTK / 4); u += 32 * kWFillWarps) {
-                    const int g = u >> 7, r = u & (kTM - 1);
-                    const int base = (r >> lgL) * per + (r & (Lr - 1)) + (kTK - 1) - 4 * g;
-                    const uint2 w0 = tb[base], w1 = tb[base - 1], w2 = tb[base - 2], w3 = tb[base - 3];
-                    const int off = (r >> 3) * (kSBO / 4) + g * (kLBO / 4) + (r & 7) * 4;
-                    *reinterpret_cast<uint4 *>(Ahi + off) = make_uint4(w0.x, w1.x, w2.x, w3.x);
-                    *reinterpret_cast<uint4 *>(Alo + off) = make_uint4(w0.y, w1.y, w2.y, w3.y);
-                }
-            }
-            stage_tv((c + 1) & 1);  // the buffer was last read in chunk c - 1, before this barrier
-            fetch(c + 2);
-            if (ok) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&sfull[st])) : "memory");
-            }
-        }
     } else {
-        // ---- accumulator sets into running (high, low) sums in TMEM columns 128.. and 192.. ----
-        const int q4 = warp & 3;
-        const uint32_t lanes = (uint32_t)(32 * q4) << 16;
+        // ---- tile t's accumulator set into running (high, low) sums in TMEM columns 256 t + 128 ..
+        // and 256 t + 192 .. ----
+        const int q4 = warp & 3, t = (warp - 2) >> 2;
+        const uint32_t lanes = (uint32_t)(32 * q4) << 16, col0 = (uint32_t)t * 256u;
         {
             uint32_t z[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) z[k] = 0u;
 #pragma unroll
             for (int b = 0; b < kTN / 16; ++b) {
-                tmem_st16w(tmem + lanes + 256u + 16u * b, z);
-                tmem_st16w(tmem + lanes + 320u + 16u * b, z);
+                tmem_st16w(tmem + lanes + col0 + 128u + 16u * b, z);
+                tmem_st16w(tmem + lanes + col0 + 192u + 16u * b, z);
             }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         }
         const int nwin = (T + kWWin - 1) / kWWin;
         for (int f = 0; f < nwin; ++f) {
-            const int set = f & 1;
-            if (!warp_wait(&afull[set], (uint32_t)(f >> 1) & 1u)) break;
+            if (!warp_wait(&afull, (uint32_t)f & 1u)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
             for (int b = 0; b < kTN / 16; ++b) {
                 uint32_t a[16], a1[16], h[16], l[16];
-                tmem_ld16w(tmem + lanes + (uint32_t)set * (2 * kTN) + 16u * b, a);
-                tmem_ld16w(tmem + lanes + (uint32_t)set * (2 * kTN) + kTN + 16u * b, a1);
-                tmem_ld16w(tmem + lanes + 256u + 16u * b, h);
-                tmem_ld16w(tmem + lanes + 320u + 16u * b, l);
+                tmem_ld16w(tmem + lanes + col0 + 16u * b, a);
+                tmem_ld16w(tmem + lanes + col0 + kTN + 16u * b, a1);
+                tmem_ld16w(tmem + lanes + col0 + 128u + 16u * b, h);
+                tmem_ld16w(tmem + lanes + col0 + 192u + 16u * b, l);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (b == kTN / 16 - 1) {  // every read of this set is complete: release it
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
-                    if (lane == 0)
-                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&aempty[set])) : "memory");
+                    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&aempty)) : "memory");
                 }
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
@@ -573,18 +584,20 @@ k1w_matvec_tc(const float4 *__restrict__ coord, const uint32_t *__restrict__ xsp
                     h[k] = __float_as_uint(hi);
                     l[k] = __float_as_uint(lo);
                 }
-                tmem_st16w(tmem + lanes + 256u + 16u * b, h);
-                tmem_st16w(tmem + lanes + 320u + 16u * b, l);
+                tmem_st16w(tmem + lanes + col0 + 128u + 16u * b, h);
+                tmem_st16w(tmem + lanes + col0 + 192u + 16u * b, l);
             }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         }
-        const long long i = row0 + 32 * q4 + lane;
+        // TMEM lane m of tile t is block row mb = 128 t + m: line mb % nb, target Lb - 1 - mb / nb
+        const int mb = 128 * t + 32 * q4 + lane;
+        const long long i = blk0 + (long long)(mb % nb) * Lb + (Lb - 1 - mb / nb);
         if (!abort_flag) {
 #pragma unroll
             for (int b = 0; b < kTN / 16; ++b) {
                 uint32_t h[16], l[16];
-                tmem_ld16w(tmem + lanes + 256u + 16u * b, h);
-                tmem_ld16w(tmem + lanes + 320u + 16u * b, l);
+                tmem_ld16w(tmem + lanes + col0 + 128u + 16u * b, h);
+                tmem_ld16w(tmem + lanes + col0 + 192u + 16u * b, l);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (i < N) {
 #pragma unroll
@@ -623,26 +636,77 @@ int launch_matvec_tc(const ie_problem *p, const double *x, long long ldx, int nr
     IE_LAUNCHED();
     const dim3 g(rt, S, groups);
     const size_t dsm = sizeof(uint32_t) * kStages * kStage;
-    const bool toep = tc_toeplitz(p);
-    const int Lr = std::min(p->n, kTM);
-    if (toep && p->dim == 2)
-        k1w_matvec_tc<2><<<g, kWThreads, kWSmem, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial,
-                                                      d_err, p->d_table_tc, p->n, Lr);
-    else if (toep)
-        k1w_matvec_tc<3><<<g, kWThreads, kWSmem, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial,
-                                                      d_err, p->d_table_tc, p->n, Lr);
-    else if (p->dim == 2)
+    if (tc_toeplitz(p)) {
+        const dim3 gw((unsigned)((p->N + kWBM - 1) / kWBM), S, groups);
+        if (!p->d_tc_strip) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            IE_TRY_CUDA(cudaStreamIsCapturing(s, &cs));
+            if (cs != cudaStreamCaptureStatusNone) {
+                ie_set_error("ie_matvec: the first IE_TENSOR call on a problem builds its strip table and must not be captured");
+                return IE_ERR_ARG;
+            }
+            IE_TRY(prepare_tc_strip(p));
+        }
+        auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encode_fn());
+        if (!encode) {
+            ie_set_error("ie_matvec: cuTensorMapEncodeTiled is not available from the driver");
+            return IE_ERR_CUDA;
+        }
+        const int n = p->n, Lb = std::min(n, kWBM), nb = kWBM / Lb;
+        CUtensorMap smap;
+        std::memset(&smap, 0, sizeof(smap));
+        if (nb > 1) {
+            // the interleaved strip table [plane][slow offset][rho][signed interleaved offset x 4
+            // entries] of TF32 words; a box is 4 nb words x (Lb + 28) rows x both planes
+            const cuuint64_t O = p->dim == 3 ? (cuuint64_t)n : 1, Q = 2 * (cuuint64_t)n, R = 2 * (cuuint64_t)n;
+            const cuuint64_t gdim[4] = {4 * Q, R, O, 2};
+            const cuuint64_t gstride[3] = {Q * 16, R * Q * 16, O * R * Q * 16};
+            const cuuint32_t box[4] = {(cuuint32_t)(4 * nb), (cuuint32_t)(Lb + 28), 1, 2};
+            const cuuint32_t estride[4] = {1, 1, 1, 1};
+            const CUresult cr = encode(&smap, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, p->d_tc_strip, gdim, gstride, box, estride,
+                                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                       CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (cr != CUDA_SUCCESS) {
+                ie_set_error("ie_matvec: cuTensorMapEncodeTiled failed for the strip table (" + std::to_string((int)cr) + ")");
+                return IE_ERR_CUDA;
+            }
+        }
+        const unsigned char *strip = static_cast<const unsigned char *>(p->d_tc_strip);
+        if (p->dim == 2)
+            k1w_matvec_tc<2><<<gw, kWThreads, kWSmem, s>>>(smap, strip, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial,
+                                                           d_err, n, Lb);
+        else
+            k1w_matvec_tc<3><<<gw, kWThreads, kWSmem, s>>>(smap, strip, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial,
+                                                           d_err, n, Lb);
+    } else if (p->dim == 2) {
         k1t_matvec_tc<2><<<g, 256, dsm, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial, d_err);
-    else
+    } else {
         k1t_matvec_tc<3><<<g, 256, dsm, s>>>(p->d_coord, xs.as<uint32_t>(), nrhs, p->N, cps, nchunks, partial, d_err);
+    }
     IE_LAUNCHED();
     return IE_OK;
 }
 
-// The Toeplitz-fed variant applies when n is a multiple of 32 and 128 rows are whole lines (n = 32,
-// 64) or part of one (n a multiple of 128), and the table is built.
+// The strip-fed variant applies when n is a multiple of 32, 256 rows are whole lines (n = 32, 64,
+// 128) or part of one (n a multiple of 256), and the strip table (128 n^3 bytes in 3D, 128 n^2 in
+// 2D) is at most 1 GiB.
 bool tc_toeplitz(const ie_problem *p) {
-    return p->d_table_tc && p->n % 32 == 0 && (p->n >= kTM ? p->n % kTM == 0 : kTM % p->n == 0);
+    const long long n = p->n;
+    const long long bytes = 128LL * n * n * (p->dim == 3 ? n : 1);
+    return p->d_table_tc && n % 32 == 0 && (n >= kWBM ? n % kWBM == 0 : kWBM % n == 0) && bytes <= kStripCap;
+}
+
+// The strip table of K1w (once per problem, on first use; synchronizes)
+int prepare_tc_strip(const ie_problem *p_) {
+    ie_problem *p = const_cast<ie_problem *>(p_);
+    if (p->d_tc_strip || !tc_toeplitz(p)) return IE_OK;
+    const long long n = p->n, rows = 2LL * (p->dim == 3 ? n : 1) * (2 * n) * (2 * n);
+    IE_TRY_CUDA(cudaMalloc(&p->d_tc_strip, sizeof(uint4) * rows));
+    tc_strip_kernel<<<(unsigned)((rows + 255) / 256), 256>>>(p->d_table_tc, p->dim, p->n, p->n < kWBM ? 1 : 0,
+                                                              static_cast<uint4 *>(p->d_tc_strip));
+    IE_LAUNCHED();
+    IE_TRY_CUDA(cudaDeviceSynchronize());
+    return IE_OK;
 }
 
 // Per |offset| q: the exact entry (FP64 table; 0 at q = 0, the diagonal being added in FP64) split
@@ -680,6 +744,7 @@ int tc_splits_toeplitz(long long tiles, int nchunks, int sms) {
 
 int tc_chunk() { return kTK; }
 int tc_rows() { return kTM; }
+int tc_block_rows() { return kWBM; }
 int tc_cols() { return kTN; }
 
 int prepare_tc() {
