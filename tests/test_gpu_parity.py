@@ -85,9 +85,12 @@ def test_matvec_multi_rhs_and_shift(dim, n, nrhs):
 
 @pytest.mark.parametrize("dim,n,nrhs,conv", [(3, 16, 64, O.GRID_TEXT), (3, 12, 70, O.GRID_TEXT),
                                              (2, 40, 20, O.GRID_TEXT), (3, 10, 1, O.GRID_TEXT),
-                                             # tiles fed from the exact per-offset table (n = 32, 64, 128k)
+                                             # strip-fed tiles from the exact per-offset table: n = 32, 64,
+                                             # 128 (several lines per 256-target block, TMA copies) and
+                                             # n = 256 (one line per block, bulk copies)
                                              (3, 32, 64, O.GRID_TEXT), (3, 32, 3, O.GRID_TABLE),
-                                             (2, 64, 16, O.GRID_TEXT), (2, 128, 9, O.GRID_TEXT)])
+                                             (2, 64, 16, O.GRID_TEXT), (2, 128, 9, O.GRID_TEXT),
+                                             (2, 256, 4, O.GRID_TEXT)])
 def test_tensor_core_matvec(dim, n, nrhs, conv):
     # tcgen05 3xTF32 contraction: FP32-class accuracy, like IE_MIXED
     N = n ** dim
@@ -189,10 +192,11 @@ def test_pcg_fft_inner_fp64_parity(dim, n, m, delta):
     assert O.true_relative_residual(dim, n, f, host(u)) <= 1e-8 * 1.05
 
 
-@pytest.mark.parametrize("residual", [0, iedd.IE_ACCURATE, iedd.IE_FFT])
+@pytest.mark.parametrize("residual", [0, iedd.IE_ACCURATE, iedd.IE_FFT, 16])
 def test_pcg_accurate_residual_modes(residual):
     # the accurate residual (replacements, verification) by the library's choice (the FP64 FFT
-    # matvec) or forced: each reports its mode and meets tol on the oracle's residual
+    # matvec) or forced (16: the FP64 regenerated sum, IE_FP64 being 0): each reports its mode and
+    # meets tol on the oracle's residual
     n, m, delta = 64, 4, 1
     f = I.grf(2, n, 0.1, 5)
     prob = iedd.ie_discretize(2, n)
@@ -200,7 +204,7 @@ def test_pcg_accurate_residual_modes(residual):
     fac = iedd.dd_factor(prob, part, iedd.IE_MIXED)
     u = torch.zeros(n * n, dtype=torch.float64, device="cuda")
     rep = iedd.pcg_solve(prob, fac, dev(f), u, tol=1e-9, precision=iedd.IE_MIXED, residual=residual)[0]
-    assert rep["accurate_mode"] == (residual or iedd.IE_FFT)
+    assert rep["accurate_mode"] == {0: iedd.IE_FFT, 16: iedd.IE_FP64}.get(residual, residual)
     assert rep["status"] == 0 and rep["accurate_matvecs"] >= 1
     assert O.true_relative_residual(2, n, f, host(u)) <= 1e-9 * 1.01
 
