@@ -283,7 +283,8 @@ def workload_rhs(name: str, seed0: int = 0):
     return np.stack([I.uniform_rhs(N, s_) for s_ in seeds], axis=1)
 
 
-def cpu_baseline(name: str, iterations: int, rows_sample: int = 2048, blocks_sample: int = 64):
+def cpu_baseline(name: str, iterations: int, rows_sample: int = 2048, blocks_sample: int = 64,
+                 iterations_from: str = "the oracle's FP64 count at 1e-8"):
     """The FP64 oracle on a bounded sample of a workload, scaled to the whole solve: the direct-sum
     matvec over ``rows_sample`` rows (C, OpenMP), the oracle's own Cholesky and triangular-solve
     apply on ``blocks_sample`` subdomains; total = factor + iterations x (matvec + apply).
@@ -315,7 +316,7 @@ def cpu_baseline(name: str, iterations: int, rows_sample: int = 2048, blocks_sam
             "sample": (f"FP64 direct-sum matvec over {rows.size} of {N} rows x {nr} right-hand side(s) (C, "
                        f"OpenMP), own Cholesky and triangular-solve apply on {len(sb)} of {len(blocks)} "
                        f"subdomains, each scaled to the full workload; total = factor + {iterations} "
-                       f"iterations (the oracle's FP64 count at 1e-8) x (matvec + apply); extrapolated"),
+                       f"iterations ({iterations_from}) x (matvec + apply); extrapolated"),
             "parts_s": {"matvec": t_mv, "apply": t_ap, "factor": t_fac}}
 
 
@@ -357,12 +358,15 @@ def run_reference(args):
     if rank != 0:
         return 0
     name = args.workload
-    iters = oracle_fp64_count(name) or 80
+    iters = oracle_fp64_count(name)
+    src = "the oracle's FP64 count at 1e-8"
+    if iters is None:
+        iters, src = 80, "an assumed 80: no stored oracle count for this workload"
     for _ in range(args.warmup):
-        cpu_baseline(name, iters)
+        cpu_baseline(name, iters, iterations_from=src)
     vals, small = [], []
     for _ in range(args.steps):
-        vals.append(cpu_baseline(name, iters))
+        vals.append(cpu_baseline(name, iters, iterations_from=src))
         small.append(oracle_measured_legs(per_step=True)["ie2d_n64_schwarz_m4_d1"]["value"])
     v = statistics.mean(x["value"] for x in vals)
     cb = dict(vals[-1])
@@ -507,7 +511,9 @@ def main():
     if not args.no_extras and rank == 0 and world == 1 and args.workload == WORKLOAD:
         line.update(extras(torch, iedd, I, dev, stream, clocks, sms, flush))
         line["warm_start"] = warm_start_leg()
-        cb = cpu_baseline(args.workload, it_oracle or last["iterations"])
+        cb = (cpu_baseline(args.workload, it_oracle) if it_oracle is not None else
+              cpu_baseline(args.workload, last["iterations"],
+                           iterations_from="the GPU's count: no stored oracle count for this workload"))
         cb["measured_end_to_end"] = oracle_measured_legs(per_step=False)
         line["cpu_baseline"] = cb
     if rank == 0:

@@ -38,7 +38,7 @@ def test_headline_config_names_the_workload():
 def test_reference_line_structure(monkeypatch, capsys):
     calls = []
 
-    def fake_baseline(name, iterations):
+    def fake_baseline(name, iterations, iterations_from=""):
         calls.append((name, iterations))
         return {"value": 10.0 + len(calls), "unit": "s", "cores": 4, "cpu": "test", "kind": "oracle",
                 "sample": "stand-in", "parts_s": {"matvec": 0.1, "apply": 0.01, "factor": 1.0}}
