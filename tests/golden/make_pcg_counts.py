@@ -2,7 +2,7 @@
 parity tests, at a tolerance where the count is well conditioned.
 
 Calls only the FP64 oracle (``oracle/ie_oracle.py``) and the seeded input generators.  Run from
-the repository root:  python tests/golden/make_pcg_counts.py [case ...]
+the repository root:  python tests/golden/make_pcg_counts.py [--jobs K] [case ...]
 
 Why a tolerance has to be chosen.  PCG minimises the A-norm of the error, not the 2-norm of the
 residual, and on these first-kind systems the residual norm of some iterations is extremely
@@ -20,7 +20,11 @@ and, as an ensemble of perturbed but equally valid versions of the same method, 
               moves a factor of blocks with cond(A_i) ~ 1e4 by up to ~1e-12, and a matvec by
               ~1e-15 of max |A x|), and ``f64n`` the right-hand side perturbed by 2^-50 of its
               largest entry (the seeded Gaussian random fields come out of an FFT, whose last bits
-              differ between machines);
+              differ between machines); ``mvd64`` every matvec perturbed by 2^-52 (|A| |x|)_i
+              (random signs): the error class of an FP64 evaluation of the defining direct sum
+              (Eq. e:dis), whose roundings are at the scale of sum_j |A_ij| |x_j|, not of |(A x)_i|
+              (at 1024^2 that is ~1e3 times larger: an exact-entry direct sum, like the tensor-core
+              one, lands there, an FFT matvec does not);
   * ``m32``   the exact subdomain inverses A_i^{-1} stored in FP32 (storage rounding only);
   * ``c32``   inverses formed from an FP32 Cholesky of A_i (LAPACK spotrf), stored in FP32;
   * ``c32p``, ``c32q``  the same after symmetric relative perturbations of A_i by 2^-24 and 2^-23
@@ -28,11 +32,15 @@ and, as an ensemble of perturbed but equally valid versions of the same method, 
   * ``c32w``  W_i = L_i^{-1} of the FP32 factor rounded to FP32 and M_i = W_i^T W_i formed in FP32
               arithmetic (the explicit-inverse pipeline with FP32 rounding at every step);
   * ``c32s``  the same with W_i formed in FP32 arithmetic too (LAPACK strtrs on the FP32 factor);
+  * ``c32d``  ``c32`` with the ``mvd64`` matvec (FP32 inverses with a direct-sum-class FP64 matvec);
   * ``mv32``  (3D only) ``c32`` with every matvec perturbed by 2^-23 |A| |x| per entry, the
-              error class of an FP32-accumulated matvec.
+              error class of an FP32-accumulated matvec;
+  * ``mv32e`` (3D only) ``c32`` with a matvec whose entries carry a fixed relative error of up to
+              2^-22 per lattice offset (the FP32 entries of a regenerated-entry matvec, the same at
+              every product) on top of the ``mv32`` accumulation error.
 A candidate tolerance (tried in the order 1e-8, 5e-9, 2e-9, 1e-9, 5e-10, 2e-10, 1e-10) is
 *stable* for a column when the FP64-level counts (``fp64``, ``p64a``, ``p64b``, ``mvn64``,
-``f64n``) span at most two consecutive values: there the FP64 count is a property of the method and not of its
+``f64n``, ``mvd64``) span at most two consecutive values: there the FP64 count is a property of the method and not of its
 rounding.
 The candidate stable for the most columns (ties: the one where the FP64-level counts agree
 exactly in the most columns, then the first) is stored with, per column, every member's count and
@@ -91,6 +99,38 @@ def history(matvec, precond, F, tol_min, max_it):
     O.pcg(matvec, precond, F, tol_min, max_it, history=h)
     H = np.array(h)
     return H.reshape(H.shape[0], -1)
+
+
+def fft_matvec_entry_error(dim, n, rel_bits, seed):
+    """The oracle's FFT route (circulant embedding of the per-offset entries, Sec. 6) with every
+    off-diagonal entry t(d) multiplied by (1 + 2^rel_bits u(|d|)), u uniform in [-1, 1] and fixed
+    per offset: a fixed perturbation of A, like FP32 entries regenerated the same way each time."""
+    spacing, _, weight, _ = O.grid_geometry(dim, n, O.GRID_TEXT)
+    size = 2 * n
+    off = np.arange(size)
+    off = np.where(off < n, off, off - size)
+    grids = np.meshgrid(*([off] * dim), indexing="ij")
+    r2 = sum(g.astype(np.float64) ** 2 for g in grids)
+    # |d| per axis, symmetric in sign (offset n is never reached by a product of the [0, n) window)
+    key = sum(np.minimum(np.abs(g), n - 1) * n ** k for k, g in enumerate(grids))
+    u = np.random.default_rng(seed).uniform(-1.0, 1.0, n ** dim)[key]
+    zero = r2 == 0.0
+    r = spacing * np.sqrt(np.where(zero, 1.0, r2))
+    c = weight * O.kernel(dim, r) * (1.0 + 2.0 ** rel_bits * u)
+    c[zero] = O.diagonal(dim, n)
+    chat = np.fft.rfftn(c)
+
+    def mv(x):
+        x = np.asarray(x, dtype=np.float64)
+        xm = x.reshape(n ** dim, -1)
+        out = np.empty_like(xm)
+        for k in range(xm.shape[1]):
+            xp = np.zeros((size,) * dim)
+            xp[tuple(slice(0, n) for _ in range(dim))] = xm[:, k].reshape((n,) * dim)
+            yp = np.fft.irfftn(chat * np.fft.rfftn(xp), s=(size,) * dim, axes=tuple(range(dim)))
+            out[:, k] = yp[tuple(slice(0, n) for _ in range(dim))].reshape(-1)
+        return out.reshape(x.shape)
+    return mv
 
 
 def inverse_apply(blocks, inverses):
@@ -162,6 +202,13 @@ def run_case(name):
         Y = y.reshape(y.shape[0], -1)
         return y + (2.0 ** -48 * np.abs(Y).max(axis=0) * np.sign(rng64.standard_normal(Y.shape))).reshape(y.shape)
 
+    rngd = np.random.default_rng(19)
+
+    def mv_direct_noisy(x):
+        y = O.matvec_fft(dim, n, x)
+        mag = np.abs(O.matvec_fft(dim, n, np.abs(x)))  # (|A| |x|)_i, up to the sign of the far-field entries in 2D
+        return y + 2.0 ** -52 * mag * np.sign(rngd.standard_normal(y.shape))
+
     tol_min, max_it = CANDIDATES[-1] / 4, 600
     H = {"fp64": history(mv, exact_apply, F, tol_min, max_it),
          "p64a": history(mv, lambda r: O.apply(p64[0], blocks, r), F, tol_min, max_it),
@@ -174,9 +221,18 @@ def run_case(name):
          "c32p": history(mv, inverse_apply(blocks, c32p), F, tol_min, max_it),
          "c32q": history(mv, inverse_apply(blocks, c32q), F, tol_min, max_it),
          "c32w": history(mv, inverse_apply(blocks, c32w), F, tol_min, max_it),
-         "c32s": history(mv, inverse_apply(blocks, c32s), F, tol_min, max_it)}
+         "c32s": history(mv, inverse_apply(blocks, c32s), F, tol_min, max_it),
+         "mvd64": history(mv_direct_noisy, exact_apply, F, tol_min, max_it),
+         "c32d": history(mv_direct_noisy, inverse_apply(blocks, c32), F, tol_min, max_it)}
     if dim == 3:
         H["mv32"] = history(mv_noisy, inverse_apply(blocks, c32), F, tol_min, max_it)
+        mv_e = fft_matvec_entry_error(dim, n, -22, 17)
+
+        def mv_entry_noisy(x):
+            y = mv_e(x)
+            mag = O.matvec_fft(dim, n, np.abs(x))
+            return y + 2.0 ** -23 * mag * noise_rng.uniform(-1.0, 1.0, y.shape)
+        H["mv32e"] = history(mv_entry_noisy, inverse_apply(blocks, c32), F, tol_min, max_it)
     ncol = F.shape[1]
 
     def col_hist(key, c):
@@ -184,7 +240,7 @@ def run_case(name):
         return h
 
     per_tol, exact = {}, {}
-    fp64_level = ("fp64", "p64a", "p64b", "mvn64", "f64n")
+    fp64_level = ("fp64", "p64a", "p64b", "mvn64", "f64n", "mvd64")
     for tol in CANDIDATES:
         cols, same = [], 0
         for c in range(ncol):
@@ -218,6 +274,13 @@ def run_case(name):
 
 
 def main(argv):
+    """python tests/golden/make_pcg_counts.py [--jobs K] [case ...]: the cases (all by default), K
+    of them at a time in separate processes; the file is rewritten as each one finishes."""
+    jobs = 1
+    if "--jobs" in argv:
+        i = argv.index("--jobs")
+        jobs = int(argv[i + 1])
+        argv = argv[:i] + argv[i + 2:]
     names = argv or list(CASES)
     data = {}
     if os.path.exists(OUT):
@@ -226,10 +289,22 @@ def main(argv):
     data["_about"] = ("Oracle PCG iteration counts (FP64, FFT matvec, stop on the recursive residual) "
                       "at a tolerance where the count is well conditioned; written by "
                       "tests/golden/make_pcg_counts.py, which calls only the oracle")
-    for name in names:
-        data[name] = run_case(name)
+
+    def store(name, entry):
+        data[name] = entry
         with open(OUT, "w") as fh:
             json.dump(data, fh, indent=1)
+
+    if jobs <= 1:
+        for name in names:
+            store(name, run_case(name))
+        return
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(max_workers=jobs, mp_context=mp.get_context("spawn")) as ex:
+        futs = {ex.submit(run_case, name): name for name in names}
+        for fut in cf.as_completed(futs):
+            store(futs[fut], fut.result())
 
 
 if __name__ == "__main__":

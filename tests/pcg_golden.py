@@ -2,9 +2,9 @@
 
 The counts are written by tests/golden/make_pcg_counts.py, which calls only the oracle.  Each
 case holds a tolerance at which the oracle's FP64 count is well conditioned (its rounding-level
-variants ``p64a``, ``p64b``, ``mvn64``, ``f64n`` span at most two consecutive counts there), and per column the FP64
+variants ``p64a``, ``p64b``, ``mvn64``, ``f64n``, ``mvd64`` span at most two consecutive counts there), and per column the FP64
 count, every ensemble member's count and whether the column is stable.  The FP32-level members
-(``m32``, ``c32``, ``c32p``, ``c32q``, ``c32w``; ``mv32`` in 3D) are the oracle with FP32 subdomain inverses
+(``m32``, ``c32``, ``c32p``, ``c32q``, ``c32w``, ``c32s``, ``c32d``; ``mv32``, ``mv32e`` in 3D) are the oracle with FP32 subdomain inverses
 (and, for ``mv32``, an FP32-class matvec): the counts a mixed-precision implementation of the
 method can be expected to reach.
 """
@@ -16,7 +16,7 @@ import os
 import numpy as np
 
 PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "pcg_counts.json")
-FP64_LEVEL = ("p64a", "p64b", "mvn64", "f64n")
+FP64_LEVEL = ("p64a", "p64b", "mvn64", "f64n", "mvd64")
 
 
 def load():
