@@ -48,6 +48,10 @@ WORKLOADS = {
                                       factor="mixed"),
     "ie2d_n256_schwarz_m16_d2": dict(dim=2, n=256, m=16, delta=2, rhs="grf", ell=0.1, seeds=1, precision="mixed",
                                      factor="mixed"),
+    # the paper's CBD preconditioner with recursive-skeletonization subdomain factors (Sec. 4.3) at
+    # N / M = 64, one layer of overlap, eps = 1e-3 (Sec. 5.2), the FP64 FFT matvec (Sec. 6)
+    "ie2d_n1024_cbd_rs_m128_d1": dict(dim=2, n=1024, m=128, delta=1, rhs="grf", ell=0.05, seeds=1, precision="fp64",
+                                      factor="rs", eps=1e-3, inner="fft"),
 }
 METRIC = "PCG time-to-1e-8 true relative residual (s)"
 L2_FLUSH_BYTES = 512 << 20
@@ -67,6 +71,11 @@ NCU_KZ = {("e2d6b85e8691647a", 1024): {"traffic": 1782236976, "tensor_pipe": 0.6
 NCU_K1W = {("c8970434ed8bad33", 32): {"traffic": 83382784, "tensor_pipe": 0.430}}
 # BF16 digit products per pair of the exact tensor-core matvec (six digits per factor, levels 0..5)
 KZ_PRODUCTS_PER_PAIR = 21
+# ncu figures of the RS factor's level-1 launches per rs_source_hash(), 2D 256^2 with M = 32^2 (the
+# same region shapes as 1024^2): FP64 pipe activity of rs_id / rs_elim and their DRAM bytes
+NCU_RS = {}
+# GB300's FP64 rate (nominal; no FP64 peak is measured on this machine)
+FP64_NOMINAL_TFLOPS = 1.25
 
 
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates per GPU
@@ -98,6 +107,12 @@ def tc_matvec_source_hash() -> str:
 def tc_exact_source_hash() -> str:
     """sha256 (16 hex digits) of the exact tensor-core matvec's source file."""
     src = open(os.path.join(ROOT, "paper_2108_12574_gb300", "csrc", "tc_exact.cu")).read()
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
+
+
+def rs_source_hash() -> str:
+    """sha256 (16 hex digits) of the recursive-skeletonization factor's source file."""
+    src = open(os.path.join(ROOT, "paper_2108_12574_gb300", "csrc", "rs.cu")).read()
     return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
@@ -180,9 +195,30 @@ def config_dict(name: str = WORKLOAD) -> dict:
     rhs = (f"GRF l={W['ell']} seed=rank" if W["rhs"] == "grf" else
            f"uniform[-1,1] seeds rank*{W['seeds']}..+{W['seeds'] - 1}" if W["seeds"] > 1 else "uniform[-1,1] seed=rank")
     prec = "fp64" if W["precision"] == "fp64" else f"mixed{W['dim']}d"
-    return {"workload": name, "dim": W["dim"], "n": W["n"], "N": W["n"] ** W["dim"], "m": W["m"],
-            "delta": W["delta"], "nrhs": W["seeds"], "rhs": rhs, "tol": TOL, "decomposition": "schwarz",
-            "precision": PRECISION_TEXT[prec], "l2": "flushed between timed steps (512 MiB write)"}
+    out = {"workload": name, "dim": W["dim"], "n": W["n"], "N": W["n"] ** W["dim"], "m": W["m"],
+           "delta": W["delta"], "nrhs": W["seeds"], "rhs": rhs, "tol": TOL, "decomposition": "schwarz",
+           "precision": PRECISION_TEXT[prec], "l2": "flushed between timed steps (512 MiB write)"}
+    if W["factor"] == "rs":
+        out.update({"decomposition": "cbd", "subdomain_solver": f"recursive skeletonization, eps={W['eps']}",
+                    "precision": "f64 throughout (FFT matvec, RS factors and apply, CG scalars)"})
+    return out
+
+
+def make_factor(iedd, prob, W, stream, fprec=None):
+    """(partition, factor) of a workload: Schwarz boxes with dense Cholesky factors, or the CBD
+    colours with recursive-skeletonization factors."""
+    if W["factor"] == "rs":
+        part = iedd.dd_partition(prob, W["m"], W["delta"], iedd.DD_CBD)
+        return part, iedd.dd_factor_rs(prob, part, eps=W["eps"], stream=stream)
+    if fprec is None:
+        fprec = iedd.IE_FP64 if W["factor"] == "fp64" else iedd.IE_MIXED
+    part = iedd.dd_partition(prob, W["m"], W["delta"], iedd.DD_SCHWARZ)
+    return part, iedd.dd_factor(prob, part, fprec, stream=stream)
+
+
+def inner_of(iedd, W) -> int:
+    """pcg_opts.inner of a workload (0: the library's choice)."""
+    return iedd.IE_FFT if W.get("inner") == "fft" else 0
 
 
 # ------------------------------------------------------------------------------------------
@@ -425,7 +461,7 @@ def main():
     N = n_w ** dim_w
     nr = W["seeds"]
     prec = iedd.IE_FP64 if W["precision"] == "fp64" else iedd.IE_MIXED
-    fprec = iedd.IE_FP64 if W["factor"] == "fp64" else iedd.IE_MIXED
+    inner = inner_of(iedd, W)
     seeds = [rank * nr + k for k in range(nr)]
     if W["rhs"] == "grf":
         f_host = np.stack([I.grf(dim_w, n_w, W["ell"], s_) for s_ in seeds])
@@ -437,12 +473,15 @@ def main():
     u = torch.zeros_like(f)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    rs_stats = {}
+
     def step(fv, uv):
         prob = iedd.ie_discretize(dim_w, n_w, device=local)
-        part = iedd.dd_partition(prob, W["m"], W["delta"], iedd.DD_SCHWARZ)
-        fac = iedd.dd_factor(prob, part, fprec, stream=stream)
+        part, fac = make_factor(iedd, prob, W, stream)
         reps = iedd.pcg_solve(prob, fac, fv, uv, tol=TOL, precision=prec, replace_every=REPLACE_EVERY,
-                              stream=stream)
+                              inner=inner, stream=stream)
+        if W["factor"] == "rs":
+            rs_stats.update(iedd.dd_rs_info(fac, stats=True)[2])
         fac.close(); part.close(); prob.close()
         return reps
 
@@ -491,7 +530,7 @@ def main():
            "h2d_bytes_per_step": int(f_host.nbytes), "d2h_bytes_per_step": int(u_host.nbytes)}
 
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    roofline, kz_inner = roofline_of(iedd, args.workload, last, clocks, sms)
+    roofline, kz_inner = roofline_of(iedd, args.workload, last, clocks, sms, rs_stats)
     cfg = config_dict(args.workload)
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
@@ -537,10 +576,27 @@ def tensor_peak(clocks: dict):
     return sustained, "sustained"
 
 
-def roofline_of(iedd, name, rep, clocks, sms):
+def roofline_of(iedd, name, rep, clocks, sms, rs_stats=None):
     """Roofline record of the inner matvec (the dominant kernel) from its CUDA-event time inside
-    pcg_solve (the library times every inner matvec on the launching stream)."""
+    pcg_solve (the library times every inner matvec on the launching stream).  For the RS-CBD
+    workload the dominant kernels are the factor's rs_id and rs_elim (the library times their
+    launches with CUDA events on its stream and counts their algorithmic FP64 flops)."""
     W = WORKLOADS[name]
+    if W["factor"] == "rs" and rs_stats:
+        flops = rs_stats["id_flops"] + rs_stats["elim_flops"]
+        t = (rs_stats["id_ms"] + rs_stats["elim_ms"]) / 1e3
+        achieved = flops / t
+        peak = FP64_NOMINAL_TFLOPS * 1e12
+        ncu = NCU_RS.get(rs_source_hash(), {})
+        return ({"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                 "frac": achieved / peak, "traffic": ncu.get("traffic"), "kernel": "rs_id + rs_elim (RS factor)",
+                 "launch_ms": t * 1e3, "fp64_flops": flops, "id_ms": rs_stats["id_ms"],
+                 "elim_ms": rs_stats["elim_ms"], "fp64_pipe_ncu": ncu.get("fp64_pipe"),
+                 "peak_basis": (f"GB300 FP64 {FP64_NOMINAL_TFLOPS} TFLOP/s nominal (no FP64 peak is measured on this "
+                                "pool); work = the factor's algorithmic FP64 flops (ID: initial norms, 4 flops per row "
+                                "and remaining column per Gram-Schmidt step, back substitution; elimination: M, B_rr, Cholesky, triangular "
+                                "inverse, L^-T L^-1, X, B_ss) / the summed CUDA-event time of its rs_id and rs_elim "
+                                "launches")}, False)
     dim_w, n_w, nr = W["dim"], W["n"], W["seeds"]
     N = n_w ** dim_w
     prec = iedd.IE_FP64 if W["precision"] == "fp64" else iedd.IE_MIXED
@@ -685,14 +741,18 @@ def timed_solves(torch, iedd, dev, stream, name, steps, inner=0, factor=None, pr
     f = torch.from_numpy(F.T.copy() if F.shape[1] > 1 else F[:, 0].copy()).to(dev)
     u = torch.zeros_like(f)
     fprec = factor if factor is not None else (iedd.IE_FP64 if W["factor"] == "fp64" else iedd.IE_MIXED)
+    if W["factor"] == "rs":
+        fprec = None
     prec = precision if precision is not None else (iedd.IE_FP64 if W["precision"] == "fp64" else iedd.IE_MIXED)
     if flush is None:
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    if not inner:
+        inner = inner_of(iedd, W)
+
     def step():
         prob = iedd.ie_discretize(W["dim"], W["n"], device=dev.index)
-        part = iedd.dd_partition(prob, W["m"], W["delta"], iedd.DD_SCHWARZ)
-        fac = iedd.dd_factor(prob, part, fprec, stream=stream)
+        part, fac = make_factor(iedd, prob, W, stream, fprec)
         reps = iedd.pcg_solve(prob, fac, f, u, tol=TOL, precision=prec, inner=inner, replace_every=REPLACE_EVERY,
                               stream=stream)
         fac.close(); part.close(); prob.close()
@@ -812,6 +872,7 @@ def extras(torch, iedd, I, dev, stream, clocks, sms, flush):
                                    f"{its} = the FP64 iteration count at 1e-8"),
                          "parts_s": {"factor": t_fac, "matvec": t_64, "apply": t_ap}}
     out["cbd"] = cbd_leg(torch, iedd, I, dev, stream)
+    out["cbd_rs"] = cbd_rs_leg(torch, iedd, dev, stream, flush)
     out["stored_matvec"] = stored_matvec_leg(torch, iedd, I, dev, stream)
     return out
 
@@ -850,6 +911,40 @@ def cbd_leg(torch, iedd, I, dev, stream, sizes=(128, 256), ell=0.1):
         prob.close()
         out[f"n{n}"] = row
     return out
+
+
+def cbd_rs_leg(torch, iedd, dev, stream, flush, name="ie2d_n1024_cbd_rs_m128_d1"):
+    """The paper's CBD preconditioner with recursive-skeletonization subdomain factors (Sec. 4.3)
+    on the same 1024^2 grid and right-hand side as the headline: whole steps (discretize +
+    partition + RS factor + FP64 PCG with the FFT matvec), CUDA events, L2 flushed; the factor
+    and the solve also timed apart (host clock, synchronized)."""
+    t, reps = timed_solves(torch, iedd, dev, stream, name, 2, flush=flush)
+    W = WORKLOADS[name]
+    prob = iedd.ie_discretize(W["dim"], W["n"], device=dev.index)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    part, fac = make_factor(iedd, prob, W, stream)
+    torch.cuda.synchronize(dev)
+    t_fac = time.perf_counter() - t0
+    levels, top = iedd.dd_rs_info(fac)
+    fac.close(); part.close(); prob.close()
+    rep = reps[0]
+    return {"workload": name, "value": t, "unit": "s", "iterations": rep["iterations"],
+            "iterations_oracle_fp64": rs_oracle_count(name), "true_relres": rep["true_relres"],
+            "factor_s": t_fac, "t_solve_matvec_s": rep["matvec_ms"] / 1e3, "t_solve_apply_s": rep["apply_ms"] / 1e3,
+            "apply_ms_per_iteration": rep["apply_ms"] / max(rep["applies"], 1), "levels": levels, "top_dofs": top,
+            "config": config_dict(name)}
+
+
+def rs_oracle_count(name: str):
+    """The oracle's RS-CBD PCG count at 1e-8 (tests/golden/rs_counts.json, written by a script that
+    calls only the oracle), or None."""
+    key = {"ie2d_n1024_cbd_rs_m128_d1": "ie2d_n1024_cbd_m128"}.get(name)
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "rs_counts.json")) as fh:
+            return int(json.load(fh)[key]["iterations"])
+    except (OSError, KeyError, ValueError, TypeError):
+        return None
 
 
 def stored_matvec_leg(torch, iedd, I, dev, stream, n=256):

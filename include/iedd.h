@@ -158,7 +158,9 @@ IEDD_API int ie_release_matrix(ie_problem *p);
  *   kind   DD_JACOBI (the boxes), DD_SCHWARZ (the extended boxes, D = M) or DD_CBD (extended
  *          boxes unioned by the parity colour (k_1 mod 2, ..., k_d mod 2), D = 2^dim)
  * Index sets are in ascending global order.  Host-side; the sets are also copied to the device.
- * Errors: IE_ERR_ARG (n % m != 0, delta < 0, a subdomain larger than 25600 points), IE_ERR_OOM.
+ * Errors: IE_ERR_ARG (n % m != 0, delta < 0, a DD_JACOBI or DD_SCHWARZ subdomain larger than 25600
+ * points; a larger DD_CBD subdomain is accepted here and refused by dd_factor, dd_factor_rs takes
+ * it), IE_ERR_OOM.
  */
 IEDD_API int dd_partition(const ie_problem *p, int m, int delta, int kind, dd_partition_t **out);
 
@@ -189,6 +191,59 @@ IEDD_API int dd_factor(const ie_problem *p, const dd_partition_t *s, int precisi
               int *info, void *stream);
 
 IEDD_API void dd_factor_destroy(dd_factor_t *f);
+
+/*
+ * dd_factor_rs -- the CBD preconditioner with every subdomain factored approximately by recursive
+ * skeletonization (Sec. 4.3, "Recursive skeletonization (RS) as subdomain solver": Eqs. e:oi,
+ * e:block, e:id, e:id_err, e:al, e:alu, e:b, e:schur), on the device, in FP64.
+ *   s     a DD_CBD partition with 2 delta <= n / m (the extended boxes of one colour are then
+ *         disjoint: the regions of Eq. e:oi); s and p must outlive the factor
+ *   opts  (host, may be NULL: defaults) relative accuracy eps of every ID (Eq. e:id_err; default
+ *         1e-3, the paper's), proxy points nproxy (default 64 in 2D, 256 in 3D) and proxy radius
+ *         rho in units of a region's longest side (default 1.5, the paper's)
+ * For each colour: level 1 takes the colour's extended boxes as regions; at every level each
+ * region's DOFs are split by an ID of A_qp (q: the other regions' DOFs of the subdomain) into
+ * skeletons s and redundant r with A_qr ~ A_qs T, computed through a proxy circle (2D; plus one
+ * constant row for the log kernel's monopole) or sphere (3D) of radius rho * side around the
+ * region's box with the DOFs of other regions inside it as explicit rows; the redundant DOFs are
+ * eliminated (B_rr = L L^T, B_ss = A_ss - B_sr B_rr^{-1} B_rs), and 2^d neighbouring regions merge
+ * into one region of the next level, until one is left, whose Schur complement is factored by
+ * dense Cholesky.  Pivots are column-pivoted Gram-Schmidt with a tie window (the lowest-index
+ * column within min(top / 2, max(1e-10 top, 1e-13 nu0)) of the largest squared norm), so that
+ * the symmetric grid's exact ties break the same way under any rounding.
+ * The result is a dd_factor_t that dd_apply and pcg_solve use like any other: z = sum_c R_c^T
+ * F_c^{-1} R_c r with the approximate factors F_c ~ A_c (symmetric positive definite).
+ * Synchronizes the stream.  Errors: IE_ERR_ARG (not DD_CBD, 2 delta > n / m, bad opts, a region
+ * above 4096 DOFs or 16384 ID rows, a last Schur complement above 8192 DOFs), IE_ERR_NOT_SPD (a
+ * non-positive pivot of some B_rr; *out stays NULL), IE_ERR_OOM, IE_ERR_CUDA.
+ */
+typedef struct {
+    double eps;   /* 0: 1e-3 */
+    int nproxy;   /* 0: 64 (2D) or 256 (3D) */
+    double rho;   /* 0: 1.5 */
+} rs_opts;
+
+IEDD_API int dd_factor_rs(const ie_problem *p, const dd_partition_t *s, const rs_opts *opts, dd_factor_t **out,
+                          void *stream);
+
+/*
+ * dd_rs_info -- shape of an RS factor: *ncolours = 2^dim; per colour c, levels[c] compression
+ * levels and top[c] DOFs at the last level (S of Sec. 5's tables).  stats[4]: the algorithmic FP64
+ * flops of the IDs and of the eliminations (counted from the regions' shapes and ranks), and the
+ * summed device time in ms of their kernel launches (CUDA events on the factor's stream).  Arrays
+ * hold 2^dim entries; any pointer may be NULL.  IE_ERR_ARG if f is not from dd_factor_rs.
+ */
+IEDD_API int dd_rs_info(const dd_factor_t *f, int *ncolours, int *levels, int *top, double *stats);
+
+/*
+ * dd_rs_export -- the regions of colour `colour` at level `level` (1-based; levels[c] + 1 is the
+ * last level): *nreg regions, *total DOFs; offsets[nreg + 1] (int64) into points[total] (int32,
+ * global grid indices), each region's DOFs with its skeletons first, in pivot order, then its
+ * redundant DOFs; rank[nreg] the skeleton counts (at the last level: the size).  Regions come in
+ * row-major order of their colour-grid coordinate.  Call once with NULL arrays for the sizes.
+ */
+IEDD_API int dd_rs_export(const dd_factor_t *f, int colour, int level, int *nreg, long long *total,
+                          long long *offsets, int *points, int *rank);
 
 /*
  * dd_apply -- z = T^{-1} r = sum_i R_i^T A_i^{-1} R_i r (Eq. e:ad), then a plain (unweighted) sum

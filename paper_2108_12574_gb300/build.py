@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libiedd.so")
 SOURCES = ["api.cu", "matvec.cu", "factor.cu", "apply.cu", "pcg.cu", "noalloc.cu", "ws_unet.cu", "stored.cu", "tc_matvec.cu",
-           "fft.cu", "tc_factor.cu", "tc_exact.cu"]
+           "fft.cu", "tc_factor.cu", "tc_exact.cu", "rs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # per-file extra flags: the FP32 SFU matvec wants flush-to-zero so log2/rsqrt map to one SFU op
 EXTRA = {"matvec.cu": ["-ftz=true"]}

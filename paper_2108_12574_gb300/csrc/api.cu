@@ -378,7 +378,7 @@ extern "C" int dd_partition(const ie_problem *p, int m, int delta, int kind, dd_
         s->max_block = std::max(s->max_block, (int)blocks[i].size());
     }
     s->total = s->offs.back();
-    if (s->max_block > kMaxBlock) {
+    if (s->max_block > kMaxBlock && kind != DD_CBD) {
         delete s;
         ie_set_error("dd_partition: a subdomain has more than " + std::to_string(kMaxBlock) + " points");
         return IE_ERR_ARG;
@@ -450,6 +450,11 @@ extern "C" int dd_factor(const ie_problem *p, const dd_partition_t *s, int preci
     if (!p || !s) { ie_set_error("dd_factor: NULL problem or partition"); return IE_ERR_ARG; }
     if (s->prob != p) { ie_set_error("dd_factor: partition belongs to another problem"); return IE_ERR_ARG; }
     if (precision != IE_FP64 && precision != IE_MIXED) { ie_set_error("dd_factor: unknown precision"); return IE_ERR_ARG; }
+    if (s->max_block > kMaxBlock) {
+        ie_set_error("dd_factor: a subdomain has more than " + std::to_string(kMaxBlock) +
+                     " points (dense factors); large CBD subdomains take dd_factor_rs");
+        return IE_ERR_ARG;
+    }
     if (precision == IE_FP64 && s->max_block > kFp64MaxBlock) {
         ie_set_error("dd_factor: IE_FP64 factors take blocks of at most " + std::to_string(kFp64MaxBlock) +
                      " points (one CTA per block); use IE_MIXED");
@@ -574,6 +579,10 @@ extern "C" void dd_factor_destroy(dd_factor_t *f) {
     cudaFree(f->d_xoff);
     for (int k = 0; k < 3; ++k) cudaFree(f->d_chunks[k]);
     cudaFree(f->d_citems);
+    if (f->rs) {  // its buffers may still be read by work in flight on any stream
+        cudaDeviceSynchronize();
+        rs_destroy(f->rs);
+    }
     delete f;
 }
 

@@ -546,6 +546,7 @@ int prepare_apply(const dd_factor_t *f) {
 
 int launch_apply(const dd_factor_t *f, const double *r, long long ldr, double *z, long long ldz, int nrhs,
                  cudaStream_t s) {
+    if (f->rs) return launch_apply_rs(f, r, ldr, z, ldz, nrhs, s);
     const ie_problem *p = f->prob;
     const dd_partition_t *part = f->part;
     DevBuf zbuf;

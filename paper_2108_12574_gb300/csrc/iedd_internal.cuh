@@ -106,6 +106,8 @@ struct dd_partition_t {
     long long *d_inv_pos = nullptr;  // total
 };
 
+struct RSFactor;  // rs.cu: recursive-skeletonization factors of the CBD subdomains
+
 struct dd_factor_t {
     const ie_problem *prob = nullptr;
     int device = 0;
@@ -136,6 +138,8 @@ struct dd_factor_t {
     // tensor-core batched apply: per block the first of its 128-row tiles (prefix sums)
     long long *d_tile_off = nullptr;
     int ntiles = 0;
+    // dd_factor_rs: the RS factors (then nblocks == 0 and none of the dense fields is used)
+    RSFactor *rs = nullptr;
 };
 
 // Classes of the explicit-inverse apply: double-float single column, double-float 4-column
@@ -240,6 +244,10 @@ int launch_factor_tc(dd_factor_t *f, const std::vector<int> &npad, const std::ve
 // writes them; results into zbuf [rhs][sum n_i]
 int launch_apply_tc(const dd_factor_t *f, const float *xh, const int *xe, int nrhs, double *zbuf, cudaStream_t s);
 int prepare_apply(const dd_factor_t *f);
+// rs.cu: z = T^{-1} r through the RS factors of f->rs; rs_destroy frees them.
+int launch_apply_rs(const dd_factor_t *f, const double *r, long long ldr, double *z, long long ldz, int nrhs,
+                    cudaStream_t s);
+void rs_destroy(RSFactor *rs);
 // z = T^{-1} r for device FP64 r (ldr) and z (ldz).
 int launch_apply(const dd_factor_t *f, const double *r, long long ldr, double *z, long long ldz,
                  int nrhs, cudaStream_t s);

@@ -1,0 +1,1510 @@
+// Recursive skeletonization (RS) of the CBD subdomains (Sec. 4.3, "Recursive skeletonization (RS)
+// as subdomain solver"; Eqs. e:oi, e:block, e:id, e:id_err, e:al, e:alu, e:b, e:schur), the
+// subdomain solver of the additive CBD preconditioner (Eqs. e:second, e:ad).
+//
+// dd_factor_rs builds, for every colour subdomain A_c = R_c A R_c^T, an approximate factorization
+// level by level on the device; dd_apply and pcg_solve reach it through launch_apply.  All of it
+// is FP64: the pivots and ranks of the IDs are decisions taken in FP64, and the factors feed an
+// FP64 preconditioner.
+//
+// Layout.  The work vector holds the colours one after another; a colour holds its level-1 regions
+// (its extended boxes, row-major by colour-grid coordinate K = k / 2) one after another; a region
+// holds its points in ascending global order.  A region of a higher level owns the positions of
+// the skeletons its children kept (children in row-major K order, each in pivot order).
+//
+// Factor kernels (one CTA per region; one launch takes every region of a level, of all colours):
+// KR1 rs_id    the ID matrix Y of the region (proxy rows h^d K(x_proxy - y), in 2D one row of h^d,
+//              and the near-field rows of A), column-major in a global workspace, then column-
+//              pivoted Gram-Schmidt on it.  The pivot is the lowest-index column whose squared norm
+//              is at least top - min(top / 2, max(1e-10 top, 1e-13 nu0)) (top: the largest
+//              remaining squared norm, nu0: the largest before the first step); norms are
+//              recomputed after every step; it stops once top <= eps^2 nu0.  Writes the rank k, the
+//              permutation (skeletons in pivot order, then the redundant columns in order) and
+//              T = R11^{-1} R12 (k x |r|, row-major) by back substitution, one thread per column.
+// KR2 rs_elim  D in the permuted order (level 1: entries of A; above: the children's B_ss blocks
+//              and entries of A between children), M = D L_p on the redundant columns
+//              (M_:r = D_:r - D_:s T), B_rr = M_rr - T^T M_sr, B_sr = M_sr, the Cholesky factor of
+//              B_rr (right-looking, column by column), its explicit inverse, X = B_rr^{-1} B_rs and
+//              B_ss = D_ss - B_sr X.  The last Schur complement of every colour is the same kernel
+//              with k = 0.
+// Apply kernels (the regions of a level own disjoint positions, so one launch takes them all):
+// KR3 rs_gather (y = r at every position), rs_down (u_r = y_r - T^T y_s, v_r = B_rr^{-1} u_r,
+//     y_s -= B_sr v_r, v_r kept in place of y_r), rs_top + rs_top_put (y_t = S^{-1} y_t),
+//     rs_up (a_r = v_r - X a_s, y_s = a_s - T a_r), rs_scatter (z_i = the sum over the positions
+//     of point i, in colour order).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "iedd_internal.cuh"
+
+namespace {
+
+constexpr int kRsThreads = 256;
+constexpr double kTieRel = 1e-10;    // pivot window, relative to the largest remaining norm
+constexpr double kTieAbs = 1e-13;    // pivot window, relative to the largest initial norm
+constexpr int kRsMaxDofs = 4096;     // largest region (DOFs) the kernels take
+constexpr int kRsMaxRows = 16384;    // largest ID matrix (rows)
+constexpr int kRsMaxTop = 8192;      // largest last Schur complement (staged in shared memory)
+constexpr int kRsTopRows = 64;       // rows of S^{-1} per CTA of rs_top
+constexpr size_t kRsWorkCap = size_t(4) << 30;  // bytes of per-launch workspace
+
+__device__ __forceinline__ double warp_allsum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// max over the CTA, returned to every thread
+__device__ double block_max(double v, double *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = sh[0];
+    for (int i = 1; i < nw; ++i) t = fmax(t, sh[i]);
+    return t;
+}
+
+// min over the CTA, returned to every thread
+__device__ int block_min(int v, int *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    int t = sh[0];
+    for (int i = 1; i < nw; ++i) t = min(t, sh[i]);
+    return t;
+}
+
+// entry of A between grid points a and b: the problem's per-offset FP64 table (entry 0: A_ii)
+__device__ __forceinline__ double a_entry(const float4 *coord, const double *t64, int n, int a, int b) {
+    const float4 pa = coord[a], pb = coord[b];
+    const long long dx = (long long)fabsf(pa.x - pb.x), dy = (long long)fabsf(pa.y - pb.y),
+                    dz = (long long)fabsf(pa.z - pb.z);
+    return t64[dx + n * (dy + (long long)n * dz)];
+}
+
+struct IdArgs {
+    int dim, n, nproxy;
+    double rho, spacing, weight, eps2;
+    const int *nb, *rows;
+    const long long *dof_off;   // per region: first natural DOF
+    const int *dof_pt;          // global point of every natural DOF
+    const long long *near_off;  // per region: first near-field point
+    const int *near_pt;
+    const int4 *geom;           // twice the centre (lattice units) and the longest side W
+    const long long *y_off, *c_off, *t_off;
+    double *Y, *C, *T;          // workspaces and the T output (k x |r| at t_off)
+    const float4 *coord;
+    const double *t64;
+    int *k_out, *perm_out;      // rank; permutation at dof_off
+    const double *ptab;         // proxy-row tables (level 1), or nullptr
+    const long long *ptab_off;  // per region: its table (by box side W), or -1 for direct evaluation
+};
+
+// The proxy rows of a region depend only on its longest side W and on the offset o = 2 x - (lo + hi
+// - 1) of a point from the box centre (lattice units, |o_d| <= W - 1): table[i][o] = h^d K(|R u_i -
+// o / 2| spacing), R = rho W, laid out [P][(2W - 1)^d].  One thread per entry.
+__global__ void rs_proxy_table(double *__restrict__ tab, int dim, int nproxy, int W, double rho, double spacing,
+                               double weight) {
+    const int side = 2 * W - 1;
+    const long long per = dim == 2 ? (long long)side * side : (long long)side * side * side;
+    const long long tot = per * nproxy;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / per);
+        long long f = e % per;
+        int o[3] = {0, 0, 0};
+        for (int d = dim - 1; d >= 0; --d) { o[d] = (int)(f % side) - (W - 1); f /= side; }
+        double u[3];
+        if (dim == 2) {
+            const double t = 2.0 * M_PI * (double)i / (double)nproxy;
+            u[0] = cos(t); u[1] = sin(t); u[2] = 0.0;
+        } else {
+            const double z = 1.0 - (2.0 * (double)i + 1.0) / (double)nproxy;
+            const double r = sqrt(fmax(1.0 - z * z, 0.0));
+            const double ph = (double)i * (M_PI * (3.0 - sqrt(5.0)));
+            u[0] = r * cos(ph); u[1] = r * sin(ph); u[2] = z;
+        }
+        const double R = rho * (double)W;
+        const double dx = R * u[0] - 0.5 * o[0], dy = R * u[1] - 0.5 * o[1], dz = R * u[2] - 0.5 * o[2];
+        const double r = spacing * sqrt(dx * dx + dy * dy + dz * dz);
+        tab[e] = dim == 2 ? weight * (-log(r) / (2.0 * M_PI)) : weight * (1.0 / (4.0 * M_PI * r));
+    }
+}
+
+// Thread-block clusters: the regions of the upper levels are few and large, so one region is
+// spread over the CTAs of a cluster (its columns, or its entries, split by rank) and the CTAs meet at
+// cluster barriers; values they exchange go through distributed shared memory.
+__device__ __forceinline__ unsigned cta_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cta_count() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+// all threads of every CTA of the cluster; release / acquire at cluster scope
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t dsmem(const void *p, unsigned rank) {
+    uint32_t a = (uint32_t)__cvta_generic_to_shared(p), out;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(a), "r"(rank));
+    return out;
+}
+__device__ __forceinline__ void dsmem_st(uint32_t addr, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ double dsmem_ld(uint32_t addr) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void dsmem_st_s32(uint32_t addr, int v) {
+    asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ int dsmem_ld_s32(uint32_t addr) {
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+constexpr int kMaxCluster = 8;
+
+// cluster-wide max / min of a CTA-uniform value: every CTA writes its value into slot[rank] of CTA
+// 0, one cluster barrier, then every CTA reads the CS slots.  A slot array may be written again
+// only after another cluster barrier has passed (the callers alternate arrays).
+__device__ double cluster_max(double v, double *slot, double *bc, unsigned cr, unsigned CS) {
+    if (threadIdx.x == 0) dsmem_st(dsmem(&slot[cr], 0), v);
+    cluster_sync_all();
+    if (threadIdx.x == 0) {
+        double t = dsmem_ld(dsmem(&slot[0], 0));
+        for (unsigned r = 1; r < CS; ++r) t = fmax(t, dsmem_ld(dsmem(&slot[r], 0)));
+        *bc = t;
+    }
+    __syncthreads();
+    return *bc;
+}
+__device__ int cluster_min(int v, int *slot, int *bc, unsigned cr, unsigned CS) {
+    if (threadIdx.x == 0) dsmem_st_s32(dsmem(&slot[cr], 0), v);
+    cluster_sync_all();
+    if (threadIdx.x == 0) {
+        int t = dsmem_ld_s32(dsmem(&slot[0], 0));
+        for (unsigned r = 1; r < CS; ++r) t = min(t, dsmem_ld_s32(dsmem(&slot[r], 0)));
+        *bc = t;
+    }
+    __syncthreads();
+    return *bc;
+}
+
+// KR1: one cluster of CS CTAs per region; CTA r owns the columns j = r (mod CS)
+__global__ void __launch_bounds__(kRsThreads) rs_id(IdArgs a, int first) {
+    extern __shared__ double smem[];
+    __shared__ double shd[32];
+    __shared__ int shi[32];
+    __shared__ double slot0[kMaxCluster], slotA[kMaxCluster], bcd;
+    __shared__ int slotB[kMaxCluster], bci;
+    const unsigned CS = cta_count(), cr = cta_rank();
+    const int bl = blockIdx.x / CS;  // region within this launch
+    const int b = first + bl;
+    const int nb = a.nb[b], rows = a.rows[b];
+    const int np = a.nproxy, mono = a.dim == 2 ? 1 : 0;
+    double *nu = smem;                  // nb (the own columns' entries are used)
+    double *nuref = nu + nb;            // nb: each column's squared norm when last computed exactly
+    double *q = nuref + nb;             // rows
+    double *dirs = q + rows;            // 3 * nproxy
+    int *skel = (int *)(dirs + 3 * np); // nb
+    int *red = skel + nb;               // nb
+    unsigned char *chosen = (unsigned char *)(red + nb);
+    double *Y = a.Y + a.y_off[bl];
+    double *C = a.C + a.c_off[bl];
+    const int *pts = a.dof_pt + a.dof_off[b];
+    const int *near = a.near_pt + a.near_off[b];
+    const int4 g = a.geom[b];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int nown = nb > (int)cr ? (nb - (int)cr + (int)CS - 1) / (int)CS : 0;  // own columns
+
+    // proxy directions: 2D angles 2 pi j / P; 3D the Fibonacci lattice
+    for (int j = tid; j < np; j += blockDim.x) {
+        if (a.dim == 2) {
+            const double t = 2.0 * M_PI * (double)j / (double)np;
+            dirs[3 * j] = cos(t); dirs[3 * j + 1] = sin(t); dirs[3 * j + 2] = 0.0;
+        } else {
+            const double z = 1.0 - (2.0 * (double)j + 1.0) / (double)np;
+            const double r = sqrt(fmax(1.0 - z * z, 0.0));
+            const double ph = (double)j * (M_PI * (3.0 - sqrt(5.0)));
+            dirs[3 * j] = r * cos(ph); dirs[3 * j + 1] = r * sin(ph); dirs[3 * j + 2] = z;
+        }
+    }
+    for (int j = tid; j < nb; j += blockDim.x) chosen[j] = 0;
+    __syncthreads();
+    const double R = a.rho * (double)g.w;
+    const double cx = 0.5 * g.x, cy = 0.5 * g.y, cz = 0.5 * g.z;
+    const long long total = (long long)rows * nown;
+    const double *tab = (a.ptab && a.ptab_off[b] >= 0) ? a.ptab + a.ptab_off[b] : nullptr;
+    const int side = 2 * g.w - 1;
+    const long long per = a.dim == 2 ? (long long)side * side : (long long)side * side * side;
+    for (long long e = tid; e < total; e += blockDim.x) {
+        const int j = (int)cr + (int)(e / rows) * (int)CS, i = (int)(e % rows);
+        double v;
+        if (i < np && tab) {
+            const float4 x = a.coord[pts[j]];
+            const int ox = 2 * (int)x.x - g.x + g.w - 1, oy = 2 * (int)x.y - g.y + g.w - 1;
+            long long f = (long long)ox * side + oy;
+            if (a.dim == 3) f = f * side + (2 * (int)x.z - g.z + g.w - 1);
+            v = tab[(long long)i * per + f];
+        } else if (i < np) {
+            const float4 x = a.coord[pts[j]];
+            const double dx = cx + R * dirs[3 * i] - (double)x.x, dy = cy + R * dirs[3 * i + 1] - (double)x.y,
+                         dz = cz + R * dirs[3 * i + 2] - (double)x.z;
+            const double r = a.spacing * sqrt(dx * dx + dy * dy + dz * dz);
+            v = a.dim == 2 ? a.weight * (-log(r) / (2.0 * M_PI)) : a.weight * (1.0 / (4.0 * M_PI * r));
+        } else if (i < np + mono) {
+            v = a.weight;
+        } else {
+            v = a_entry(a.coord, a.t64, a.n, near[i - np - mono], pts[j]);
+        }
+        Y[(long long)j * rows + i] = v;
+    }
+    __syncthreads();
+    for (int j = (int)cr + warp * (int)CS; j < nb; j += nwarps * (int)CS) {
+        const double *y = Y + (long long)j * rows;
+        double s = 0.0;
+        for (int i = lane; i < rows; i += 32) s += y[i] * y[i];
+        s = warp_allsum(s);
+        if (lane == 0) { nu[j] = s; nuref[j] = s; }
+    }
+    __syncthreads();
+    double lm = 0.0;
+    for (int j = (int)cr + tid * (int)CS; j < nb; j += (int)(blockDim.x * CS)) lm = fmax(lm, nu[j]);
+    const double nu0 = cluster_max(block_max(lm, shd), slot0, &bcd, cr, CS);
+    const int steps = min(rows, nb);
+    int k = 0;
+    if (nu0 > 0.0) {
+        for (int step = 0; step < steps; ++step) {
+            lm = -1.0;
+            for (int j = (int)cr + tid * (int)CS; j < nb; j += (int)(blockDim.x * CS))
+                if (!chosen[j]) lm = fmax(lm, nu[j]);
+            const double top = cluster_max(block_max(lm, shd), slotA, &bcd, cr, CS);
+            if (!(top > a.eps2 * nu0)) break;
+            const double window = fmin(0.5 * top, fmax(kTieRel * top, kTieAbs * nu0));
+            const double thr = top - window;
+            int li = INT_MAX;
+            for (int j = (int)cr + tid * (int)CS; j < nb; j += (int)(blockDim.x * CS))
+                if (!chosen[j] && nu[j] >= thr) { li = j; break; }
+            const int js = cluster_min(block_min(li, shi), slotB, &bci, cr, CS);
+            if (js >= nb) break;  // no candidate (only possible with NaN norms)
+            const unsigned owner = (unsigned)js % CS;
+            if (cr == owner) {
+                const double norm = sqrt(nu[js]);
+                const double *yp = Y + (long long)js * rows;
+                for (int i = tid; i < rows; i += blockDim.x) q[i] = yp[i] / norm;
+                if (tid == 0) C[(long long)step * nb + js] = norm;
+            }
+            if (tid == 0) {
+                chosen[js] = 1;
+                skel[step] = js;
+            }
+            cluster_sync_all();  // the pivot column q is in its owner's shared memory
+            if (cr != owner) {
+                const uint32_t qa = dsmem(q, owner);
+                for (int i = tid; i < rows; i += blockDim.x) q[i] = dsmem_ld(qa + 8u * (uint32_t)i);
+            }
+            __syncthreads();
+            for (int j = (int)cr + warp * (int)CS; j < nb; j += nwarps * (int)CS) {
+                if (chosen[j]) continue;
+                double *y = Y + (long long)j * rows;
+                double s = 0.0;
+                for (int i = lane; i < rows; i += 32) s += q[i] * y[i];
+                s = warp_allsum(s);
+                for (int i = lane; i < rows; i += 32) y[i] -= q[i] * s;
+                // downdated squared norm, recomputed from the column (each lane re-reads the entries
+                // it wrote) once it falls below 1e-2 of its last exact value: its error then stays
+                // below ~1e-12 relative and 1e-14 nu0, far inside the pivot window, so the pivots
+                // and the rank are those of recomputing every step
+                double nn = nu[j] - s * s;
+                if (nn < 1e-2 * nuref[j]) {
+                    double t = 0.0;
+                    for (int i = lane; i < rows; i += 32) t += y[i] * y[i];
+                    nn = warp_allsum(t);
+                    if (lane == 0) nuref[j] = nn;
+                }
+                if (lane == 0) { nu[j] = fmax(nn, 0.0); C[(long long)step * nb + j] = s; }
+            }
+            __syncthreads();
+            k = step + 1;
+        }
+    }
+    cluster_sync_all();  // every CTA's C entries visible to the whole cluster
+    int *perm = a.perm_out + a.dof_off[b];
+    if (tid == 0) {
+        int c = 0;
+        for (int j = 0; j < nb; ++j)
+            if (!chosen[j]) red[c++] = j;
+        if (cr == 0) {
+            a.k_out[b] = k;
+            for (int i = 0; i < k; ++i) perm[i] = skel[i];
+            for (int i = 0; i < c; ++i) perm[k + i] = red[i];
+        }
+    }
+    __syncthreads();
+    const int nr = nb - k;
+    double *T = a.T + a.t_off[b];
+    for (int ci = (int)cr * blockDim.x + tid; ci < nr; ci += (int)(blockDim.x * CS)) {
+        const int col = red[ci];
+        for (int i = k - 1; i >= 0; --i) {
+            double t = __ldcg(&C[(long long)i * nb + col]);
+            for (int l = i + 1; l < k; ++l) t -= __ldcg(&C[(long long)i * nb + skel[l]]) * T[(long long)l * nr + ci];
+            T[(long long)i * nr + ci] = t / __ldcg(&C[(long long)i * nb + skel[i]]);
+        }
+    }
+}
+
+struct ElimArgs {
+    int n;
+    const int *nb, *k;
+    const long long *dof_off;    // natural DOFs / permutation
+    const int *dof_pt, *perm;
+    const long long *child_off;  // per region: first child record (none at level 1)
+    const int *child_start;      // per child: first natural DOF
+    const int *child_k;
+    const unsigned long long *child_bss;  // per child: device address of its B_ss (k x k)
+    const long long *t_in;       // T of rs_id
+    const double *Tin;
+    const long long *e_off;      // workspace
+    double *E;
+    const long long *t_off, *b_off, *s_off;
+    double *Tout, *Bsr, *X, *Binv, *Bss;
+    const float4 *coord;
+    const double *t64;
+    int *info;
+};
+
+constexpr int kPanel = 32;  // panel width of the blocked Cholesky and triangular inverse
+
+__device__ __forceinline__ double ldw(const double *p, bool cg) { return cg ? __ldcg(p) : *p; }
+
+// KR2: one cluster of CS CTAs per region; every phase splits its entries over the cluster's
+// threads and ends at a cluster barrier.  With more than one CTA, workspace values that another
+// CTA wrote are read from L2 (ldw).
+__global__ void __launch_bounds__(kRsThreads) rs_elim(ElimArgs a, int first) {
+    __shared__ int sh_bad;
+    __shared__ double sh_blk[kPanel * kPanel];
+    const unsigned CS = cta_count(), cr = cta_rank();
+    const bool cg = CS > 1;  // values written by another CTA are read from L2
+    const int bl = blockIdx.x / CS;
+    const int b = first + bl;
+    const int nb = a.nb[b], k = a.k[b], nr = nb - k;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const long long g0 = (long long)cr * blockDim.x + tid, gs = (long long)CS * blockDim.x;
+    const int gw0 = (int)cr * nwarps + warp, gws = (int)CS * nwarps;  // cluster-wide warp index
+    const int *perm = a.perm + a.dof_off[b];
+    const int *pts = a.dof_pt + a.dof_off[b];
+    double *D = a.E + a.e_off[bl];                   // nb x nb, permuted order
+    double *M = D + (long long)nb * nb;              // nb x nr
+    double *B = M + (long long)nb * nr;              // nr x nr
+    const long long c0 = a.child_off[b], c1 = a.child_off[b + 1];
+    if (tid == 0) sh_bad = 0;
+    const long long tot = (long long)nb * nb;
+    for (long long e = g0; e < tot; e += gs) {
+        const int ra = (int)(e / nb), rb = (int)(e % nb);
+        const int ja = perm[ra], jb = perm[rb];
+        double v;
+        int ca = -1, cb = -1;
+        for (long long c = c0; c < c1; ++c) {
+            const int cs = a.child_start[c], ce = cs + a.child_k[c];
+            if (ja >= cs && ja < ce) ca = (int)c;
+            if (jb >= cs && jb < ce) cb = (int)c;
+        }
+        if (ca >= 0 && ca == cb) {
+            const double *S = reinterpret_cast<const double *>(a.child_bss[ca]);
+            const int kc = a.child_k[ca], cs = a.child_start[ca];
+            v = S[(long long)(ja - cs) * kc + (jb - cs)];
+        } else {
+            v = a_entry(a.coord, a.t64, a.n, pts[ja], pts[jb]);
+        }
+        D[e] = v;
+    }
+    cluster_sync_all();
+    const double *T = a.Tin + a.t_in[b];
+    // M_:r = D_:r - D_:s T
+    for (long long e = g0; e < (long long)nb * nr; e += gs) {
+        const int r = (int)(e / nr), i = (int)(e % nr);
+        double v = ldw(&D[(long long)r * nb + k + i], cg);
+        for (int l = 0; l < k; ++l) v -= ldw(&D[(long long)r * nb + l], cg) * T[(long long)l * nr + i];
+        M[e] = v;
+    }
+    cluster_sync_all();
+    // B_rr = M_rr - T^T M_sr;  B_sr = M_sr;  T and B_ss's D_ss part to their stores
+    for (long long e = g0; e < (long long)nr * nr; e += gs) {
+        const int i = (int)(e / nr), j = (int)(e % nr);
+        double v = ldw(&M[(long long)(k + i) * nr + j], cg);
+        for (int l = 0; l < k; ++l) v -= T[(long long)l * nr + i] * ldw(&M[(long long)l * nr + j], cg);
+        B[e] = v;
+    }
+    double *Bsr = a.Bsr + a.t_off[b], *Tout = a.Tout + a.t_off[b], *Bss = a.Bss + a.s_off[b];
+    for (long long e = g0; e < (long long)k * nr; e += gs) {
+        Bsr[e] = ldw(&M[e], cg);
+        Tout[e] = T[e];
+    }
+    for (long long e = g0; e < (long long)k * k; e += gs) {
+        const int l = (int)(e / k), m = (int)(e % k);
+        Bss[e] = ldw(&D[(long long)l * nb + m], cg);
+    }
+    cluster_sync_all();
+    // Cholesky B_rr = L L^T in place (lower triangle), right-looking in panels of kPanel columns:
+    // rank 0 factors the diagonal block in shared memory, the cluster solves the rows below it and
+    // updates the trailing lower triangle
+    for (int j0 = 0; j0 < nr; j0 += kPanel) {
+        const int jb = min(kPanel, nr - j0);
+        if (cr == 0) {
+            for (int e = tid; e < jb * jb; e += blockDim.x)
+                sh_blk[e] = ldw(&B[(long long)(j0 + e / jb) * nr + j0 + e % jb], cg);
+            __syncthreads();
+            for (int j = 0; j < jb; ++j) {
+                if (tid == 0) {
+                    const double d = sh_blk[j * jb + j];
+                    if (!(d > 0.0)) {
+                        if (!sh_bad) a.info[b] = j0 + j;
+                        sh_bad = 1;
+                    } else {
+                        sh_blk[j * jb + j] = sqrt(d);
+                    }
+                }
+                __syncthreads();
+                if (sh_bad) break;
+                for (int i = j + 1 + tid; i < jb; i += blockDim.x) sh_blk[i * jb + j] /= sh_blk[j * jb + j];
+                __syncthreads();
+                for (int e = tid; e < jb * jb; e += blockDim.x) {
+                    const int i = e / jb, c = e % jb;
+                    if (c > j && c <= i) sh_blk[e] -= sh_blk[i * jb + j] * sh_blk[c * jb + j];
+                }
+                __syncthreads();
+            }
+            for (int e = tid; e < jb * jb; e += blockDim.x)
+                if (e % jb <= e / jb) B[(long long)(j0 + e / jb) * nr + j0 + e % jb] = sh_blk[e];
+            if (tid == 0 && sh_bad)
+                for (unsigned r = 1; r < CS; ++r) dsmem_st_s32(dsmem(&sh_bad, r), 1);
+        }
+        cluster_sync_all();
+        if (sh_bad) return;
+        // panel: L[i][j0:j0+jb] = B[i][j0:j0+jb] L_dd^{-T} for i >= j0 + jb (one row per thread)
+        for (long long i = j0 + jb + g0; i < nr; i += gs) {
+            double *row = B + i * nr + j0;
+            for (int c = 0; c < jb; ++c) {
+                double t = ldw(&row[c], cg);
+                for (int l = 0; l < c; ++l) t -= row[l] * ldw(&B[(long long)(j0 + c) * nr + j0 + l], cg);
+                row[c] = t / ldw(&B[(long long)(j0 + c) * nr + j0 + c], cg);
+            }
+        }
+        cluster_sync_all();
+        // trailing update of the lower triangle: B[i][c] -= L[i][panel] . L[c][panel], j0+jb <= c <= i
+        const int t0 = j0 + jb;
+        for (int i = t0 + gw0; i < nr; i += gws) {
+            const double *li = B + (long long)i * nr + j0;
+            for (int c = t0 + lane; c <= i; c += 32) {
+                const double *lc = B + (long long)c * nr + j0;
+                double t = 0.0;
+                for (int l = 0; l < jb; ++l) t += ldw(&li[l], cg) * ldw(&lc[l], cg);
+                B[(long long)i * nr + c] = ldw(&B[(long long)i * nr + c], cg) - t;
+            }
+        }
+        cluster_sync_all();
+    }
+    // L^{-1} (lower) into D's storage by blocks of kPanel rows: first every row's products with the
+    // rows already solved (one entry per thread), then the forward substitution inside the block
+    // (one column per thread)
+    double *Li = D;
+    for (int i0 = 0; i0 < nr; i0 += kPanel) {
+        const int ib = min(kPanel, nr - i0);
+        for (long long e = g0; e < (long long)ib * (i0 + ib); e += gs) {
+            const int i = i0 + (int)(e / (i0 + ib)), c = (int)(e % (i0 + ib));
+            if (c > i) continue;
+            double t = (i == c) ? 1.0 : 0.0;
+            for (int l = c; l < i0; ++l) t -= ldw(&B[(long long)i * nr + l], cg) * ldw(&Li[(long long)l * nr + c], cg);
+            Li[(long long)i * nr + c] = t;
+        }
+        cluster_sync_all();
+        for (long long c = g0; c < i0 + ib; c += gs) {
+            for (int i = max(i0, (int)c); i < i0 + ib; ++i) {
+                double t = ldw(&Li[(long long)i * nr + c], cg);
+                for (int l = max(i0, (int)c); l < i; ++l) t -= ldw(&B[(long long)i * nr + l], cg) * Li[(long long)l * nr + c];
+                Li[(long long)i * nr + c] = t / ldw(&B[(long long)i * nr + i], cg);
+            }
+        }
+        cluster_sync_all();
+    }
+    // B_rr^{-1} = L^{-T} L^{-1}
+    double *Bi = a.Binv + a.b_off[b];
+    for (long long e = g0; e < (long long)nr * nr; e += gs) {
+        const int i = (int)(e / nr), j = (int)(e % nr);
+        double v = 0.0;
+        for (int l = max(i, j); l < nr; ++l) v += ldw(&Li[(long long)l * nr + i], cg) * ldw(&Li[(long long)l * nr + j], cg);
+        Bi[e] = v;
+    }
+    cluster_sync_all();
+    // X = B_rr^{-1} B_rs  (nr x k)
+    double *X = a.X + a.t_off[b];
+    for (long long e = g0; e < (long long)nr * k; e += gs) {
+        const int i = (int)(e / k), l = (int)(e % k);
+        double v = 0.0;
+        for (int j = 0; j < nr; ++j) v += ldw(&Bi[(long long)i * nr + j], cg) * ldw(&Bsr[(long long)l * nr + j], cg);
+        X[e] = v;
+    }
+    cluster_sync_all();
+    // B_ss = D_ss - B_sr X
+    for (long long e = g0; e < (long long)k * k; e += gs) {
+        const int l = (int)(e / k), m = (int)(e % k);
+        double v = ldw(&Bss[e], cg);
+        for (int i = 0; i < nr; ++i) v -= ldw(&Bsr[(long long)l * nr + i], cg) * ldw(&X[(long long)i * k + m], cg);
+        Bss[e] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Apply kernels
+// ---------------------------------------------------------------------------------------------
+__global__ void rs_gather(const double *__restrict__ r, long long ldr, const int *__restrict__ pos2pt,
+                          long long ntot, double *__restrict__ y) {
+    const int c = blockIdx.y;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ntot; i += (long long)gridDim.x * blockDim.x)
+        y[(long long)c * ntot + i] = r[(long long)c * ldr + pos2pt[i]];
+}
+
+struct LevelArgs {
+    const int *nb, *k;
+    const long long *pos_off;  // per region: first position (skeletons first, then redundant)
+    const int *pos;
+    const long long *t_off, *b_off;
+    const double *T, *Bsr, *X, *Binv;
+};
+
+__global__ void __launch_bounds__(kRsThreads) rs_down(LevelArgs a, double *__restrict__ y, long long ntot) {
+    extern __shared__ double sm[];
+    const int b = blockIdx.x;
+    const int nb = a.nb[b], k = a.k[b], nr = nb - k;
+    if (nr == 0) return;
+    double *yv = y + (long long)blockIdx.y * ntot;
+    const int *pos = a.pos + a.pos_off[b];
+    const double *T = a.T + a.t_off[b], *Bsr = a.Bsr + a.t_off[b], *Bi = a.Binv + a.b_off[b];
+    double *ys = sm, *u = ys + k, *v = u + nr;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int l = tid; l < k; l += blockDim.x) ys[l] = yv[pos[l]];
+    __syncthreads();
+    for (int i = tid; i < nr; i += blockDim.x) {
+        double t = yv[pos[k + i]];
+        for (int l = 0; l < k; ++l) t -= T[(long long)l * nr + i] * ys[l];
+        u[i] = t;
+    }
+    __syncthreads();
+    for (int i = warp; i < nr; i += nwarps) {
+        const double *row = Bi + (long long)i * nr;
+        double t = 0.0;
+        for (int j = lane; j < nr; j += 32) t += row[j] * u[j];
+        t = warp_allsum(t);
+        if (lane == 0) v[i] = t;
+    }
+    __syncthreads();
+    for (int l = warp; l < k; l += nwarps) {
+        const double *row = Bsr + (long long)l * nr;
+        double t = 0.0;
+        for (int j = lane; j < nr; j += 32) t += row[j] * v[j];
+        t = warp_allsum(t);
+        if (lane == 0) yv[pos[l]] = ys[l] - t;
+    }
+    for (int i = tid; i < nr; i += blockDim.x) yv[pos[k + i]] = v[i];
+}
+
+__global__ void __launch_bounds__(kRsThreads) rs_up(LevelArgs a, double *__restrict__ y, long long ntot) {
+    extern __shared__ double sm[];
+    const int b = blockIdx.x;
+    const int nb = a.nb[b], k = a.k[b], nr = nb - k;
+    if (nr == 0) return;
+    double *yv = y + (long long)blockIdx.y * ntot;
+    const int *pos = a.pos + a.pos_off[b];
+    const double *T = a.T + a.t_off[b], *X = a.X + a.t_off[b];
+    double *as = sm, *ar = as + k;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int l = tid; l < k; l += blockDim.x) as[l] = yv[pos[l]];
+    __syncthreads();
+    for (int i = tid; i < nr; i += blockDim.x) {
+        double t = yv[pos[k + i]];
+        const double *row = X + (long long)i * k;
+        for (int l = 0; l < k; ++l) t -= row[l] * as[l];
+        ar[i] = t;
+        yv[pos[k + i]] = t;
+    }
+    __syncthreads();
+    for (int l = warp; l < k; l += nwarps) {
+        const double *row = T + (long long)l * nr;
+        double t = 0.0;
+        for (int j = lane; j < nr; j += 32) t += row[j] * ar[j];
+        t = warp_allsum(t);
+        if (lane == 0) yv[pos[l]] = as[l] - t;
+    }
+}
+
+// y_t = S^{-1} y_t for every colour's last level: CTA (item) = kRsTopRows rows of one colour
+__global__ void __launch_bounds__(kRsThreads) rs_top(const int2 *__restrict__ items, const int *__restrict__ nt,
+                                                     const long long *__restrict__ pos_off, const int *__restrict__ pos,
+                                                     const long long *__restrict__ b_off, const double *__restrict__ Sinv,
+                                                     const double *__restrict__ y, long long ntot,
+                                                     double *__restrict__ tmp, long long ttot) {
+    extern __shared__ double sm[];
+    const int2 it = items[blockIdx.x];
+    const int c = it.x, r0 = it.y, S = nt[c];
+    const double *yv = y + (long long)blockIdx.y * ntot;
+    const int *ps = pos + pos_off[c];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int j = tid; j < S; j += blockDim.x) sm[j] = yv[ps[j]];
+    __syncthreads();
+    const double *Si = Sinv + b_off[c];
+    double *out = tmp + (long long)blockIdx.y * ttot + pos_off[c];
+    const int r1 = min(r0 + kRsTopRows, S);
+    for (int i = r0 + warp; i < r1; i += nwarps) {
+        const double *row = Si + (long long)i * S;
+        double t = 0.0;
+        for (int j = lane; j < S; j += 32) t += row[j] * sm[j];
+        t = warp_allsum(t);
+        if (lane == 0) out[i] = t;
+    }
+}
+
+__global__ void rs_top_put(const int *__restrict__ pos, long long ttot, const double *__restrict__ tmp,
+                           double *__restrict__ y, long long ntot) {
+    const int c = blockIdx.y;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ttot; i += (long long)gridDim.x * blockDim.x)
+        y[(long long)c * ntot + pos[i]] = tmp[(long long)c * ttot + i];
+}
+
+__global__ void rs_scatter(const double *__restrict__ y, long long ntot, const long long *__restrict__ inv_ptr,
+                           const int *__restrict__ inv_pos, double *__restrict__ z, long long ldz, long long N) {
+    const int c = blockIdx.y;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        double t = 0.0;
+        for (long long q = inv_ptr[i]; q < inv_ptr[i + 1]; ++q) t += y[(long long)c * ntot + inv_pos[q]];
+        z[(long long)c * ldz + i] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------------------
+// device copy of a host vector from the stream-ordered pool (the copy from pageable memory has
+// left the host buffer when the call returns)
+template <class T> int to_dev(T **d, const std::vector<T> &h, cudaStream_t s) {
+    *d = nullptr;
+    IE_TRY_CUDA(cudaMallocAsync((void **)d, sizeof(T) * std::max<size_t>(h.size(), 1), s));
+    if (!h.empty()) IE_TRY_CUDA(cudaMemcpyAsync(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s));
+    return IE_OK;
+}
+template <class T> void dfree(T *p, cudaStream_t s) {
+    if (p) cudaFreeAsync((void *)p, s);
+}
+
+struct Region {
+    int colour = 0;
+    std::array<int, 3> K{{0, 0, 0}}, lo{{0, 0, 0}}, hi{{1, 1, 1}};
+    std::vector<int> nat;          // positions of the DOFs, natural order
+    std::vector<int> child;        // indices of the children in the previous level
+    std::vector<int> child_start;  // first natural DOF of each child
+};
+
+}  // namespace
+
+// One compression level (or the top: k = 0) as the apply reads it.
+struct RSLevel {
+    int nreg = 0, max_nb = 0, max_k = 0;
+    std::vector<int> colour, nb, k;
+    std::vector<long long> pos_off;  // nreg + 1
+    std::vector<int> pos;            // skeletons first (pivot order), then redundant
+    int *d_nb = nullptr, *d_k = nullptr, *d_pos = nullptr;
+    long long *d_pos_off = nullptr, *d_t_off = nullptr, *d_b_off = nullptr;
+    double *d_T = nullptr, *d_Bsr = nullptr, *d_X = nullptr, *d_Binv = nullptr;
+    void release() {
+        cudaFree(d_nb); cudaFree(d_k); cudaFree(d_pos); cudaFree(d_pos_off); cudaFree(d_t_off);
+        cudaFree(d_b_off); cudaFree(d_T); cudaFree(d_Bsr); cudaFree(d_X); cudaFree(d_Binv);
+    }
+};
+
+struct RSFactor {
+    int dim = 0, ncol = 0, nproxy = 0;
+    double eps = 0, rho = 0;
+    long long ntot = 0;
+    std::vector<int> pos2pt;
+    int *d_pos2pt = nullptr;
+    long long *d_inv_ptr = nullptr;
+    int *d_inv_pos = nullptr;
+    std::vector<RSLevel> levels;
+    std::vector<int> colour_levels;  // compression levels of each colour
+    RSLevel top;                     // one region per colour, k = 0, Binv = S^{-1}
+    int nitems = 0;
+    int2 *d_items = nullptr;         // rs_top work items (colour, first row)
+    // algorithmic FP64 flops of the IDs (initial norms, a dot product and an update of every
+    // remaining column per Gram-Schmidt step, back substitution) and of the
+    // eliminations (M, B_rr, Cholesky, triangular inverse, L^-T L^-1, X, B_ss), and the summed
+    // device time of their launches (CUDA events on the factor's stream)
+    double id_flops = 0, elim_flops = 0, id_ms = 0, elim_ms = 0;
+    ~RSFactor() {
+        cudaFree(d_pos2pt); cudaFree(d_inv_ptr); cudaFree(d_inv_pos); cudaFree(d_items);
+        for (auto &l : levels) l.release();
+        top.release();
+    }
+};
+
+void rs_destroy(RSFactor *rs) { delete rs; }
+
+namespace {
+
+// CUDA-event time of the launches between start() and stop() on one stream, accumulated
+struct LaunchTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    LaunchTimer() { cudaEventCreate(&a); cudaEventCreate(&b); }
+    ~LaunchTimer() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    void start(cudaStream_t s) { cudaEventRecord(a, s); }
+    // after the stream was synchronized
+    void stop_add(cudaStream_t s, double &ms) {
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, a, b) == cudaSuccess) ms += t;
+    }
+};
+
+// CTAs per region: one at the wide levels, up to kMaxCluster when a level has too few regions to
+// give every SM two CTAs
+int cluster_size_for(int nreg, int sms) {
+    int cs = 1;
+    while (cs < kMaxCluster && (long long)nreg * cs < 2LL * sms) cs *= 2;
+    return cs;
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_clustered(void (*kern)(KArgs...), int nclusters, int cs, size_t smem, cudaStream_t s,
+                             Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nclusters * cs));
+    cfg.blockDim = dim3(kRsThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// consecutive runs of regions whose workspace (doubles) stays under the cap
+std::vector<std::pair<int, int>> chunks_by(const std::vector<long long> &cost) {
+    std::vector<std::pair<int, int>> out;
+    const long long cap = (long long)(kRsWorkCap / sizeof(double));
+    int s = 0;
+    long long acc = 0;
+    for (int i = 0; i < (int)cost.size(); ++i) {
+        if (i > s && acc + cost[(size_t)i] > cap) {
+            out.push_back({s, i});
+            s = i;
+            acc = 0;
+        }
+        acc += cost[(size_t)i];
+    }
+    if ((int)cost.size() > s) out.push_back({s, (int)cost.size()});
+    return out;
+}
+
+// The elimination (KR2) of `regs` (level 1 when prev == nullptr), whose ranks and permutations are
+// known; fills lvl's stores and, per region, the device address of its B_ss.
+int run_elim(const ie_problem *p, const std::vector<Region> &regs, const std::vector<int> &perm_h,
+             const std::vector<long long> &nat_off, int *d_nat_pt, int *d_perm, const std::vector<int> &kv,
+             const std::vector<unsigned long long> &prev_bss, const std::vector<int> &prev_k, const double *d_Tin,
+             const std::vector<long long> &t_in, RSLevel &lvl, double **d_bss, std::vector<unsigned long long> &bss_addr,
+             cudaStream_t s, std::string &err, double &ms, double &flops) {
+    (void)perm_h;
+    const int nreg = (int)regs.size();
+    std::vector<long long> t_off((size_t)nreg + 1, 0), b_off((size_t)nreg + 1, 0), s_off((size_t)nreg + 1, 0);
+    std::vector<long long> child_off((size_t)nreg + 1, 0);
+    std::vector<int> child_start, child_k;
+    std::vector<unsigned long long> child_bss;
+    for (int b = 0; b < nreg; ++b) {
+        const long long nb = (long long)regs[(size_t)b].nat.size(), k = kv[(size_t)b], nr = nb - k;
+        t_off[(size_t)b + 1] = t_off[(size_t)b] + k * nr;
+        b_off[(size_t)b + 1] = b_off[(size_t)b] + nr * nr;
+        s_off[(size_t)b + 1] = s_off[(size_t)b] + k * k;
+        for (size_t c = 0; c < regs[(size_t)b].child.size(); ++c) {
+            const int ch = regs[(size_t)b].child[c];
+            child_start.push_back(regs[(size_t)b].child_start[c]);
+            child_k.push_back(prev_k[(size_t)ch]);
+            child_bss.push_back(prev_bss[(size_t)ch]);
+        }
+        child_off[(size_t)b + 1] = (long long)child_start.size();
+    }
+    std::vector<int> nbv((size_t)nreg);
+    for (int b = 0; b < nreg; ++b) nbv[(size_t)b] = (int)regs[(size_t)b].nat.size();
+    IE_TRY_CUDA(cudaMallocAsync((void **)&lvl.d_T, sizeof(double) * std::max<long long>(t_off.back(), 1), s));
+    IE_TRY_CUDA(cudaMallocAsync((void **)&lvl.d_Bsr, sizeof(double) * std::max<long long>(t_off.back(), 1), s));
+    IE_TRY_CUDA(cudaMallocAsync((void **)&lvl.d_X, sizeof(double) * std::max<long long>(t_off.back(), 1), s));
+    IE_TRY_CUDA(cudaMallocAsync((void **)&lvl.d_Binv, sizeof(double) * std::max<long long>(b_off.back(), 1), s));
+    IE_TRY_CUDA(cudaMallocAsync((void **)d_bss, sizeof(double) * std::max<long long>(s_off.back(), 1), s));
+    IE_TRY(to_dev(&lvl.d_t_off, t_off, s));
+    IE_TRY(to_dev(&lvl.d_b_off, b_off, s));
+    int *d_nb = nullptr, *d_k = nullptr, *d_cstart = nullptr, *d_ck = nullptr, *d_info = nullptr;
+    long long *d_noff = nullptr, *d_coff = nullptr, *d_soff = nullptr, *d_tin = nullptr, *d_eoff = nullptr;
+    unsigned long long *d_cbss = nullptr;
+    double *d_E = nullptr;
+    int st = IE_OK;
+    auto cleanup = [&]() {
+        dfree(d_nb, s); dfree(d_k, s); dfree(d_cstart, s); dfree(d_ck, s); dfree(d_info, s); dfree(d_noff, s);
+        dfree(d_coff, s); dfree(d_soff, s); dfree(d_tin, s); dfree(d_eoff, s); dfree(d_cbss, s); dfree(d_E, s);
+    };
+    std::vector<int> info_h((size_t)nreg, -1);
+    do {
+        if ((st = to_dev(&d_nb, nbv, s)) != IE_OK) break;
+        if ((st = to_dev(&d_k, kv, s)) != IE_OK) break;
+        if ((st = to_dev(&d_cstart, child_start, s)) != IE_OK) break;
+        if ((st = to_dev(&d_ck, child_k, s)) != IE_OK) break;
+        if ((st = to_dev(&d_cbss, child_bss, s)) != IE_OK) break;
+        if ((st = to_dev(&d_info, info_h, s)) != IE_OK) break;
+        if ((st = to_dev(&d_noff, nat_off, s)) != IE_OK) break;
+        if ((st = to_dev(&d_coff, child_off, s)) != IE_OK) break;
+        if ((st = to_dev(&d_soff, s_off, s)) != IE_OK) break;
+        if ((st = to_dev(&d_tin, t_in, s)) != IE_OK) break;
+        std::vector<long long> cost((size_t)nreg);
+        for (int b = 0; b < nreg; ++b) {
+            const long long nb = nbv[(size_t)b], nr = nb - kv[(size_t)b];
+            cost[(size_t)b] = nb * nb + nb * nr + nr * nr;
+            const double kd = kv[(size_t)b], nbd = (double)nb, nrd = (double)nr;
+            flops += 2.0 * nbd * nrd * kd + 2.0 * nrd * nrd * kd + nrd * nrd * nrd + 2.0 * nrd * nrd * kd +
+                     2.0 * kd * kd * nrd;
+        }
+        for (auto ch : chunks_by(cost)) {
+            std::vector<long long> e_off;
+            long long acc = 0;
+            for (int b = ch.first; b < ch.second; ++b) { e_off.push_back(acc); acc += cost[(size_t)b]; }
+            dfree(d_eoff, s); d_eoff = nullptr;
+            dfree(d_E, s); d_E = nullptr;
+            if ((st = to_dev(&d_eoff, e_off, s)) != IE_OK) break;
+            cudaError_t e = cudaMallocAsync((void **)&d_E, sizeof(double) * std::max<long long>(acc, 1), s);
+            if (e != cudaSuccess) { err = "dd_factor_rs: workspace allocation failed"; st = IE_ERR_OOM; break; }
+            ElimArgs A{p->n, d_nb, d_k, d_noff, d_nat_pt, d_perm, d_coff, d_cstart, d_ck, d_cbss, d_tin, d_Tin, d_eoff, d_E,
+                       lvl.d_t_off, lvl.d_b_off, d_soff, lvl.d_T, lvl.d_Bsr, lvl.d_X, lvl.d_Binv, *d_bss, p->d_coord,
+                       p->d_table64, d_info};
+            LaunchTimer tm;
+            tm.start(s);
+            e = launch_clustered(rs_elim, ch.second - ch.first, cluster_size_for(ch.second - ch.first, p->sm_count), 0,
+                                 s, A, ch.first);
+            if (!ie_capturing()) ie_count_launches(1);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e == cudaSuccess) tm.stop_add(s, ms);
+            if (e != cudaSuccess) { err = std::string("dd_factor_rs: ") + cudaGetErrorString(e); st = IE_ERR_CUDA; break; }
+        }
+        if (st != IE_OK) break;
+        if (cudaMemcpyAsync(info_h.data(), d_info, sizeof(int) * nreg, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            err = "dd_factor_rs: info copy failed"; st = IE_ERR_CUDA; break;
+        }
+        for (int b = 0; b < nreg; ++b)
+            if (info_h[(size_t)b] >= 0) {
+                err = "dd_factor_rs: region " + std::to_string(b) + " (colour " + std::to_string(regs[(size_t)b].colour) +
+                      "): B_rr has a non-positive pivot at " + std::to_string(info_h[(size_t)b]);
+                st = IE_ERR_NOT_SPD;
+                break;
+            }
+    } while (0);
+    cleanup();
+    if (st != IE_OK) return st;
+    bss_addr.resize((size_t)nreg);
+    for (int b = 0; b < nreg; ++b) bss_addr[(size_t)b] = (unsigned long long)(*d_bss + s_off[(size_t)b]);
+    return IE_OK;
+}
+
+}  // namespace
+
+extern "C" int dd_factor_rs(const ie_problem *p, const dd_partition_t *s, const rs_opts *opts, dd_factor_t **out,
+                            void *stream) {
+    if (!out) { ie_set_error("dd_factor_rs: out is NULL"); return IE_ERR_ARG; }
+    *out = nullptr;
+    if (!p || !s) { ie_set_error("dd_factor_rs: NULL problem or partition"); return IE_ERR_ARG; }
+    if (s->prob != p) { ie_set_error("dd_factor_rs: partition belongs to another problem"); return IE_ERR_ARG; }
+    if (s->kind != DD_CBD) { ie_set_error("dd_factor_rs: the partition must be DD_CBD"); return IE_ERR_ARG; }
+    const int dim = p->dim, n = p->n, m = s->m, delta = s->delta, w = n / m;
+    if (2 * delta > w) {
+        ie_set_error("dd_factor_rs: the regions of a colour overlap (needs 2 delta <= n / m)");
+        return IE_ERR_ARG;
+    }
+    double eps = opts ? opts->eps : 0.0, rho = opts ? opts->rho : 0.0;
+    int nproxy = opts ? opts->nproxy : 0;
+    if (eps == 0.0) eps = 1e-3;
+    if (rho == 0.0) rho = 1.5;
+    if (nproxy == 0) nproxy = dim == 2 ? 64 : 256;
+    if (!(eps > 0.0 && eps < 1.0) || !(rho > 0.5 * std::sqrt((double)dim)) || nproxy < 4 || nproxy > 4096) {
+        ie_set_error("dd_factor_rs: need 0 < eps < 1, rho > sqrt(dim)/2 (the proxy surface encloses its box), "
+                     "4 <= nproxy <= 4096");
+        return IE_ERR_ARG;
+    }
+    DeviceGuard guard(p->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    RSFactor *rs = new (std::nothrow) RSFactor();
+    if (!rs) { ie_set_error("dd_factor_rs: out of host memory"); return IE_ERR_OOM; }
+    rs->dim = dim; rs->ncol = 1 << dim; rs->eps = eps; rs->rho = rho; rs->nproxy = nproxy;
+    std::string err;
+    auto fail = [&](int code) {
+        delete rs;
+        ie_set_error(err.empty() ? "dd_factor_rs: " + std::string(ie_last_error()) : err);
+        return code;
+    };
+
+    // level-1 regions: the extended boxes of each colour, row-major by K = k / 2
+    const int ncol = rs->ncol;
+    std::vector<std::vector<Region>> cur((size_t)ncol);
+    std::vector<int> G((size_t)ncol * 3, 1);
+    for (int c = 0; c < ncol; ++c) {
+        int cd[3] = {0, 0, 0}, Gd[3] = {1, 1, 1};
+        for (int d = 0; d < dim; ++d) {
+            cd[d] = (c >> (dim - 1 - d)) & 1;
+            Gd[d] = (m - cd[d] + 1) / 2;
+        }
+        for (int K0 = 0; K0 < Gd[0]; ++K0)
+            for (int K1 = 0; K1 < Gd[1]; ++K1)
+                for (int K2 = 0; K2 < (dim == 3 ? Gd[2] : 1); ++K2) {
+                    Region r;
+                    r.colour = c;
+                    const int Ks[3] = {K0, K1, K2};
+                    for (int d = 0; d < dim; ++d) {
+                        const int kk = 2 * Ks[d] + cd[d];
+                        r.K[(size_t)d] = Ks[d];
+                        r.lo[(size_t)d] = std::max(kk * w - delta, 0);
+                        r.hi[(size_t)d] = std::min((kk + 1) * w + delta, n);
+                    }
+                    for (int i = r.lo[0]; i < r.hi[0]; ++i)
+                        for (int j = r.lo[1]; j < r.hi[1]; ++j)
+                            for (int l = r.lo[2]; l < r.hi[2]; ++l) {
+                                const int pt = dim == 2 ? i * n + j : (i * n + j) * n + l;
+                                r.nat.push_back((int)rs->pos2pt.size());
+                                rs->pos2pt.push_back(pt);
+                            }
+                    cur[(size_t)c].push_back(std::move(r));
+                }
+    }
+    rs->ntot = (long long)rs->pos2pt.size();
+    rs->colour_levels.assign((size_t)ncol, 0);
+    std::vector<int> lat((size_t)rs->ntot * 3, 0);  // lattice coordinates of every position
+    for (long long q = 0; q < rs->ntot; ++q) {
+        int pt = rs->pos2pt[(size_t)q];
+        for (int d = dim - 1; d >= 0; --d) { lat[(size_t)q * 3 + d] = pt % n; pt /= n; }
+    }
+    if (to_dev(&rs->d_pos2pt, rs->pos2pt, st) != IE_OK) return fail(IE_ERR_CUDA);
+
+    // previous level's ranks and B_ss addresses, per colour (indices into that colour's list)
+    std::vector<std::vector<int>> prev_k((size_t)ncol);
+    std::vector<std::vector<unsigned long long>> prev_bss((size_t)ncol);
+    std::vector<double *> bss_bufs;
+    auto free_bss = [&]() { for (double *b : bss_bufs) dfree(b, st); bss_bufs.clear(); };
+    const int mono = dim == 2 ? 1 : 0;
+    int status = IE_OK;
+
+    for (int level = 0; status == IE_OK; ++level) {
+        // regions of this level: every colour with more than one region left
+        std::vector<Region> regs;
+        std::vector<int> reg_col_index;
+        for (int c = 0; c < ncol; ++c) {
+            if (cur[(size_t)c].size() <= 1) continue;
+            for (size_t i = 0; i < cur[(size_t)c].size(); ++i) {
+                regs.push_back(cur[(size_t)c][i]);
+                reg_col_index.push_back((int)i);
+            }
+        }
+        if (regs.empty()) break;
+        const int nreg = (int)regs.size();
+        // near fields: DOFs of the other regions of the colour strictly inside the proxy surface,
+        // decided in lattice units: |2 x - (lo + hi - 1)|^2 < (2 rho W)^2
+        std::vector<long long> nat_off((size_t)nreg + 1, 0), near_off((size_t)nreg + 1, 0);
+        std::vector<int> nat_pt, near_pt, rows((size_t)nreg), nbv((size_t)nreg);
+        std::vector<int4> geom((size_t)nreg);
+        // per colour: the extent of the regions along each axis as a function of that axis's
+        // colour-grid coordinate (true for the boxes and for every merged level), and K -> region
+        struct Axes {
+            int G[3] = {1, 1, 1};
+            std::vector<int> lo[3], hi[3], at;
+        };
+        std::vector<Axes> axes((size_t)ncol);
+        for (int c = 0; c < ncol; ++c) {
+            if (cur[(size_t)c].size() <= 1) continue;
+            Axes &A = axes[(size_t)c];
+            for (const Region &r : cur[(size_t)c])
+                for (int d = 0; d < 3; ++d) A.G[d] = std::max(A.G[d], r.K[(size_t)d] + 1);
+            for (int d = 0; d < 3; ++d) { A.lo[d].assign((size_t)A.G[d], 0); A.hi[d].assign((size_t)A.G[d], 0); }
+            A.at.assign((size_t)A.G[0] * A.G[1] * A.G[2], -1);
+            for (size_t i = 0; i < cur[(size_t)c].size(); ++i) {
+                const Region &r = cur[(size_t)c][i];
+                for (int d = 0; d < 3; ++d) {
+                    A.lo[d][(size_t)r.K[(size_t)d]] = r.lo[(size_t)d];
+                    A.hi[d][(size_t)r.K[(size_t)d]] = r.hi[(size_t)d];
+                }
+                A.at[((size_t)r.K[0] * A.G[1] + r.K[1]) * A.G[2] + r.K[2]] = (int)i;
+            }
+        }
+        for (int b = 0; b < nreg; ++b) {
+            const Region &r = regs[(size_t)b];
+            int W = 0, tc[3] = {0, 0, 0};
+            for (int d = 0; d < dim; ++d) {
+                W = std::max(W, r.hi[(size_t)d] - r.lo[(size_t)d]);
+                tc[d] = r.lo[(size_t)d] + r.hi[(size_t)d] - 1;
+            }
+            geom[(size_t)b] = make_int4(tc[0], tc[1], tc[2], W);
+            for (int pos : r.nat) nat_pt.push_back(rs->pos2pt[(size_t)pos]);
+            nat_off[(size_t)b + 1] = (long long)nat_pt.size();
+            nbv[(size_t)b] = (int)r.nat.size();
+        }
+        // the near fields of the regions are independent: host threads take contiguous ranges
+        std::vector<std::vector<int>> nears((size_t)nreg);
+        auto near_range = [&](int b0, int b1) {
+            for (int b = b0; b < b1; ++b) {
+                const Region &r = regs[(size_t)b];
+                const int4 gm = geom[(size_t)b];
+                const int W = gm.w, tc[3] = {gm.x, gm.y, gm.z};
+                const double bound = (2.0 * rho * W) * (2.0 * rho * W);
+                const double R = rho * W;  // bounding-box tests first (lattice units)
+                const Axes &A = axes[(size_t)r.colour];
+                std::vector<int> cand[3];
+                std::vector<double> gap2[3];
+                for (int d = 0; d < 3; ++d) {
+                    for (int K = 0; K < A.G[d]; ++K) {
+                        double g = 0.0;
+                        if (d < dim) {
+                            const double c = 0.5 * tc[d];
+                            g = std::max({(double)A.lo[d][(size_t)K] - c, 0.0, c - (double)(A.hi[d][(size_t)K] - 1)});
+                        }
+                        if (g < R) { cand[d].push_back(K); gap2[d].push_back(g * g); }
+                    }
+                }
+                std::vector<int> &out = nears[(size_t)b];
+                for (size_t i0 = 0; i0 < cand[0].size(); ++i0)
+                    for (size_t i1 = 0; i1 < cand[1].size(); ++i1)
+                        for (size_t i2 = 0; i2 < cand[2].size(); ++i2) {
+                            if (gap2[0][i0] + gap2[1][i1] + gap2[2][i2] >= R * R) continue;
+                            const int oi = A.at[((size_t)cand[0][i0] * A.G[1] + cand[1][i1]) * A.G[2] + cand[2][i2]];
+                            if (oi < 0 || oi == reg_col_index[(size_t)b]) continue;
+                            const Region &o = cur[(size_t)r.colour][(size_t)oi];
+                            for (int pos : o.nat) {
+                                double d2 = 0.0;
+                                for (int d = 0; d < dim; ++d) {
+                                    const double t = 2.0 * lat[(size_t)pos * 3 + d] - tc[d];
+                                    d2 += t * t;
+                                }
+                                if (d2 < bound) out.push_back(rs->pos2pt[(size_t)pos]);
+                            }
+                        }
+            }
+        };
+        {
+            const int nth = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), nreg / 64));
+            std::vector<std::thread> pool;
+            for (int t = 1; t < nth; ++t)
+                pool.emplace_back(near_range, (int)((long long)nreg * t / nth), (int)((long long)nreg * (t + 1) / nth));
+            near_range(0, (int)((long long)nreg / nth));
+            for (auto &th : pool) th.join();
+        }
+        for (int b = 0; b < nreg; ++b) {
+            near_pt.insert(near_pt.end(), nears[(size_t)b].begin(), nears[(size_t)b].end());
+            near_off[(size_t)b + 1] = (long long)near_pt.size();
+            rows[(size_t)b] = nproxy + mono + (int)nears[(size_t)b].size();
+            if (nbv[(size_t)b] > kRsMaxDofs || rows[(size_t)b] > kRsMaxRows) {
+                err = "dd_factor_rs: a region has " + std::to_string(nbv[(size_t)b]) + " DOFs and " +
+                      std::to_string(rows[(size_t)b]) + " ID rows (limits " + std::to_string(kRsMaxDofs) + ", " +
+                      std::to_string(kRsMaxRows) + ")";
+                status = IE_ERR_ARG;
+                break;
+            }
+        }
+        if (status != IE_OK) break;
+        // level 1: the proxy rows from one table per distinct longest side W (the boxes share a few)
+        double *d_ptab = nullptr;
+        long long *d_ptaboff = nullptr;
+        if (level == 0) {
+            std::map<int, long long> tab_of;
+            long long tab_len = 0;
+            std::vector<long long> ptab_off((size_t)nreg, -1);
+            for (int b = 0; b < nreg; ++b) {
+                const int W = geom[(size_t)b].w;
+                if (!tab_of.count(W)) {
+                    const long long side = 2 * W - 1;
+                    tab_of[W] = tab_len;
+                    tab_len += (dim == 2 ? side * side : side * side * side) * nproxy;
+                }
+                ptab_off[(size_t)b] = tab_of[W];
+            }
+            if (cudaMallocAsync((void **)&d_ptab, sizeof(double) * std::max<long long>(tab_len, 1), st) != cudaSuccess) {
+                err = "dd_factor_rs: proxy table allocation failed"; status = IE_ERR_OOM; break;
+            }
+            for (auto &tw : tab_of) {
+                rs_proxy_table<<<4 * p->sm_count, 256, 0, st>>>(d_ptab + tw.second, dim, nproxy, tw.first, rho, p->spacing,
+                                                                p->weight);
+                if (!ie_capturing()) ie_count_launches(1);
+            }
+            if ((status = to_dev(&d_ptaboff, ptab_off, st)) != IE_OK) { dfree(d_ptab, st); break; }
+        }
+        // KR1 over chunks of regions (workspace Y and C)
+        std::vector<long long> tt_off((size_t)nreg + 1, 0), cost((size_t)nreg);
+        for (int b = 0; b < nreg; ++b) {
+            const long long nb = nbv[(size_t)b];
+            tt_off[(size_t)b + 1] = tt_off[(size_t)b] + (nb * nb) / 4 + 1;
+            cost[(size_t)b] = (long long)rows[(size_t)b] * nb + std::min<long long>(rows[(size_t)b], nb) * nb;
+        }
+        int *d_nb = nullptr, *d_rows = nullptr, *d_natpt = nullptr, *d_nearpt = nullptr, *d_k = nullptr, *d_perm = nullptr;
+        long long *d_natoff = nullptr, *d_nearoff = nullptr, *d_ttoff = nullptr, *d_yoff = nullptr, *d_coff = nullptr;
+        int4 *d_geom = nullptr;
+        double *d_Tt = nullptr, *d_Y = nullptr, *d_C = nullptr;
+        std::vector<int> kv((size_t)nreg), perm((size_t)nat_off.back());
+        auto lfree = [&]() {
+            dfree(d_nb, st); dfree(d_rows, st); dfree(d_natpt, st); dfree(d_nearpt, st); dfree(d_k, st); dfree(d_perm, st);
+            dfree(d_natoff, st); dfree(d_nearoff, st); dfree(d_ttoff, st); dfree(d_yoff, st); dfree(d_coff, st);
+            dfree(d_geom, st); dfree(d_Tt, st); dfree(d_Y, st); dfree(d_C, st); dfree(d_ptab, st); dfree(d_ptaboff, st);
+        };
+        do {
+            if ((status = to_dev(&d_nb, nbv, st)) != IE_OK) break;
+            if ((status = to_dev(&d_rows, rows, st)) != IE_OK) break;
+            if ((status = to_dev(&d_natpt, nat_pt, st)) != IE_OK) break;
+            if ((status = to_dev(&d_nearpt, near_pt, st)) != IE_OK) break;
+            if ((status = to_dev(&d_natoff, nat_off, st)) != IE_OK) break;
+            if ((status = to_dev(&d_nearoff, near_off, st)) != IE_OK) break;
+            if ((status = to_dev(&d_ttoff, tt_off, st)) != IE_OK) break;
+            if ((status = to_dev(&d_geom, geom, st)) != IE_OK) break;
+            if ((status = to_dev(&d_k, kv, st)) != IE_OK) break;
+            if ((status = to_dev(&d_perm, perm, st)) != IE_OK) break;
+            if (cudaMallocAsync((void **)&d_Tt, sizeof(double) * tt_off.back(), st) != cudaSuccess) { status = IE_ERR_OOM; break; }
+            for (auto ch : chunks_by(cost)) {
+                std::vector<long long> yoff, coff;
+                long long ya = 0, ca = 0;
+                int mx_nb = 0, mx_rows = 0;
+                for (int b = ch.first; b < ch.second; ++b) {
+                    yoff.push_back(ya); coff.push_back(ca);
+                    ya += (long long)rows[(size_t)b] * nbv[(size_t)b];
+                    ca += std::min<long long>(rows[(size_t)b], nbv[(size_t)b]) * nbv[(size_t)b];
+                    mx_nb = std::max(mx_nb, nbv[(size_t)b]);
+                    mx_rows = std::max(mx_rows, rows[(size_t)b]);
+                }
+                dfree(d_yoff, st); dfree(d_coff, st); dfree(d_Y, st); dfree(d_C, st);
+                d_yoff = d_coff = nullptr; d_Y = d_C = nullptr;
+                if ((status = to_dev(&d_yoff, yoff, st)) != IE_OK) break;
+                if ((status = to_dev(&d_coff, coff, st)) != IE_OK) break;
+                if (cudaMallocAsync((void **)&d_Y, sizeof(double) * std::max<long long>(ya, 1), st) != cudaSuccess ||
+                    cudaMallocAsync((void **)&d_C, sizeof(double) * std::max<long long>(ca, 1), st) != cudaSuccess) {
+                    err = "dd_factor_rs: workspace allocation failed"; status = IE_ERR_OOM; break;
+                }
+                const size_t smem = sizeof(double) * (2 * (size_t)mx_nb + mx_rows + 3 * (size_t)nproxy) +
+                                    sizeof(int) * 2 * (size_t)mx_nb + (size_t)mx_nb + 16;
+                if (smem > 227 * 1024) { err = "dd_factor_rs: ID shared memory exceeds 227 KB"; status = IE_ERR_ARG; break; }
+                if (cudaFuncSetAttribute(rs_id, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+                    err = "dd_factor_rs: cudaFuncSetAttribute failed"; status = IE_ERR_CUDA; break;
+                }
+                IdArgs A{dim, n, nproxy, rho, p->spacing, p->weight, eps * eps, d_nb, d_rows, d_natoff, d_natpt,
+                         d_nearoff, d_nearpt, d_geom, d_yoff, d_coff, d_ttoff, d_Y, d_C, d_Tt, p->d_coord,
+                         p->d_table64, d_k, d_perm, d_ptab, d_ptaboff};
+                LaunchTimer tm;
+                tm.start(st);
+                cudaError_t e = launch_clustered(rs_id, ch.second - ch.first,
+                                                 cluster_size_for(ch.second - ch.first, p->sm_count), smem, st, A,
+                                                 ch.first);
+                if (!ie_capturing()) ie_count_launches(1);
+                if (e == cudaSuccess) e = cudaGetLastError();
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                if (e == cudaSuccess) tm.stop_add(st, rs->id_ms);
+                if (e != cudaSuccess) { err = std::string("dd_factor_rs: ") + cudaGetErrorString(e); status = IE_ERR_CUDA; break; }
+            }
+            if (status != IE_OK) break;
+            dfree(d_Y, st); dfree(d_C, st); d_Y = d_C = nullptr;
+            if (cudaMemcpyAsync(kv.data(), d_k, sizeof(int) * nreg, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaMemcpyAsync(perm.data(), d_perm, sizeof(int) * perm.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                err = "dd_factor_rs: copy of the ranks failed"; status = IE_ERR_CUDA; break;
+            }
+            for (int b = 0; b < nreg; ++b) {
+                const double r = rows[(size_t)b], nbd = nbv[(size_t)b], kd = kv[(size_t)b];
+                rs->id_flops += 2.0 * r * nbd + 4.0 * r * (kd * nbd - kd * (kd + 1.0) / 2.0) + (nbd - kd) * kd * kd;
+            }
+            // KR2
+            std::vector<unsigned long long> pbss;
+            std::vector<int> pk;
+            for (const Region &r : regs) {
+                (void)r;
+            }
+            // the children of this level's regions live in prev_* of their colour; flatten per region
+            std::vector<Region> eregs = regs;
+            for (int b = 0; b < nreg; ++b) {
+                Region &r = eregs[(size_t)b];
+                for (int &ch : r.child) {
+                    pk.push_back(prev_k[(size_t)r.colour][(size_t)ch]);
+                    pbss.push_back(prev_bss[(size_t)r.colour][(size_t)ch]);
+                    ch = (int)pk.size() - 1;
+                }
+            }
+            RSLevel lvl;
+            double *d_bss = nullptr;
+            std::vector<unsigned long long> baddr;
+            status = run_elim(p, eregs, perm, nat_off, d_natpt, d_perm, kv, pbss, pk, d_Tt, tt_off, lvl, &d_bss, baddr,
+                              st, err, rs->elim_ms, rs->elim_flops);
+            if (d_bss) bss_bufs.push_back(d_bss);
+            if (status != IE_OK) { lvl.release(); break; }
+            // the apply's view of the level
+            lvl.nreg = nreg;
+            lvl.pos_off.assign((size_t)nreg + 1, 0);
+            for (int b = 0; b < nreg; ++b) {
+                const Region &r = regs[(size_t)b];
+                lvl.colour.push_back(r.colour);
+                lvl.nb.push_back(nbv[(size_t)b]);
+                lvl.k.push_back(kv[(size_t)b]);
+                lvl.max_nb = std::max(lvl.max_nb, nbv[(size_t)b]);
+                lvl.max_k = std::max(lvl.max_k, kv[(size_t)b]);
+                for (int t = 0; t < nbv[(size_t)b]; ++t)
+                    lvl.pos.push_back(r.nat[(size_t)perm[(size_t)(nat_off[(size_t)b] + t)]]);
+                lvl.pos_off[(size_t)b + 1] = (long long)lvl.pos.size();
+            }
+            if ((status = to_dev(&lvl.d_nb, lvl.nb, st)) != IE_OK || (status = to_dev(&lvl.d_k, lvl.k, st)) != IE_OK ||
+                (status = to_dev(&lvl.d_pos, lvl.pos, st)) != IE_OK || (status = to_dev(&lvl.d_pos_off, lvl.pos_off, st)) != IE_OK) {
+                lvl.release();
+                break;
+            }
+            rs->levels.push_back(std::move(lvl));
+            // merge 2^d regions by K >> 1 (row-major), children in their level order
+            for (int c = 0; c < ncol; ++c) {
+                if (cur[(size_t)c].size() <= 1) continue;
+                rs->colour_levels[(size_t)c] = level + 1;
+                prev_k[(size_t)c].clear();
+                prev_bss[(size_t)c].clear();
+            }
+            for (int b = 0; b < nreg; ++b) {
+                const int c = regs[(size_t)b].colour;
+                prev_k[(size_t)c].push_back(kv[(size_t)b]);
+                prev_bss[(size_t)c].push_back(baddr[(size_t)b]);
+            }
+            for (int c = 0; c < ncol; ++c) {
+                if (cur[(size_t)c].size() <= 1) continue;
+                std::map<std::array<int, 3>, std::vector<int>> groups;
+                for (size_t i = 0; i < cur[(size_t)c].size(); ++i) {
+                    const Region &r = cur[(size_t)c][i];
+                    groups[{r.K[0] >> 1, r.K[1] >> 1, r.K[2] >> 1}].push_back((int)i);
+                }
+                std::vector<Region> nxt;
+                // the level's regions of colour c, in order: find this colour's first region index
+                int base = 0;
+                while (base < nreg && regs[(size_t)base].colour != c) ++base;
+                for (auto &g : groups) {
+                    Region r;
+                    r.colour = c;
+                    r.K = g.first;
+                    for (int d = 0; d < 3; ++d) { r.lo[(size_t)d] = INT_MAX; r.hi[(size_t)d] = INT_MIN; }
+                    for (int i : g.second) {
+                        const Region &ch = cur[(size_t)c][(size_t)i];
+                        const int b = base + i;
+                        r.child.push_back(i);
+                        r.child_start.push_back((int)r.nat.size());
+                        for (int t = 0; t < kv[(size_t)b]; ++t)
+                            r.nat.push_back(ch.nat[(size_t)perm[(size_t)(nat_off[(size_t)b] + t)]]);
+                        for (int d = 0; d < 3; ++d) {
+                            r.lo[(size_t)d] = std::min(r.lo[(size_t)d], ch.lo[(size_t)d]);
+                            r.hi[(size_t)d] = std::max(r.hi[(size_t)d], ch.hi[(size_t)d]);
+                        }
+                    }
+                    nxt.push_back(std::move(r));
+                }
+                cur[(size_t)c] = std::move(nxt);
+            }
+        } while (0);
+        lfree();
+    }
+    if (status != IE_OK) { free_bss(); return fail(status); }
+
+    // the last Schur complement of every colour: KR2 with k = 0
+    {
+        std::vector<Region> tops;
+        std::vector<int> pk;
+        std::vector<unsigned long long> pbss;
+        for (int c = 0; c < ncol; ++c) {
+            Region r = cur[(size_t)c][0];
+            for (int &ch : r.child) {
+                pk.push_back(prev_k[(size_t)c][(size_t)ch]);
+                pbss.push_back(prev_bss[(size_t)c][(size_t)ch]);
+                ch = (int)pk.size() - 1;
+            }
+            if ((int)r.nat.size() > kRsMaxTop) {
+                err = "dd_factor_rs: a last Schur complement has " + std::to_string(r.nat.size()) + " DOFs (limit " +
+                      std::to_string(kRsMaxTop) + ")";
+                free_bss();
+                return fail(IE_ERR_ARG);
+            }
+            tops.push_back(std::move(r));
+        }
+        std::vector<long long> nat_off((size_t)ncol + 1, 0), t_in((size_t)ncol + 1, 0);
+        std::vector<int> nat_pt, perm, kv((size_t)ncol, 0);
+        for (int c = 0; c < ncol; ++c) {
+            for (size_t t = 0; t < tops[(size_t)c].nat.size(); ++t) {
+                nat_pt.push_back(rs->pos2pt[(size_t)tops[(size_t)c].nat[t]]);
+                perm.push_back((int)t);
+            }
+            nat_off[(size_t)c + 1] = (long long)nat_pt.size();
+        }
+        int *d_natpt = nullptr, *d_perm = nullptr;
+        double *d_Tt = nullptr, *d_bss = nullptr;
+        std::vector<unsigned long long> baddr;
+        status = to_dev(&d_natpt, nat_pt, st);
+        if (status == IE_OK) status = to_dev(&d_perm, perm, st);
+        if (status == IE_OK && cudaMallocAsync((void **)&d_Tt, sizeof(double), st) != cudaSuccess) status = IE_ERR_OOM;
+        if (status == IE_OK)
+            status = run_elim(p, tops, perm, nat_off, d_natpt, d_perm, kv, pbss, pk, d_Tt, t_in, rs->top, &d_bss, baddr,
+                              st, err, rs->elim_ms, rs->elim_flops);
+        dfree(d_natpt, st); dfree(d_perm, st); dfree(d_Tt, st); dfree(d_bss, st);
+        free_bss();
+        if (status != IE_OK) return fail(status);
+        RSLevel &tp = rs->top;
+        tp.nreg = ncol;
+        tp.pos_off.assign((size_t)ncol + 1, 0);
+        for (int c = 0; c < ncol; ++c) {
+            tp.colour.push_back(c);
+            tp.nb.push_back((int)tops[(size_t)c].nat.size());
+            tp.k.push_back(0);
+            tp.max_nb = std::max(tp.max_nb, tp.nb.back());
+            tp.pos.insert(tp.pos.end(), tops[(size_t)c].nat.begin(), tops[(size_t)c].nat.end());
+            tp.pos_off[(size_t)c + 1] = (long long)tp.pos.size();
+        }
+        std::vector<int2> items;
+        for (int c = 0; c < ncol; ++c)
+            for (int r0 = 0; r0 < tp.nb[(size_t)c]; r0 += kRsTopRows) items.push_back(make_int2(c, r0));
+        rs->nitems = (int)items.size();
+        if ((status = to_dev(&tp.d_nb, tp.nb, st)) != IE_OK || (status = to_dev(&tp.d_k, tp.k, st)) != IE_OK ||
+            (status = to_dev(&tp.d_pos, tp.pos, st)) != IE_OK || (status = to_dev(&tp.d_pos_off, tp.pos_off, st)) != IE_OK ||
+            (status = to_dev(&rs->d_items, items, st)) != IE_OK)
+            return fail(status);
+    }
+    // point -> its positions (one per colour that holds it), in colour order
+    {
+        std::vector<long long> inv_ptr((size_t)p->N + 1, 0);
+        std::vector<int> inv_pos((size_t)rs->ntot);
+        for (long long q = 0; q < rs->ntot; ++q) inv_ptr[(size_t)rs->pos2pt[(size_t)q] + 1]++;
+        for (long long i = 0; i < p->N; ++i) inv_ptr[(size_t)i + 1] += inv_ptr[(size_t)i];
+        std::vector<long long> fill(inv_ptr.begin(), inv_ptr.end() - 1);
+        for (long long q = 0; q < rs->ntot; ++q) inv_pos[(size_t)fill[(size_t)rs->pos2pt[(size_t)q]]++] = (int)q;
+        if ((status = to_dev(&rs->d_inv_ptr, inv_ptr, st)) != IE_OK || (status = to_dev(&rs->d_inv_pos, inv_pos, st)) != IE_OK)
+            return fail(status);
+    }
+    // the apply kernels stage up to 2 * 4096 (levels) or 8192 (top) doubles: allow the full 227 KB
+    // once, here (outside any stream capture); the attribute only ever grows
+    {
+        const int full = 227 * 1024;
+        if (cudaFuncSetAttribute(rs_down, cudaFuncAttributeMaxDynamicSharedMemorySize, full) != cudaSuccess ||
+            cudaFuncSetAttribute(rs_up, cudaFuncAttributeMaxDynamicSharedMemorySize, full) != cudaSuccess ||
+            cudaFuncSetAttribute(rs_top, cudaFuncAttributeMaxDynamicSharedMemorySize, full) != cudaSuccess) {
+            err = "dd_factor_rs: cudaFuncSetAttribute failed";
+            return fail(IE_ERR_CUDA);
+        }
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) { err = "dd_factor_rs: stream synchronize failed"; return fail(IE_ERR_CUDA); }
+    dd_factor_t *f = new (std::nothrow) dd_factor_t();
+    if (!f) { err = "dd_factor_rs: out of host memory"; return fail(IE_ERR_OOM); }
+    f->prob = p; f->device = p->device; f->part = s; f->precision = IE_FP64; f->nblocks = 0;
+    f->rs = rs;
+    *out = f;
+    return IE_OK;
+}
+
+int launch_apply_rs(const dd_factor_t *f, const double *r, long long ldr, double *z, long long ldz, int nrhs,
+                    cudaStream_t s) {
+    const RSFactor *rs = f->rs;
+    const ie_problem *p = f->prob;
+    DevBuf yb, tb;
+    IE_TRY(yb.alloc(sizeof(double) * (size_t)rs->ntot * nrhs, s));
+    const long long ttot = rs->top.pos_off.back();
+    IE_TRY(tb.alloc(sizeof(double) * (size_t)std::max<long long>(ttot, 1) * nrhs, s));
+    double *y = yb.as<double>();
+    const unsigned gx = (unsigned)std::min<long long>((rs->ntot + 255) / 256, 4096);
+    rs_gather<<<dim3(gx, nrhs), 256, 0, s>>>(r, ldr, rs->d_pos2pt, rs->ntot, y);
+    IE_LAUNCHED();
+    for (const RSLevel &l : rs->levels) {
+        LevelArgs a{l.d_nb, l.d_k, l.d_pos_off, l.d_pos, l.d_t_off, l.d_b_off, l.d_T, l.d_Bsr, l.d_X, l.d_Binv};
+        const size_t sm = sizeof(double) * (size_t)(2 * l.max_nb);
+        rs_down<<<dim3(l.nreg, nrhs), kRsThreads, sm, s>>>(a, y, rs->ntot);
+        IE_LAUNCHED();
+    }
+    {
+        const RSLevel &t = rs->top;
+        const size_t sm = sizeof(double) * (size_t)t.max_nb;
+        rs_top<<<dim3(rs->nitems, nrhs), kRsThreads, sm, s>>>(rs->d_items, t.d_nb, t.d_pos_off, t.d_pos, t.d_b_off,
+                                                             t.d_Binv, y, rs->ntot, tb.as<double>(), ttot);
+        IE_LAUNCHED();
+        rs_top_put<<<dim3((unsigned)std::max<long long>((ttot + 255) / 256, 1), nrhs), 256, 0, s>>>(
+            t.d_pos, ttot, tb.as<double>(), y, rs->ntot);
+        IE_LAUNCHED();
+    }
+    for (auto it = rs->levels.rbegin(); it != rs->levels.rend(); ++it) {
+        const RSLevel &l = *it;
+        LevelArgs a{l.d_nb, l.d_k, l.d_pos_off, l.d_pos, l.d_t_off, l.d_b_off, l.d_T, l.d_Bsr, l.d_X, l.d_Binv};
+        const size_t sm = sizeof(double) * (size_t)l.max_nb;
+        rs_up<<<dim3(l.nreg, nrhs), kRsThreads, sm, s>>>(a, y, rs->ntot);
+        IE_LAUNCHED();
+    }
+    const unsigned gz = (unsigned)std::min<long long>((p->N + 255) / 256, 4096);
+    rs_scatter<<<dim3(gz, nrhs), 256, 0, s>>>(y, rs->ntot, rs->d_inv_ptr, rs->d_inv_pos, z, ldz, p->N);
+    IE_LAUNCHED();
+    return IE_OK;
+}
+
+extern "C" int dd_rs_info(const dd_factor_t *f, int *ncolours, int *levels, int *top, double *stats) {
+    if (!f || !f->rs) { ie_set_error("dd_rs_info: not an RS factor"); return IE_ERR_ARG; }
+    const RSFactor *rs = f->rs;
+    if (ncolours) *ncolours = rs->ncol;
+    if (stats) {
+        stats[0] = rs->id_flops;
+        stats[1] = rs->elim_flops;
+        stats[2] = rs->id_ms;
+        stats[3] = rs->elim_ms;
+    }
+    for (int c = 0; c < rs->ncol; ++c) {
+        if (levels) levels[c] = rs->colour_levels[(size_t)c];
+        if (top) top[c] = rs->top.nb[(size_t)c];
+    }
+    return IE_OK;
+}
+
+extern "C" int dd_rs_export(const dd_factor_t *f, int colour, int level, int *nreg, long long *total,
+                            long long *offsets, int *points, int *rank) {
+    if (!f || !f->rs) { ie_set_error("dd_rs_export: not an RS factor"); return IE_ERR_ARG; }
+    const RSFactor *rs = f->rs;
+    if (colour < 0 || colour >= rs->ncol) { ie_set_error("dd_rs_export: colour out of range"); return IE_ERR_ARG; }
+    const int nl = rs->colour_levels[(size_t)colour];
+    if (level < 1 || level > nl + 1) { ie_set_error("dd_rs_export: level out of range"); return IE_ERR_ARG; }
+    const RSLevel &l = level <= nl ? rs->levels[(size_t)level - 1] : rs->top;
+    int cnt = 0;
+    long long tot = 0;
+    for (int b = 0; b < l.nreg; ++b) {
+        if (l.colour[(size_t)b] != colour) continue;
+        const long long o0 = l.pos_off[(size_t)b], o1 = l.pos_off[(size_t)b + 1];
+        if (offsets) offsets[cnt] = tot;
+        if (rank) rank[cnt] = level <= nl ? l.k[(size_t)b] : (int)(o1 - o0);
+        if (points)
+            for (long long q = o0; q < o1; ++q) points[tot + (q - o0)] = rs->pos2pt[(size_t)l.pos[(size_t)q]];
+        tot += o1 - o0;
+        ++cnt;
+    }
+    if (offsets) offsets[cnt] = tot;
+    if (nreg) *nreg = cnt;
+    if (total) *total = tot;
+    return IE_OK;
+}

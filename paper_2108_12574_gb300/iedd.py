@@ -31,7 +31,7 @@ EXPORTS = ("ie_last_error", "ie_version", "ie_discretize", "ie_problem_info", "i
            "dd_factor_destroy", "dd_apply", "ie_kernel_launches", "pcg_default_opts", "pcg_solve",
            "ie_matvec_noalloc", "ws_create", "ws_destroy", "ws_num_params", "ws_get_params", "ws_set_params",
            "ws_forward_raw", "ws_backward_raw", "ws_train_step", "ws_predict", "ie_store_matrix",
-           "ie_release_matrix", "ie_autotune", "ie_autotune_report")
+           "ie_release_matrix", "ie_autotune", "ie_autotune_report", "dd_factor_rs", "dd_rs_info", "dd_rs_export")
 IE_NOALLOC_MAX_N = 4194304 - 1024
 
 
@@ -46,6 +46,10 @@ class PcgOpts(ctypes.Structure):
                 ("replace_every", ctypes.c_int), ("use_x0", ctypes.c_int), ("timeout_s", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("verify", ctypes.c_int), ("inner", ctypes.c_int),
                 ("residual", ctypes.c_int)]
+
+
+class RsOpts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("nproxy", ctypes.c_int), ("rho", ctypes.c_double)]
 
 
 class PcgReport(ctypes.Structure):
@@ -85,6 +89,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dd_partition_destroy": (None, [vp]),
         "dd_factor": (i, [vp, vp, i, P(vp), P(i), vp]),
         "dd_factor_destroy": (None, [vp]),
+        "dd_factor_rs": (i, [vp, vp, P(RsOpts), P(vp), vp]),
+        "dd_rs_info": (i, [vp, P(i), vp, vp, vp]),
+        "dd_rs_export": (i, [vp, i, i, P(i), P(ll), vp, vp, vp]),
         "dd_apply": (i, [vp, vp, vp, i, ll, vp]),
         "ie_kernel_launches": (ll, [i]),
         "ie_autotune": (i, [i]),
@@ -269,6 +276,43 @@ def dd_factor(prob: Problem, part: Partition, precision: int = IE_MIXED, stream=
             fac.close()
         raise err
     return fac
+
+
+def dd_factor_rs(prob: Problem, part: Partition, eps: float = 0.0, nproxy: int = 0, rho: float = 0.0,
+                 stream=None) -> Factor:
+    """RS factors of the CBD subdomains (0 selects the library's default for eps, nproxy, rho)."""
+    out = ctypes.c_void_p()
+    opts = RsOpts(eps, nproxy, rho)
+    _check(load_library().dd_factor_rs(prob.ptr, part.ptr, ctypes.byref(opts), ctypes.byref(out), _stream(stream)))
+    return Factor(out, prob, part, IE_FP64)
+
+
+def dd_rs_info(fac: Factor, stats: bool = False):
+    """(levels per colour, last-level DOFs per colour) of an RS factor; with ``stats`` also a dict
+    of the factor's FP64 flops and kernel times (id_flops, elim_flops, id_ms, elim_ms)."""
+    nc = ctypes.c_int()
+    lv = np.zeros(8, dtype=np.int32)
+    tp = np.zeros(8, dtype=np.int32)
+    st = np.zeros(4, dtype=np.float64)
+    _check(load_library().dd_rs_info(fac.ptr, ctypes.byref(nc), lv.ctypes.data, tp.ctypes.data, st.ctypes.data))
+    out = (lv[:nc.value].tolist(), tp[:nc.value].tolist())
+    if stats:
+        return out + (dict(zip(("id_flops", "elim_flops", "id_ms", "elim_ms"), st.tolist())),)
+    return out
+
+
+def dd_rs_export(fac: Factor, colour: int, level: int):
+    """Regions of one colour at one level (1-based; the last level is levels[colour] + 1): a list of
+    (points: int64 global indices with the skeletons first in pivot order, rank)."""
+    lib = load_library()
+    nreg, tot = ctypes.c_int(), ctypes.c_longlong()
+    _check(lib.dd_rs_export(fac.ptr, colour, level, ctypes.byref(nreg), ctypes.byref(tot), None, None, None))
+    offs = np.zeros(nreg.value + 1, dtype=np.int64)
+    pts = np.zeros(max(tot.value, 1), dtype=np.int32)
+    rk = np.zeros(max(nreg.value, 1), dtype=np.int32)
+    _check(lib.dd_rs_export(fac.ptr, colour, level, ctypes.byref(nreg), ctypes.byref(tot), offs.ctypes.data,
+                            pts.ctypes.data, rk.ctypes.data))
+    return [(pts[offs[b]:offs[b + 1]].astype(np.int64), int(rk[b])) for b in range(nreg.value)]
 
 
 def dd_apply(fac: Factor, r, z, stream=None):

@@ -1,0 +1,189 @@
+"""GPU recursive-skeletonization CBD preconditioner vs the FP64 CPU oracle, through the C ABI.
+
+What is compared (Sec. 4.3; oracle/rs_oracle.py):
+  * the skeleton sets, in pivot order, and the ranks of every region at every level: bit-exact
+    integers (the ID's pivots are FP64 decisions on both sides, with the same tie window);
+  * z = T^{-1} r through the RS factors: relative 2-norm error <= 1e-10 (FP64 factors; the
+    oracle's own round-off on these sizes is ~1e-13);
+  * PCG with the RS preconditioner (FP64 mode): iterations within +-1 of the oracle's, and when
+    equal the solution within 1e-10 (relative L2) of the oracle's;
+  * at 1024^2 with M = 128^2 (the paper's N / M = 64): sampled level-1 regions against the
+    oracle's ID of that region alone, the factor's shape against the stored oracle run, and the
+    PCG count against the stored oracle count (tests/golden/rs_counts.json, written by
+    tests/golden/make_rs_counts.py, which calls only the oracle).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import ie_oracle as O  # noqa: E402
+from oracle import rs_oracle as RS  # noqa: E402
+from paper_2108_12574_gb300 import iedd  # noqa: E402
+from paper_2108_12574_gb300 import inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "rs_counts.json")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+    torch.cuda.init()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+# (dim, n, m, delta, eps, nproxy, grid, a_shift): several levels, odd colour grids (m = 10, 3:
+# colours with 5 / 4 or 2 / 1 regions per axis, a colour with a single region), a 2-layer
+# overlap, the table grid, a shift, and m = 2 (one region per colour: no compression at all)
+CASES = [
+    (2, 64, 8, 1, 1e-3, 64, O.GRID_TEXT, 0.0),
+    (2, 96, 12, 2, 1e-6, 64, O.GRID_TEXT, 0.0),
+    (2, 80, 10, 1, 1e-3, 48, O.GRID_TABLE, 0.5),
+    (2, 64, 2, 1, 1e-3, 64, O.GRID_TEXT, 0.0),
+    (3, 16, 4, 1, 1e-3, 128, O.GRID_TEXT, 0.0),
+    (3, 12, 3, 1, 1e-4, 96, O.GRID_TEXT, 0.0),
+]
+
+
+def _gpu_factor(dim, n, m, delta, eps, nproxy, grid, a_shift):
+    prob = iedd.ie_discretize(dim, n, a_shift=a_shift, grid=grid)
+    part = iedd.dd_partition(prob, m, delta, iedd.DD_CBD)
+    fac = iedd.dd_factor_rs(prob, part, eps=eps, nproxy=nproxy)
+    return prob, part, fac
+
+
+_ORACLE = {}
+
+
+def _oracle_factor(dim, n, m, delta, eps, nproxy, grid, a_shift):
+    key = (dim, n, m, delta, eps, nproxy, grid, a_shift)
+    if key not in _ORACLE:
+        _ORACLE[key] = RS.factor(dim, n, m, delta, eps, nproxy, convention=grid, a_shift=a_shift)
+    return _ORACLE[key]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_rs_skeletons_and_ranks_match_oracle(case):
+    prob, part, fac = _gpu_factor(*case)
+    F = _oracle_factor(*case)
+    levels, top = iedd.dd_rs_info(fac)
+    assert levels == [len(fc["levels"]) for fc in F]
+    assert top == RS.top_dofs(F)
+    for c, fc in enumerate(F):
+        for lev in range(1, len(fc["levels"]) + 2):
+            g = iedd.dd_rs_export(fac, c, lev)
+            o = RS.regions_at(fc, lev)
+            assert len(g) == len(o)
+            for (gp, gk), (op, ok) in zip(g, o):
+                assert gk == ok, (c, lev)
+                assert np.array_equal(gp, op), (c, lev)
+    fac.close()
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_rs_apply_matches_oracle(case):
+    dim, n = case[0], case[1]
+    prob, part, fac = _gpu_factor(*case)
+    F = _oracle_factor(*case)
+    N = n ** dim
+    r = np.random.default_rng(3).uniform(-1.0, 1.0, (3, N))
+    z = torch.zeros((3, N), dtype=torch.float64, device="cuda")
+    iedd.dd_apply(fac, dev(r), z)
+    zg = host(z)
+    for k in range(3):
+        zo = RS.apply(F, r[k])
+        assert np.linalg.norm(zg[k] - zo) <= 1e-10 * np.linalg.norm(zo)
+    fac.close()
+
+
+def test_rs_with_two_regions_per_axis_is_the_dense_cbd():
+    """m = 2: every colour is one region, so the RS factor is the exact dense CBD factor."""
+    case = (2, 64, 2, 1, 1e-3, 64, O.GRID_TEXT, 0.0)
+    prob, part, fac = _gpu_factor(*case)
+    blocks = O.partition(2, 64, 2, 1, O.CBD)
+    factors = O.factor(2, 64, blocks)
+    r = np.random.default_rng(5).uniform(-1.0, 1.0, 64 * 64)
+    z = torch.zeros(64 * 64, dtype=torch.float64, device="cuda")
+    iedd.dd_apply(fac, dev(r), z)
+    zo = O.apply(factors, blocks, r)
+    assert np.linalg.norm(host(z) - zo) <= 1e-10 * np.linalg.norm(zo)
+    fac.close()
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[2], CASES[4]])
+def test_rs_pcg_matches_oracle(case):
+    dim, n = case[0], case[1]
+    prob, part, fac = _gpu_factor(*case)
+    F = _oracle_factor(*case)
+    N = n ** dim
+    f = I.uniform_rhs(N, 0)
+    tol = 1e-8
+    grid, a_shift = case[6], case[7]
+    A = O.dense_matrix(dim, n, grid, a_shift)
+    uo, ito, _ = O.pcg(lambda x: A @ x, lambda r: RS.apply(F, r), f, tol, 500)
+    u = torch.zeros(N, dtype=torch.float64, device="cuda")
+    rep = iedd.pcg_solve(prob, fac, dev(f), u, tol=tol, precision=iedd.IE_FP64, max_it=500)[0]
+    assert abs(rep["iterations"] - ito) <= 1
+    if rep["iterations"] == ito:
+        assert np.linalg.norm(host(u) - uo) <= 1e-10 * np.linalg.norm(uo)
+    assert np.linalg.norm(f - A @ host(u)) <= 1.05 * tol * np.linalg.norm(f)
+    fac.close()
+
+
+def test_rs_rejects_bad_arguments():
+    prob = iedd.ie_discretize(2, 32)
+    sch = iedd.dd_partition(prob, 4, 1, iedd.DD_SCHWARZ)
+    with pytest.raises(iedd.IEError):
+        iedd.dd_factor_rs(prob, sch)                      # not a CBD partition
+    wide = iedd.dd_partition(prob, 8, 3, iedd.DD_CBD)      # 2 delta > w: the regions overlap
+    with pytest.raises(iedd.IEError):
+        iedd.dd_factor_rs(prob, wide)
+    cbd = iedd.dd_partition(prob, 4, 1, iedd.DD_CBD)
+    with pytest.raises(iedd.IEError):
+        iedd.dd_factor_rs(prob, cbd, eps=2.0)
+
+
+@pytest.mark.skipif(not os.path.exists(GOLDEN), reason="no stored oracle run")
+def test_rs_1024_against_oracle():
+    """1024^2, M = 128^2, delta = 1, eps = 1e-3 (the paper's weak-scaling row): sampled level-1
+    regions against the oracle's ID of each alone, the factor's shape and the PCG count against
+    the stored oracle run, and the true residual."""
+    gold = json.load(open(GOLDEN))["ie2d_n1024_cbd_m128"]
+    dim, n, m, delta, eps, nproxy = 2, 1024, 128, 1, 1e-3, 64
+    prob = iedd.ie_discretize(dim, n)
+    part = iedd.dd_partition(prob, m, delta, iedd.DD_CBD)
+    fac = iedd.dd_factor_rs(prob, part, eps=eps, nproxy=nproxy)
+    levels, top = iedd.dd_rs_info(fac)
+    assert levels == gold["levels"] and top == gold["top"]
+    rng = np.random.default_rng(11)
+    regs = RS.colour_regions(dim, n, m, delta)
+    for c in range(4):
+        g = iedd.dd_rs_export(fac, c, 1)
+        for idx in rng.choice(len(regs[c]), 6, replace=False):
+            op, ok = RS.level1_id(dim, n, m, delta, c, int(idx), eps, nproxy)
+            gp, gk = g[int(idx)]
+            assert gk == ok and np.array_equal(gp, op)
+    for c in range(4):
+        ranks = [[k for _, k in iedd.dd_rs_export(fac, c, lev)] for lev in range(1, levels[c] + 1)]
+        assert [sum(r) for r in ranks] == gold["rank_sums"][c]
+    f = I.grf(2, n, 0.05, 0)
+    u = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+    rep = iedd.pcg_solve(prob, fac, dev(f), u, tol=1e-8, precision=iedd.IE_FP64, inner=iedd.IE_FFT,
+                         residual=iedd.IE_FFT, verify=1, max_it=200)[0]
+    assert abs(rep["iterations"] - gold["iterations"]) <= 1
+    assert rep["true_relres"] <= 1.05e-8
+    fac.close()
