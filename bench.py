@@ -73,7 +73,8 @@ NCU_K1W = {("c8970434ed8bad33", 32): {"traffic": 83382784, "tensor_pipe": 0.430}
 KZ_PRODUCTS_PER_PAIR = 21
 # ncu figures of the RS factor's level-1 launches per rs_source_hash(), 2D 256^2 with M = 32^2 (the
 # same region shapes as 1024^2): FP64 pipe activity of rs_id / rs_elim and their DRAM bytes
-NCU_RS = {}
+NCU_RS = {"d144f1272b2e88d6": {"fp64_pipe": {"rs_id": 0.736, "rs_elim": 0.725},
+                               "dram_bytes_256": {"rs_id": 1519575200, "rs_elim": 325328233}}}
 # GB300's FP64 rate (nominal; no FP64 peak is measured on this machine)
 FP64_NOMINAL_TFLOPS = 1.25
 
@@ -124,7 +125,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=WORKLOAD)
     ap.add_argument("--no-extras", action="store_true", help="skip FP64-plain and CPU-baseline legs")
-    ap.add_argument("--kernel", choices=["k1", "k2", "kd", "tc", "kz", "stored", "fft", "apply", "factor", "ws_train",
+    ap.add_argument("--kernel", choices=["k1", "k2", "kd", "tc", "kz", "stored", "fft", "apply", "factor", "rs", "rs_apply", "ws_train",
                                          "ws_predict"], default=None,
                     help="profiling case: run one hot operation twice on a --dim/--n/--nrhs problem and exit")
     ap.add_argument("--dim", type=int, default=2)
@@ -161,6 +162,20 @@ def kernel_case(args):
         return 0
     X = torch.from_numpy(I.uniform_rhs_batch(N, range(args.nrhs)).T.copy()).cuda()
     Y = torch.zeros_like(X)
+    if args.kernel in ("rs", "rs_apply"):
+        # the RS factor of a CBD partition into boxes of 8^d points, one layer of overlap, eps = 1e-3
+        # (the paper's N / M = 64 in 2D, 512 in 3D); rs_apply then applies it
+        part = iedd.dd_partition(prob, args.n // 8, 1, iedd.DD_CBD)
+        for _ in range(2):
+            fac = iedd.dd_factor_rs(prob, part, eps=1e-3)
+            if args.kernel == "rs_apply":
+                iedd.dd_apply(fac, X, Y)
+            torch.cuda.synchronize()
+            levels, top, st = iedd.dd_rs_info(fac, stats=True)
+            fac.close()
+        print(json.dumps({"kernel_case": args.kernel, "dim": args.dim, "n": args.n, "levels": levels, "top": top,
+                          "stats": st, "ok": True}))
+        return 0
     m = args.n // 16 if args.dim == 2 else args.n // 8
     for _ in range(2):
         if args.kernel in ("k1", "k2", "kd", "tc", "kz", "stored", "fft"):
