@@ -327,21 +327,17 @@ extern "C" int dd_partition(const ie_problem *p, int m, int delta, int kind, dd_
     long long M = 1;
     for (int d = 0; d < dim; ++d) M *= m;
 
-    // every extended box, enumerated row-major so its indices come out ascending
-    std::vector<std::vector<int>> boxes((size_t)M);
-    std::vector<int> colour((size_t)M);
-    for (long long b = 0; b < M; ++b) {
+    // every extended box (Jacobi, Schwarz), enumerated row-major so its indices come out ascending
+    std::vector<std::vector<int>> boxes((size_t)(kind == DD_CBD ? 0 : M));
+    for (long long b = 0; b < (long long)boxes.size(); ++b) {
         int k[3] = {0, 0, 0};
         long long t = b;
         for (int d = dim - 1; d >= 0; --d) { k[d] = (int)(t % m); t /= m; }
         int lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
-        int c = 0;
         for (int d = 0; d < dim; ++d) {
             lo[d] = std::max(k[d] * w - ext, 0);
             hi[d] = std::min((k[d] + 1) * w + ext, n);
-            c = c * 2 + (k[d] & 1);
         }
-        colour[(size_t)b] = c;
         auto &v = boxes[(size_t)b];
         if (dim == 2) {
             for (int i = lo[0]; i < hi[0]; ++i)
@@ -354,14 +350,32 @@ extern "C" int dd_partition(const ie_problem *p, int m, int delta, int kind, dd_
     }
     std::vector<std::vector<int>> blocks;
     if (kind == DD_CBD) {
+        // A colour's boxes are the product of one parity per axis, so their union is the product of
+        // the per-axis unions of the extended intervals [k w - ext, (k + 1) w + ext), k of that
+        // parity: emit the points of that product in grid order (ascending, no duplicates).
         int ncol = 1 << dim;
         for (int c = 0; c < ncol; ++c) {
+            std::vector<std::vector<int>> axis((size_t)dim);
+            for (int d = 0; d < dim; ++d) {
+                const int par = (c >> (dim - 1 - d)) & 1;
+                std::vector<char> in((size_t)n, 0);
+                for (int k = par; k < m; k += 2)
+                    for (int x = std::max(k * w - ext, 0); x < std::min((k + 1) * w + ext, n); ++x) in[(size_t)x] = 1;
+                for (int x = 0; x < n; ++x)
+                    if (in[(size_t)x]) axis[(size_t)d].push_back(x);
+            }
             std::vector<int> u;
-            for (long long b = 0; b < M; ++b)
-                if (colour[(size_t)b] == c) u.insert(u.end(), boxes[(size_t)b].begin(), boxes[(size_t)b].end());
+            if (dim == 2) {
+                u.reserve(axis[0].size() * axis[1].size());
+                for (int i : axis[0])
+                    for (int j : axis[1]) u.push_back(i * n + j);
+            } else {
+                u.reserve(axis[0].size() * axis[1].size() * axis[2].size());
+                for (int i : axis[0])
+                    for (int j : axis[1])
+                        for (int l : axis[2]) u.push_back((i * n + j) * n + l);
+            }
             if (u.empty()) continue;
-            std::sort(u.begin(), u.end());
-            u.erase(std::unique(u.begin(), u.end()), u.end());
             blocks.push_back(std::move(u));
         }
     } else {
