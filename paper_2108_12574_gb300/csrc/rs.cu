@@ -491,6 +491,7 @@ __device__ void tile_mm(int M, int N, int K, LA la, LB lb, OUT out, bool lower_t
 // KR2: one cluster of CS CTAs per region; every phase splits its entries over the cluster's
 // threads and ends at a cluster barrier.  With more than one CTA, workspace values that another
 // CTA wrote are read from L2 (ldw).
+template <bool kWithTiles>
 __global__ void __launch_bounds__(kRsThreads) rs_elim(ElimArgs a, int first) {
     __shared__ int sh_bad;
     __shared__ double sh_blk[kPanel * kPanel];
@@ -500,7 +501,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_elim(ElimArgs a, int first) {
     const int bl = blockIdx.x / CS;
     const int b = first + bl;
     const int nb = a.nb[b], k = a.k[b], nr = nb - k;
-    const bool tiled = nr >= kTiledFrom;
+    const bool tiled = kWithTiles && nr >= kTiledFrom;  // the plain variant keeps the register count low
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const long long g0 = (long long)cr * blockDim.x + tid, gs = (long long)CS * blockDim.x;
     const int gw0 = (int)cr * nwarps + warp, gws = (int)CS * nwarps;  // cluster-wide warp index
@@ -1043,8 +1044,10 @@ int run_elim(const ie_problem *p, const std::vector<Region> &regs, const std::ve
                        p->d_table64, d_info};
             LaunchTimer tm;
             tm.start(s);
-            e = launch_clustered(rs_elim, ch.second - ch.first, cluster_size_for(ch.second - ch.first, p->sm_count), 0,
-                                 s, A, ch.first);
+            int max_nr = 0;
+            for (int b = ch.first; b < ch.second; ++b) max_nr = std::max(max_nr, nbv[(size_t)b] - kv[(size_t)b]);
+            e = launch_clustered(max_nr >= kTiledFrom ? rs_elim<true> : rs_elim<false>, ch.second - ch.first,
+                                 cluster_size_for(ch.second - ch.first, p->sm_count), 0, s, A, ch.first);
             if (!ie_capturing()) ie_count_launches(1);
             if (e == cudaSuccess) e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
