@@ -73,7 +73,7 @@ NCU_K1W = {("c8970434ed8bad33", 32): {"traffic": 83382784, "tensor_pipe": 0.430}
 KZ_PRODUCTS_PER_PAIR = 21
 # ncu figures of the RS factor's level-1 launches per rs_source_hash(), 2D 256^2 with M = 32^2 (the
 # same region shapes as 1024^2): FP64 pipe activity of rs_id / rs_elim and their DRAM bytes
-NCU_RS = {"0d026486e3e2f383": {"fp64_pipe": {"rs_id": 0.734, "rs_elim": 0.725},
+NCU_RS = {"f0901695951aead9": {"fp64_pipe": {"rs_id": 0.734, "rs_elim": 0.725},
                                "dram_bytes_256": {"rs_id": 1515883561, "rs_elim": 325845367}}}
 # GB300's FP64 rate (nominal; no FP64 peak is measured on this machine)
 FP64_NOMINAL_TFLOPS = 1.25
@@ -112,9 +112,12 @@ def tc_exact_source_hash() -> str:
 
 
 def rs_source_hash() -> str:
-    """sha256 (16 hex digits) of the recursive-skeletonization factor's source file."""
+    """sha256 (16 hex digits) of the RS factor kernels' source text (the entry lookup, rs_proxy_table,
+    rs_id, the tiled products and rs_elim: up to the first apply kernel), the key of their ncu
+    figures."""
     src = open(os.path.join(ROOT, "paper_2108_12574_gb300", "csrc", "rs.cu")).read()
-    return hashlib.sha256(src.encode()).hexdigest()[:16]
+    a, b = src.index("__device__ __forceinline__ double a_entry"), src.index("__global__ void rs_gather")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
 def parse():
@@ -948,7 +951,36 @@ def cbd_rs_leg(torch, iedd, dev, stream, flush, name="ie2d_n1024_cbd_rs_m128_d1"
             "iterations_oracle_fp64": rs_oracle_count(name), "true_relres": rep["true_relres"],
             "factor_s": t_fac, "t_solve_matvec_s": rep["matvec_ms"] / 1e3, "t_solve_apply_s": rep["apply_ms"] / 1e3,
             "apply_ms_per_iteration": rep["apply_ms"] / max(rep["applies"], 1), "levels": levels, "top_dofs": top,
-            "config": config_dict(name)}
+            "config": config_dict(name), "cpu_baseline": rs_cpu_baseline(name, rep["iterations"])}
+
+
+def rs_cpu_baseline(name: str, iterations: int, n_sample: int = 256):
+    """The FP64 oracle's RS-CBD solve, timed on an n_sample^d grid with the workload's box size,
+    overlap and eps (the RS factor and apply: the whole of that grid) and scaled to the workload by
+    N, with the oracle's FFT matvec measured at the workload's size; total = factor + iterations x
+    (matvec + apply).  Extrapolated, and labelled so."""
+    from oracle import ie_oracle as O
+    from oracle import rs_oracle as RS
+    from paper_2108_12574_gb300 import inputs as I
+    W = WORKLOADS[name]
+    dim, n = W["dim"], W["n"]
+    N, Ns = n ** dim, n_sample ** dim
+    m_s = n_sample // (n // W["m"])
+    t0 = time.perf_counter()
+    F = RS.factor(dim, n_sample, m_s, W["delta"], W["eps"], 64 if dim == 2 else 256)
+    t_fac = (time.perf_counter() - t0) * N / Ns
+    t0 = time.perf_counter()
+    RS.apply(F, I.uniform_rhs(Ns, 0))
+    t_ap = (time.perf_counter() - t0) * N / Ns
+    t0 = time.perf_counter()
+    O.matvec_fft(dim, n, I.uniform_rhs(N, 0))
+    t_mv = time.perf_counter() - t0
+    return {"value": t_fac + iterations * (t_mv + t_ap), "unit": "s", "cores": oracle_cores(), "cpu": cpu_model(),
+            "kind": "oracle", "workload": name, "extrapolated": True,
+            "sample": (f"the oracle's RS factor and one apply on the whole {n_sample}^{dim} grid with the same box "
+                       f"size ({m_s}^{dim} boxes), scaled by N to {n}^{dim}; its FFT matvec measured at {n}^{dim}; "
+                       f"total = factor + {iterations} iterations x (matvec + apply); extrapolated"),
+            "parts_s": {"factor": t_fac, "apply": t_ap, "matvec": t_mv}}
 
 
 def rs_oracle_count(name: str):

@@ -41,7 +41,10 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <new>
+#include <stdexcept>
 #include <string>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -744,7 +747,8 @@ __global__ void __launch_bounds__(kRsThreads) rs_down(LevelArgs a, double *__res
     __syncthreads();
     for (int i = tid; i < nr; i += blockDim.x) {
         double t = yv[pos[k + i]];
-        for (int l = 0; l < k; ++l) t -= T[(long long)l * nr + i] * ys[l];
+#pragma unroll 8
+        for (int l = 0; l < k; ++l) t -= T[(long long)l * nr + i] * ys[l];  // unrolled: loads in flight
         u[i] = t;
     }
     __syncthreads();
@@ -781,6 +785,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_up(LevelArgs a, double *__restr
     for (int i = tid; i < nr; i += blockDim.x) {
         double t = yv[pos[k + i]];
         const double *row = X + (long long)i * k;
+#pragma unroll 8
         for (int l = 0; l < k; ++l) t -= row[l] * as[l];
         ar[i] = t;
         yv[pos[k + i]] = t;
@@ -1076,8 +1081,25 @@ int run_elim(const ie_problem *p, const std::vector<Region> &regs, const std::ve
 
 }  // namespace
 
+static int factor_rs_impl(const ie_problem *p, const dd_partition_t *s, const rs_opts *opts, dd_factor_t **out,
+                          void *stream);
+
 extern "C" int dd_factor_rs(const ie_problem *p, const dd_partition_t *s, const rs_opts *opts, dd_factor_t **out,
                             void *stream) {
+    // host containers and threads may throw; nothing may cross the C ABI
+    try {
+        return factor_rs_impl(p, s, opts, out, stream);
+    } catch (const std::bad_alloc &) {
+        ie_set_error("dd_factor_rs: out of host memory");
+        return IE_ERR_OOM;
+    } catch (const std::exception &e) {
+        ie_set_error(std::string("dd_factor_rs: ") + e.what());
+        return IE_ERR_ARG;
+    }
+}
+
+static int factor_rs_impl(const ie_problem *p, const dd_partition_t *s, const rs_opts *opts, dd_factor_t **out,
+                          void *stream) {
     if (!out) { ie_set_error("dd_factor_rs: out is NULL"); return IE_ERR_ARG; }
     *out = nullptr;
     if (!p || !s) { ie_set_error("dd_factor_rs: NULL problem or partition"); return IE_ERR_ARG; }
@@ -1256,9 +1278,18 @@ extern "C" int dd_factor_rs(const ie_problem *p, const dd_partition_t *s, const 
         {
             const int nth = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), nreg / 64));
             std::vector<std::thread> pool;
-            for (int t = 1; t < nth; ++t)
-                pool.emplace_back(near_range, (int)((long long)nreg * t / nth), (int)((long long)nreg * (t + 1) / nth));
+            int spawned = 1;  // ranges [0, spawned) of nth run on threads (range 0 here); the rest below
+            for (int t = 1; t < nth; ++t) {
+                try {
+                    pool.emplace_back(near_range, (int)((long long)nreg * t / nth), (int)((long long)nreg * (t + 1) / nth));
+                    spawned = t + 1;
+                } catch (const std::system_error &) {
+                    break;  // no more threads: the remaining ranges run on this one
+                }
+            }
             near_range(0, (int)((long long)nreg / nth));
+            for (int t = spawned; t < nth; ++t)
+                near_range((int)((long long)nreg * t / nth), (int)((long long)nreg * (t + 1) / nth));
             for (auto &th : pool) th.join();
         }
         for (int b = 0; b < nreg; ++b) {

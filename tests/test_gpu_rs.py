@@ -213,3 +213,24 @@ def test_rs_reproduces_the_papers_weak_scaling_rows(dim, n, m, S, nit, levels):
     assert rep["status"] == 0 and rep["true_relres"] <= 2e-12, rep
     assert abs(rep["iterations"] - nit) <= 4, rep["iterations"]
     fac.close()
+
+
+def test_rs_pcg_batch_of_right_hand_sides_matches_oracle():
+    """Four right-hand sides in one pcg_solve call with the RS factor (the apply's columns run as
+    the grid's second dimension): per-column counts within +-1 of the oracle's, and solutions."""
+    case = (3, 16, 4, 1, 1e-3, 128, O.GRID_TEXT, 0.0)
+    dim, n = case[0], case[1]
+    N = n ** dim
+    prob, part, fac = _gpu_factor(*case)
+    F = _oracle_factor(*case)
+    Fh = I.uniform_rhs_batch(N, range(4))                      # N x 4
+    A = O.dense_matrix(dim, n)
+    Uo, ito, _ = O.pcg(lambda x: A @ x, lambda r: RS.apply(F, r), Fh, 1e-8, 500)
+    U = torch.zeros((4, N), dtype=torch.float64, device="cuda")
+    reps = iedd.pcg_solve(prob, fac, dev(Fh.T.copy()), U, tol=1e-8, precision=iedd.IE_FP64, max_it=500)
+    Ug = host(U)
+    for k in range(4):
+        assert abs(reps[k]["iterations"] - int(ito[k])) <= 1, (k, reps[k]["iterations"], ito[k])
+        if reps[k]["iterations"] == int(ito[k]):
+            assert np.linalg.norm(Ug[k] - Uo[:, k]) <= 1e-10 * np.linalg.norm(Uo[:, k])
+    fac.close()
