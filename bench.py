@@ -52,6 +52,11 @@ WORKLOADS = {
     # N / M = 64, one layer of overlap, eps = 1e-3 (Sec. 5.2), the FP64 FFT matvec (Sec. 6)
     "ie2d_n1024_cbd_rs_m128_d1": dict(dim=2, n=1024, m=128, delta=1, rhs="grf", ell=0.05, seeds=1, precision="fp64",
                                       factor="rs", eps=1e-3, inner="fft"),
+    # the same beyond the dense-CBD limit: the paper's weak-scaling rows (Sec. 5, N / M = 64 in 2D, 512 in 3D)
+    "ie2d_n2048_cbd_rs_m256_d1": dict(dim=2, n=2048, m=256, delta=1, rhs="grf", ell=0.05, seeds=1, precision="fp64",
+                                      factor="rs", eps=1e-3, inner="fft"),
+    "ie3d_n64_cbd_rs_m8_d1": dict(dim=3, n=64, m=8, delta=1, rhs="uniform", seeds=1, precision="fp64", factor="rs",
+                                  eps=1e-3, inner="fft"),
 }
 METRIC = "PCG time-to-1e-8 true relative residual (s)"
 L2_FLUSH_BYTES = 512 << 20
@@ -891,6 +896,13 @@ def extras(torch, iedd, I, dev, stream, clocks, sms, flush):
                          "parts_s": {"factor": t_fac, "matvec": t_64, "apply": t_ap}}
     out["cbd"] = cbd_leg(torch, iedd, I, dev, stream)
     out["cbd_rs"] = cbd_rs_leg(torch, iedd, dev, stream, flush)
+    scale = {}
+    for name in ("ie2d_n2048_cbd_rs_m256_d1", "ie3d_n64_cbd_rs_m8_d1"):
+        t, reps = timed_solves(torch, iedd, dev, stream, name, 2, flush=flush)
+        scale[name] = {"value": t, "unit": "s", "iterations": reps[0]["iterations"],
+                       "true_relres": reps[0]["true_relres"], "t_solve_matvec_s": reps[0]["matvec_ms"] / 1e3,
+                       "t_solve_apply_s": reps[0]["apply_ms"] / 1e3, "config": config_dict(name)}
+    out["cbd_rs_scale"] = scale
     out["stored_matvec"] = stored_matvec_leg(torch, iedd, I, dev, stream)
     return out
 
