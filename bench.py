@@ -611,12 +611,15 @@ def roofline_of(iedd, name, rep, clocks, sms, rs_stats=None):
         achieved = flops / t
         peak = FP64_NOMINAL_TFLOPS * 1e12
         ncu = NCU_RS.get(rs_source_hash(), {})
+        fma = iedd.ie_fp64_fma_rate(0)
         return ({"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                 "frac": achieved / peak, "traffic": ncu.get("traffic"), "kernel": "rs_id + rs_elim (RS factor)",
+                 "frac": achieved / peak, "fp64_fma_measured_tflops": fma, "frac_of_measured_fma": achieved / 1e12 / fma,
+                 "traffic": ncu.get("traffic"), "kernel": "rs_id + rs_elim (RS factor)",
                  "launch_ms": t * 1e3, "fp64_flops": flops, "id_ms": rs_stats["id_ms"],
                  "elim_ms": rs_stats["elim_ms"], "fp64_pipe_ncu": ncu.get("fp64_pipe"),
-                 "peak_basis": (f"GB300 FP64 {FP64_NOMINAL_TFLOPS} TFLOP/s nominal (no FP64 peak is measured on this "
-                                "pool); work = the factor's algorithmic FP64 flops (ID: initial norms, 4 flops per row "
+                 "peak_basis": (f"GB300 FP64 {FP64_NOMINAL_TFLOPS} TFLOP/s nominal (no FP64 peak in the pool's "
+                                "measured peaks; fp64_fma_measured_tflops: this device's FP64 FMA loop, "
+                                "ie_fp64_fma_rate); work = the factor's algorithmic FP64 flops (ID: initial norms, 4 flops per row "
                                 "and remaining column per Gram-Schmidt step, back substitution; elimination: M, B_rr, Cholesky, triangular "
                                 "inverse, L^-T L^-1, X, B_ss) / the summed CUDA-event time of its rs_id and rs_elim "
                                 "launches")}, False)

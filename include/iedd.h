@@ -383,6 +383,15 @@ IEDD_API int ws_predict(ws_model *w, const ie_problem *p, const double *f, doubl
 IEDD_API long long ie_kernel_launches(int reset);
 
 /*
+ * ie_fp64_fma_rate -- instrumentation (not in the paper): the FP64 FMA throughput of `device` in
+ * TFLOP/s (2 flops per FMA), measured by a kernel of eight independent FMA chains per thread on
+ * every SM (8 CTAs of 256 threads per SM), best of five timed launches after a warm-up (CUDA
+ * events).  The denominator for the FP64-bound kernels' roofline (the RS factor).  Synchronous;
+ * IE_ERR_ARG for a NULL out, IE_ERR_CUDA on a CUDA failure.
+ */
+IEDD_API int ie_fp64_fma_rate(int device, double *tflops);
+
+/*
  * ie_autotune -- the library's autotuner (not in the paper): launch shapes of the explicit-inverse
  * apply (rows per work item, rows per warp pass, loads in flight) and of the FFT passes (lines per
  * CTA) are chosen by timing every candidate once per problem shape, at dd_factor and at the first

@@ -1635,6 +1635,56 @@ int launch_apply_rs(const dd_factor_t *f, const double *r, long long ldr, double
     return IE_OK;
 }
 
+namespace {
+// eight independent FMA chains per thread; the sum is stored only if it is never what it is, so the
+// chains cannot be dropped
+__global__ void __launch_bounds__(256) fp64_fma_chains(double *sink, int iters) {
+    double a[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = 1e-3 * (threadIdx.x + c);
+    const double m = 0.9999999, d = 1e-9;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a[c] = fma(a[c], m, d);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) t += a[c];
+    if (t == -1.0) sink[0] = t;
+}
+}  // namespace
+
+extern "C" int ie_fp64_fma_rate(int device, double *tflops) {
+    if (!tflops) { ie_set_error("ie_fp64_fma_rate: out is NULL"); return IE_ERR_ARG; }
+    DeviceGuard g(device);
+    int sms = 0;
+    IE_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    double *sink = nullptr;
+    IE_TRY_CUDA(cudaMalloc(&sink, sizeof(double)));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int iters = 1 << 14, blocks = 8 * sms, threads = 256;
+    float best = 0.f;
+    int st = IE_OK;
+    for (int rep = 0; rep < 6 && st == IE_OK; ++rep) {
+        cudaEventRecord(e0, nullptr);
+        fp64_fma_chains<<<blocks, threads>>>(sink, iters);
+        if (!ie_capturing()) ie_count_launches(1);
+        cudaEventRecord(e1, nullptr);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) { st = IE_ERR_CUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && (best == 0.f || ms < best)) best = ms;  // rep 0 warms up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (st != IE_OK) { ie_set_error("ie_fp64_fma_rate: kernel failed"); return st; }
+    *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
+    return IE_OK;
+}
+
 extern "C" int dd_rs_info(const dd_factor_t *f, int *ncolours, int *levels, int *top, double *stats) {
     if (!f || !f->rs) { ie_set_error("dd_rs_info: not an RS factor"); return IE_ERR_ARG; }
     const RSFactor *rs = f->rs;

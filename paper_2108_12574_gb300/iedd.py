@@ -31,7 +31,7 @@ EXPORTS = ("ie_last_error", "ie_version", "ie_discretize", "ie_problem_info", "i
            "dd_factor_destroy", "dd_apply", "ie_kernel_launches", "pcg_default_opts", "pcg_solve",
            "ie_matvec_noalloc", "ws_create", "ws_destroy", "ws_num_params", "ws_get_params", "ws_set_params",
            "ws_forward_raw", "ws_backward_raw", "ws_train_step", "ws_predict", "ie_store_matrix",
-           "ie_release_matrix", "ie_autotune", "ie_autotune_report", "dd_factor_rs", "dd_rs_info", "dd_rs_export")
+           "ie_release_matrix", "ie_autotune", "ie_autotune_report", "dd_factor_rs", "dd_rs_info", "dd_rs_export", "ie_fp64_fma_rate")
 IE_NOALLOC_MAX_N = 4194304 - 1024
 
 
@@ -92,6 +92,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "dd_factor_rs": (i, [vp, vp, P(RsOpts), P(vp), vp]),
         "dd_rs_info": (i, [vp, P(i), vp, vp, vp]),
         "dd_rs_export": (i, [vp, i, i, P(i), P(ll), vp, vp, vp]),
+        "ie_fp64_fma_rate": (i, [i, P(d)]),
         "dd_apply": (i, [vp, vp, vp, i, ll, vp]),
         "ie_kernel_launches": (ll, [i]),
         "ie_autotune": (i, [i]),
@@ -313,6 +314,13 @@ def dd_rs_export(fac: Factor, colour: int, level: int):
     _check(lib.dd_rs_export(fac.ptr, colour, level, ctypes.byref(nreg), ctypes.byref(tot), offs.ctypes.data,
                             pts.ctypes.data, rk.ctypes.data))
     return [(pts[offs[b]:offs[b + 1]].astype(np.int64), int(rk[b])) for b in range(nreg.value)]
+
+
+def ie_fp64_fma_rate(device: int = 0) -> float:
+    """The device's measured FP64 FMA throughput in TFLOP/s (instrumentation)."""
+    out = ctypes.c_double()
+    _check(load_library().ie_fp64_fma_rate(device, ctypes.byref(out)))
+    return out.value
 
 
 def dd_apply(fac: Factor, r, z, stream=None):

@@ -234,3 +234,10 @@ def test_rs_pcg_batch_of_right_hand_sides_matches_oracle():
         if reps[k]["iterations"] == int(ito[k]):
             assert np.linalg.norm(Ug[k] - Uo[:, k]) <= 1e-10 * np.linalg.norm(Uo[:, k])
     fac.close()
+
+
+def test_fp64_fma_rate_is_measured():
+    """The measured FP64 FMA throughput (the RS factor's roofline denominator) is a plausible rate:
+    above the RS factor's own achieved FP64 rate, below the FP32 tensor figures."""
+    r = iedd.ie_fp64_fma_rate(0)
+    assert 0.2 < r < 100.0, r
