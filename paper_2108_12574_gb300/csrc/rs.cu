@@ -689,27 +689,28 @@ __global__ void __launch_bounds__(kRsThreads) rs_elim(ElimArgs a, int first) {
         }
     }
     cluster_sync_all();
-    // X = B_rr^{-1} B_rs  (nr x k)
-    double *X = a.X + a.t_off[b];
+    // X = B_rr^{-1} B_rs, stored transposed: X^T = B_sr B_rr^{-1} (k x nr, B_rr^{-1} symmetric), so
+    // that the apply's threads read it coalesced
+    double *Xt = a.X + a.t_off[b];
     if (tiled) {
-        tile_mm(nr, k, nr, ViewRM{Bi, nr, cg}, ViewT{Bsr, nr, cg}, OutSet{X, k, 1.0}, false, 0, cr, CS, sh_a, sh_b);
+        tile_mm(k, nr, nr, ViewRM{Bsr, nr, cg}, ViewRM{Bi, nr, cg}, OutSet{Xt, nr, 1.0}, false, 0, cr, CS, sh_a, sh_b);
     } else {
-        for (long long e = g0; e < (long long)nr * k; e += gs) {
-            const int i = (int)(e / k), l = (int)(e % k);
+        for (long long e = g0; e < (long long)k * nr; e += gs) {
+            const int l = (int)(e / nr), i = (int)(e % nr);
             double v = 0.0;
-            for (int j = 0; j < nr; ++j) v += ldw(&Bi[(long long)i * nr + j], cg) * ldw(&Bsr[(long long)l * nr + j], cg);
-            X[e] = v;
+            for (int j = 0; j < nr; ++j) v += ldw(&Bsr[(long long)l * nr + j], cg) * ldw(&Bi[(long long)j * nr + i], cg);
+            Xt[e] = v;
         }
     }
     cluster_sync_all();
-    // B_ss = D_ss - B_sr X
+    // B_ss = D_ss - B_sr X  (X[i][m] = Xt[m][i])
     if (tiled) {
-        tile_mm(k, k, nr, ViewRM{Bsr, nr, cg}, ViewRM{X, k, cg}, OutSub{Bss, k, cg}, false, 0, cr, CS, sh_a, sh_b);
+        tile_mm(k, k, nr, ViewRM{Bsr, nr, cg}, ViewT{Xt, nr, cg}, OutSub{Bss, k, cg}, false, 0, cr, CS, sh_a, sh_b);
     } else {
         for (long long e = g0; e < (long long)k * k; e += gs) {
             const int l = (int)(e / k), m = (int)(e % k);
             double v = ldw(&Bss[e], cg);
-            for (int i = 0; i < nr; ++i) v -= ldw(&Bsr[(long long)l * nr + i], cg) * ldw(&X[(long long)i * k + m], cg);
+            for (int i = 0; i < nr; ++i) v -= ldw(&Bsr[(long long)l * nr + i], cg) * ldw(&Xt[(long long)m * nr + i], cg);
             Bss[e] = v;
         }
     }
@@ -723,6 +724,39 @@ __global__ void rs_gather(const double *__restrict__ r, long long ldr, const int
     const int c = blockIdx.y;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ntot; i += (long long)gridDim.x * blockDim.x)
         y[(long long)c * ntot + i] = r[(long long)c * ldr + pos2pt[i]];
+}
+
+// out[i] = sum_j M[i ld + j] x[j] for rows i = first, first + stride, ... < nrows: one warp per row,
+// four rows per pass so that four rows' loads are in flight; x in shared memory.  fin(i, sum) is
+// called by lane 0.
+template <class Fin>
+__device__ __forceinline__ void warp_rows_gemv(const double *__restrict__ M, long long ld, int nrows, int ncols,
+                                               const double *x, int first, int stride, Fin fin) {
+    const int lane = threadIdx.x & 31;
+    int i = first;
+    for (; i + 3 * stride < nrows; i += 4 * stride) {
+        const double *r0 = M + (long long)i * ld, *r1 = r0 + stride * ld, *r2 = r1 + stride * ld, *r3 = r2 + stride * ld;
+        double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+        for (int j = lane; j < ncols; j += 32) {
+            const double xj = x[j];
+            t0 += r0[j] * xj;
+            t1 += r1[j] * xj;
+            t2 += r2[j] * xj;
+            t3 += r3[j] * xj;
+        }
+        t0 = warp_allsum(t0);
+        t1 = warp_allsum(t1);
+        t2 = warp_allsum(t2);
+        t3 = warp_allsum(t3);
+        if (lane == 0) { fin(i, t0); fin(i + stride, t1); fin(i + 2 * stride, t2); fin(i + 3 * stride, t3); }
+    }
+    for (; i < nrows; i += stride) {
+        const double *r0 = M + (long long)i * ld;
+        double t0 = 0.0;
+        for (int j = lane; j < ncols; j += 32) t0 += r0[j] * x[j];
+        t0 = warp_allsum(t0);
+        if (lane == 0) fin(i, t0);
+    }
 }
 
 struct LevelArgs {
@@ -742,7 +776,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_down(LevelArgs a, double *__res
     const int *pos = a.pos + a.pos_off[b];
     const double *T = a.T + a.t_off[b], *Bsr = a.Bsr + a.t_off[b], *Bi = a.Binv + a.b_off[b];
     double *ys = sm, *u = ys + k, *v = u + nr;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, nwarps = blockDim.x >> 5;
     for (int l = tid; l < k; l += blockDim.x) ys[l] = yv[pos[l]];
     __syncthreads();
     for (int i = tid; i < nr; i += blockDim.x) {
@@ -752,21 +786,17 @@ __global__ void __launch_bounds__(kRsThreads) rs_down(LevelArgs a, double *__res
         u[i] = t;
     }
     __syncthreads();
-    for (int i = warp; i < nr; i += nwarps) {
-        const double *row = Bi + (long long)i * nr;
+    // v = B_rr^{-1} u: B_rr^{-1} is symmetric, so output j is column j -- one thread per output,
+    // loads coalesced across threads and no warp reductions (on GB300 those FP64 adds cost as much
+    // as the products)
+    for (int j = tid; j < nr; j += blockDim.x) {
         double t = 0.0;
-        for (int j = lane; j < nr; j += 32) t += row[j] * u[j];
-        t = warp_allsum(t);
-        if (lane == 0) v[i] = t;
+#pragma unroll 4
+        for (int i = 0; i < nr; ++i) t += Bi[(long long)i * nr + j] * u[i];
+        v[j] = t;
     }
     __syncthreads();
-    for (int l = warp; l < k; l += nwarps) {
-        const double *row = Bsr + (long long)l * nr;
-        double t = 0.0;
-        for (int j = lane; j < nr; j += 32) t += row[j] * v[j];
-        t = warp_allsum(t);
-        if (lane == 0) yv[pos[l]] = ys[l] - t;
-    }
+    warp_rows_gemv(Bsr, nr, k, nr, v, warp, nwarps, [&](int l, double t) { yv[pos[l]] = ys[l] - t; });
     for (int i = tid; i < nr; i += blockDim.x) yv[pos[k + i]] = v[i];
 }
 
@@ -777,27 +807,20 @@ __global__ void __launch_bounds__(kRsThreads) rs_up(LevelArgs a, double *__restr
     if (nr == 0) return;
     double *yv = y + (long long)blockIdx.y * ntot;
     const int *pos = a.pos + a.pos_off[b];
-    const double *T = a.T + a.t_off[b], *X = a.X + a.t_off[b];
+    const double *T = a.T + a.t_off[b], *Xt = a.X + a.t_off[b];
     double *as = sm, *ar = as + k;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, nwarps = blockDim.x >> 5;
     for (int l = tid; l < k; l += blockDim.x) as[l] = yv[pos[l]];
     __syncthreads();
-    for (int i = tid; i < nr; i += blockDim.x) {
+    for (int i = tid; i < nr; i += blockDim.x) {  // X a_s with X^T stored: coalesced over i
         double t = yv[pos[k + i]];
-        const double *row = X + (long long)i * k;
 #pragma unroll 8
-        for (int l = 0; l < k; ++l) t -= row[l] * as[l];
+        for (int l = 0; l < k; ++l) t -= Xt[(long long)l * nr + i] * as[l];
         ar[i] = t;
         yv[pos[k + i]] = t;
     }
     __syncthreads();
-    for (int l = warp; l < k; l += nwarps) {
-        const double *row = T + (long long)l * nr;
-        double t = 0.0;
-        for (int j = lane; j < nr; j += 32) t += row[j] * ar[j];
-        t = warp_allsum(t);
-        if (lane == 0) yv[pos[l]] = as[l] - t;
-    }
+    warp_rows_gemv(T, nr, k, nr, ar, warp, nwarps, [&](int l, double t) { yv[pos[l]] = as[l] - t; });
 }
 
 // y_t = S^{-1} y_t for every colour's last level: CTA (item) = kRsTopRows rows of one colour
@@ -811,19 +834,13 @@ __global__ void __launch_bounds__(kRsThreads) rs_top(const int2 *__restrict__ it
     const int c = it.x, r0 = it.y, S = nt[c];
     const double *yv = y + (long long)blockIdx.y * ntot;
     const int *ps = pos + pos_off[c];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, nwarps = blockDim.x >> 5;
     for (int j = tid; j < S; j += blockDim.x) sm[j] = yv[ps[j]];
     __syncthreads();
     const double *Si = Sinv + b_off[c];
     double *out = tmp + (long long)blockIdx.y * ttot + pos_off[c];
     const int r1 = min(r0 + kRsTopRows, S);
-    for (int i = r0 + warp; i < r1; i += nwarps) {
-        const double *row = Si + (long long)i * S;
-        double t = 0.0;
-        for (int j = lane; j < S; j += 32) t += row[j] * sm[j];
-        t = warp_allsum(t);
-        if (lane == 0) out[i] = t;
-    }
+    warp_rows_gemv(Si, S, r1, S, sm, r0 + warp, nwarps, [&](int i, double t) { out[i] = t; });
 }
 
 __global__ void rs_top_put(const int *__restrict__ pos, long long ttot, const double *__restrict__ tmp,
@@ -874,6 +891,8 @@ struct RSLevel {
     std::vector<int> colour, nb, k;
     std::vector<long long> pos_off;  // nreg + 1
     std::vector<int> pos;            // skeletons first (pivot order), then redundant
+    // device stores per region: T and B_sr (k x |r|), X stored as X^T = B_sr B_rr^{-1} (k x |r|),
+    // B_rr^{-1} (|r| x |r|), all row-major
     int *d_nb = nullptr, *d_k = nullptr, *d_pos = nullptr;
     long long *d_pos_off = nullptr, *d_t_off = nullptr, *d_b_off = nullptr;
     double *d_T = nullptr, *d_Bsr = nullptr, *d_X = nullptr, *d_Binv = nullptr;
