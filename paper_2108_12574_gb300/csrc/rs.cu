@@ -12,22 +12,26 @@
 // holds its points in ascending global order.  A region of a higher level owns the positions of
 // the skeletons its children kept (children in row-major K order, each in pivot order).
 //
-// Factor kernels (one CTA per region; one launch takes every region of a level, of all colours):
-// KR1 rs_id    the ID matrix Y of the region (proxy rows h^d K(x_proxy - y), in 2D one row of h^d,
-//              and the near-field rows of A), column-major in a global workspace, then column-
-//              pivoted Gram-Schmidt on it.  The pivot is the lowest-index column whose squared norm
-//              is at least top - min(top / 2, max(1e-10 top, 1e-13 nu0)) (top: the largest
-//              remaining squared norm, nu0: the largest before the first step); norms are
-//              recomputed after every step; it stops once top <= eps^2 nu0.  Writes the rank k, the
-//              permutation (skeletons in pivot order, then the redundant columns in order) and
-//              T = R11^{-1} R12 (k x |r|, row-major) by back substitution, one thread per column.
+// Factor kernels (one region per CTA, or per thread-block cluster of up to 8 CTAs on the levels
+// with few regions; one launch takes every region of a level, of all colours):
+// KR1 rs_id    the ID matrix Y of the region (proxy rows h^d K(x_proxy - y) -- at level 1 from a
+//              table per box side --, in 2D one row of h^d, and the near-field rows of A),
+//              column-major in a global workspace, then column-pivoted Gram-Schmidt on it, one warp
+//              per column.  The pivot is the lowest-index column whose squared norm is at least
+//              top - min(top / 2, max(1e-10 top, 1e-13 nu0)) (top: the largest remaining squared
+//              norm, nu0: the largest before the first step); norms are downdated and recomputed
+//              once they fall below 1e-2 of their last exact value; it stops once top <= eps^2 nu0.
+//              Writes the rank k, the permutation (skeletons in pivot order, then the redundant
+//              columns in order) and T = R11^{-1} R12 (k x |r|, row-major) by back substitution, one
+//              thread per column.
 // KR2 rs_elim  D in the permuted order (level 1: entries of A; above: the children's B_ss blocks
 //              and entries of A between children), M = D L_p on the redundant columns
 //              (M_:r = D_:r - D_:s T), B_rr = M_rr - T^T M_sr, B_sr = M_sr, the Cholesky factor of
 //              B_rr (right-looking in 32-column panels), its explicit inverse (L^{-1} by 32-row
-//              blocks, then L^{-T} L^{-1}), X = B_rr^{-1} B_rs and B_ss = D_ss - B_sr X; the products
-//              of regions with |r| >= 512 in shared-memory tiles.  The last Schur complement of every colour is the same kernel
-//              with k = 0.
+//              blocks, then L^{-T} L^{-1}), X = B_rr^{-1} B_rs (stored as X^T = B_sr B_rr^{-1}) and
+//              B_ss = D_ss - B_sr X; for regions with |r| >= 512 (a second instantiation) the
+//              products in shared-memory tiles.  The last Schur complement of every colour is the
+//              same kernel with k = 0.
 // Apply kernels (the regions of a level own disjoint positions, so one launch takes them all):
 // KR3 rs_gather (y = r at every position), rs_down (u_r = y_r - T^T y_s, v_r = B_rr^{-1} u_r,
 //     y_s -= B_sr v_r, v_r kept in place of y_r), rs_top + rs_top_put (y_t = S^{-1} y_t),
