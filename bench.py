@@ -78,8 +78,8 @@ NCU_K1W = {("c8970434ed8bad33", 32): {"traffic": 83382784, "tensor_pipe": 0.430}
 KZ_PRODUCTS_PER_PAIR = 21
 # ncu figures of the RS factor's level-1 launches per rs_source_hash(), 2D 256^2 with M = 32^2 (the
 # same region shapes as 1024^2): FP64 pipe activity of rs_id / rs_elim and their DRAM bytes
-NCU_RS = {"f0901695951aead9": {"fp64_pipe": {"rs_id": 0.734, "rs_elim": 0.725},
-                               "dram_bytes_256": {"rs_id": 1515883561, "rs_elim": 325845367}}}
+NCU_RS = {"ae5a2a3237e2c633": {"fp64_pipe": {"rs_id": 0.737, "rs_elim": 0.698},
+                               "dram_bytes_256": {"rs_id": 1516905437, "rs_elim": 398942244}}}
 # GB300's FP64 rate (nominal; no FP64 peak is measured on this machine)
 FP64_NOMINAL_TFLOPS = 1.25
 

@@ -698,24 +698,29 @@ __global__ void __launch_bounds__(kRsThreads) rs_elim(ElimArgs a, int first) {
     double *Xt = a.X + a.t_off[b];
     if (tiled) {
         tile_mm(k, nr, nr, ViewRM{Bsr, nr, cg}, ViewRM{Bi, nr, cg}, OutSet{Xt, nr, 1.0}, false, 0, cr, CS, sh_a, sh_b);
-    } else {
-        for (long long e = g0; e < (long long)k * nr; e += gs) {
-            const int l = (int)(e / nr), i = (int)(e % nr);
-            double v = 0.0;
-            for (int j = 0; j < nr; ++j) v += ldw(&Bsr[(long long)l * nr + j], cg) * ldw(&Bi[(long long)j * nr + i], cg);
-            Xt[e] = v;
-        }
-    }
-    cluster_sync_all();
-    // B_ss = D_ss - B_sr X  (X[i][m] = Xt[m][i])
-    if (tiled) {
+        cluster_sync_all();
+        // B_ss = D_ss - B_sr X  (X[i][m] = Xt[m][i])
         tile_mm(k, k, nr, ViewRM{Bsr, nr, cg}, ViewT{Xt, nr, cg}, OutSub{Bss, k, cg}, false, 0, cr, CS, sh_a, sh_b);
     } else {
+        // X (nr x k, row-major) in the dead L^{-1} storage: the loops below read it coalesced
+        double *X = D;
+        for (long long e = g0; e < (long long)nr * k; e += gs) {
+            const int i = (int)(e / k), l = (int)(e % k);
+            double v = 0.0;
+            for (int j = 0; j < nr; ++j) v += ldw(&Bi[(long long)i * nr + j], cg) * ldw(&Bsr[(long long)l * nr + j], cg);
+            X[e] = v;
+        }
+        cluster_sync_all();
+        // B_ss = D_ss - B_sr X, and X^T to the store
         for (long long e = g0; e < (long long)k * k; e += gs) {
             const int l = (int)(e / k), m = (int)(e % k);
             double v = ldw(&Bss[e], cg);
-            for (int i = 0; i < nr; ++i) v -= ldw(&Bsr[(long long)l * nr + i], cg) * ldw(&Xt[(long long)m * nr + i], cg);
+            for (int i = 0; i < nr; ++i) v -= ldw(&Bsr[(long long)l * nr + i], cg) * ldw(&X[(long long)i * k + m], cg);
             Bss[e] = v;
+        }
+        for (long long e = g0; e < (long long)k * nr; e += gs) {
+            const int l = (int)(e / nr), i = (int)(e % nr);
+            Xt[e] = ldw(&X[(long long)i * k + l], cg);
         }
     }
 }
