@@ -3,7 +3,8 @@
 Each case patches one plausible slip into oracle/rs_oracle.py -- a dropped term or a wrong sign
 in compress-then-eliminate (Eqs. e:al, e:alu, e:b), a skipped operator in the application, the
 Schur update left out of the merged block (Eq. e:schur), the near field left out of the proxy
-ID (Eq. e:id) -- and checks that the named pin of test_oracle_rs.py now fails.
+ID (Eq. e:id) in 2D and 3D, a 3D proxy sphere flattened onto its equator or cut to a polar cap --
+and checks that the named pin of test_oracle_rs.py now fails.
 """
 import numpy as np
 import pytest
@@ -125,3 +126,42 @@ def test_proxy_id_without_the_near_field_is_caught(monkeypatch):
         return orig(dim, n, lo, hi, own, np.zeros(0, dtype=np.int64), nproxy, rho, convention)
     monkeypatch.setattr(RS, "id_matrix", no_near)
     assert not _id_bound_pin()
+
+
+def _id_bound_pin_3d():
+    """test_proxy_id_meets_the_bound_on_the_full_block_3d over every region of one colour."""
+    dim, n, m, delta, eps = 3, 16, 4, 1, 1e-3
+    regs = RS.colour_regions(dim, n, m, delta)[0]
+    P = O.points(dim, n)
+    _, _, wgt, _ = O.grid_geometry(dim, n)
+    allp = np.concatenate([r["points"] for r in regs])
+    for r in regs:
+        p = r["points"]
+        q = np.setdiff1d(allp, p)
+        d = P[q][:, None, :] - P[p][None, :, :]
+        A = wgt * O.kernel(dim, np.sqrt((d * d).sum(axis=2)))
+        Y, _ = RS.id_matrix(dim, n, r["lo"], r["hi"], p, q, 128)
+        skel, red, T = RS.interp_decomp(Y, eps)
+        if not np.linalg.norm(A[:, red] - A[:, skel] @ T) <= eps * np.linalg.norm(A[:, red]):
+            return False
+    return True
+
+
+def test_unmutated_oracle_passes_the_3d_pin():
+    assert _id_bound_pin_3d()
+
+
+@pytest.mark.parametrize("variant", ["flattened", "polar_cap", "no_near"])
+def test_3d_proxy_slips_are_caught(monkeypatch, variant):
+    orig_dirs, orig_id = RS.proxy_directions, RS.id_matrix
+    if variant == "flattened":    # the sphere's points squashed onto its equator
+        monkeypatch.setattr(RS, "proxy_directions",
+                            lambda dim, P: orig_dirs(dim, P) * np.array([1.0, 1.0, 0.0]) if dim == 3 else orig_dirs(dim, P))
+    elif variant == "polar_cap":  # only the first eighth of the Fibonacci lattice
+        monkeypatch.setattr(RS, "proxy_directions",
+                            lambda dim, P: orig_dirs(dim, P)[: P // 8] if dim == 3 else orig_dirs(dim, P))
+    else:
+        def no_near(dim, n, lo, hi, own, others, nproxy, rho=1.5, convention=O.GRID_TEXT):
+            return orig_id(dim, n, lo, hi, own, np.zeros(0, dtype=np.int64), nproxy, rho, convention)
+        monkeypatch.setattr(RS, "id_matrix", no_near)
+    assert not _id_bound_pin_3d()
