@@ -241,3 +241,32 @@ def test_fp64_fma_rate_is_measured():
     above the RS factor's own achieved FP64 rate, below the FP32 tensor figures."""
     r = iedd.ie_fp64_fma_rate(0)
     assert 0.2 < r < 100.0, r
+
+
+PAPER_TABLE = os.path.join(os.path.dirname(__file__), "golden", "rs_paper_table.json")
+
+
+@pytest.mark.parametrize("table,key", [("t:cbd_strong_2d", "256_8"), ("t:cbd_strong_2d", "256_16"),
+                                       ("t:cbd_strong_2d", "256_32"), ("t:cbd_strong_2d", "256_64"),
+                                       ("t:cbd_weak_2d", "512_64"), ("t:cbd_weak_2d", "1024_128"),
+                                       ("t:cbd_strong_3d", "32_4")])
+def test_rs_matches_the_stored_oracle_runs_of_the_papers_rows(table, key):
+    """The oracle's runs of Sec. 5's CBD rows (tests/golden/rs_paper_table.json, written by a script
+    that calls only the oracle; table grid, eps = 1e-3, one layer of overlap, uniform[-1, 1] seed 0):
+    the GPU's last-level sizes equal the oracle's in every colour (the same skeleton decisions), and
+    its PCG count to 1e-12 is within 1 of the oracle's."""
+    row = json.load(open(PAPER_TABLE))[table][key]
+    n, m = (int(v) for v in key.split("_"))
+    dim = 3 if table.endswith("3d") else 2
+    prob = iedd.ie_discretize(dim, n, grid=iedd.IE_GRID_TABLE)
+    part = iedd.dd_partition(prob, m, 1, iedd.DD_CBD)
+    fac = iedd.dd_factor_rs(prob, part, eps=1e-3, nproxy=row["nproxy"])
+    _, top = iedd.dd_rs_info(fac)
+    assert top == row["oracle_S_all"]
+    N = n ** dim
+    f = torch.from_numpy(I.uniform_rhs(N, 0)).cuda()
+    u = torch.zeros(N, dtype=torch.float64, device="cuda")
+    rep = iedd.pcg_solve(prob, fac, f, u, tol=1e-12, precision=iedd.IE_FP64, inner=iedd.IE_FFT,
+                         residual=iedd.IE_FFT, max_it=400, check=False)[0]
+    assert abs(rep["iterations"] - row["oracle_n_it"]) <= 1, (rep["iterations"], row["oracle_n_it"])
+    fac.close()
