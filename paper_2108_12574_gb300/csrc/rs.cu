@@ -999,6 +999,187 @@ std::vector<std::pair<int, int>> chunks_by(const std::vector<long long> &cost) {
     return out;
 }
 
+// The host's plan of one level: its regions (every colour with more than one region left, colour by
+// colour), their natural DOFs as points, their near fields, ID row counts and box geometry.  Pure
+// host work, so the next level's plan can run beside this level's eliminations.
+struct LevelPlan {
+    std::vector<Region> regs;
+    std::vector<int> reg_col_index;            // index of each region within its colour's list
+    std::vector<long long> nat_off, near_off;  // per region: offsets into nat_pt / near_pt
+    std::vector<int> nat_pt, near_pt, rows, nbv;
+    std::vector<int4> geom;                    // (lo + hi - 1 per axis, longest side W)
+    std::string err;                           // set when a region exceeds the kernels' limits
+};
+
+void plan_level(const std::vector<std::vector<Region>> &cur, int dim, int nproxy, int mono, double rho,
+                const std::vector<int> &pos2pt, const std::vector<int> &lat, LevelPlan &L) {
+    L = LevelPlan();
+    const int ncol = (int)cur.size();
+    for (int c = 0; c < ncol; ++c) {
+        if (cur[(size_t)c].size() <= 1) continue;
+        for (size_t i = 0; i < cur[(size_t)c].size(); ++i) {
+            L.regs.push_back(cur[(size_t)c][i]);
+            L.reg_col_index.push_back((int)i);
+        }
+    }
+    if (L.regs.empty()) return;
+    const std::vector<Region> &regs = L.regs;
+    const int nreg = (int)regs.size();
+    // near fields: DOFs of the other regions of the colour strictly inside the proxy surface,
+    // decided in lattice units: |2 x - (lo + hi - 1)|^2 < (2 rho W)^2
+    L.nat_off.assign((size_t)nreg + 1, 0);
+    L.near_off.assign((size_t)nreg + 1, 0);
+    L.rows.assign((size_t)nreg, 0);
+    L.nbv.assign((size_t)nreg, 0);
+    L.geom.assign((size_t)nreg, int4());
+    // per colour: the extent of the regions along each axis as a function of that axis's
+    // colour-grid coordinate (true for the boxes and for every merged level), and K -> region
+    struct Axes {
+        int G[3] = {1, 1, 1};
+        std::vector<int> lo[3], hi[3], at;
+    };
+    std::vector<Axes> axes((size_t)ncol);
+    for (int c = 0; c < ncol; ++c) {
+        if (cur[(size_t)c].size() <= 1) continue;
+        Axes &A = axes[(size_t)c];
+        for (const Region &r : cur[(size_t)c])
+            for (int d = 0; d < 3; ++d) A.G[d] = std::max(A.G[d], r.K[(size_t)d] + 1);
+        for (int d = 0; d < 3; ++d) { A.lo[d].assign((size_t)A.G[d], 0); A.hi[d].assign((size_t)A.G[d], 0); }
+        A.at.assign((size_t)A.G[0] * A.G[1] * A.G[2], -1);
+        for (size_t i = 0; i < cur[(size_t)c].size(); ++i) {
+            const Region &r = cur[(size_t)c][i];
+            for (int d = 0; d < 3; ++d) {
+                A.lo[d][(size_t)r.K[(size_t)d]] = r.lo[(size_t)d];
+                A.hi[d][(size_t)r.K[(size_t)d]] = r.hi[(size_t)d];
+            }
+            A.at[((size_t)r.K[0] * A.G[1] + r.K[1]) * A.G[2] + r.K[2]] = (int)i;
+        }
+    }
+    for (int b = 0; b < nreg; ++b) {
+        const Region &r = regs[(size_t)b];
+        int W = 0, tc[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) {
+            W = std::max(W, r.hi[(size_t)d] - r.lo[(size_t)d]);
+            tc[d] = r.lo[(size_t)d] + r.hi[(size_t)d] - 1;
+        }
+        L.geom[(size_t)b] = make_int4(tc[0], tc[1], tc[2], W);
+        for (int pos : r.nat) L.nat_pt.push_back(pos2pt[(size_t)pos]);
+        L.nat_off[(size_t)b + 1] = (long long)L.nat_pt.size();
+        L.nbv[(size_t)b] = (int)r.nat.size();
+    }
+    // the near fields of the regions are independent: host threads take contiguous ranges
+    std::vector<std::vector<int>> nears((size_t)nreg);
+    auto near_range = [&](int b0, int b1) {
+        for (int b = b0; b < b1; ++b) {
+            const Region &r = regs[(size_t)b];
+            const int4 gm = L.geom[(size_t)b];
+            const int W = gm.w, tc[3] = {gm.x, gm.y, gm.z};
+            const double bound = (2.0 * rho * W) * (2.0 * rho * W);
+            const double R = rho * W;  // bounding-box tests first (lattice units)
+            const Axes &A = axes[(size_t)r.colour];
+            std::vector<int> cand[3];
+            std::vector<double> gap2[3];
+            for (int d = 0; d < 3; ++d) {
+                for (int K = 0; K < A.G[d]; ++K) {
+                    double g = 0.0;
+                    if (d < dim) {
+                        const double c = 0.5 * tc[d];
+                        g = std::max({(double)A.lo[d][(size_t)K] - c, 0.0, c - (double)(A.hi[d][(size_t)K] - 1)});
+                    }
+                    if (g < R) { cand[d].push_back(K); gap2[d].push_back(g * g); }
+                }
+            }
+            std::vector<int> &out = nears[(size_t)b];
+            for (size_t i0 = 0; i0 < cand[0].size(); ++i0)
+                for (size_t i1 = 0; i1 < cand[1].size(); ++i1)
+                    for (size_t i2 = 0; i2 < cand[2].size(); ++i2) {
+                        if (gap2[0][i0] + gap2[1][i1] + gap2[2][i2] >= R * R) continue;
+                        const int oi = A.at[((size_t)cand[0][i0] * A.G[1] + cand[1][i1]) * A.G[2] + cand[2][i2]];
+                        if (oi < 0 || oi == L.reg_col_index[(size_t)b]) continue;
+                        const Region &o = cur[(size_t)r.colour][(size_t)oi];
+                        for (int pos : o.nat) {
+                            double d2 = 0.0;
+                            for (int d = 0; d < dim; ++d) {
+                                const double t = 2.0 * lat[(size_t)pos * 3 + d] - tc[d];
+                                d2 += t * t;
+                            }
+                            if (d2 < bound) out.push_back(pos2pt[(size_t)pos]);
+                        }
+                    }
+        }
+    };
+    {
+        const int nth = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), nreg / 64));
+        std::vector<std::thread> pool;
+        int spawned = 1;  // ranges [0, spawned) of nth run on threads (range 0 here); the rest below
+        for (int t = 1; t < nth; ++t) {
+            try {
+                pool.emplace_back(near_range, (int)((long long)nreg * t / nth), (int)((long long)nreg * (t + 1) / nth));
+                spawned = t + 1;
+            } catch (const std::system_error &) {
+                break;  // no more threads: the remaining ranges run on this one
+            }
+        }
+        near_range(0, (int)((long long)nreg / nth));
+        for (int t = spawned; t < nth; ++t)
+            near_range((int)((long long)nreg * t / nth), (int)((long long)nreg * (t + 1) / nth));
+        for (auto &th : pool) th.join();
+    }
+    for (int b = 0; b < nreg; ++b) {
+        L.near_pt.insert(L.near_pt.end(), nears[(size_t)b].begin(), nears[(size_t)b].end());
+        L.near_off[(size_t)b + 1] = (long long)L.near_pt.size();
+        L.rows[(size_t)b] = nproxy + mono + (int)nears[(size_t)b].size();
+        if (L.nbv[(size_t)b] > kRsMaxDofs || L.rows[(size_t)b] > kRsMaxRows) {
+            L.err = "dd_factor_rs: a region has " + std::to_string(L.nbv[(size_t)b]) + " DOFs and " +
+                    std::to_string(L.rows[(size_t)b]) + " ID rows (limits " + std::to_string(kRsMaxDofs) + ", " +
+                    std::to_string(kRsMaxRows) + ")";
+            return;
+        }
+    }
+}
+
+// The next level's regions: per colour with more than one region, the regions merged 2^d at a time
+// by K >> 1 (row-major), each holding its children's skeletons in the children's level order (the
+// children are the level's regions `regs`, whose ranks kv and ID permutations perm are known);
+// a colour with one region left keeps it.
+std::vector<std::vector<Region>> merge_level(const std::vector<std::vector<Region>> &cur,
+                                             const std::vector<Region> &regs, const std::vector<int> &kv,
+                                             const std::vector<int> &perm, const std::vector<long long> &nat_off) {
+    const int ncol = (int)cur.size(), nreg = (int)regs.size();
+    std::vector<std::vector<Region>> next((size_t)ncol);
+    for (int c = 0; c < ncol; ++c) {
+        if (cur[(size_t)c].size() <= 1) { next[(size_t)c] = cur[(size_t)c]; continue; }
+        std::map<std::array<int, 3>, std::vector<int>> groups;
+        for (size_t i = 0; i < cur[(size_t)c].size(); ++i) {
+            const Region &r = cur[(size_t)c][i];
+            groups[{r.K[0] >> 1, r.K[1] >> 1, r.K[2] >> 1}].push_back((int)i);
+        }
+        // the level's regions of colour c, in order: find this colour's first region index
+        int base = 0;
+        while (base < nreg && regs[(size_t)base].colour != c) ++base;
+        for (auto &g : groups) {
+            Region r;
+            r.colour = c;
+            r.K = g.first;
+            for (int d = 0; d < 3; ++d) { r.lo[(size_t)d] = INT_MAX; r.hi[(size_t)d] = INT_MIN; }
+            for (int i : g.second) {
+                const Region &ch = cur[(size_t)c][(size_t)i];
+                const int b = base + i;
+                r.child.push_back(i);
+                r.child_start.push_back((int)r.nat.size());
+                for (int t = 0; t < kv[(size_t)b]; ++t)
+                    r.nat.push_back(ch.nat[(size_t)perm[(size_t)(nat_off[(size_t)b] + t)]]);
+                for (int d = 0; d < 3; ++d) {
+                    r.lo[(size_t)d] = std::min(r.lo[(size_t)d], ch.lo[(size_t)d]);
+                    r.hi[(size_t)d] = std::max(r.hi[(size_t)d], ch.hi[(size_t)d]);
+                }
+            }
+            next[(size_t)c].push_back(std::move(r));
+        }
+    }
+    return next;
+}
+
 // The elimination (KR2) of `regs` (level 1 when prev == nullptr), whose ranks and permutations are
 // known; fills lvl's stores and, per region, the device address of its B_ss.
 int run_elim(const ie_problem *p, const std::vector<Region> &regs, const std::vector<int> &perm_h,
@@ -1209,130 +1390,16 @@ static int factor_rs_impl(const ie_problem *p, const dd_partition_t *s, const rs
     const int mono = dim == 2 ? 1 : 0;
     int status = IE_OK;
 
+    LevelPlan plan;
+    plan_level(cur, dim, nproxy, mono, rho, rs->pos2pt, lat, plan);
     for (int level = 0; status == IE_OK; ++level) {
-        // regions of this level: every colour with more than one region left
-        std::vector<Region> regs;
-        std::vector<int> reg_col_index;
-        for (int c = 0; c < ncol; ++c) {
-            if (cur[(size_t)c].size() <= 1) continue;
-            for (size_t i = 0; i < cur[(size_t)c].size(); ++i) {
-                regs.push_back(cur[(size_t)c][i]);
-                reg_col_index.push_back((int)i);
-            }
-        }
-        if (regs.empty()) break;
+        if (!plan.err.empty()) { err = plan.err; status = IE_ERR_ARG; break; }
+        if (plan.regs.empty()) break;
+        const std::vector<Region> &regs = plan.regs;
+        const std::vector<long long> &nat_off = plan.nat_off, &near_off = plan.near_off;
+        const std::vector<int> &nat_pt = plan.nat_pt, &near_pt = plan.near_pt, &rows = plan.rows, &nbv = plan.nbv;
+        const std::vector<int4> &geom = plan.geom;
         const int nreg = (int)regs.size();
-        // near fields: DOFs of the other regions of the colour strictly inside the proxy surface,
-        // decided in lattice units: |2 x - (lo + hi - 1)|^2 < (2 rho W)^2
-        std::vector<long long> nat_off((size_t)nreg + 1, 0), near_off((size_t)nreg + 1, 0);
-        std::vector<int> nat_pt, near_pt, rows((size_t)nreg), nbv((size_t)nreg);
-        std::vector<int4> geom((size_t)nreg);
-        // per colour: the extent of the regions along each axis as a function of that axis's
-        // colour-grid coordinate (true for the boxes and for every merged level), and K -> region
-        struct Axes {
-            int G[3] = {1, 1, 1};
-            std::vector<int> lo[3], hi[3], at;
-        };
-        std::vector<Axes> axes((size_t)ncol);
-        for (int c = 0; c < ncol; ++c) {
-            if (cur[(size_t)c].size() <= 1) continue;
-            Axes &A = axes[(size_t)c];
-            for (const Region &r : cur[(size_t)c])
-                for (int d = 0; d < 3; ++d) A.G[d] = std::max(A.G[d], r.K[(size_t)d] + 1);
-            for (int d = 0; d < 3; ++d) { A.lo[d].assign((size_t)A.G[d], 0); A.hi[d].assign((size_t)A.G[d], 0); }
-            A.at.assign((size_t)A.G[0] * A.G[1] * A.G[2], -1);
-            for (size_t i = 0; i < cur[(size_t)c].size(); ++i) {
-                const Region &r = cur[(size_t)c][i];
-                for (int d = 0; d < 3; ++d) {
-                    A.lo[d][(size_t)r.K[(size_t)d]] = r.lo[(size_t)d];
-                    A.hi[d][(size_t)r.K[(size_t)d]] = r.hi[(size_t)d];
-                }
-                A.at[((size_t)r.K[0] * A.G[1] + r.K[1]) * A.G[2] + r.K[2]] = (int)i;
-            }
-        }
-        for (int b = 0; b < nreg; ++b) {
-            const Region &r = regs[(size_t)b];
-            int W = 0, tc[3] = {0, 0, 0};
-            for (int d = 0; d < dim; ++d) {
-                W = std::max(W, r.hi[(size_t)d] - r.lo[(size_t)d]);
-                tc[d] = r.lo[(size_t)d] + r.hi[(size_t)d] - 1;
-            }
-            geom[(size_t)b] = make_int4(tc[0], tc[1], tc[2], W);
-            for (int pos : r.nat) nat_pt.push_back(rs->pos2pt[(size_t)pos]);
-            nat_off[(size_t)b + 1] = (long long)nat_pt.size();
-            nbv[(size_t)b] = (int)r.nat.size();
-        }
-        // the near fields of the regions are independent: host threads take contiguous ranges
-        std::vector<std::vector<int>> nears((size_t)nreg);
-        auto near_range = [&](int b0, int b1) {
-            for (int b = b0; b < b1; ++b) {
-                const Region &r = regs[(size_t)b];
-                const int4 gm = geom[(size_t)b];
-                const int W = gm.w, tc[3] = {gm.x, gm.y, gm.z};
-                const double bound = (2.0 * rho * W) * (2.0 * rho * W);
-                const double R = rho * W;  // bounding-box tests first (lattice units)
-                const Axes &A = axes[(size_t)r.colour];
-                std::vector<int> cand[3];
-                std::vector<double> gap2[3];
-                for (int d = 0; d < 3; ++d) {
-                    for (int K = 0; K < A.G[d]; ++K) {
-                        double g = 0.0;
-                        if (d < dim) {
-                            const double c = 0.5 * tc[d];
-                            g = std::max({(double)A.lo[d][(size_t)K] - c, 0.0, c - (double)(A.hi[d][(size_t)K] - 1)});
-                        }
-                        if (g < R) { cand[d].push_back(K); gap2[d].push_back(g * g); }
-                    }
-                }
-                std::vector<int> &out = nears[(size_t)b];
-                for (size_t i0 = 0; i0 < cand[0].size(); ++i0)
-                    for (size_t i1 = 0; i1 < cand[1].size(); ++i1)
-                        for (size_t i2 = 0; i2 < cand[2].size(); ++i2) {
-                            if (gap2[0][i0] + gap2[1][i1] + gap2[2][i2] >= R * R) continue;
-                            const int oi = A.at[((size_t)cand[0][i0] * A.G[1] + cand[1][i1]) * A.G[2] + cand[2][i2]];
-                            if (oi < 0 || oi == reg_col_index[(size_t)b]) continue;
-                            const Region &o = cur[(size_t)r.colour][(size_t)oi];
-                            for (int pos : o.nat) {
-                                double d2 = 0.0;
-                                for (int d = 0; d < dim; ++d) {
-                                    const double t = 2.0 * lat[(size_t)pos * 3 + d] - tc[d];
-                                    d2 += t * t;
-                                }
-                                if (d2 < bound) out.push_back(rs->pos2pt[(size_t)pos]);
-                            }
-                        }
-            }
-        };
-        {
-            const int nth = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), nreg / 64));
-            std::vector<std::thread> pool;
-            int spawned = 1;  // ranges [0, spawned) of nth run on threads (range 0 here); the rest below
-            for (int t = 1; t < nth; ++t) {
-                try {
-                    pool.emplace_back(near_range, (int)((long long)nreg * t / nth), (int)((long long)nreg * (t + 1) / nth));
-                    spawned = t + 1;
-                } catch (const std::system_error &) {
-                    break;  // no more threads: the remaining ranges run on this one
-                }
-            }
-            near_range(0, (int)((long long)nreg / nth));
-            for (int t = spawned; t < nth; ++t)
-                near_range((int)((long long)nreg * t / nth), (int)((long long)nreg * (t + 1) / nth));
-            for (auto &th : pool) th.join();
-        }
-        for (int b = 0; b < nreg; ++b) {
-            near_pt.insert(near_pt.end(), nears[(size_t)b].begin(), nears[(size_t)b].end());
-            near_off[(size_t)b + 1] = (long long)near_pt.size();
-            rows[(size_t)b] = nproxy + mono + (int)nears[(size_t)b].size();
-            if (nbv[(size_t)b] > kRsMaxDofs || rows[(size_t)b] > kRsMaxRows) {
-                err = "dd_factor_rs: a region has " + std::to_string(nbv[(size_t)b]) + " DOFs and " +
-                      std::to_string(rows[(size_t)b]) + " ID rows (limits " + std::to_string(kRsMaxDofs) + ", " +
-                      std::to_string(kRsMaxRows) + ")";
-                status = IE_ERR_ARG;
-                break;
-            }
-        }
-        if (status != IE_OK) break;
         // level 1: the proxy rows from one table per distinct longest side W (the boxes share a few)
         double *d_ptab = nullptr;
         long long *d_ptaboff = nullptr;
@@ -1376,6 +1443,11 @@ static int factor_rs_impl(const ie_problem *p, const dd_partition_t *s, const rs
             dfree(d_natoff, st); dfree(d_nearoff, st); dfree(d_ttoff, st); dfree(d_yoff, st); dfree(d_coff, st);
             dfree(d_geom, st); dfree(d_Tt, st); dfree(d_Y, st); dfree(d_C, st); dfree(d_ptab, st); dfree(d_ptaboff, st);
         };
+        std::vector<std::vector<Region>> next_cur;
+        LevelPlan next_plan;
+        std::string plan_err;
+        int plan_code = IE_OK;
+        bool next_level = false;
         do {
             if ((status = to_dev(&d_nb, nbv, st)) != IE_OK) break;
             if ((status = to_dev(&d_rows, rows, st)) != IE_OK) break;
@@ -1438,12 +1510,34 @@ static int factor_rs_impl(const ie_problem *p, const dd_partition_t *s, const rs
                 const double r = rows[(size_t)b], nbd = nbv[(size_t)b], kd = kv[(size_t)b];
                 rs->id_flops += 2.0 * r * nbd + 4.0 * r * (kd * nbd - kd * (kd + 1.0) / 2.0) + (nbd - kd) * kd * kd;
             }
+            // the next level's regions and plan (host work) on a worker thread, beside KR2 on the
+            // device: both only read this level's regions, ranks and permutations
+            auto plan_next = [&]() {
+                try {
+                    next_cur = merge_level(cur, regs, kv, perm, nat_off);
+                    plan_level(next_cur, dim, nproxy, mono, rho, rs->pos2pt, lat, next_plan);
+                } catch (const std::bad_alloc &) {
+                    plan_err = "dd_factor_rs: out of host memory";
+                    plan_code = IE_ERR_OOM;
+                } catch (const std::exception &e) {
+                    plan_err = std::string("dd_factor_rs: ") + e.what();
+                    plan_code = IE_ERR_ARG;
+                }
+            };
+            std::thread planner;
+            try {
+                planner = std::thread(plan_next);
+            } catch (const std::system_error &) {
+                plan_next();  // no thread: plan here, before KR2
+            }
+            struct Joiner {  // joins the planner on every way out of this block
+                std::thread &t;
+                ~Joiner() { if (t.joinable()) t.join(); }
+            } joiner{planner};
+            auto join_planner = [&]() { if (planner.joinable()) planner.join(); };
             // KR2
             std::vector<unsigned long long> pbss;
             std::vector<int> pk;
-            for (const Region &r : regs) {
-                (void)r;
-            }
             // the children of this level's regions live in prev_* of their colour; flatten per region
             std::vector<Region> eregs = regs;
             for (int b = 0; b < nreg; ++b) {
@@ -1460,7 +1554,9 @@ static int factor_rs_impl(const ie_problem *p, const dd_partition_t *s, const rs
             status = run_elim(p, eregs, perm, nat_off, d_natpt, d_perm, kv, pbss, pk, d_Tt, tt_off, lvl, &d_bss, baddr,
                               st, err, rs->elim_ms, rs->elim_flops);
             if (d_bss) bss_bufs.push_back(d_bss);
+            join_planner();
             if (status != IE_OK) { lvl.release(); break; }
+            if (plan_code != IE_OK) { err = plan_err; status = plan_code; lvl.release(); break; }
             // the apply's view of the level
             lvl.nreg = nreg;
             lvl.pos_off.assign((size_t)nreg + 1, 0);
@@ -1481,7 +1577,7 @@ static int factor_rs_impl(const ie_problem *p, const dd_partition_t *s, const rs
                 break;
             }
             rs->levels.push_back(std::move(lvl));
-            // merge 2^d regions by K >> 1 (row-major), children in their level order
+            // the previous level's ranks and B_ss addresses, per colour, for the next level
             for (int c = 0; c < ncol; ++c) {
                 if (cur[(size_t)c].size() <= 1) continue;
                 rs->colour_levels[(size_t)c] = level + 1;
@@ -1493,40 +1589,12 @@ static int factor_rs_impl(const ie_problem *p, const dd_partition_t *s, const rs
                 prev_k[(size_t)c].push_back(kv[(size_t)b]);
                 prev_bss[(size_t)c].push_back(baddr[(size_t)b]);
             }
-            for (int c = 0; c < ncol; ++c) {
-                if (cur[(size_t)c].size() <= 1) continue;
-                std::map<std::array<int, 3>, std::vector<int>> groups;
-                for (size_t i = 0; i < cur[(size_t)c].size(); ++i) {
-                    const Region &r = cur[(size_t)c][i];
-                    groups[{r.K[0] >> 1, r.K[1] >> 1, r.K[2] >> 1}].push_back((int)i);
-                }
-                std::vector<Region> nxt;
-                // the level's regions of colour c, in order: find this colour's first region index
-                int base = 0;
-                while (base < nreg && regs[(size_t)base].colour != c) ++base;
-                for (auto &g : groups) {
-                    Region r;
-                    r.colour = c;
-                    r.K = g.first;
-                    for (int d = 0; d < 3; ++d) { r.lo[(size_t)d] = INT_MAX; r.hi[(size_t)d] = INT_MIN; }
-                    for (int i : g.second) {
-                        const Region &ch = cur[(size_t)c][(size_t)i];
-                        const int b = base + i;
-                        r.child.push_back(i);
-                        r.child_start.push_back((int)r.nat.size());
-                        for (int t = 0; t < kv[(size_t)b]; ++t)
-                            r.nat.push_back(ch.nat[(size_t)perm[(size_t)(nat_off[(size_t)b] + t)]]);
-                        for (int d = 0; d < 3; ++d) {
-                            r.lo[(size_t)d] = std::min(r.lo[(size_t)d], ch.lo[(size_t)d]);
-                            r.hi[(size_t)d] = std::max(r.hi[(size_t)d], ch.hi[(size_t)d]);
-                        }
-                    }
-                    nxt.push_back(std::move(r));
-                }
-                cur[(size_t)c] = std::move(nxt);
-            }
+            cur = std::move(next_cur);
+            next_level = true;
         } while (0);
         lfree();
+        if (!next_level) break;
+        plan = std::move(next_plan);
     }
     if (status != IE_OK) { free_bss(); return fail(status); }
 
