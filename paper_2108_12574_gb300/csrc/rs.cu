@@ -44,7 +44,10 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <map>
+#include <memory>
+#include <mutex>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -999,6 +1002,102 @@ std::vector<std::pair<int, int>> chunks_by(const std::vector<long long> &cost) {
     return out;
 }
 
+// Joins a host thread on every way out of a scope.
+struct JoinOnExit {
+    std::thread &t;
+    ~JoinOnExit() { if (t.joinable()) t.join(); }
+};
+
+// f(b0, b1) over [0, n) in contiguous ranges, on up to hardware_concurrency host threads of at
+// least `grain` items each; a range whose thread cannot be started runs on the caller.  The first
+// exception a range throws is rethrown here once every thread has ended.
+template <class F> void host_ranges(long long n, long long grain, const F &f) {
+    const long long hc = std::max(1u, std::thread::hardware_concurrency());
+    const long long nth = std::max(1LL, std::min(hc, n / std::max(grain, 1LL)));
+    std::exception_ptr first;
+    std::mutex mu;
+    auto guarded = [&](long long b0, long long b1) {
+        try {
+            f(b0, b1);
+        } catch (...) {
+            std::lock_guard<std::mutex> g(mu);
+            if (!first) first = std::current_exception();
+        }
+    };
+    std::vector<std::thread> pool;
+    long long spawned = 1;  // ranges [0, spawned) run on threads (range 0 here); the rest below
+    for (long long t = 1; t < nth; ++t) {
+        try {
+            pool.emplace_back(guarded, n * t / nth, n * (t + 1) / nth);
+            spawned = t + 1;
+        } catch (const std::system_error &) {
+            break;
+        }
+    }
+    guarded(0LL, n / nth);
+    for (long long t = spawned; t < nth; ++t) guarded(n * t / nth, n * (t + 1) / nth);
+    for (auto &th : pool) th.join();
+    if (first) std::rethrow_exception(first);
+}
+
+// The level-1 regions: the extended boxes of each colour, row-major by K = k / 2 (k the box's index
+// along an axis, colour bit k mod 2), each holding its positions in ascending global order.
+// pos2pt[q] is the point at position q; lat[3 q + d] its lattice coordinate along axis d (0 for
+// d >= dim).  Returns the number of positions.
+long long level1_regions(int dim, int n, int m, int delta, std::vector<std::vector<Region>> &cur,
+                         std::vector<int> &pos2pt, std::unique_ptr<int[]> &lat) {
+    const int ncol = 1 << dim, w = n / m;
+    cur.assign((size_t)ncol, std::vector<Region>());
+    std::vector<std::pair<int, int>> flat;  // (colour, index) of every region
+    std::vector<long long> q0(1, 0);        // first position of every region
+    for (int c = 0; c < ncol; ++c) {
+        int cd[3] = {0, 0, 0}, Gd[3] = {1, 1, 1};
+        for (int d = 0; d < dim; ++d) {
+            cd[d] = (c >> (dim - 1 - d)) & 1;
+            Gd[d] = (m - cd[d] + 1) / 2;
+        }
+        for (int K0 = 0; K0 < Gd[0]; ++K0)
+            for (int K1 = 0; K1 < Gd[1]; ++K1)
+                for (int K2 = 0; K2 < (dim == 3 ? Gd[2] : 1); ++K2) {
+                    Region r;
+                    r.colour = c;
+                    const int Ks[3] = {K0, K1, K2};
+                    long long size = 1;
+                    for (int d = 0; d < dim; ++d) {
+                        const int kk = 2 * Ks[d] + cd[d];
+                        r.K[(size_t)d] = Ks[d];
+                        r.lo[(size_t)d] = std::max(kk * w - delta, 0);
+                        r.hi[(size_t)d] = std::min((kk + 1) * w + delta, n);
+                        size *= r.hi[(size_t)d] - r.lo[(size_t)d];
+                    }
+                    flat.emplace_back(c, (int)cur[(size_t)c].size());
+                    q0.push_back(q0.back() + size);
+                    cur[(size_t)c].push_back(std::move(r));
+                }
+    }
+    const long long ntot = q0.back();
+    pos2pt.resize((size_t)ntot);
+    lat.reset(new int[(size_t)ntot * 3]);
+    int *L = lat.get();
+    host_ranges((long long)flat.size(), 64, [&](long long b0, long long b1) {
+        for (long long b = b0; b < b1; ++b) {
+            Region &r = cur[(size_t)flat[(size_t)b].first][(size_t)flat[(size_t)b].second];
+            long long q = q0[(size_t)b];
+            r.nat.resize((size_t)(q0[(size_t)b + 1] - q));
+            for (int i = r.lo[0]; i < r.hi[0]; ++i)
+                for (int j = r.lo[1]; j < r.hi[1]; ++j)
+                    for (int l = r.lo[2]; l < r.hi[2]; ++l, ++q) {
+                        r.nat[(size_t)(q - q0[(size_t)b])] = (int)q;
+                        pos2pt[(size_t)q] = dim == 2 ? i * n + j : (i * n + j) * n + l;
+                        L[q * 3] = i;
+                        L[q * 3 + 1] = j;
+                        L[q * 3 + 2] = dim == 3 ? l : 0;
+                    }
+        }
+    });
+    return ntot;
+}
+
 // The host's plan of one level: its regions (every colour with more than one region left, colour by
 // colour), their natural DOFs as points, their near fields, ID row counts and box geometry.  Pure
 // host work, so the next level's plan can run beside this level's eliminations.
@@ -1012,26 +1111,31 @@ struct LevelPlan {
 };
 
 void plan_level(const std::vector<std::vector<Region>> &cur, int dim, int nproxy, int mono, double rho,
-                const std::vector<int> &pos2pt, const std::vector<int> &lat, LevelPlan &L) {
+                const std::vector<int> &pos2pt, const int *lat, LevelPlan &L) {
     L = LevelPlan();
     const int ncol = (int)cur.size();
+    std::vector<std::pair<int, int>> src;  // (colour, index) of every region of the level
     for (int c = 0; c < ncol; ++c) {
         if (cur[(size_t)c].size() <= 1) continue;
-        for (size_t i = 0; i < cur[(size_t)c].size(); ++i) {
-            L.regs.push_back(cur[(size_t)c][i]);
-            L.reg_col_index.push_back((int)i);
-        }
+        for (size_t i = 0; i < cur[(size_t)c].size(); ++i) src.emplace_back(c, (int)i);
     }
-    if (L.regs.empty()) return;
-    const std::vector<Region> &regs = L.regs;
-    const int nreg = (int)regs.size();
-    // near fields: DOFs of the other regions of the colour strictly inside the proxy surface,
-    // decided in lattice units: |2 x - (lo + hi - 1)|^2 < (2 rho W)^2
+    if (src.empty()) return;
+    const int nreg = (int)src.size();
+    L.regs.resize((size_t)nreg);
+    L.reg_col_index.resize((size_t)nreg);
     L.nat_off.assign((size_t)nreg + 1, 0);
     L.near_off.assign((size_t)nreg + 1, 0);
     L.rows.assign((size_t)nreg, 0);
     L.nbv.assign((size_t)nreg, 0);
     L.geom.assign((size_t)nreg, int4());
+    for (int b = 0; b < nreg; ++b) {
+        const Region &r = cur[(size_t)src[(size_t)b].first][(size_t)src[(size_t)b].second];
+        L.reg_col_index[(size_t)b] = src[(size_t)b].second;
+        L.nbv[(size_t)b] = (int)r.nat.size();
+        L.nat_off[(size_t)b + 1] = L.nat_off[(size_t)b] + (long long)r.nat.size();
+    }
+    L.nat_pt.resize((size_t)L.nat_off.back());
+    const std::vector<Region> &regs = L.regs;
     // per colour: the extent of the regions along each axis as a function of that axis's
     // colour-grid coordinate (true for the boxes and for every merged level), and K -> region
     struct Axes {
@@ -1055,22 +1159,27 @@ void plan_level(const std::vector<std::vector<Region>> &cur, int dim, int nproxy
             A.at[((size_t)r.K[0] * A.G[1] + r.K[1]) * A.G[2] + r.K[2]] = (int)i;
         }
     }
-    for (int b = 0; b < nreg; ++b) {
-        const Region &r = regs[(size_t)b];
-        int W = 0, tc[3] = {0, 0, 0};
-        for (int d = 0; d < dim; ++d) {
-            W = std::max(W, r.hi[(size_t)d] - r.lo[(size_t)d]);
-            tc[d] = r.lo[(size_t)d] + r.hi[(size_t)d] - 1;
-        }
-        L.geom[(size_t)b] = make_int4(tc[0], tc[1], tc[2], W);
-        for (int pos : r.nat) L.nat_pt.push_back(pos2pt[(size_t)pos]);
-        L.nat_off[(size_t)b + 1] = (long long)L.nat_pt.size();
-        L.nbv[(size_t)b] = (int)r.nat.size();
-    }
-    // the near fields of the regions are independent: host threads take contiguous ranges
+    // the regions are independent: host threads take contiguous ranges of them, first for their
+    // copies, points and geometry, then for their near fields -- DOFs of the other regions of the
+    // colour strictly inside the proxy surface, decided in lattice units:
+    // |2 x - (lo + hi - 1)|^2 < (2 rho W)^2
     std::vector<std::vector<int>> nears((size_t)nreg);
-    auto near_range = [&](int b0, int b1) {
-        for (int b = b0; b < b1; ++b) {
+    host_ranges(nreg, 64, [&](long long b0, long long b1) {
+        for (long long b = b0; b < b1; ++b) {
+            Region &r = L.regs[(size_t)b];
+            r = cur[(size_t)src[(size_t)b].first][(size_t)src[(size_t)b].second];
+            int W = 0, tc[3] = {0, 0, 0};
+            for (int d = 0; d < dim; ++d) {
+                W = std::max(W, r.hi[(size_t)d] - r.lo[(size_t)d]);
+                tc[d] = r.lo[(size_t)d] + r.hi[(size_t)d] - 1;
+            }
+            L.geom[(size_t)b] = make_int4(tc[0], tc[1], tc[2], W);
+            int *np = L.nat_pt.data() + L.nat_off[(size_t)b];
+            for (size_t t = 0; t < r.nat.size(); ++t) np[t] = pos2pt[(size_t)r.nat[t]];
+        }
+    });
+    host_ranges(nreg, 64, [&](long long b0, long long b1) {
+        for (long long b = b0; b < b1; ++b) {
             const Region &r = regs[(size_t)b];
             const int4 gm = L.geom[(size_t)b];
             const int W = gm.w, tc[3] = {gm.x, gm.y, gm.z};
@@ -1107,27 +1216,9 @@ void plan_level(const std::vector<std::vector<Region>> &cur, int dim, int nproxy
                         }
                     }
         }
-    };
-    {
-        const int nth = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), nreg / 64));
-        std::vector<std::thread> pool;
-        int spawned = 1;  // ranges [0, spawned) of nth run on threads (range 0 here); the rest below
-        for (int t = 1; t < nth; ++t) {
-            try {
-                pool.emplace_back(near_range, (int)((long long)nreg * t / nth), (int)((long long)nreg * (t + 1) / nth));
-                spawned = t + 1;
-            } catch (const std::system_error &) {
-                break;  // no more threads: the remaining ranges run on this one
-            }
-        }
-        near_range(0, (int)((long long)nreg / nth));
-        for (int t = spawned; t < nth; ++t)
-            near_range((int)((long long)nreg * t / nth), (int)((long long)nreg * (t + 1) / nth));
-        for (auto &th : pool) th.join();
-    }
+    });
     for (int b = 0; b < nreg; ++b) {
-        L.near_pt.insert(L.near_pt.end(), nears[(size_t)b].begin(), nears[(size_t)b].end());
-        L.near_off[(size_t)b + 1] = (long long)L.near_pt.size();
+        L.near_off[(size_t)b + 1] = L.near_off[(size_t)b] + (long long)nears[(size_t)b].size();
         L.rows[(size_t)b] = nproxy + mono + (int)nears[(size_t)b].size();
         if (L.nbv[(size_t)b] > kRsMaxDofs || L.rows[(size_t)b] > kRsMaxRows) {
             L.err = "dd_factor_rs: a region has " + std::to_string(L.nbv[(size_t)b]) + " DOFs and " +
@@ -1136,6 +1227,13 @@ void plan_level(const std::vector<std::vector<Region>> &cur, int dim, int nproxy
             return;
         }
     }
+    L.near_pt.resize((size_t)L.near_off.back());
+    host_ranges(nreg, 64, [&](long long b0, long long b1) {
+        for (long long b = b0; b < b1; ++b) {
+            std::copy(nears[(size_t)b].begin(), nears[(size_t)b].end(), L.near_pt.begin() + L.near_off[(size_t)b]);
+            std::vector<int>().swap(nears[(size_t)b]);
+        }
+    });
 }
 
 // The next level's regions: per colour with more than one region, the regions merged 2^d at a time
@@ -1180,8 +1278,10 @@ std::vector<std::vector<Region>> merge_level(const std::vector<std::vector<Regio
     return next;
 }
 
-// The elimination (KR2) of `regs` (level 1 when prev == nullptr), whose ranks and permutations are
-// known; fills lvl's stores and, per region, the device address of its B_ss.
+// The elimination (KR2) of `regs`, whose ranks and permutations are known; prev_k / prev_bss hold
+// the ranks and B_ss addresses of the regions' children (none at level 1), flattened region by
+// region in each region's child order.  Fills lvl's stores and, per region, the device address of
+// its B_ss.
 int run_elim(const ie_problem *p, const std::vector<Region> &regs, const std::vector<int> &perm_h,
              const std::vector<long long> &nat_off, int *d_nat_pt, int *d_perm, const std::vector<int> &kv,
              const std::vector<unsigned long long> &prev_bss, const std::vector<int> &prev_k, const double *d_Tin,
@@ -1199,7 +1299,7 @@ int run_elim(const ie_problem *p, const std::vector<Region> &regs, const std::ve
         b_off[(size_t)b + 1] = b_off[(size_t)b] + nr * nr;
         s_off[(size_t)b + 1] = s_off[(size_t)b] + k * k;
         for (size_t c = 0; c < regs[(size_t)b].child.size(); ++c) {
-            const int ch = regs[(size_t)b].child[c];
+            const size_t ch = child_start.size();  // the child's index in the flattened lists
             child_start.push_back(regs[(size_t)b].child_start[c]);
             child_k.push_back(prev_k[(size_t)ch]);
             child_bss.push_back(prev_bss[(size_t)ch]);
@@ -1335,7 +1435,9 @@ static int factor_rs_impl(const ie_problem *p, const dd_partition_t *s, const rs
     if (!rs) { ie_set_error("dd_factor_rs: out of host memory"); return IE_ERR_OOM; }
     rs->dim = dim; rs->ncol = 1 << dim; rs->eps = eps; rs->rho = rho; rs->nproxy = nproxy;
     std::string err;
+    std::thread inverter;  // builds the point -> positions map from rs->pos2pt (below)
     auto fail = [&](int code) {
+        if (inverter.joinable()) inverter.join();
         delete rs;
         ie_set_error(err.empty() ? "dd_factor_rs: " + std::string(ie_last_error()) : err);
         return code;
@@ -1343,43 +1445,34 @@ static int factor_rs_impl(const ie_problem *p, const dd_partition_t *s, const rs
 
     // level-1 regions: the extended boxes of each colour, row-major by K = k / 2
     const int ncol = rs->ncol;
-    std::vector<std::vector<Region>> cur((size_t)ncol);
-    std::vector<int> G((size_t)ncol * 3, 1);
-    for (int c = 0; c < ncol; ++c) {
-        int cd[3] = {0, 0, 0}, Gd[3] = {1, 1, 1};
-        for (int d = 0; d < dim; ++d) {
-            cd[d] = (c >> (dim - 1 - d)) & 1;
-            Gd[d] = (m - cd[d] + 1) / 2;
-        }
-        for (int K0 = 0; K0 < Gd[0]; ++K0)
-            for (int K1 = 0; K1 < Gd[1]; ++K1)
-                for (int K2 = 0; K2 < (dim == 3 ? Gd[2] : 1); ++K2) {
-                    Region r;
-                    r.colour = c;
-                    const int Ks[3] = {K0, K1, K2};
-                    for (int d = 0; d < dim; ++d) {
-                        const int kk = 2 * Ks[d] + cd[d];
-                        r.K[(size_t)d] = Ks[d];
-                        r.lo[(size_t)d] = std::max(kk * w - delta, 0);
-                        r.hi[(size_t)d] = std::min((kk + 1) * w + delta, n);
-                    }
-                    for (int i = r.lo[0]; i < r.hi[0]; ++i)
-                        for (int j = r.lo[1]; j < r.hi[1]; ++j)
-                            for (int l = r.lo[2]; l < r.hi[2]; ++l) {
-                                const int pt = dim == 2 ? i * n + j : (i * n + j) * n + l;
-                                r.nat.push_back((int)rs->pos2pt.size());
-                                rs->pos2pt.push_back(pt);
-                            }
-                    cur[(size_t)c].push_back(std::move(r));
-                }
-    }
-    rs->ntot = (long long)rs->pos2pt.size();
+    std::vector<std::vector<Region>> cur;
+    std::unique_ptr<int[]> lat;  // lattice coordinates of every position
+    rs->ntot = level1_regions(dim, n, m, delta, cur, rs->pos2pt, lat);
     rs->colour_levels.assign((size_t)ncol, 0);
-    std::vector<int> lat((size_t)rs->ntot * 3, 0);  // lattice coordinates of every position
-    for (long long q = 0; q < rs->ntot; ++q) {
-        int pt = rs->pos2pt[(size_t)q];
-        for (int d = dim - 1; d >= 0; --d) { lat[(size_t)q * 3 + d] = pt % n; pt /= n; }
+    // point -> its positions (one per colour that holds it), in colour order: for the application's
+    // overlap sum; built on a host thread while the levels are factored
+    std::vector<long long> inv_ptr;
+    std::vector<int> inv_pos;
+    bool inv_ok = false;
+    auto build_inverse = [&]() {
+        try {
+            inv_ptr.assign((size_t)p->N + 1, 0);
+            inv_pos.resize((size_t)rs->ntot);
+            for (long long q = 0; q < rs->ntot; ++q) inv_ptr[(size_t)rs->pos2pt[(size_t)q] + 1]++;
+            for (long long i = 0; i < p->N; ++i) inv_ptr[(size_t)i + 1] += inv_ptr[(size_t)i];
+            std::vector<long long> fill(inv_ptr.begin(), inv_ptr.end() - 1);
+            for (long long q = 0; q < rs->ntot; ++q) inv_pos[(size_t)fill[(size_t)rs->pos2pt[(size_t)q]]++] = (int)q;
+            inv_ok = true;
+        } catch (...) {
+            inv_ok = false;  // reported after the join
+        }
+    };
+    try {
+        inverter = std::thread(build_inverse);
+    } catch (const std::system_error &) {
+        build_inverse();
     }
+    JoinOnExit join_inverter{inverter};
     if (to_dev(&rs->d_pos2pt, rs->pos2pt, st) != IE_OK) return fail(IE_ERR_CUDA);
 
     // previous level's ranks and B_ss addresses, per colour (indices into that colour's list)
@@ -1391,7 +1484,7 @@ static int factor_rs_impl(const ie_problem *p, const dd_partition_t *s, const rs
     int status = IE_OK;
 
     LevelPlan plan;
-    plan_level(cur, dim, nproxy, mono, rho, rs->pos2pt, lat, plan);
+    plan_level(cur, dim, nproxy, mono, rho, rs->pos2pt, lat.get(), plan);
     for (int level = 0; status == IE_OK; ++level) {
         if (!plan.err.empty()) { err = plan.err; status = IE_ERR_ARG; break; }
         if (plan.regs.empty()) break;
@@ -1510,12 +1603,21 @@ static int factor_rs_impl(const ie_problem *p, const dd_partition_t *s, const rs
                 const double r = rows[(size_t)b], nbd = nbv[(size_t)b], kd = kv[(size_t)b];
                 rs->id_flops += 2.0 * r * nbd + 4.0 * r * (kd * nbd - kd * (kd + 1.0) / 2.0) + (nbd - kd) * kd * kd;
             }
-            // the next level's regions and plan (host work) on a worker thread, beside KR2 on the
-            // device: both only read this level's regions, ranks and permutations
+            // the next level's regions and plan, and this level's positions in the permuted order
+            // (the apply's view), on a worker thread beside KR2 on the device: all of it only reads
+            // this level's regions, ranks and permutations
+            std::vector<int> lv_pos;
+            std::vector<long long> lv_pos_off;
             auto plan_next = [&]() {
                 try {
+                    lv_pos.resize((size_t)nat_off.back());
+                    lv_pos_off.assign(nat_off.begin(), nat_off.end());
+                    for (int b = 0; b < nreg; ++b)
+                        for (int t = 0; t < nbv[(size_t)b]; ++t)
+                            lv_pos[(size_t)(nat_off[(size_t)b] + t)] =
+                                regs[(size_t)b].nat[(size_t)perm[(size_t)(nat_off[(size_t)b] + t)]];
                     next_cur = merge_level(cur, regs, kv, perm, nat_off);
-                    plan_level(next_cur, dim, nproxy, mono, rho, rs->pos2pt, lat, next_plan);
+                    plan_level(next_cur, dim, nproxy, mono, rho, rs->pos2pt, lat.get(), next_plan);
                 } catch (const std::bad_alloc &) {
                     plan_err = "dd_factor_rs: out of host memory";
                     plan_code = IE_ERR_OOM;
@@ -1530,28 +1632,21 @@ static int factor_rs_impl(const ie_problem *p, const dd_partition_t *s, const rs
             } catch (const std::system_error &) {
                 plan_next();  // no thread: plan here, before KR2
             }
-            struct Joiner {  // joins the planner on every way out of this block
-                std::thread &t;
-                ~Joiner() { if (t.joinable()) t.join(); }
-            } joiner{planner};
+            JoinOnExit join_on_exit{planner};
             auto join_planner = [&]() { if (planner.joinable()) planner.join(); };
             // KR2
             std::vector<unsigned long long> pbss;
             std::vector<int> pk;
             // the children of this level's regions live in prev_* of their colour; flatten per region
-            std::vector<Region> eregs = regs;
-            for (int b = 0; b < nreg; ++b) {
-                Region &r = eregs[(size_t)b];
-                for (int &ch : r.child) {
+            for (const Region &r : regs)
+                for (int ch : r.child) {
                     pk.push_back(prev_k[(size_t)r.colour][(size_t)ch]);
                     pbss.push_back(prev_bss[(size_t)r.colour][(size_t)ch]);
-                    ch = (int)pk.size() - 1;
                 }
-            }
             RSLevel lvl;
             double *d_bss = nullptr;
             std::vector<unsigned long long> baddr;
-            status = run_elim(p, eregs, perm, nat_off, d_natpt, d_perm, kv, pbss, pk, d_Tt, tt_off, lvl, &d_bss, baddr,
+            status = run_elim(p, regs, perm, nat_off, d_natpt, d_perm, kv, pbss, pk, d_Tt, tt_off, lvl, &d_bss, baddr,
                               st, err, rs->elim_ms, rs->elim_flops);
             if (d_bss) bss_bufs.push_back(d_bss);
             join_planner();
@@ -1559,18 +1654,15 @@ static int factor_rs_impl(const ie_problem *p, const dd_partition_t *s, const rs
             if (plan_code != IE_OK) { err = plan_err; status = plan_code; lvl.release(); break; }
             // the apply's view of the level
             lvl.nreg = nreg;
-            lvl.pos_off.assign((size_t)nreg + 1, 0);
             for (int b = 0; b < nreg; ++b) {
-                const Region &r = regs[(size_t)b];
-                lvl.colour.push_back(r.colour);
+                lvl.colour.push_back(regs[(size_t)b].colour);
                 lvl.nb.push_back(nbv[(size_t)b]);
                 lvl.k.push_back(kv[(size_t)b]);
                 lvl.max_nb = std::max(lvl.max_nb, nbv[(size_t)b]);
                 lvl.max_k = std::max(lvl.max_k, kv[(size_t)b]);
-                for (int t = 0; t < nbv[(size_t)b]; ++t)
-                    lvl.pos.push_back(r.nat[(size_t)perm[(size_t)(nat_off[(size_t)b] + t)]]);
-                lvl.pos_off[(size_t)b + 1] = (long long)lvl.pos.size();
             }
+            lvl.pos = std::move(lv_pos);
+            lvl.pos_off = std::move(lv_pos_off);
             if ((status = to_dev(&lvl.d_nb, lvl.nb, st)) != IE_OK || (status = to_dev(&lvl.d_k, lvl.k, st)) != IE_OK ||
                 (status = to_dev(&lvl.d_pos, lvl.pos, st)) != IE_OK || (status = to_dev(&lvl.d_pos_off, lvl.pos_off, st)) != IE_OK) {
                 lvl.release();
@@ -1605,10 +1697,9 @@ static int factor_rs_impl(const ie_problem *p, const dd_partition_t *s, const rs
         std::vector<unsigned long long> pbss;
         for (int c = 0; c < ncol; ++c) {
             Region r = cur[(size_t)c][0];
-            for (int &ch : r.child) {
+            for (int ch : r.child) {
                 pk.push_back(prev_k[(size_t)c][(size_t)ch]);
                 pbss.push_back(prev_bss[(size_t)c][(size_t)ch]);
-                ch = (int)pk.size() - 1;
             }
             if ((int)r.nat.size() > kRsMaxTop) {
                 err = "dd_factor_rs: a last Schur complement has " + std::to_string(r.nat.size()) + " DOFs (limit " +
@@ -1659,17 +1750,11 @@ static int factor_rs_impl(const ie_problem *p, const dd_partition_t *s, const rs
             (status = to_dev(&rs->d_items, items, st)) != IE_OK)
             return fail(status);
     }
-    // point -> its positions (one per colour that holds it), in colour order
-    {
-        std::vector<long long> inv_ptr((size_t)p->N + 1, 0);
-        std::vector<int> inv_pos((size_t)rs->ntot);
-        for (long long q = 0; q < rs->ntot; ++q) inv_ptr[(size_t)rs->pos2pt[(size_t)q] + 1]++;
-        for (long long i = 0; i < p->N; ++i) inv_ptr[(size_t)i + 1] += inv_ptr[(size_t)i];
-        std::vector<long long> fill(inv_ptr.begin(), inv_ptr.end() - 1);
-        for (long long q = 0; q < rs->ntot; ++q) inv_pos[(size_t)fill[(size_t)rs->pos2pt[(size_t)q]]++] = (int)q;
-        if ((status = to_dev(&rs->d_inv_ptr, inv_ptr, st)) != IE_OK || (status = to_dev(&rs->d_inv_pos, inv_pos, st)) != IE_OK)
-            return fail(status);
-    }
+    // the point -> positions map built beside the levels
+    if (inverter.joinable()) inverter.join();
+    if (!inv_ok) { err = "dd_factor_rs: out of host memory"; return fail(IE_ERR_OOM); }
+    if ((status = to_dev(&rs->d_inv_ptr, inv_ptr, st)) != IE_OK || (status = to_dev(&rs->d_inv_pos, inv_pos, st)) != IE_OK)
+        return fail(status);
     // the apply kernels stage up to 2 * 4096 (levels) or 8192 (top) doubles: allow the full 227 KB
     // once, here (outside any stream capture); the attribute only ever grows
     {
