@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <mutex>
 #include <map>
+#include <memory>
 #include <vector>
 
 #include "iedd_internal.cuh"
@@ -313,7 +314,22 @@ extern "C" int ie_matvec(const ie_problem *p, const double *x, double *y, int nr
 // ---------------------------------------------------------------------------------------------
 static const int kMaxBlock = kInvMaxPad;  // the largest block the mixed factor and apply take
 
+static int partition_impl(const ie_problem *p, int m, int delta, int kind, dd_partition_t **out);
+
 extern "C" int dd_partition(const ie_problem *p, int m, int delta, int kind, dd_partition_t **out) {
+    // host containers and threads may throw; nothing may cross the C ABI
+    try {
+        return partition_impl(p, m, delta, kind, out);
+    } catch (const std::bad_alloc &) {
+        ie_set_error("dd_partition: out of host memory");
+        return IE_ERR_OOM;
+    } catch (const std::exception &e) {
+        ie_set_error(std::string("dd_partition: ") + e.what());
+        return IE_ERR_ARG;
+    }
+}
+
+static int partition_impl(const ie_problem *p, int m, int delta, int kind, dd_partition_t **out) {
     if (!out) { ie_set_error("dd_partition: out is NULL"); return IE_ERR_ARG; }
     *out = nullptr;
     if (!p) { ie_set_error("dd_partition: NULL problem"); return IE_ERR_ARG; }
@@ -327,86 +343,153 @@ extern "C" int dd_partition(const ie_problem *p, int m, int delta, int kind, dd_
     long long M = 1;
     for (int d = 0; d < dim; ++d) M *= m;
 
-    // every extended box (Jacobi, Schwarz), enumerated row-major so its indices come out ascending
-    std::vector<std::vector<int>> boxes((size_t)(kind == DD_CBD ? 0 : M));
-    for (long long b = 0; b < (long long)boxes.size(); ++b) {
-        int k[3] = {0, 0, 0};
-        long long t = b;
-        for (int d = dim - 1; d >= 0; --d) { k[d] = (int)(t % m); t /= m; }
-        int lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
-        for (int d = 0; d < dim; ++d) {
-            lo[d] = std::max(k[d] * w - ext, 0);
-            hi[d] = std::min((k[d] + 1) * w + ext, n);
-        }
-        auto &v = boxes[(size_t)b];
-        if (dim == 2) {
-            for (int i = lo[0]; i < hi[0]; ++i)
-                for (int j = lo[1]; j < hi[1]; ++j) v.push_back(i * n + j);
-        } else {
-            for (int i = lo[0]; i < hi[0]; ++i)
-                for (int j = lo[1]; j < hi[1]; ++j)
-                    for (int l = lo[2]; l < hi[2]; ++l) v.push_back((i * n + j) * n + l);
-        }
-    }
-    std::vector<std::vector<int>> blocks;
-    if (kind == DD_CBD) {
-        // A colour's boxes are the product of one parity per axis, so their union is the product of
-        // the per-axis unions of the extended intervals [k w - ext, (k + 1) w + ext), k of that
-        // parity: emit the points of that product in grid order (ascending, no duplicates).
-        int ncol = 1 << dim;
-        for (int c = 0; c < ncol; ++c) {
-            std::vector<std::vector<int>> axis((size_t)dim);
-            for (int d = 0; d < dim; ++d) {
-                const int par = (c >> (dim - 1 - d)) & 1;
-                std::vector<char> in((size_t)n, 0);
-                for (int k = par; k < m; k += 2)
-                    for (int x = std::max(k * w - ext, 0); x < std::min((k + 1) * w + ext, n); ++x) in[(size_t)x] = 1;
-                for (int x = 0; x < n; ++x)
-                    if (in[(size_t)x]) axis[(size_t)d].push_back(x);
-            }
-            std::vector<int> u;
-            if (dim == 2) {
-                u.reserve(axis[0].size() * axis[1].size());
-                for (int i : axis[0])
-                    for (int j : axis[1]) u.push_back(i * n + j);
-            } else {
-                u.reserve(axis[0].size() * axis[1].size() * axis[2].size());
-                for (int i : axis[0])
-                    for (int j : axis[1])
-                        for (int l : axis[2]) u.push_back((i * n + j) * n + l);
-            }
-            if (u.empty()) continue;
-            blocks.push_back(std::move(u));
-        }
-    } else {
-        blocks = std::move(boxes);
-    }
-
     dd_partition_t *s = new (std::nothrow) dd_partition_t();
     if (!s) { ie_set_error("dd_partition: out of host memory"); return IE_ERR_OOM; }
     s->prob = p; s->device = p->device; s->kind = kind; s->m = m; s->delta = ext;
-    s->nblocks = (int)blocks.size();
-    s->offs.assign(blocks.size() + 1, 0);
-    for (size_t i = 0; i < blocks.size(); ++i) {
-        s->offs[i + 1] = s->offs[i] + (long long)blocks[i].size();
-        s->max_block = std::max(s->max_block, (int)blocks[i].size());
-    }
-    s->total = s->offs.back();
-    if (s->max_block > kMaxBlock && kind != DD_CBD) {
-        delete s;
-        ie_set_error("dd_partition: a subdomain has more than " + std::to_string(kMaxBlock) + " points");
-        return IE_ERR_ARG;
-    }
-    s->idx.reserve((size_t)s->total);
-    for (auto &b : blocks) s->idx.insert(s->idx.end(), b.begin(), b.end());
-
     // inverse map (point -> positions of its occurrences, in increasing block order)
-    std::vector<long long> inv_ptr((size_t)p->N + 1, 0), inv_pos((size_t)s->total);
-    for (long long q = 0; q < s->total; ++q) inv_ptr[(size_t)s->idx[(size_t)q] + 1]++;
-    for (long long i = 0; i < p->N; ++i) inv_ptr[(size_t)i + 1] += inv_ptr[(size_t)i];
-    {
-        std::vector<long long> fill(inv_ptr.begin(), inv_ptr.end() - 1);
-        for (long long q = 0; q < s->total; ++q) inv_pos[(size_t)fill[(size_t)s->idx[(size_t)q]]++] = q;
+    std::unique_ptr<long long[]> inv_ptr, inv_pos;
+    if (kind == DD_CBD) {
+        // A colour's boxes are the product of one parity per axis, so their union is the product of
+        // the per-axis unions of the extended intervals [k w - ext, (k + 1) w + ext), k of that
+        // parity: its points in grid order (ascending, no duplicates).  rank[d][par][x] is the
+        // index of coordinate x in axis d's union for that parity, or -1.
+        std::vector<int> axis[3][2], rank[3][2];
+        for (int d = 0; d < 3; ++d)
+            for (int par = 0; par < 2; ++par) {
+                if (d >= dim) {  // a missing axis: the single coordinate 0
+                    axis[d][par].assign(1, 0);
+                    rank[d][par].assign(1, 0);
+                    continue;
+                }
+                std::vector<char> in((size_t)n, 0);
+                for (int k = par; k < m; k += 2)
+                    for (int x = std::max(k * w - ext, 0); x < std::min((k + 1) * w + ext, n); ++x) in[(size_t)x] = 1;
+                rank[d][par].assign((size_t)n, -1);
+                for (int x = 0; x < n; ++x)
+                    if (in[(size_t)x]) {
+                        rank[d][par][(size_t)x] = (int)axis[d][par].size();
+                        axis[d][par].push_back(x);
+                    }
+            }
+        // the colours with points, in colour order: one block each
+        struct Colour {
+            int par[3];
+            long long len[3], off;
+        };
+        std::vector<Colour> cols;
+        long long total = 0;
+        for (int c = 0; c < (1 << dim); ++c) {
+            Colour k{};
+            long long size = 1;
+            for (int d = 0; d < 3; ++d) {
+                k.par[d] = d < dim ? (c >> (dim - 1 - d)) & 1 : 0;
+                k.len[d] = (long long)axis[d][k.par[d]].size();
+                size *= k.len[d];
+            }
+            if (size == 0) continue;
+            k.off = total;
+            total += size;
+            cols.push_back(k);
+        }
+        s->nblocks = (int)cols.size();
+        s->offs.assign(cols.size() + 1, 0);
+        for (size_t b = 0; b < cols.size(); ++b) {
+            s->offs[b + 1] = cols[b].off + cols[b].len[0] * cols[b].len[1] * cols[b].len[2];
+            s->max_block = std::max(s->max_block, (int)(s->offs[b + 1] - s->offs[b]));
+        }
+        s->total = total;
+        // the blocks' points, one (block, axis-0 coordinate) line per item, on host threads
+        s->idx.resize((size_t)total);
+        std::vector<std::pair<int, int>> lines;
+        for (size_t b = 0; b < cols.size(); ++b)
+            for (int r0 = 0; r0 < (int)cols[b].len[0]; ++r0) lines.emplace_back((int)b, r0);
+        const long long per_line = std::max<long long>(total / std::max<long long>((long long)lines.size(), 1), 1);
+        host_ranges((long long)lines.size(), std::max<long long>(1, (1 << 16) / per_line), [&](long long l0, long long l1) {
+            for (long long l = l0; l < l1; ++l) {
+                const Colour &k = cols[(size_t)lines[(size_t)l].first];
+                const int r0 = lines[(size_t)l].second, i = axis[0][k.par[0]][(size_t)r0];
+                long long q = k.off + (long long)r0 * k.len[1] * k.len[2];
+                for (int j : axis[1][k.par[1]])
+                    for (int x : axis[2][k.par[2]]) s->idx[(size_t)q++] = dim == 2 ? i * n + j : (i * n + j) * n + x;
+            }
+        });
+        // the inverse map in closed form: point (x_0, .., x_{dim-1}) sits in every colour whose
+        // unions hold all its coordinates, at the colour's offset plus its row-major rank there;
+        // counted per chunk of points, scanned, then filled chunk by chunk on host threads
+        const long long N = p->N;
+        inv_ptr.reset(new long long[(size_t)N + 1]);
+        inv_pos.reset(new long long[(size_t)std::max<long long>(total, 1)]);
+        long long *ip = inv_ptr.get(), *pp = inv_pos.get();
+        auto occurrences = [&](long long i, long long *out) {  // writes the positions, returns their count
+            int x[3] = {0, 0, 0};
+            for (int d = dim - 1; d >= 0; --d) { x[d] = (int)(i % n); i /= n; }
+            int cnt = 0;
+            for (const Colour &k : cols) {
+                long long pos = 0;
+                bool inside = true;
+                for (int d = 0; d < 3 && inside; ++d) {
+                    const int r = rank[d][k.par[d]][(size_t)x[d]];
+                    inside = r >= 0;
+                    pos = pos * k.len[d] + r;
+                }
+                if (!inside) continue;
+                if (out) out[cnt] = k.off + pos;
+                ++cnt;
+            }
+            return cnt;
+        };
+        const long long nchunk = std::max<long long>(1, std::min<long long>(N >> 14, 1024));  // >= 16K points each
+        std::vector<long long> csum((size_t)nchunk + 1, 0);
+        host_ranges(nchunk, 1, [&](long long c0, long long c1) {
+            for (long long c = c0; c < c1; ++c) {
+                long long acc = 0;
+                for (long long i = N * c / nchunk; i < N * (c + 1) / nchunk; ++i) acc += occurrences(i, nullptr);
+                csum[(size_t)c + 1] = acc;
+            }
+        });
+        for (long long c = 0; c < nchunk; ++c) csum[(size_t)c + 1] += csum[(size_t)c];
+        ip[0] = 0;
+        host_ranges(nchunk, 1, [&](long long c0, long long c1) {
+            for (long long c = c0; c < c1; ++c) {
+                long long acc = csum[(size_t)c];
+                for (long long i = N * c / nchunk; i < N * (c + 1) / nchunk; ++i) {
+                    acc += occurrences(i, pp + acc);
+                    ip[i + 1] = acc;
+                }
+            }
+        });
+    } else {
+        // every extended box, enumerated row-major so its indices come out ascending
+        s->nblocks = (int)M;
+        s->offs.assign((size_t)M + 1, 0);
+        for (long long b = 0; b < M; ++b) {
+            int k[3] = {0, 0, 0};
+            long long t = b;
+            for (int d = dim - 1; d >= 0; --d) { k[d] = (int)(t % m); t /= m; }
+            int lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+            for (int d = 0; d < dim; ++d) {
+                lo[d] = std::max(k[d] * w - ext, 0);
+                hi[d] = std::min((k[d] + 1) * w + ext, n);
+            }
+            for (int i = lo[0]; i < hi[0]; ++i)
+                for (int j = lo[1]; j < hi[1]; ++j)
+                    for (int l = lo[2]; l < hi[2]; ++l) s->idx.push_back(dim == 2 ? i * n + j : (i * n + j) * n + l);
+            s->offs[(size_t)b + 1] = (long long)s->idx.size();
+            s->max_block = std::max(s->max_block, (int)(s->offs[(size_t)b + 1] - s->offs[(size_t)b]));
+        }
+        s->total = s->offs.back();
+        if (s->max_block > kMaxBlock) {
+            delete s;
+            ie_set_error("dd_partition: a subdomain has more than " + std::to_string(kMaxBlock) + " points");
+            return IE_ERR_ARG;
+        }
+        inv_ptr.reset(new long long[(size_t)p->N + 1]());
+        inv_pos.reset(new long long[(size_t)std::max<long long>(s->total, 1)]);
+        long long *ip = inv_ptr.get(), *pp = inv_pos.get();
+        for (long long q = 0; q < s->total; ++q) ip[(size_t)s->idx[(size_t)q] + 1]++;
+        for (long long i = 0; i < p->N; ++i) ip[i + 1] += ip[i];
+        std::vector<long long> fill(ip, ip + p->N);
+        for (long long q = 0; q < s->total; ++q) pp[fill[(size_t)s->idx[(size_t)q]]++] = q;
     }
 
     DeviceGuard g(p->device);
@@ -418,12 +501,12 @@ extern "C" int dd_partition(const ie_problem *p, int m, int delta, int kind, dd_
     cudaError_t e;
     if ((e = cudaMalloc(&s->d_offs, sizeof(long long) * s->offs.size())) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&s->d_idx, sizeof(int) * std::max<long long>(s->total, 1))) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&s->d_inv_ptr, sizeof(long long) * inv_ptr.size())) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&s->d_inv_ptr, sizeof(long long) * ((size_t)p->N + 1))) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&s->d_inv_pos, sizeof(long long) * std::max<long long>(s->total, 1))) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpy(s->d_offs, s->offs.data(), sizeof(long long) * s->offs.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpy(s->d_idx, s->idx.data(), sizeof(int) * s->total, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
-    if ((e = cudaMemcpy(s->d_inv_ptr, inv_ptr.data(), sizeof(long long) * inv_ptr.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
-    if ((e = cudaMemcpy(s->d_inv_pos, inv_pos.data(), sizeof(long long) * s->total, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(s->d_inv_ptr, inv_ptr.get(), sizeof(long long) * ((size_t)p->N + 1), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(s->d_inv_pos, inv_pos.get(), sizeof(long long) * s->total, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
     *out = s;
     return IE_OK;
 }

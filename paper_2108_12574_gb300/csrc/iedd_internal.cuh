@@ -3,8 +3,13 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <exception>
+#include <mutex>
 #include <string>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 #include "iedd.h"
@@ -42,6 +47,41 @@ void ie_set_capturing(bool on);
         int s_ = (expr);                                                                       \
         if (s_ != IE_OK) return s_;                                                            \
     } while (0)
+
+// ---------------------------------------------------------------------------------------------
+// Host threads
+// ---------------------------------------------------------------------------------------------
+// f(b0, b1) over [0, n) in contiguous ranges, on up to hardware_concurrency host threads of at
+// least `grain` items each; a range whose thread cannot be started runs on the caller.  The first
+// exception a range throws is rethrown here once every thread has ended.
+template <class F> void host_ranges(long long n, long long grain, const F &f) {
+    const long long hc = std::max(1u, std::thread::hardware_concurrency());
+    const long long nth = std::max(1LL, std::min(hc, n / std::max(grain, 1LL)));
+    std::exception_ptr first;
+    std::mutex mu;
+    auto guarded = [&](long long b0, long long b1) {
+        try {
+            f(b0, b1);
+        } catch (...) {
+            std::lock_guard<std::mutex> g(mu);
+            if (!first) first = std::current_exception();
+        }
+    };
+    std::vector<std::thread> pool;
+    long long spawned = 1;  // ranges [0, spawned) run on threads (range 0 here); the rest below
+    for (long long t = 1; t < nth; ++t) {
+        try {
+            pool.emplace_back(guarded, n * t / nth, n * (t + 1) / nth);
+            spawned = t + 1;
+        } catch (const std::system_error &) {
+            break;
+        }
+    }
+    guarded(0LL, n / nth);
+    for (long long t = spawned; t < nth; ++t) guarded(n * t / nth, n * (t + 1) / nth);
+    for (auto &th : pool) th.join();
+    if (first) std::rethrow_exception(first);
+}
 
 // Scoped device context: makes `dev` current and restores the previous device on exit.
 struct DeviceGuard {
