@@ -375,7 +375,9 @@ def test_stored_matrix_too_large_is_refused():
 
 PART_CASES = [(2, 64, 4, 1, O.SCHWARZ), (2, 512, 32, 2, O.SCHWARZ), (3, 32, 4, 1, O.SCHWARZ),
               (2, 12, 3, 1, O.CBD), (3, 8, 4, 1, O.CBD), (2, 30, 5, 2, O.JACOBI), (2, 20, 4, 3, O.SCHWARZ),
-              (2, 24, 3, 5, O.CBD)]
+              (2, 24, 3, 5, O.CBD),
+              # CBD large enough that the library builds the blocks on host threads
+              (2, 1024, 128, 1, O.CBD), (3, 64, 8, 1, O.CBD), (2, 512, 64, 3, O.CBD)]
 
 
 @pytest.mark.parametrize("dim,n,m,delta,kind", PART_CASES)
