@@ -1248,12 +1248,10 @@ std::vector<std::vector<Region>> merge_level(const std::vector<std::vector<Regio
 // the ranks and B_ss addresses of the regions' children (none at level 1), flattened region by
 // region in each region's child order.  Fills lvl's stores and, per region, the device address of
 // its B_ss.
-int run_elim(const ie_problem *p, const std::vector<Region> &regs, const std::vector<int> &perm_h,
-             const std::vector<long long> &nat_off, int *d_nat_pt, int *d_perm, const std::vector<int> &kv,
-             const std::vector<unsigned long long> &prev_bss, const std::vector<int> &prev_k, const double *d_Tin,
+int run_elim(const ie_problem *p, const std::vector<Region> &regs, const std::vector<long long> &nat_off,
+             int *d_nat_pt, int *d_perm, const std::vector<int> &kv, const std::vector<unsigned long long> &prev_bss, const std::vector<int> &prev_k, const double *d_Tin,
              const std::vector<long long> &t_in, RSLevel &lvl, double **d_bss, std::vector<unsigned long long> &bss_addr,
              cudaStream_t s, std::string &err, double &ms, double &flops) {
-    (void)perm_h;
     const int nreg = (int)regs.size();
     std::vector<long long> t_off((size_t)nreg + 1, 0), b_off((size_t)nreg + 1, 0), s_off((size_t)nreg + 1, 0);
     std::vector<long long> child_off((size_t)nreg + 1, 0);
@@ -1612,7 +1610,7 @@ static int factor_rs_impl(const ie_problem *p, const dd_partition_t *s, const rs
             RSLevel lvl;
             double *d_bss = nullptr;
             std::vector<unsigned long long> baddr;
-            status = run_elim(p, regs, perm, nat_off, d_natpt, d_perm, kv, pbss, pk, d_Tt, tt_off, lvl, &d_bss, baddr,
+            status = run_elim(p, regs, nat_off, d_natpt, d_perm, kv, pbss, pk, d_Tt, tt_off, lvl, &d_bss, baddr,
                               st, err, rs->elim_ms, rs->elim_flops);
             if (d_bss) bss_bufs.push_back(d_bss);
             join_planner();
@@ -1691,7 +1689,7 @@ static int factor_rs_impl(const ie_problem *p, const dd_partition_t *s, const rs
         if (status == IE_OK) status = to_dev(&d_perm, perm, st);
         if (status == IE_OK && cudaMallocAsync((void **)&d_Tt, sizeof(double), st) != cudaSuccess) status = IE_ERR_OOM;
         if (status == IE_OK)
-            status = run_elim(p, tops, perm, nat_off, d_natpt, d_perm, kv, pbss, pk, d_Tt, t_in, rs->top, &d_bss, baddr,
+            status = run_elim(p, tops, nat_off, d_natpt, d_perm, kv, pbss, pk, d_Tt, t_in, rs->top, &d_bss, baddr,
                               st, err, rs->elim_ms, rs->elim_flops);
         dfree(d_natpt, st); dfree(d_perm, st); dfree(d_Tt, st); dfree(d_bss, st);
         free_bss();
