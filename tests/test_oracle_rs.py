@@ -3,7 +3,8 @@ mathematics fix -- none compares the oracle with itself:
 
   * the ID on matrices of known rank and on exact ties (its definition, Eq. e:id);
   * the proxy trick: the ID computed from the proxy and near-field rows meets Eq. e:id_err
-    against the FULL off-diagonal block A_qp of the subdomain;
+    against the FULL off-diagonal block A_qp of the subdomain, at the first level and at every
+    merged level above it;
   * compress-then-eliminate (Eqs. e:al, e:alu, e:b, e:schur): F_c^{-1} A_c - I shrinks in
     proportion to eps (a dropped term, a wrong sign or a transposed T leaves an O(1) error),
     F_c^{-1} is symmetric positive definite, and with one region per colour (no compression)
@@ -87,6 +88,37 @@ def test_proxy_id_meets_the_bound_on_the_full_block_3d():
         skel, red, T = RS.interp_decomp(Y, eps)
         assert skel.size == k and np.array_equal(pts[skel], pts[:k])
         assert np.linalg.norm(A[:, red] - A[:, skel] @ T) <= eps * np.linalg.norm(A[:, red])
+
+
+def upper_level_id_ratios(dim, n, m, delta, eps, nproxy):
+    """Per compression level above the first, the worst ||A_qr - A_qs T|| / (eps ||A_qr||) over its
+    regions, q the colour's other active DOFs at that level.  The blocks between different regions
+    of a level are still entries of A (every Schur update of the levels below stays inside one
+    region), so the proxy ID of a merged region answers to Eq. e:id_err against them too."""
+    F = RS.factor(dim, n, m, delta, eps, nproxy)
+    P = O.points(dim, n)
+    _, _, wgt, _ = O.grid_geometry(dim, n)
+    worst = {}
+    for fc in F:
+        for lv, recs in enumerate(fc["levels"][1:], start=2):
+            active = np.concatenate([r["dofs"] for r in recs])
+            for rec in recs:
+                if rec["red"].size == 0:
+                    continue
+                p = fc["points"][rec["dofs"]]
+                q = fc["points"][np.setdiff1d(active, rec["dofs"])]
+                d = P[q][:, None, :] - P[p][None, :, :]
+                A = wgt * O.kernel(dim, np.sqrt((d * d).sum(axis=2)))
+                Aqr, Aqs = A[:, rec["red"]], A[:, rec["skel"]]
+                ratio = np.linalg.norm(Aqr - Aqs @ rec["T"]) / (eps * np.linalg.norm(Aqr))
+                worst[lv] = max(worst.get(lv, 0.0), ratio)
+    return worst
+
+
+@pytest.mark.parametrize("n,m,eps", [(96, 12, 1e-3), (64, 8, 1e-6)])
+def test_proxy_id_meets_the_bound_at_the_merged_levels(n, m, eps):
+    worst = upper_level_id_ratios(2, n, m, 1, eps, 64)
+    assert worst and all(r <= 1.0 for r in worst.values()), worst
 
 
 # --- compress-then-eliminate (Eqs. e:al, e:alu, e:b, e:schur) ---------------------------------

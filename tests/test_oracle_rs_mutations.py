@@ -3,8 +3,8 @@
 Each case patches one plausible slip into oracle/rs_oracle.py -- a dropped term or a wrong sign
 in compress-then-eliminate (Eqs. e:al, e:alu, e:b), a skipped operator in the application, the
 Schur update left out of the merged block (Eq. e:schur), the near field left out of the proxy
-ID (Eq. e:id) in 2D and 3D, a 3D proxy sphere flattened onto its equator or cut to a polar cap --
-and checks that the named pin of test_oracle_rs.py now fails.
+ID (Eq. e:id) in 2D and 3D or at the merged levels only, a 3D proxy sphere flattened onto its
+equator or cut to a polar cap -- and checks that the named pin of test_oracle_rs.py now fails.
 """
 import numpy as np
 import pytest
@@ -165,3 +165,20 @@ def test_3d_proxy_slips_are_caught(monkeypatch, variant):
             return orig_id(dim, n, lo, hi, own, np.zeros(0, dtype=np.int64), nproxy, rho, convention)
         monkeypatch.setattr(RS, "id_matrix", no_near)
     assert not _id_bound_pin_3d()
+
+
+def test_near_field_dropped_at_the_merged_levels_is_caught(monkeypatch):
+    """Level 1 keeps its near field, so the level-1 pin cannot see the slip; the merged-level pin
+    (test_proxy_id_meets_the_bound_at_the_merged_levels) does."""
+    from test_oracle_rs import upper_level_id_ratios
+    orig = RS.id_matrix
+    box = 64 // 8 + 2   # the extended box side of the 64^2 grid with 8^2 boxes, one layer of overlap
+
+    def near_at_level1_only(dim, n, lo, hi, own, others, nproxy, rho=1.5, convention=O.GRID_TEXT):
+        if int((np.asarray(hi) - np.asarray(lo)).max()) > box:
+            others = np.zeros(0, dtype=np.int64)
+        return orig(dim, n, lo, hi, own, others, nproxy, rho, convention)
+    monkeypatch.setattr(RS, "id_matrix", near_at_level1_only)
+    assert _id_bound_pin()
+    worst = upper_level_id_ratios(2, 64, 8, 1, EPS, 64)
+    assert max(worst.values()) > 1.0, worst
