@@ -121,6 +121,13 @@ def test_proxy_id_meets_the_bound_at_the_merged_levels(n, m, eps):
     assert worst and all(r <= 1.0 for r in worst.values()), worst
 
 
+@pytest.mark.slow
+def test_proxy_id_meets_the_bound_at_the_merged_levels_3d():
+    # 20^3 with 5^3 boxes: 3 x 3 x 3 regions per colour at level 1, 2 x 2 x 2 merged ones at level 2
+    worst = upper_level_id_ratios(3, 20, 5, 1, 1e-3, 128)
+    assert worst and all(r <= 1.0 for r in worst.values()), worst
+
+
 # --- compress-then-eliminate (Eqs. e:al, e:alu, e:b, e:schur) ---------------------------------
 
 def _inverse_error(dim, n, m, delta, eps, nproxy):
