@@ -76,6 +76,20 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.ie_kernel_launches(0) >= 0
 
 
+def test_rs_entry_points_reject_null_arguments_without_gpu(lib):
+    from paper_2108_12574_gb300 import iedd
+    assert lib.dd_factor_rs(None, None, None, None, None) == iedd.IE_ERR_ARG
+    assert b"out is NULL" in lib.ie_last_error()
+    out = ctypes.c_void_p(1234)
+    assert lib.dd_factor_rs(None, None, None, ctypes.byref(out), None) == iedd.IE_ERR_ARG
+    assert out.value is None  # *out is cleared before the other checks
+    nc = ctypes.c_int(-1)
+    assert lib.dd_rs_info(None, ctypes.byref(nc), None, None, None) == iedd.IE_ERR_ARG
+    assert nc.value == -1 and b"not an RS factor" in lib.ie_last_error()
+    assert lib.dd_rs_export(None, 0, 1, None, None, None, None, None) == iedd.IE_ERR_ARG
+    assert lib.ie_fp64_fma_rate(0, None) == iedd.IE_ERR_ARG
+
+
 def test_default_opts(lib):
     from paper_2108_12574_gb300 import iedd
     o = iedd.pcg_default_opts()
